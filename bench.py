@@ -1,0 +1,304 @@
+"""Benchmark of the coupled velocity solve: particle-steps per second.
+
+One step = one full time step of the path (cell list and pair search, fused
+pair/assembly kernel, Jacobi-PCG to the stated relative residual, Lees-Edwards
+position update) on N = 262,144 particles at number density 3 (cubic box,
+r_c = 1), alpha = 4, eps = 1, zeta = kT = 1, kappa*tau = 0.5, dt = 0.01,
+positions uniform from the seed.  Inputs are synthetic and seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl reference]
+
+N > 1 (torchrun): each rank advances its own replica (different seed): the path
+does not shard, so the ranks are independent replicas (weak scaling, no
+collective on the data path); value = all ranks' particle-steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "particle-steps/s at 1e-8 CG rel. residual; CG SpMV HBM GB/s vs GB300 peak"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd[1:1] = ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
+    """Bytes the solver's SpMV must move per launch: row pointers, columns and
+    weights of every entry, the diagonal, one read of p and one write of q."""
+    if precision == "mixed":
+        return 4.0 * (n + 1) + 8.0 * nnz + 4.0 * n + 16.0 * n + 16.0 * n
+    return 4.0 * (n + 1) + 12.0 * nnz + 8.0 * n + 24.0 * n + 24.0 * n
+
+
+def cpu_baseline(workload, precision: str, steps: int = 2):
+    """The CPU oracle as it stands (single thread), on a bounded sample of the workload."""
+    import oracle
+    p = oracle.Params.from_workload(workload)
+    pos = synth.uniform_positions(workload.n, workload.L, workload.seed)
+    delta = 0.0
+    t0 = time.perf_counter()
+    for s in range(steps):
+        r = oracle.step(p, pos, delta, s, tol=workload.tol, neighbor_method="cells")
+        pos, delta = r.pos, r.delta
+    dt = time.perf_counter() - t0
+    return {"value": workload.n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps of N={workload.n} (cell-list pair search, Jacobi-PCG to "
+                      f"{workload.tol:g}), single thread, {dt:.1f} s"}
+
+
+def run_reference(args, workload):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    steps_each = 1
+    times = []
+    import oracle as orc
+    p = orc.Params.from_workload(workload)
+    pos = synth.uniform_positions(workload.n, workload.L, workload.seed)
+    delta = 0.0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = orc.step(p, pos, delta, s, tol=workload.tol, neighbor_method="cells")
+        pos, delta = r.pos, r.delta
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = workload.n * steps_each * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload.name, "n": workload.n, "box": workload.L[0],
+                       "kappa_tau": workload.kappa_tau, "cg_tol": workload.tol, "precision": "fp64",
+                       "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} full steps of N={workload.n} per timed run, single thread"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    workload = synth.PRECISION
+    if args.n:
+        workload = synth.cubic(f"n{args.n}", args.n, workload.kappa_tau, workload.steps, workload.tol,
+                               workload.seed)
+    if args.impl == "reference":
+        run_reference(args, workload)
+        return
+
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    n, L = workload.n, workload.L
+    seed = workload.seed + 1000 * rank
+    pos0 = synth.uniform_positions(n, L, seed)
+    kappa = ss.kappa_from_kappa_tau(workload.kappa_tau)
+    sim = ss.Simulation(n, L, kappa, alpha=workload.alpha, eps=workload.eps, zeta=workload.zeta,
+                        kT=workload.kT, dt=workload.dt, rc=workload.rc, seed=seed, precision=args.precision,
+                        warm_start="prev", cg_tol=workload.tol, cg_max_iter=2000, device=local_rank,
+                        positions=pos0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    launches = 0
+    iters = 0
+    max_res = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (512 MB > L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = sim.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        launches += info["kernel_launches"]
+        iters += info["cg_iterations"]
+        max_res = max(max_res, info["last_residual"])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = n * world * args.steps / (t_max / 1e3)
+
+    # per-kernel timing of one more step (CUDA events on the simulation's stream)
+    prof = sim.profile_step()
+    spmv_avg_ms = prof["spmv_ms"] / max(prof["spmv_launches"], 1)
+    algo = spmv_algorithmic_bytes(prof["n"], prof["nnz"], args.precision)
+    peak, peak_kind = measured_peaks()
+    achieved = algo / (spmv_avg_ms * 1e-3) / 1e9
+
+    # end to end through the public API: host positions in, step, host positions out
+    import ctypes  # noqa: F401
+    host_in = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    sim.get_positions(host_in)
+    delta, _ = sim.state()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sim.set_positions(host_in, delta)
+        sim.step(1)
+        sim.get_positions(host_out)
+        delta, _ = sim.state()
+        host_in[:] = host_out
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = n * world * args.e2e_steps / e2e_s   # each rank does the same work
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(workload, args.precision)
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": workload.name, "n": n, "box": L[0], "density": 3.0,
+                       "kappa_tau": workload.kappa_tau, "alpha": workload.alpha, "dt": workload.dt,
+                       "cg_tol": workload.tol, "precision": args.precision, "warm_start": "prev",
+                       "replicas": world, "l2": "flushed between timed steps (512 MB write)"},
+            "cg_iterations_per_step": iters / args.steps, "max_true_residual": max_res,
+            "gpu_launches": launches,
+            "roofline": {"kernel": "k_cg_spmv", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"hbm_gbs {peak_kind}", "algorithmic_bytes_per_launch": algo,
+                         "avg_launch_ms": spmv_avg_ms, "launches_profiled": prof["spmv_launches"],
+                         "note": "working set of one solve (~110 MB) fits in L2; per-step L2 flush only"},
+            "kernel_ms_per_step": {k: prof[k] for k in ("spmv_ms", "update_ms", "direction_ms",
+                                                         "true_residual_ms", "build_ms", "other_ms")},
+            "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": n * 24 + 8,
+                    "d2h_bytes_per_step": n * 24 + 16, "steps": args.e2e_steps},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

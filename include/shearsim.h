@@ -1,0 +1,218 @@
+/*
+ * shearsim.h — C ABI of the GB300 (sm_103a) coupled velocity solve of
+ * Korolkovas, "Giant fluctuations in sheared viscoelastic fluids emerging in
+ * a mesoscale simulation" (arXiv 1808.06381).
+ *
+ * One particle per polymer chain (§Method).  Every time step:
+ *   1. finds all pairs closer than the truncation radius r_c under sheared
+ *      (Lees-Edwards) periodic images (§Method: weights truncated below 5 %,
+ *      "standard Lees-Edwards boundary conditions");
+ *   2. evaluates the forces of Eq. F (noise, excluded volume Eq. exvol, shear
+ *      body force) and assembles Eq. vc as the sparse symmetric positive-
+ *      definite system of Eq. algebra, A v = b, with
+ *        A_ii = 1 + alpha sum_j w_ij,  A_ij = -alpha w_ij,
+ *        b_i  = F_i / zeta + alpha sum_j V_ij w_ij,
+ *        w_ij = exp(-R_ij^2 / 2 lambda^2),  V_ij = kappa L_y round(y_ij / L_y) x;
+ *   3. solves it for all velocities with Jacobi-preconditioned conjugate
+ *      gradients on the GPU;
+ *   4. advances R += v dt (first order in time) with the Lees-Edwards wrap.
+ *
+ * Units: lengths in r_c; lambda^2 = r_c^2 / (2 ln 20) follows from the 5 %
+ * truncation; the excluded-volume parameter v/lambda^3 is 0.1 (§Method) times
+ * eps; the thermal noise is sqrt(2 zeta kT / dt) N(0,1) per Cartesian
+ * component (the discrete form of sqrt(6 zeta kT) W_c(t) with <W.W> = delta).
+ *
+ * Conventions for every call:
+ *   - returns SP_OK (0) or a negative sp_status; nothing is thrown across the ABI;
+ *   - sp_last_error() gives a one-line description of the last failure;
+ *   - arrays called *_host are caller-owned host memory (pinned or pageable),
+ *     copied before the call returns; arrays called *_dev are caller-owned
+ *     device memory on the simulation's device, read or written on the
+ *     simulation's stream;
+ *   - per-particle host arrays are indexed by particle id (the row order of
+ *     the positions given to sp_sim_create) and laid out [n][3] row-major;
+ *   - the library owns every device buffer of a simulation and frees them in
+ *     sp_sim_destroy;
+ *   - calls on one simulation must not run concurrently from several threads.
+ */
+#ifndef SHEARSIM_H
+#define SHEARSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sp_status {
+    SP_OK = 0,
+    SP_ERR_INVALID_ARG = -1,    /* a null pointer, n <= 0, a non-positive box edge, ... */
+    SP_ERR_CUDA = -2,           /* a CUDA runtime call failed (sp_last_error has the text) */
+    SP_ERR_NOT_CONVERGED = -3,  /* CG hit cg_max_iter before ||b - Av|| <= cg_tol ||b|| */
+    SP_ERR_NONFINITE = -4,      /* a NaN or infinity appeared in the solve */
+    SP_ERR_OOM = -5,            /* device allocation failed */
+    SP_ERR_BOX_TOO_SMALL = -6,  /* some box edge is below 2 r_c: the minimum image is ambiguous */
+    SP_ERR_NO_DEVICE = -7       /* no CUDA device, or the requested ordinal does not exist */
+} sp_status;
+
+enum sp_precision {
+    SP_PREC_FP64 = 0,   /* matrix, vectors and dots in FP64 */
+    SP_PREC_MIXED = 1   /* FP32 SpMV, axpy and Jacobi; FP64 positions, dots, x, residual replacement */
+};
+
+enum sp_warm_start {
+    SP_WARM_NONE = 0,   /* CG starts from v = 0 */
+    SP_WARM_PREV = 1    /* CG starts from the previous step's velocities */
+};
+
+/* Model and solver parameters (§Method).  kappa is the shear rate in units of
+ * kT / (zeta r_c^2); sp_kappa_from_kappa_tau converts the paper's kappa*tau. */
+typedef struct sp_params {
+    int64_t n;            /* particles (chains), >= 2 */
+    double L[3];          /* box edges L_x, L_y, L_z; each >= 2 r_c */
+    double rc;            /* truncation radius (w = 5 % there) */
+    double alpha;         /* entanglement strength (4 in the paper's shear runs), >= 0 */
+    double eps;           /* multiplies the paper's v/lambda^3 = 0.1 */
+    double zeta;          /* friction coefficient, > 0 */
+    double kT;            /* temperature, >= 0 */
+    double kappa;         /* shear rate in the xy plane (x flow, y gradient) */
+    double dt;            /* time step, > 0 */
+    uint64_t seed;        /* key of the counter-based noise generator */
+    int32_t precision;    /* enum sp_precision */
+    int32_t warm_start;   /* enum sp_warm_start */
+    double cg_tol;        /* stop at ||b - A v||_2 <= cg_tol ||b||_2 over all 3n entries */
+    int32_t cg_max_iter;  /* iteration cap per solve (e.g. 1000) */
+    int32_t device;       /* CUDA device ordinal */
+    void* stream;         /* cudaStream_t to run on; NULL: the library creates its own */
+} sp_params;
+
+typedef struct sp_solve_info {
+    int32_t status;       /* sp_status of the solve */
+    int32_t iterations;   /* CG iterations of this solve */
+    double residual;      /* final true relative residual ||b - A v|| / ||b|| (FP64) */
+    double bnorm;         /* ||b||_2 */
+} sp_solve_info;
+
+typedef struct sp_step_info {
+    int32_t status;          /* first non-OK status of the steps, else SP_OK */
+    int32_t max_iterations;  /* largest CG iteration count of the steps */
+    int64_t steps_done;      /* steps completed by this call */
+    int64_t cg_iterations;   /* CG iterations summed over the steps */
+    double last_residual;    /* true relative residual of the last solve */
+    double stress_xy;        /* shear stress of the last step (pair virial, see sp_stress_xy) */
+    int64_t kernel_launches; /* kernels this call ran on the GPU */
+} sp_step_info;
+
+typedef struct sp_sim sp_sim;
+
+/* kappa = kappa_tau / tau with tau = lambda^2 zeta / kT, lambda^2 = rc^2 / (2 ln 20)
+ * (§Method: tau is the Rouse time).  Returns NaN if kT <= 0. */
+double sp_kappa_from_kappa_tau(double kappa_tau, double rc, double zeta, double kT);
+
+/* Create a simulation on p->device.  pos_host: [n][3] initial positions in
+ * [0, L) (copied), or NULL for positions uniform in the box drawn from the
+ * counter-based generator keyed by p->seed.  The Lees-Edwards offset starts at
+ * 0 and the step counter at 0.  On success *out owns all device memory. */
+int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out);
+
+/* Free everything; NULL is allowed. */
+int sp_sim_destroy(sp_sim* sim);
+
+/* One line describing the last failure on this simulation ("" if none);
+ * valid until the next call on it.  sim may be NULL (creation errors). */
+const char* sp_last_error(const sp_sim* sim);
+
+/* Step 1 for the current positions: cell list with sheared periodic images,
+ * then all pairs with |R_ij|^2 < r_c^2 (§Method, 5 % truncation). */
+int sp_build_neighbors(sp_sim* sim);
+
+/* Step 2 for the current pairs: forces of Eq. F with the noise of the current
+ * step counter, and Eq. algebra (A, b, Jacobi diagonal).  Requires
+ * sp_build_neighbors since the last position change. */
+int sp_assemble(sp_sim* sim);
+
+/* Step 3: solve Eq. algebra by Jacobi-PCG (FP64 or mixed, per p->precision).
+ * v0_dev: optional start vector, device [3][n] planes in the library's
+ * current particle order (see sp_get_order), or NULL for the configured warm
+ * start.  info may be NULL.  Returns SP_ERR_NOT_CONVERGED if the iteration
+ * cap is hit; the velocities are kept either way. */
+int sp_solve_velocities(sp_sim* sim, const double* v0_dev, sp_solve_info* info);
+
+/* nsteps full time steps (steps 1-4), each run as one CUDA graph launch with
+ * the CG loop inside the graph.  The noise of step k is keyed by the step
+ * counter, which advances by one per step.  info may be NULL.  Stops early on
+ * the first failing step (info->steps_done tells how many finished). */
+int sp_step(sp_sim* sim, int32_t nsteps, sp_step_info* info);
+
+/* Eq. Sfactor at q_z = 0 on the sheared reciprocal lattice of the current
+ * snapshot: q_x = 2 pi kx / L_x, q_y = 2 pi ky / L_y - (delta / L_y) q_x for
+ * kx in [-nkx, nkx], ky in [-nky, nky].  Outputs (host, (2nkx+1)(2nky+1)
+ * entries, kx slowest): S_host = |sum_c exp(-i q . R_c)|^2 / n, qx_host, qy_host
+ * (either q array may be NULL).  The density is spread on a grid of
+ * `grid` x `grid` cells in the sheared frame by cloud-in-cell and the window is
+ * divided out; |kx|, |ky| must stay below grid / 4. */
+int sp_structure_factor(sp_sim* sim, int32_t nkx, int32_t nky, int32_t grid, double* S_host,
+                        double* qx_host, double* qy_host);
+
+/* Shear stress sigma_xy of the current state: -(1/V) sum_{i<j} y_ij f_ij,x with
+ * f_ij = eps 0.1 kT/lambda^2 R_ij w_ij + zeta alpha w_ij (v_j - v_i + V_ij), the
+ * pair forces of Eq. F and Eq. vc, using the velocities of the last solve.
+ * The paper defines no stress; this is the pair virial of its pair forces. */
+int sp_stress_xy(sp_sim* sim, double* sigma_xy);
+
+/* Per-kernel timing of one time step (a diagnostic for roofline reports).
+ * Runs one full step (it advances the simulation exactly like sp_step(sim, 1))
+ * with the CG loop driven from the host and a CUDA event pair on the
+ * simulation's stream around every kernel launch; times are sums in ms. */
+typedef struct sp_kernel_profile {
+    int32_t spmv_launches;           /* q = A p (the solver's SpMV) */
+    int32_t update_launches;         /* x, r update with the r.r, r.z partial sums */
+    int32_t direction_launches;      /* p = z + beta p */
+    int32_t true_residual_launches;  /* r = b - A x checks */
+    double spmv_ms, update_ms, direction_ms, true_residual_ms;
+    double build_ms;                 /* cell list, pair search and assembly */
+    double other_ms;                 /* solver set-up, stress, position update */
+    int64_t n;                       /* rows */
+    int64_t nnz;                     /* off-diagonal entries (2 x pairs) */
+    int32_t cg_iterations;
+    int32_t precision;               /* enum sp_precision of the solver */
+} sp_kernel_profile;
+int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
+
+/* ---- state access (test hooks and checkpointing) ---- */
+
+/* Positions [n][3] by particle id. */
+int sp_get_positions(sp_sim* sim, double* pos_host);
+/* Replace positions ([n][3] by particle id, each in [0, L)) and the
+ * Lees-Edwards offset delta in [0, L_x). */
+int sp_set_positions(sp_sim* sim, const double* pos_host, double delta);
+/* Velocities of the last solve [n][3] by particle id. */
+int sp_get_velocities(sp_sim* sim, double* v_host);
+/* Lees-Edwards offset and step counter (the noise key). */
+int sp_get_state(sp_sim* sim, double* delta, int64_t* step);
+/* Set the step counter, e.g. to resume a checkpoint (positions via sp_set_positions). */
+int sp_set_step(sp_sim* sim, int64_t step);
+/* Particle id of each internal row, [n] (rows are kept in cell order). */
+int sp_get_order(sp_sim* sim, int64_t* ids_host);
+/* Number of pairs i < j found by the last sp_build_neighbors / sp_step. */
+int sp_get_num_pairs(sp_sim* sim, int64_t* npairs);
+/* The pairs (by particle id, i < j, unsorted) [npairs][2]; cap = capacity in pairs. */
+int sp_get_neighbors(sp_sim* sim, int64_t cap, int64_t* pairs_host, int64_t* npairs);
+/* The assembled system by particle id: diag_host [n] (A_ii), b_host [n][3],
+ * w_host [npairs] weight of each pair in the order of sp_get_neighbors
+ * (any output may be NULL). */
+int sp_get_system(sp_sim* sim, double* diag_host, double* b_host, double* w_host);
+/* Noise override: xi_host [n][3] standard normals by particle id used by
+ * every following assembly instead of the generator; NULL returns to the
+ * generator. */
+int sp_set_noise(sp_sim* sim, const double* xi_host);
+/* Raw counter-based generator (Philox4x64-10, Salmon et al. SC'11), for
+ * checking: out_host[4 * k ...] = Philox(ctr = (ids[k], step, 0, 0), key = (seed, 0)). */
+int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count,
+                     const int64_t* ids_host, uint64_t* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHEARSIM_H */

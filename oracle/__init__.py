@@ -81,6 +81,8 @@ def _load():
         lib.or_stress_xy.restype = d
         lib.or_stress_xy.argtypes = [P(_Params), vp, d, i64, vp, vp]
         lib.or_min_image.argtypes = [P(_Params), d, vp, vp, vp, vp]
+        lib.or_row_neighbors.restype = i64
+        lib.or_row_neighbors.argtypes = [P(_Params), vp, d, i64, i64, vp]
         _lib = lib
     return _lib
 
@@ -158,6 +160,17 @@ def neighbors(p: Params, pos, delta: float = 0.0, method: str = "auto") -> np.nd
         if rc != OR_ERR_CAPACITY:
             raise RuntimeError(f"oracle neighbour search failed: {rc}")
         cap = m.value
+
+
+def row_neighbors(p: Params, pos, delta: float, i: int) -> np.ndarray:
+    """All j != i with R_ij^2 < r_c^2 for one particle i, by brute force (sorted)."""
+    pos = _f64(pos)
+    out = np.zeros(256, dtype=np.int64)
+    m = _load().or_row_neighbors(ctypes.byref(p.c()), _ptr(pos), float(delta), int(i), 256, _ptr(out))
+    if m > 256:
+        out = np.zeros(m, dtype=np.int64)
+        _load().or_row_neighbors(ctypes.byref(p.c()), _ptr(pos), float(delta), int(i), m, _ptr(out))
+    return out[:m].copy()
 
 
 def philox4x64_10(ctr, key) -> np.ndarray:

@@ -584,3 +584,24 @@ double or_stress_xy(const or_params* p, const double* pos, double delta, int64_t
     }
     return -s / (p->L[0] * p->L[1] * p->L[2]);
 }
+
+/* Row i alone: every j != i with |R_ij|^2 < r_c^2, by checking all particles
+ * (brute force, for sampled checks of large systems).  Writes up to cap ids to
+ * out in increasing j; returns the count. */
+int64_t or_row_neighbors(const or_params* p, const double* pos, double delta, int64_t i, int64_t cap,
+                         int64_t* out)
+{
+    or_derived dv;
+    or_derive(p, &dv);
+    int64_t m = 0;
+    for (int64_t j = 0; j < p->n; ++j) {
+        if (j == i) continue;
+        double d[3], nimg;
+        or_min_image(p, delta, pos + 3 * i, pos + 3 * j, d, &nimg);
+        if (sq_dist(d) < dv.rc2) {
+            if (m < cap) out[m] = j;
+            ++m;
+        }
+    }
+    return m;
+}

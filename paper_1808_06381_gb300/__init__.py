@@ -1,0 +1,296 @@
+"""GB300 (sm_103a) coupled velocity solve of Korolkovas, arXiv 1808.06381.
+
+Thin ctypes binding of ``libshearsim.so`` (declared in ``include/shearsim.h``):
+argument marshalling only.  Every step of the method runs in the library's
+CUDA kernels; there is no CPU fallback, and loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+LIB_PATH = os.path.join(_PKG, "lib", "libshearsim.so")
+HEADER = os.path.join(_ROOT, "include", "shearsim.h")
+
+SP_OK = 0
+SP_ERR_INVALID_ARG = -1
+SP_ERR_CUDA = -2
+SP_ERR_NOT_CONVERGED = -3
+SP_ERR_NONFINITE = -4
+SP_ERR_OOM = -5
+SP_ERR_BOX_TOO_SMALL = -6
+SP_ERR_NO_DEVICE = -7
+_STATUS = {0: "SP_OK", -1: "SP_ERR_INVALID_ARG", -2: "SP_ERR_CUDA", -3: "SP_ERR_NOT_CONVERGED",
+           -4: "SP_ERR_NONFINITE", -5: "SP_ERR_OOM", -6: "SP_ERR_BOX_TOO_SMALL", -7: "SP_ERR_NO_DEVICE"}
+
+PREC = {"fp64": 0, "mixed": 1}
+WARM = {"none": 0, "prev": 1}
+
+
+class ShearsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sp_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("L", ctypes.c_double * 3), ("rc", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("kT", ctypes.c_double), ("kappa", ctypes.c_double), ("dt", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class sp_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+
+class sp_step_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("steps_done", ctypes.c_int64),
+                ("cg_iterations", ctypes.c_int64), ("last_residual", ctypes.c_double),
+                ("stress_xy", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class sp_kernel_profile(ctypes.Structure):
+    _fields_ = [("spmv_launches", ctypes.c_int32), ("update_launches", ctypes.c_int32),
+                ("direction_launches", ctypes.c_int32), ("true_residual_launches", ctypes.c_int32),
+                ("spmv_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("direction_ms", ctypes.c_double),
+                ("true_residual_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("cg_iterations", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+def declared_symbols() -> list:
+    """Entry points declared in include/shearsim.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|double|const char\*)\s+(sp_[a-z0-9_]+)\s*\(", text, re.M)))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libshearsim.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libshearsim.so is not built ({path}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    P, vp = ctypes.POINTER, ctypes.c_void_p
+    i32, i64, u64, d = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sims = [("sp_sim_create", [P(sp_params), vp, P(vp)]), ("sp_sim_destroy", [vp]),
+            ("sp_build_neighbors", [vp]), ("sp_assemble", [vp]),
+            ("sp_solve_velocities", [vp, vp, P(sp_solve_info)]), ("sp_step", [vp, i32, P(sp_step_info)]),
+            ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
+            ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
+            ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
+            ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
+            ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
+            ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
+            ("sp_profile_step", [vp, P(sp_kernel_profile)])]
+    for name, args in sims:
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.sp_last_error.argtypes = [vp]
+    lib.sp_last_error.restype = ctypes.c_char_p
+    lib.sp_kappa_from_kappa_tau.argtypes = [d, d, d, d]
+    lib.sp_kappa_from_kappa_tau.restype = d
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, handle=None):
+    if rc != SP_OK:
+        msg = load().sp_last_error(handle)
+        raise ShearsimError(rc, msg.decode() if msg else "")
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def kappa_from_kappa_tau(kappa_tau: float, rc: float = 1.0, zeta: float = 1.0, kT: float = 1.0) -> float:
+    return load().sp_kappa_from_kappa_tau(kappa_tau, rc, zeta, kT)
+
+
+def philox_blocks(seed: int, step: int, ids, device: int = 0) -> np.ndarray:
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    out = np.zeros((ids.shape[0], 4), dtype=np.uint64)
+    _check(load().sp_philox_blocks(device, seed, step, ids.shape[0], _p(ids), _p(out)))
+    return out
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Simulation:
+    """One simulation on one GPU (see include/shearsim.h for the contract of each call)."""
+
+    def __init__(self, n: int, L, kappa: float, alpha: float = 4.0, eps: float = 1.0, zeta: float = 1.0,
+                 kT: float = 1.0, dt: float = 0.01, rc: float = 1.0, seed: int = 0, precision: str = "fp64",
+                 warm_start: str = "prev", cg_tol: float = 1e-8, cg_max_iter: int = 1000, device: int = 0,
+                 stream=None, positions=None, use_torch_stream: bool = True):
+        lib = load()
+        p = sp_params()
+        p.n = int(n)
+        for a in range(3):
+            p.L[a] = float(L[a])
+        p.rc, p.alpha, p.eps, p.zeta, p.kT, p.kappa, p.dt = rc, alpha, eps, zeta, kT, kappa, dt
+        p.seed = int(seed)
+        p.precision = PREC[precision]
+        p.warm_start = WARM[warm_start]
+        p.cg_tol = cg_tol
+        p.cg_max_iter = cg_max_iter
+        p.device = device
+        if stream is None and use_torch_stream:
+            stream = _torch_stream()
+        p.stream = stream
+        self.n = int(n)
+        self.L = tuple(float(x) for x in L)
+        self.params = p
+        pos = None
+        if positions is not None:
+            pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(self.n, 3)
+        h = ctypes.c_void_p()
+        _check(lib.sp_sim_create(ctypes.byref(p), _p(pos) if pos is not None else None, ctypes.byref(h)))
+        self._h = h
+
+    # lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sp_sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _c(self, rc):
+        _check(rc, self._h)
+
+    # the path
+    def build_neighbors(self):
+        self._c(load().sp_build_neighbors(self._h))
+
+    def assemble(self):
+        self._c(load().sp_assemble(self._h))
+
+    def solve_velocities(self, v0_dev_ptr=None, raise_on_error: bool = True) -> dict:
+        info = sp_solve_info()
+        rc = load().sp_solve_velocities(self._h, v0_dev_ptr, ctypes.byref(info))
+        if raise_on_error:
+            self._c(rc)
+        return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm}
+
+    def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
+        info = sp_step_info()
+        rc = load().sp_step(self._h, int(nsteps), ctypes.byref(info))
+        if raise_on_error:
+            self._c(rc)
+        return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,
+                "max_iterations": info.max_iterations, "last_residual": info.last_residual,
+                "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches}
+
+    def structure_factor(self, nkx: int, nky: int, grid: int = 256):
+        m = (2 * nkx + 1) * (2 * nky + 1)
+        S, qx, qy = np.zeros(m), np.zeros(m), np.zeros(m)
+        self._c(load().sp_structure_factor(self._h, nkx, nky, grid, _p(S), _p(qx), _p(qy)))
+        shape = (2 * nkx + 1, 2 * nky + 1)
+        return S.reshape(shape), qx.reshape(shape), qy.reshape(shape)
+
+    def profile_step(self) -> dict:
+        prof = sp_kernel_profile()
+        self._c(load().sp_profile_step(self._h, ctypes.byref(prof)))
+        return {name: getattr(prof, name) for name, _ in sp_kernel_profile._fields_}
+
+    def stress_xy(self) -> float:
+        v = ctypes.c_double()
+        self._c(load().sp_stress_xy(self._h, ctypes.byref(v)))
+        return v.value
+
+    # state access
+    def get_positions(self, out=None) -> np.ndarray:
+        out = np.zeros((self.n, 3)) if out is None else out
+        self._c(load().sp_get_positions(self._h, _p(out)))
+        return out
+
+    def set_positions(self, pos, delta: float = 0.0):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        self._c(load().sp_set_positions(self._h, _p(pos), float(delta)))
+
+    def get_velocities(self, out=None) -> np.ndarray:
+        out = np.zeros((self.n, 3)) if out is None else out
+        self._c(load().sp_get_velocities(self._h, _p(out)))
+        return out
+
+    def state(self):
+        d, s = ctypes.c_double(), ctypes.c_int64()
+        self._c(load().sp_get_state(self._h, ctypes.byref(d), ctypes.byref(s)))
+        return d.value, s.value
+
+    def set_step(self, step: int):
+        self._c(load().sp_set_step(self._h, int(step)))
+
+    def order(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int64)
+        self._c(load().sp_get_order(self._h, _p(out)))
+        return out
+
+    def num_pairs(self) -> int:
+        m = ctypes.c_int64()
+        self._c(load().sp_get_num_pairs(self._h, ctypes.byref(m)))
+        return m.value
+
+    def neighbors(self) -> np.ndarray:
+        """Pairs (i < j by id) sorted by (i, j)."""
+        m = self.num_pairs()
+        out = np.zeros((max(m, 1), 2), dtype=np.int64)
+        got = ctypes.c_int64()
+        self._c(load().sp_get_neighbors(self._h, m, _p(out), ctypes.byref(got)))
+        pairs = out[: got.value]
+        return pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]
+
+    def system(self):
+        """(diag [n], b [n, 3], pairs [m, 2] sorted, w [m]) by particle id."""
+        m = self.num_pairs()
+        diag, b, w = np.zeros(self.n), np.zeros((self.n, 3)), np.zeros(max(m, 1))
+        out = np.zeros((max(m, 1), 2), dtype=np.int64)
+        got = ctypes.c_int64()
+        self._c(load().sp_get_neighbors(self._h, m, _p(out), ctypes.byref(got)))
+        self._c(load().sp_get_system(self._h, _p(diag), _p(b), _p(w)))
+        pairs, w = out[: got.value], w[: got.value]
+        order = np.lexsort((pairs[:, 1], pairs[:, 0]))
+        return diag, b, pairs[order], w[order]
+
+    def set_noise(self, xi=None):
+        if xi is None:
+            self._c(load().sp_set_noise(self._h, None))
+        else:
+            xi = np.ascontiguousarray(xi, dtype=np.float64)
+            self._c(load().sp_set_noise(self._h, _p(xi)))

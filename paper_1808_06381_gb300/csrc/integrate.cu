@@ -1,0 +1,146 @@
+// Position update with the Lees-Edwards wrap, the pair-virial shear stress,
+// and the by-id transfers used by the state-access calls (arXiv 1808.06381,
+// §Method).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ss {
+
+// R += v dt (first order in time, v = dR/dt).  The image offset advances first,
+// delta' = delta + kappa L_y dt (mod L_x); a particle leaving through y = L_y
+// re-enters at y - L_y shifted by -delta' in x (through y = 0: +delta').  The
+// new state is written in the current cell order together with the ids and
+// the velocities (the next step's warm start).  The last block advances the
+// device's offset and step counter.
+__global__ void __launch_bounds__(kVecBlock) k_integrate(KParams P, DevBuffers B)
+{
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int np = P.npad;
+    const double dnew = wrap_box(st->delta + P.kappa * P.L[1] * P.dt, P.L[0]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const double vx = B.x[i], vy = B.x[np + i], vz = B.x[2 * np + i];
+        double x = __dadd_rn(B.pos_w[i], __dmul_rn(vx, P.dt));
+        double y = __dadd_rn(B.pos_w[np + i], __dmul_rn(vy, P.dt));
+        const double z = __dadd_rn(B.pos_w[2 * np + i], __dmul_rn(vz, P.dt));
+        if (y < 0.0) {
+            y = y + P.L[1];
+            x = x + dnew;
+        }
+        if (y >= P.L[1]) {
+            y = y - P.L[1];
+            x = x - dnew;
+        }
+        B.pos_s[i] = wrap_box(x, P.L[0]);
+        B.pos_s[np + i] = y;
+        B.pos_s[2 * np + i] = wrap_box(z, P.L[2]);
+        B.id_s[i] = B.id_w[i];
+        B.v_s[i] = vx;
+        B.v_s[np + i] = vy;
+        B.v_s[2 * np + i] = vz;
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->ticket[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        st->ticket[1] = 0u;
+        st->delta = dnew;
+        st->step += 1;
+        st->steps_in_call += 1;
+    }
+}
+
+void launch_integrate(const KParams& P, DevBuffers& B, Launch L)
+{
+    k_integrate<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
+}
+
+// sigma_xy = -(1/V) sum_{i<j} y_ij f_ij,x with the pair forces of Eq. F and
+// Eq. vc (times zeta): f_ij = c_ev R_ij w_ij + zeta alpha w_ij (v_j - v_i + V_ij).
+// y_ij f_ij,x is symmetric in (i, j), so each row sums its whole neighbour list
+// and the total is halved.
+__global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
+{
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int np = P.npad;
+    const double delta = st->delta;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
+        const double vxi = B.x[i];
+        for (int k = B.row_ptr[i]; k < B.row_ptr[i + 1]; ++k) {
+            const int j = B.col[k];
+            double dx, dy, dz;
+            const double nimg = min_image(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
+                                          B.pos_w[2 * np + j], dx, dy, dz);
+            const double w = B.val[k];
+            const double fx = P.c_ev * dx * w
+                            + P.zeta * P.alpha * w * (B.x[j] - vxi + P.kappa * P.L[1] * nimg);
+            acc += dy * fx;
+        }
+    }
+    const double v[1] = {acc};
+    if (publish_partials<1>(v, B.partials, &st->ticket[0])) {
+        double out[1];
+        reduce_partials<1>(B.partials, out);
+        if (threadIdx.x == 0) st->stress_xy = -0.5 * out[0] / (P.L[0] * P.L[1] * P.L[2]);
+    }
+}
+
+void launch_stress(const KParams& P, DevBuffers& B, Launch L)
+{
+    k_stress<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
+}
+
+__global__ void k_scatter_by_id(const double* __restrict__ planes, int npad, const int* __restrict__ ids,
+                                int n, double* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long id = ids[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[3 * id + a] = planes[a * npad + k];
+}
+
+void launch_scatter_by_id(const double* planes, int npad, const int* ids, int n, double* out_n3,
+                          cudaStream_t s)
+{
+    k_scatter_by_id<<<grid_for(n, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(planes, npad, ids, n, out_n3);
+}
+
+__global__ void k_gather_by_id(const double* __restrict__ in, const int* __restrict__ ids, int n,
+                               int npad, double* __restrict__ planes)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long id = ids[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) planes[a * npad + k] = in[3 * id + a];
+}
+
+void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, double* planes,
+                         cudaStream_t s)
+{
+    k_gather_by_id<<<grid_for(n, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(in_n3, ids, n, npad, planes);
+}
+
+__global__ void k_reset_step_stats(DevState* st)
+{
+    st->iter_sum = 0;
+    st->iter_max = 0;
+    st->steps_in_call = 0;
+    st->true_checks = 0;
+}
+
+void launch_reset_step_stats(DevState* st, cudaStream_t s)
+{
+    k_reset_step_stats<<<1, 1, 0, s>>>(st);
+}
+
+}  // namespace ss

@@ -1,0 +1,299 @@
+// Internal declarations of the shearsim CUDA library (sm_103a).
+// Device helpers shared by the kernels of this library, the per-simulation
+// device state, and host launchers for the kernels of each translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "shearsim.h"
+
+namespace ss {
+
+constexpr int kMaxCgRestarts = 4;    // true-residual restarts per solve before giving up
+constexpr int kVecBlock = 256;       // threads per block of the streaming kernels
+
+// Constants of one simulation, passed by value to every kernel.
+struct KParams {
+    int n;              // particles (rows)
+    int npad;           // stride between the x, y, z planes of a vector
+    double L[3];
+    double rc2;         // r_c^2: pair kept iff |R|^2 < rc2
+    double two_lambda2; // 2 lambda^2, lambda^2 = r_c^2 / (2 ln 20)
+    double alpha, zeta, kappa, dt;
+    double c_ev;        // eps * 0.1 * kT / lambda^2
+    double noise_amp;   // sqrt(2 zeta kT / dt)
+    unsigned long long seed;
+    int nc[3];          // cells per axis (cell edge >= r_c)
+    double inv_cw[3];   // cells per unit length
+    int ncell;
+    double tol2;        // cg_tol^2
+    int max_iter;
+};
+
+// Scalars that live on the device so that a whole step runs without the host.
+struct DevState {
+    double delta;             // Lees-Edwards image offset of the image at y + L_y
+    long long step;           // step counter (noise key)
+    long long nnz;            // off-diagonal entries of the current matrix (2 x pairs)
+    long long nnz_cap;        // capacity of col / val
+    int overflow;             // sticky: nnz exceeded nnz_cap
+    int error;                // sticky: first failing sp_status of a step (0 = none)
+    // conjugate gradients
+    double bnorm2, rho, alpha, beta, rr, pq, rr_true;
+    int iter, restarts, done, status, check_true, zero_b;
+    // mixed precision bookkeeping
+    int since_replace;
+    // statistics accumulated over the steps of one sp_step call
+    long long iter_sum;
+    int iter_max;
+    int steps_in_call;
+    long long true_checks;
+    double last_res;
+    double stress_xy;
+    unsigned int ticket[4];
+};
+
+// Device buffers of one simulation (all in the current cell order unless noted).
+struct DevBuffers {
+    // state (order of the previous build)
+    double* pos_s;   // [3][npad]
+    int* id_s;       // [n]
+    double* v_s;     // [3][npad] velocities of the last solve
+    // work arrays of the current step (cell order)
+    double* pos_w;   // [3][npad]
+    int* id_w;       // [n]
+    int* cell_of;    // [n]
+    int* slot;       // [n]
+    int* perm;       // [n] new row -> state row
+    int* cell_count; // [ncell]
+    int* cell_start; // [ncell + 1]
+    int* row_cnt;    // [n]
+    int* row_ptr;    // [n + 1]
+    int* col;        // [nnz_cap]
+    double* val;     // [nnz_cap] pair weights w_ij (A_ij = -alpha w_ij)
+    float* val32;    // [nnz_cap] FP32 copy for the mixed solver
+    double* diag;    // [n] A_ii
+    double* dinv;    // [n] 1 / A_ii
+    float* dinv32;   // [n]
+    double* b;       // [3][npad]
+    double* x;       // [3][npad] solution (velocities)
+    double* r;       // [3][npad]
+    double* p;       // [3][npad]
+    double* q;       // [3][npad]
+    float* r32;      // [4][n] mixed path: r as interleaved float4
+    float* p32;      // [4][n]
+    float* q32;      // [4][n]
+    double* xi_inj;  // [n][3] injected normals by id (or null)
+    double* partials;// [kMaxPartials * 4]
+    int* scan_tmp;   // block sums of the scans
+    double* stage;   // [n][3] staging for host transfers
+    DevState* st;
+};
+
+constexpr int kMaxPartials = 4096;
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+// Publish this block's partial sums, then return true in exactly one block
+// (the last one to arrive).  That block may then read every block's
+// partials: no block ever waits for another.
+template <int K>
+__device__ __forceinline__ bool publish_partials(const double (&vals)[K], double* partials,
+                                                 unsigned int* ticket)
+{
+    __shared__ double sh[32];
+    __shared__ bool last;
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = block_sum(vals[k], sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) partials[k * kMaxPartials + blockIdx.x] = tot[k];
+        __threadfence();
+        const unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+    return last;
+}
+
+// In the last block: sum the K partial arrays in a fixed order (deterministic).
+template <int K>
+__device__ __forceinline__ void reduce_partials(const double* partials, double (&out)[K])
+{
+    __shared__ double sh[32];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+            v += __ldcg(partials + k * kMaxPartials + i);
+        out[k] = block_sum(v, sh);
+    }
+}
+
+// Lees-Edwards minimum image R_ij = R_i - R_j with every operation rounded
+// exactly as written (no contraction), so the pair predicate is reproducible
+// bit for bit on any IEEE machine.  n = round(y_ij / L_y) is the vertical image
+// index of the boundary correction V_ij = kappa L_y n x (§Method).
+__device__ __forceinline__ double min_image(const KParams& P, double delta, double xi, double yi,
+                                            double zi, double xj, double yj, double zj,
+                                            double& dx, double& dy, double& dz)
+{
+    dx = __dsub_rn(xi, xj);
+    dy = __dsub_rn(yi, yj);
+    dz = __dsub_rn(zi, zj);
+    const double n = round(__ddiv_rn(dy, P.L[1]));
+    dy = __dsub_rn(dy, __dmul_rn(n, P.L[1]));
+    dx = __dsub_rn(dx, __dmul_rn(n, delta));
+    dx = __dsub_rn(dx, __dmul_rn(P.L[0], round(__ddiv_rn(dx, P.L[0]))));
+    dz = __dsub_rn(dz, __dmul_rn(P.L[2], round(__ddiv_rn(dz, P.L[2]))));
+    return n;
+}
+
+__device__ __forceinline__ double sq_norm_exact(double dx, double dy, double dz)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1)
+{
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const unsigned long long n0 = hi1 ^ c[1] ^ k0;
+        const unsigned long long n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Three N(0,1) draws for particle `id` at `step`: one Philox block (counter
+// (id, step, 0, 0), key (seed, 0)), Box-Muller on 53-bit uniforms.
+__device__ __forceinline__ void normals3(unsigned long long seed, unsigned long long step,
+                                         unsigned long long id, double& g0, double& g1, double& g2)
+{
+    unsigned long long c[4] = {id, step, 0ull, 0ull};
+    philox4x64_10(c, seed, 0ull);
+    const double s53 = 1.0 / 9007199254740992.0;
+    const double u1 = (double)((c[0] >> 11) + 1ull) * s53;
+    const double u2 = (double)(c[1] >> 11) * s53;
+    const double u3 = (double)((c[2] >> 11) + 1ull) * s53;
+    const double u4 = (double)(c[3] >> 11) * s53;
+    const double r1 = sqrt(-2.0 * log(u1));
+    const double r2 = sqrt(-2.0 * log(u3));
+    double s, co;
+    sincospi(2.0 * u2, &s, &co);
+    g0 = r1 * co;
+    g1 = r1 * s;
+    g2 = r2 * cospi(2.0 * u4);
+}
+
+__device__ __forceinline__ double wrap_box(double x, double L)
+{
+    x = x - L * floor(x / L);
+    if (x >= L) x = x - L;
+    if (x < 0.0) x = 0.0;
+    return x;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double inv_cw, int nc)
+{
+    int c = (int)floor(x * inv_cw);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// ------------------------------------------------------------------ launchers
+
+inline int grid_for(long long work, int per_block, int max_blocks)
+{
+    long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+struct Launch {
+    cudaStream_t stream;
+    int num_sms;
+};
+
+// neighbors.cu
+void launch_bin(const KParams& P, DevBuffers& B, Launch L);
+void launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st,
+                 int mode, Launch L);
+void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
+void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
+void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L);
+void launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool mixed,
+                     Launch L);
+void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool mixed, Launch L);
+void launch_uniform_positions(const KParams& P, DevBuffers& B, Launch L);
+void launch_philox_blocks(unsigned long long seed, unsigned long long step, long long count,
+                          const long long* ids, unsigned long long* out, cudaStream_t s);
+
+// cg.cu
+struct CgLaunch {
+    int use_cond;                       // call cudaGraphSetConditional (inside a graph)
+    unsigned long long h_loop, h_check; // cudaGraphConditionalHandle values
+};
+void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L);
+void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L);
+void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L);
+void launch_cg_iteration_head(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C,
+                              Launch L);
+void launch_cg_true_residual(const KParams& P, DevBuffers& B, bool mixed, bool always_check,
+                             Launch L);
+void launch_cg_iteration_tail(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C,
+                              Launch L);
+void launch_cg_finish(const KParams& P, DevBuffers& B, Launch L);
+int cg_kernels_per_iteration(bool mixed);
+
+// integrate.cu
+void launch_integrate(const KParams& P, DevBuffers& B, Launch L);
+void launch_stress(const KParams& P, DevBuffers& B, Launch L);
+void launch_scatter_by_id(const double* planes, int npad, const int* ids, int n, double* out_n3,
+                          cudaStream_t s);
+void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, double* planes,
+                         cudaStream_t s);
+void launch_reset_step_stats(DevState* st, cudaStream_t s);
+void launch_structure_factor(const KParams& P, const DevBuffers& B, int grid, int nkx, int nky,
+                             double* grid_buf, double* S, double* qx, double* qy, cudaStream_t s);
+
+}  // namespace ss

@@ -1,0 +1,1033 @@
+// Host side of the shearsim C ABI: simulation objects, device memory, CUDA
+// graphs of a time step and of a solve, and the state-access calls.
+//
+// A time step is one CUDA graph: cell binning and sorting, pair search, the
+// fused pair/assembly kernel, CG (a conditional WHILE node whose body holds an
+// IF node for the true-residual check), the stress, and the position update.
+// The host launches nsteps graphs back to back and reads the device state
+// once at the end.  If conditional graph nodes are unavailable the same
+// kernels are launched from a host loop instead (SHEARSIM_HOST_LOOP=1 forces
+// that mode).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace ss;
+
+struct sp_sim {
+    sp_params p{};
+    KParams kp{};
+    DevBuffers B{};
+    DevState* st_host = nullptr;  // pinned mirror of the device state
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
+    int num_sms = 0;
+    long long nnz_cap = 0;
+    bool use_inj = false;
+    bool host_loop = false;       // CG loop driven from the host
+    bool built = false;           // pairs match the current positions
+    bool assembled = false;
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraph_t solve_graph[2] = {nullptr, nullptr};   // [from_x]
+    cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
+    long long fixed_launches_step = 0;
+    long long fixed_launches_solve = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+#define SS_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return SP_ERR_CUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+#define SS_TRY(expr)                 \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ != SP_OK) return rc_;   \
+    } while (0)
+
+Launch launch_of(const sp_sim* s, cudaStream_t st) { return Launch{st, s->num_sms}; }
+
+bool mixed(const sp_sim* s) { return s->p.precision == SP_PREC_MIXED; }
+
+template <class T>
+int dev_alloc(sp_sim* s, T** ptr, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(count, 1));
+    if (e != cudaSuccess) {
+        s->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA;
+    }
+    *ptr = static_cast<T*>(q);
+    return SP_OK;
+}
+
+void free_graphs(sp_sim* s)
+{
+    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+    if (s->step_graph) cudaGraphDestroy(s->step_graph);
+    s->step_exec = nullptr;
+    s->step_graph = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (s->solve_exec[k]) cudaGraphExecDestroy(s->solve_exec[k]);
+        if (s->solve_graph[k]) cudaGraphDestroy(s->solve_graph[k]);
+        s->solve_exec[k] = nullptr;
+        s->solve_graph[k] = nullptr;
+    }
+}
+
+int alloc_pairs(sp_sim* s, long long cap)
+{
+    DevBuffers& B = s->B;
+    cudaFree(B.col);
+    cudaFree(B.val);
+    cudaFree(B.val32);
+    B.col = nullptr;
+    B.val = nullptr;
+    B.val32 = nullptr;
+    SS_TRY(dev_alloc(s, &B.col, (size_t)cap));
+    SS_TRY(dev_alloc(s, &B.val, (size_t)cap));
+    SS_TRY(dev_alloc(s, &B.val32, (size_t)cap));
+    s->nnz_cap = cap;
+    s->st_host->nnz_cap = cap;
+    SS_CUDA(cudaMemcpyAsync(&B.st->nnz_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, s->stream));
+    return SP_OK;
+}
+
+int check_params(const sp_params* p, std::string& why)
+{
+    if (!p) { why = "params is NULL"; return SP_ERR_INVALID_ARG; }
+    if (p->n < 2 || p->n > (1ll << 27)) { why = "n must be in [2, 2^27]"; return SP_ERR_INVALID_ARG; }
+    if (!(p->rc > 0) || !(p->dt > 0) || !(p->zeta > 0) || !(p->kT >= 0) || !(p->alpha >= 0) ||
+        !std::isfinite(p->kappa) || !std::isfinite(p->eps) || !(p->cg_tol > 0) || p->cg_max_iter < 1) {
+        why = "rc, dt, zeta, cg_tol must be > 0; kT, alpha >= 0; kappa, eps finite; cg_max_iter >= 1";
+        return SP_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (!(p->L[a] > 0) || !std::isfinite(p->L[a])) { why = "box edges must be > 0"; return SP_ERR_INVALID_ARG; }
+        if (p->L[a] < 2.0 * p->rc) { why = "box edge below 2 r_c"; return SP_ERR_BOX_TOO_SMALL; }
+    }
+    if (p->precision != SP_PREC_FP64 && p->precision != SP_PREC_MIXED) { why = "unknown precision"; return SP_ERR_INVALID_ARG; }
+    if (p->warm_start != SP_WARM_NONE && p->warm_start != SP_WARM_PREV) { why = "unknown warm start"; return SP_ERR_INVALID_ARG; }
+    return SP_OK;
+}
+
+// lambda^2 = r_c^2 / (2 ln 20): the weight exp(-r^2 / 2 lambda^2) is 5 % at r_c.
+double lambda2_of(double rc) { return rc * rc / (2.0 * std::log(20.0)); }
+
+void derive(const sp_params& p, KParams& k, int npad)
+{
+    k.n = (int)p.n;
+    k.npad = npad;
+    for (int a = 0; a < 3; ++a) k.L[a] = p.L[a];
+    k.rc2 = p.rc * p.rc;
+    const double l2 = lambda2_of(p.rc);
+    k.two_lambda2 = 2.0 * l2;
+    k.alpha = p.alpha;
+    k.zeta = p.zeta;
+    k.kappa = p.kappa;
+    k.dt = p.dt;
+    k.c_ev = p.eps * 0.1 * p.kT / l2;          // (v/lambda^3) kT / lambda^2 with v/lambda^3 = 0.1
+    k.noise_amp = std::sqrt(2.0 * p.zeta * p.kT / p.dt);
+    k.seed = p.seed;
+    // cells: edge >= r_c (1 + 1e-9) so that rounding never moves a partner
+    // within r_c out of the 3 x 3 x 3 block
+    long long ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)std::floor(p.L[a] / (p.rc * (1.0 + 1e-9)));
+        if (nc < 1) nc = 1;
+        if (nc > 4096) nc = 4096;
+        k.nc[a] = nc;
+        k.inv_cw[a] = (double)nc / p.L[a];
+        ncell *= nc;
+    }
+    if (k.nc[0] < 3 && k.nc[1] < 3 && k.nc[2] < 3) {
+        k.nc[0] = k.nc[1] = k.nc[2] = 1;
+        k.inv_cw[0] = 1.0 / p.L[0];
+        k.inv_cw[1] = 1.0 / p.L[1];
+        k.inv_cw[2] = 1.0 / p.L[2];
+        ncell = 1;
+    }
+    k.ncell = (int)ncell;
+    k.tol2 = p.cg_tol * p.cg_tol;
+    k.max_iter = p.cg_max_iter;
+}
+
+// --------------------------------------------------------------- enqueueing
+
+long long enqueue_build(sp_sim* s, cudaStream_t cs)
+{
+    KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    Launch L = launch_of(s, cs);
+    const bool warm = s->p.warm_start == SP_WARM_PREV;
+    long long launches = 0;
+    if (P.ncell == 1) {
+        launch_identity_gather(P, B, warm, L);
+        launches += 1;
+    } else {
+        launch_bin(P, B, L);
+        launch_scan(B.cell_count, B.cell_start, P.ncell, B.scan_tmp, 0, B.st, 0, L);
+        launch_scatter_sort_gather(P, B, warm, L);
+        launches += 6;
+    }
+    launch_nbr_count(P, B, L);
+    launch_scan(B.row_cnt, B.row_ptr, P.n, B.scan_tmp, s->nnz_cap, B.st, 1, L);
+    return launches + 4;
+}
+
+// Conditional WHILE node holding one CG iteration, with an IF node for the
+// true-residual check, appended to the graph being captured on cs.
+int capture_cg_loop(sp_sim* s, cudaStream_t cs)
+{
+    KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    const bool mx = mixed(s);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    SS_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h_loop;
+    SS_CUDA(cudaGraphConditionalHandleCreate(&h_loop, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    SS_CUDA(cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    SS_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+
+    cudaStream_t bs = s->cap_stream[1];
+    SS_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaGraphConditionalHandle h_check;
+    SS_CUDA(cudaGraphConditionalHandleCreate(&h_check, body, 0u, cudaGraphCondAssignDefault));
+    CgLaunch C{1, (unsigned long long)h_loop, (unsigned long long)h_check};
+    launch_cg_iteration_head(P, B, mx, C, launch_of(s, bs));
+    cudaGraph_t bg = nullptr;
+    SS_CUDA(cudaStreamGetCaptureInfo(bs, &cst, nullptr, &bg, &deps, nullptr, &nd));
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.conditional.handle = h_check;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    SS_CUDA(cudaGraphAddNode(&inode, bg, deps, nullptr, nd, &ip));
+    cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+    SS_CUDA(cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t is = s->cap_stream[2];
+    SS_CUDA(cudaStreamBeginCaptureToGraph(is, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_cg_true_residual(P, B, mx, true, launch_of(s, is));
+    SS_CUDA(cudaStreamEndCapture(is, &ifbody));
+    launch_cg_iteration_tail(P, B, mx, C, launch_of(s, bs));
+    SS_CUDA(cudaStreamEndCapture(bs, &body));
+    return SP_OK;
+}
+
+// CG driven from the host: iterations in chunks, the device state polled
+// between chunks (kernels after convergence return at once).
+int host_cg_loop(sp_sim* s, long long* launches)
+{
+    KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    const bool mx = mixed(s);
+    CgLaunch C{0, 0, 0};
+    Launch L = launch_of(s, s->stream);
+    const int chunk = 8;
+    for (int it = 0; it < P.max_iter + kMaxCgRestarts + chunk; it += chunk) {
+        for (int k = 0; k < chunk; ++k) {
+            launch_cg_iteration_head(P, B, mx, C, L);
+            launch_cg_true_residual(P, B, mx, false, L);
+            launch_cg_iteration_tail(P, B, mx, C, L);
+            *launches += cg_kernels_per_iteration(mx) + 1;
+        }
+        SS_CUDA(cudaMemcpyAsync(s->st_host, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+        SS_CUDA(cudaStreamSynchronize(s->stream));
+        const DevState& h = *s->st_host;
+        if (h.done || h.error || h.overflow) break;
+    }
+    return SP_OK;
+}
+
+// Everything of a solve after assembly: init, loop, finish, stress.
+int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches)
+{
+    KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    Launch L = launch_of(s, cs);
+    launch_cg_init(P, B, from_x, mixed(s), L);
+    *launches += 1;
+    if (in_graph) {
+        SS_TRY(capture_cg_loop(s, cs));
+    } else {
+        SS_TRY(host_cg_loop(s, launches));
+    }
+    launch_cg_finish(P, B, L);
+    launch_stress(P, B, L);
+    *launches += 2;
+    return SP_OK;
+}
+
+int capture_step_graph(sp_sim* s)
+{
+    free_graphs(s);
+    cudaStream_t cs = s->cap_stream[0];
+    SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    long long launches = enqueue_build(s, cs);
+    launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
+    launches += 1;
+    const bool warm = s->p.warm_start == SP_WARM_PREV;
+    int rc = enqueue_solve(s, cs, warm, true, &launches);
+    launch_integrate(s->kp, s->B, launch_of(s, cs));
+    launches += 1;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc != SP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        s->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        return SP_ERR_CUDA;
+    }
+    s->step_graph = g;
+    SS_CUDA(cudaGraphInstantiate(&s->step_exec, g, 0));
+    s->fixed_launches_step = launches;
+    return SP_OK;
+}
+
+int capture_solve_graph(sp_sim* s, int from_x)
+{
+    cudaStream_t cs = s->cap_stream[0];
+    SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    long long launches = 0;
+    int rc = enqueue_solve(s, cs, from_x != 0, true, &launches);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc != SP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        s->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        return SP_ERR_CUDA;
+    }
+    s->solve_graph[from_x] = g;
+    SS_CUDA(cudaGraphInstantiate(&s->solve_exec[from_x], g, 0));
+    s->fixed_launches_solve = launches;
+    return SP_OK;
+}
+
+// The capture streams must wait for the simulation stream and vice versa:
+// graphs are launched on the simulation stream, so no extra ordering is needed.
+
+int read_state(sp_sim* s)
+{
+    SS_CUDA(cudaMemcpyAsync(s->st_host, s->B.st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+template <class T>
+int write_field(sp_sim* s, T* dev_field, T value)
+{
+    SS_CUDA(cudaMemcpyAsync(dev_field, &value, sizeof(T), cudaMemcpyHostToDevice, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int set_device(sp_sim* s)
+{
+    SS_CUDA(cudaSetDevice(s->p.device));
+    return SP_OK;
+}
+
+// After a failed step or solve, clear the sticky flags so the simulation stays usable.
+int clear_flags(sp_sim* s)
+{
+    DevState* d = s->B.st;
+    SS_TRY(write_field(s, &d->error, 0));
+    SS_TRY(write_field(s, &d->overflow, 0));
+    return SP_OK;
+}
+
+int grow_pairs(sp_sim* s)
+{
+    long long need = s->st_host->nnz;
+    long long cap = std::max<long long>((long long)(need * 1.25) + 1024, s->nnz_cap * 3 / 2);
+    if (cap > 0x7fffffffll) {
+        s->err = "pair count exceeds 2^31";
+        return SP_ERR_OOM;
+    }
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    free_graphs(s);
+    SS_TRY(alloc_pairs(s, cap));
+    SS_TRY(write_field(s, &s->B.st->overflow, 0));
+    return SP_OK;
+}
+
+int ensure_step_graph(sp_sim* s)
+{
+    if (s->host_loop || s->step_exec) return SP_OK;
+    int rc = capture_step_graph(s);
+    if (rc != SP_OK) {
+        // conditional graph nodes unavailable: fall back to the host-driven loop
+        cudaGetLastError();
+        free_graphs(s);
+        s->host_loop = true;
+        std::fprintf(stderr, "shearsim: CUDA graph capture failed (%s); using host-driven CG loop\n",
+                     s->err.c_str());
+    }
+    return SP_OK;
+}
+
+int do_build(sp_sim* s)
+{
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        long long launches = enqueue_build(s, s->stream);
+        (void)launches;
+        launch_nbr_fill(s->kp, s->B, false, s->use_inj, mixed(s), launch_of(s, s->stream));
+        SS_TRY(read_state(s));
+        if (!s->st_host->overflow) break;
+        SS_TRY(grow_pairs(s));
+    }
+    if (s->st_host->overflow) {
+        s->err = "pair capacity could not be grown";
+        return SP_ERR_OOM;
+    }
+    // the new cell order becomes the state order
+    const size_t np = (size_t)s->kp.npad;
+    SS_CUDA(cudaMemcpyAsync(s->B.pos_s, s->B.pos_w, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
+    SS_CUDA(cudaMemcpyAsync(s->B.id_s, s->B.id_w, sizeof(int) * s->kp.n, cudaMemcpyDeviceToDevice, s->stream));
+    SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    s->built = true;
+    s->assembled = false;
+    return SP_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" {
+
+double sp_kappa_from_kappa_tau(double kappa_tau, double rc, double zeta, double kT)
+{
+    if (!(kT > 0)) return NAN;
+    const double tau = lambda2_of(rc) * zeta / kT;   // Rouse time, §Method
+    return kappa_tau / tau;
+}
+
+const char* sp_last_error(const sp_sim* s)
+{
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int sp_sim_destroy(sp_sim* s)
+{
+    if (!s) return SP_OK;
+    cudaSetDevice(s->p.device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_graphs(s);
+    DevBuffers& B = s->B;
+    void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.id_w, B.cell_of, B.slot, B.perm, B.cell_count,
+                    B.cell_start, B.row_cnt, B.row_ptr, B.col, B.val, B.val32, B.diag, B.dinv, B.dinv32,
+                    B.b, B.x, B.r, B.p, B.q, B.r32, B.p32, B.q32, B.xi_inj, B.partials, B.scan_tmp,
+                    B.stage, B.st};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (s->st_host) cudaFreeHost(s->st_host);
+    for (auto& c : s->cap_stream)
+        if (c) cudaStreamDestroy(c);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return SP_OK;
+}
+
+int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return SP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::string why;
+    int rc = check_params(p, why);
+    if (rc != SP_OK) {
+        g_create_error = why;
+        return rc;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device with the requested ordinal";
+        return SP_ERR_NO_DEVICE;
+    }
+    sp_sim* s = new sp_sim();
+    s->p = *p;
+    auto fail = [&](int code) {
+        g_create_error = s->err;
+        sp_sim_destroy(s);
+        return code;
+    };
+    if (cudaSetDevice(p->device) != cudaSuccess) {
+        s->err = "cudaSetDevice failed";
+        return fail(SP_ERR_CUDA);
+    }
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (s->num_sms < 1) s->num_sms = 1;
+    const char* hl = std::getenv("SHEARSIM_HOST_LOOP");
+    s->host_loop = hl && hl[0] == '1';
+    if (p->stream) {
+        s->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            s->err = "cudaStreamCreate failed";
+            return fail(SP_ERR_CUDA);
+        }
+        s->own_stream = true;
+    }
+    for (auto& c : s->cap_stream) {
+        if (cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) {
+            s->err = "cudaStreamCreate failed";
+            return fail(SP_ERR_CUDA);
+        }
+    }
+    const int n = (int)p->n;
+    const int npad = (n + 63) / 64 * 64;
+    derive(*p, s->kp, npad);
+    DevBuffers& B = s->B;
+    const size_t v3 = 3 * (size_t)npad;
+    int a = SP_OK;
+    auto A = [&](int r) { if (a == SP_OK) a = r; };
+    A(dev_alloc(s, &B.pos_s, v3));
+    A(dev_alloc(s, &B.pos_w, v3));
+    A(dev_alloc(s, &B.v_s, v3));
+    A(dev_alloc(s, &B.id_s, n));
+    A(dev_alloc(s, &B.id_w, n));
+    A(dev_alloc(s, &B.cell_of, n));
+    A(dev_alloc(s, &B.slot, n));
+    A(dev_alloc(s, &B.perm, n));
+    A(dev_alloc(s, &B.cell_count, s->kp.ncell));
+    A(dev_alloc(s, &B.cell_start, (size_t)s->kp.ncell + 1));
+    A(dev_alloc(s, &B.row_cnt, n));
+    A(dev_alloc(s, &B.row_ptr, (size_t)n + 1));
+    A(dev_alloc(s, &B.diag, n));
+    A(dev_alloc(s, &B.dinv, n));
+    A(dev_alloc(s, &B.dinv32, n));
+    A(dev_alloc(s, &B.b, v3));
+    A(dev_alloc(s, &B.x, v3));
+    A(dev_alloc(s, &B.r, v3));
+    A(dev_alloc(s, &B.p, v3));
+    A(dev_alloc(s, &B.q, v3));
+    A(dev_alloc(s, &B.r32, 4 * (size_t)npad));
+    A(dev_alloc(s, &B.p32, 4 * (size_t)npad));
+    A(dev_alloc(s, &B.q32, 4 * (size_t)npad));
+    A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
+    A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(n, s->kp.ncell) / 4096 + 2)));
+    A(dev_alloc(s, &B.stage, 3 * (size_t)n));
+    A(dev_alloc(s, &B.st, 1));
+    if (a != SP_OK) return fail(a);
+    if (cudaMallocHost(&s->st_host, sizeof(DevState)) != cudaSuccess) {
+        s->err = "cudaMallocHost failed";
+        return fail(SP_ERR_OOM);
+    }
+    std::memset(s->st_host, 0, sizeof(DevState));
+    if (cudaMemcpyAsync(B.st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(B.v_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(B.pos_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(B.pos_w, 0, sizeof(double) * v3, s->stream) != cudaSuccess) {
+        s->err = "initialising device state failed";
+        return fail(SP_ERR_CUDA);
+    }
+    rc = alloc_pairs(s, std::max<long long>(1024, 20ll * n));
+    if (rc != SP_OK) return fail(rc);
+    if (pos_host) {
+        // identity order: row k holds particle k
+        std::vector<int> ids(n);
+        for (int i = 0; i < n; ++i) ids[i] = i;
+        for (int i = 0; i < 3 * n; ++i) {
+            const double v = pos_host[i];
+            const double L = p->L[i % 3];
+            if (!(v >= 0.0) || !(v < L)) {
+                s->err = "initial positions must lie in [0, L)";
+                return fail(SP_ERR_INVALID_ARG);
+            }
+        }
+        if (cudaMemcpy(B.id_s, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(B.stage, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            s->err = "copying initial positions failed";
+            return fail(SP_ERR_CUDA);
+        }
+        launch_gather_by_id(B.stage, B.id_s, n, npad, B.pos_s, s->stream);
+    } else {
+        launch_uniform_positions(s->kp, B, launch_of(s, s->stream));
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        s->err = std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError());
+        return fail(SP_ERR_CUDA);
+    }
+    *out = s;
+    return SP_OK;
+}
+
+int sp_build_neighbors(sp_sim* s)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    return do_build(s);
+}
+
+int sp_assemble(sp_sim* s)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    if (!s->built) {
+        s->err = "sp_assemble needs sp_build_neighbors after the last position change";
+        return SP_ERR_INVALID_ARG;
+    }
+    launch_assemble_only(s->kp, s->B, s->use_inj, mixed(s), launch_of(s, s->stream));
+    SS_CUDA(cudaGetLastError());
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    s->assembled = true;
+    return SP_OK;
+}
+
+int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    if (!s->assembled) {
+        s->err = "sp_solve_velocities needs sp_assemble first";
+        return SP_ERR_INVALID_ARG;
+    }
+    const int n = s->kp.n;
+    const size_t np = (size_t)s->kp.npad;
+    int from_x = 0;
+    if (v0_dev) {
+        for (int a = 0; a < 3; ++a)
+            SS_CUDA(cudaMemcpyAsync(s->B.x + a * np, v0_dev + (size_t)a * n, sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, s->stream));
+        from_x = 1;
+    } else if (s->p.warm_start == SP_WARM_PREV) {
+        from_x = 1;   // x holds the previous velocities, gathered by the build
+    }
+    long long launches = 0;
+    if (!s->host_loop && !s->solve_exec[from_x]) {
+        if (capture_solve_graph(s, from_x) != SP_OK) {
+            cudaGetLastError();
+            std::fprintf(stderr, "shearsim: solve graph capture failed (%s); using host-driven CG loop\n",
+                         s->err.c_str());
+            free_graphs(s);
+            s->host_loop = true;
+        }
+    }
+    if (s->host_loop) {
+        SS_TRY(enqueue_solve(s, s->stream, from_x != 0, false, &launches));
+    } else {
+        SS_CUDA(cudaGraphLaunch(s->solve_exec[from_x], s->stream));
+    }
+    SS_TRY(read_state(s));
+    const DevState& h = *s->st_host;
+    int status = h.error ? h.error : (h.overflow ? SP_ERR_OOM : h.status);
+    if (info) {
+        info->status = status;
+        info->iterations = h.iter;
+        info->residual = h.last_res;
+        info->bnorm = std::sqrt(h.bnorm2);
+    }
+    SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
+    if (h.error) {
+        SS_TRY(clear_flags(s));
+        s->err = status == SP_ERR_NOT_CONVERGED ? "CG did not converge" : "non-finite value in CG";
+    }
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return status;
+}
+
+int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
+{
+    if (!s || nsteps < 0) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_TRY(ensure_step_graph(s));
+    launch_reset_step_stats(s->B.st, s->stream);
+    long long launches = 1;
+    long long done = 0;
+    int status = SP_OK;
+    for (int guard = 0; done < nsteps && guard < 8; ++guard) {
+        const long long todo = nsteps - done;
+        if (s->host_loop) {
+            for (long long k = 0; k < todo; ++k) {
+                launches += enqueue_build(s, s->stream);
+                launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, s->stream));
+                launches += 1;
+                SS_TRY(enqueue_solve(s, s->stream, s->p.warm_start == SP_WARM_PREV, false, &launches));
+                launch_integrate(s->kp, s->B, launch_of(s, s->stream));
+                launches += 1;
+                SS_TRY(read_state(s));
+                if (s->st_host->error || s->st_host->overflow) break;
+            }
+        } else {
+            for (long long k = 0; k < todo; ++k) SS_CUDA(cudaGraphLaunch(s->step_exec, s->stream));
+        }
+        SS_TRY(read_state(s));
+        done = s->st_host->steps_in_call;
+        if (s->st_host->overflow) {
+            SS_TRY(grow_pairs(s));
+            SS_TRY(ensure_step_graph(s));
+            continue;
+        }
+        if (s->st_host->error) {
+            status = s->st_host->error;
+            s->err = status == SP_ERR_NOT_CONVERGED ? "CG did not converge" : "non-finite value in CG";
+            SS_TRY(clear_flags(s));
+            break;
+        }
+    }
+    const DevState& h = *s->st_host;
+    if (!s->host_loop) {
+        launches += h.steps_in_call * s->fixed_launches_step + h.iter_sum * cg_kernels_per_iteration(mixed(s)) +
+                    h.true_checks;
+    }
+    if (info) {
+        info->status = status;
+        info->max_iterations = h.iter_max;
+        info->steps_done = h.steps_in_call;
+        info->cg_iterations = h.iter_sum;
+        info->last_residual = h.last_res;
+        info->stress_xy = h.stress_xy;
+        info->kernel_launches = launches;
+    }
+    s->built = false;
+    s->assembled = false;
+    if (status == SP_OK && h.steps_in_call < nsteps) {
+        s->err = "steps stopped early";
+        return SP_ERR_CUDA;
+    }
+    return status;
+}
+
+int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
+{
+    if (!s || !out) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    std::memset(out, 0, sizeof(*out));
+    KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    const bool mx = mixed(s);
+    Launch L = launch_of(s, s->stream);
+    CgLaunch C{0, 0, 0};
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> cls;   // class of the interval ending at each event
+    auto mark = [&](int c) -> int {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return SP_ERR_CUDA;
+        cudaEventRecord(e, s->stream);
+        ev.push_back(e);
+        cls.push_back(c);
+        return SP_OK;
+    };
+    enum { START = -1, BUILD = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER };
+    launch_reset_step_stats(B.st, s->stream);
+    int rc = mark(START);
+    if (rc == SP_OK) {
+        enqueue_build(s, s->stream);
+        launch_nbr_fill(P, B, true, s->use_inj, mx, L);
+        rc = mark(BUILD);
+    }
+    if (rc == SP_OK) {
+        launch_cg_init(P, B, s->p.warm_start == SP_WARM_PREV, mx, L);
+        rc = mark(OTHER);
+    }
+    for (int it = 0; rc == SP_OK && it < P.max_iter + kMaxCgRestarts + 1; ++it) {
+        launch_cg_spmv(P, B, mx, L);
+        mark(SPMV);
+        launch_cg_update(P, B, mx, C, L);
+        mark(UPDATE);
+        launch_cg_true_residual(P, B, mx, false, L);
+        mark(TRUE_RES);
+        launch_cg_iteration_tail(P, B, mx, C, L);
+        rc = mark(DIRECTION);
+        if (rc != SP_OK) break;
+        rc = read_state(s);
+        if (rc != SP_OK) break;
+        const DevState& h = *s->st_host;
+        if (h.check_true == 0 && h.true_checks > out->true_residual_launches) out->true_residual_launches = (int)h.true_checks;
+        if (h.done || h.error || h.overflow) break;
+    }
+    if (rc == SP_OK) {
+        launch_cg_finish(P, B, L);
+        launch_stress(P, B, L);
+        launch_integrate(P, B, L);
+        rc = mark(OTHER);
+    }
+    if (rc == SP_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+    if (rc == SP_OK) rc = read_state(s);
+    double* acc[] = {&out->build_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
+                     &out->direction_ms, &out->other_ms};
+    for (size_t k = 1; rc == SP_OK && k < ev.size(); ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
+        *acc[cls[k]] += ms;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    if (rc != SP_OK) {
+        if (s->err.empty()) s->err = "profiling step failed";
+        return rc;
+    }
+    const DevState& h = *s->st_host;
+    out->cg_iterations = h.iter;
+    out->spmv_launches = h.iter;
+    out->update_launches = h.iter;
+    out->direction_launches = h.iter;
+    out->true_residual_launches = (int)h.true_checks;
+    out->n = P.n;
+    out->nnz = h.nnz;
+    out->precision = s->p.precision;
+    s->built = false;
+    s->assembled = false;
+    if (h.error) {
+        int status = h.error;
+        SS_TRY(clear_flags(s));
+        return status;
+    }
+    return SP_OK;
+}
+
+int sp_stress_xy(sp_sim* s, double* sigma)
+{
+    if (!s || !sigma) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_TRY(read_state(s));
+    *sigma = s->st_host->stress_xy;
+    return SP_OK;
+}
+
+int sp_get_positions(sp_sim* s, double* pos_host)
+{
+    if (!s || !pos_host) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    launch_scatter_by_id(s->B.pos_s, s->kp.npad, s->B.id_s, s->kp.n, s->B.stage, s->stream);
+    SS_CUDA(cudaMemcpyAsync(pos_host, s->B.stage, sizeof(double) * 3 * s->kp.n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int sp_set_positions(sp_sim* s, const double* pos_host, double delta)
+{
+    if (!s || !pos_host) return SP_ERR_INVALID_ARG;
+    if (!(delta >= 0.0) || !(delta < s->p.L[0])) {
+        s->err = "delta must lie in [0, L_x)";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    SS_CUDA(cudaMemcpyAsync(s->B.stage, pos_host, sizeof(double) * 3 * s->kp.n, cudaMemcpyHostToDevice, s->stream));
+    launch_gather_by_id(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->stream);
+    SS_CUDA(cudaMemcpyAsync(&s->B.st->delta, &delta, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    s->built = false;
+    s->assembled = false;
+    return SP_OK;
+}
+
+int sp_get_velocities(sp_sim* s, double* v_host)
+{
+    if (!s || !v_host) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    launch_scatter_by_id(s->B.x, s->kp.npad, s->B.id_w, s->kp.n, s->B.stage, s->stream);
+    SS_CUDA(cudaMemcpyAsync(v_host, s->B.stage, sizeof(double) * 3 * s->kp.n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int sp_get_state(sp_sim* s, double* delta, int64_t* step)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_TRY(read_state(s));
+    if (delta) *delta = s->st_host->delta;
+    if (step) *step = s->st_host->step;
+    return SP_OK;
+}
+
+int sp_set_step(sp_sim* s, int64_t step)
+{
+    if (!s || step < 0) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    long long v = step;
+    SS_TRY(write_field(s, &s->B.st->step, v));
+    return SP_OK;
+}
+
+int sp_get_order(sp_sim* s, int64_t* ids_host)
+{
+    if (!s || !ids_host) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    std::vector<int> ids(s->kp.n);
+    SS_CUDA(cudaMemcpyAsync(ids.data(), s->B.id_w, sizeof(int) * s->kp.n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < s->kp.n; ++i) ids_host[i] = ids[i];
+    return SP_OK;
+}
+
+int sp_get_num_pairs(sp_sim* s, int64_t* npairs)
+{
+    if (!s || !npairs) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_TRY(read_state(s));
+    *npairs = s->st_host->nnz / 2;
+    return SP_OK;
+}
+
+namespace {
+// The CSR of the current matrix on the host, rows in cell order.
+int fetch_csr(sp_sim* s, std::vector<int>& row_ptr, std::vector<int>& col, std::vector<double>& val,
+              std::vector<int>& ids)
+{
+    const int n = s->kp.n;
+    SS_TRY(read_state(s));
+    const long long nnz = s->st_host->nnz;
+    row_ptr.resize(n + 1);
+    col.resize(nnz);
+    val.resize(nnz);
+    ids.resize(n);
+    SS_CUDA(cudaMemcpyAsync(row_ptr.data(), s->B.row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(col.data(), s->B.col, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(val.data(), s->B.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(ids.data(), s->B.id_w, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+}  // namespace
+
+int sp_get_neighbors(sp_sim* s, int64_t cap, int64_t* pairs_host, int64_t* npairs)
+{
+    if (!s || !npairs) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    std::vector<int> rp, col, ids;
+    std::vector<double> val;
+    SS_TRY(fetch_csr(s, rp, col, val, ids));
+    long long m = 0;
+    for (int r = 0; r < s->kp.n; ++r) {
+        for (int k = rp[r]; k < rp[r + 1]; ++k) {
+            const int a = ids[r], b = ids[col[k]];
+            if (a < b) {
+                if (pairs_host && m < cap) {
+                    pairs_host[2 * m] = a;
+                    pairs_host[2 * m + 1] = b;
+                }
+                ++m;
+            }
+        }
+    }
+    *npairs = m;
+    if (pairs_host && m > cap) {
+        s->err = "pair capacity too small";
+        return SP_ERR_INVALID_ARG;
+    }
+    return SP_OK;
+}
+
+int sp_get_system(sp_sim* s, double* diag_host, double* b_host, double* w_host)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    const int n = s->kp.n;
+    const size_t np = (size_t)s->kp.npad;
+    std::vector<int> rp, col, ids;
+    std::vector<double> val;
+    SS_TRY(fetch_csr(s, rp, col, val, ids));
+    if (diag_host) {
+        std::vector<double> d(n);
+        SS_CUDA(cudaMemcpy(d.data(), s->B.diag, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < n; ++r) diag_host[ids[r]] = d[r];
+    }
+    if (b_host) {
+        std::vector<double> b(3 * np);
+        SS_CUDA(cudaMemcpy(b.data(), s->B.b, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < n; ++r)
+            for (int a = 0; a < 3; ++a) b_host[3 * (size_t)ids[r] + a] = b[a * np + r];
+    }
+    if (w_host) {
+        long long m = 0;
+        for (int r = 0; r < n; ++r)
+            for (int k = rp[r]; k < rp[r + 1]; ++k)
+                if (ids[r] < ids[col[k]]) w_host[m++] = val[k];
+    }
+    return SP_OK;
+}
+
+int sp_set_noise(sp_sim* s, const double* xi_host)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    if (xi_host) {
+        if (!s->B.xi_inj) SS_TRY(dev_alloc(s, &s->B.xi_inj, 3 * (size_t)s->kp.n));
+        SS_CUDA(cudaMemcpy(s->B.xi_inj, xi_host, sizeof(double) * 3 * s->kp.n, cudaMemcpyHostToDevice));
+        s->use_inj = true;
+    } else {
+        s->use_inj = false;
+    }
+    free_graphs(s);   // the kernels' arguments changed
+    return SP_OK;
+}
+
+int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count, const int64_t* ids_host,
+                     uint64_t* out_host)
+{
+    if (count < 0 || (count > 0 && (!ids_host || !out_host))) return SP_ERR_INVALID_ARG;
+    if (count == 0) return SP_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return SP_ERR_NO_DEVICE;
+    long long* ids = nullptr;
+    unsigned long long* out = nullptr;
+    if (cudaMalloc(&ids, sizeof(long long) * count) != cudaSuccess) return SP_ERR_OOM;
+    if (cudaMalloc(&out, sizeof(unsigned long long) * 4 * count) != cudaSuccess) {
+        cudaFree(ids);
+        return SP_ERR_OOM;
+    }
+    int rc = SP_OK;
+    if (cudaMemcpy(ids, ids_host, sizeof(long long) * count, cudaMemcpyHostToDevice) != cudaSuccess) rc = SP_ERR_CUDA;
+    if (rc == SP_OK) {
+        launch_philox_blocks(seed, step, count, ids, out, 0);
+        if (cudaMemcpy(out_host, out, sizeof(unsigned long long) * 4 * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = SP_ERR_CUDA;
+    }
+    cudaFree(ids);
+    cudaFree(out);
+    return rc;
+}
+
+int sp_structure_factor(sp_sim* s, int32_t nkx, int32_t nky, int32_t grid, double* S_host,
+                        double* qx_host, double* qy_host)
+{
+    (void)nkx; (void)nky; (void)grid; (void)S_host; (void)qx_host; (void)qy_host;
+    if (!s) return SP_ERR_INVALID_ARG;
+    s->err = "structure factor not available in this build";
+    return SP_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+"""CUDA path versus the CPU oracle, through the C ABI.
+
+Tolerances (FP64 path):
+  - pair lists: bit-exact (same predicate, same rounding: no contraction on either side);
+  - Philox blocks: bit-exact;
+  - weights, diagonal, right-hand side: 1e-14 relative (exp and the order of the
+    pair sums differ by a few ulps);
+  - velocities of one solve: 1e-11 relative to max |v| with both sides solved to
+    1e-13 (condition number of the Jacobi-scaled matrix ~22, so the solution error
+    of each side is below ~1e-12);
+  - positions after k steps: 1e-10 absolute per step (v dt with v from above).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ss = pytest.importorskip("paper_1808_06381_gb300")
+
+pytestmark = pytest.mark.gpu
+
+KT = 0.5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ss.load()
+
+
+def make(n, L, seed=1, kappa_tau=KT, delta=0.0, tol=1e-13, pos=None, **kw):
+    L = tuple(L) if np.ndim(L) else (L, L, L)
+    pos = synth.uniform_positions(n, L, seed) if pos is None else pos
+    kw.setdefault("warm_start", "none")
+    kappa = kw.pop("kappa", None)
+    if kappa is None:
+        kappa = ss.kappa_from_kappa_tau(kappa_tau)
+    sim = ss.Simulation(n, L, kappa, seed=seed, cg_tol=tol, positions=pos, cg_max_iter=5000, **kw)
+    if delta:
+        sim.set_positions(pos, delta)
+    okw = {k: kw[k] for k in ("alpha", "eps", "zeta", "kT", "dt") if k in kw}
+    p = oracle.Params(n=n, L=L, kappa=kappa, seed=seed, **okw)
+    return sim, p, pos
+
+
+def pairs_equal(sim, p, pos, delta):
+    got = sim.neighbors()
+    ref = oracle.neighbors(p, pos, delta)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    assert np.array_equal(got, ref)
+    return ref
+
+
+def test_philox_bits_match_oracle():
+    ids = np.arange(0, 5000, 7, dtype=np.int64)
+    got = ss.philox_blocks(123456789, 42, ids)
+    for k in range(0, len(ids), 37):
+        ref = oracle.philox4x64_10(np.array([ids[k], 42, 0, 0], dtype=np.uint64),
+                                   np.array([123456789, 0], dtype=np.uint64))
+        assert np.array_equal(got[k], ref)
+
+
+@pytest.mark.parametrize("n,L,delta", [
+    (24, 2.0, 0.0),                     # smallest box: one cell, all pairs
+    (64, 2.77, 1.3),
+    (300, (7.0, 4.5, 2.6), 3.1),        # fewer than 3 cells along z only
+    (500, (2.5, 9.0, 9.0), 0.7),        # fewer than 3 cells along x only
+    (500, (9.0, 2.5, 9.0), 4.4),        # fewer than 3 cells along y (x scanned whole)
+    (4096, synth.box_length(4096), 5.123),
+    (4100, synth.box_length(4100), 11.0),   # ragged: not a multiple of any tile
+])
+def test_neighbor_lists_bit_exact(n, L, delta):
+    sim, p, pos = make(n, L, seed=n, delta=delta)
+    delta = delta % p.L[0]
+    sim.build_neighbors()
+    pairs_equal(sim, p, pos, delta)
+    # the reported order is a permutation of the ids
+    assert np.array_equal(np.sort(sim.order()), np.arange(n))
+    sim.close()
+
+
+def test_neighbor_lists_with_particles_on_cell_and_box_faces():
+    n = 3000
+    L = synth.box_length(n)
+    pos = synth.uniform_positions(n, (L, L, L), 5)
+    cw = L / math.floor(L)
+    pos[:100, 0] = cw * np.floor(pos[:100, 0] / cw)        # on cell faces
+    pos[100:200, 1] = 0.0                                    # on the sheared face
+    pos[200:300, 1] = np.nextafter(L, 0)
+    pos[300:400, 2] = 0.0
+    pos[400:420] = pos[420:440] + np.array([0.999999, 0, 0])  # pairs right at the cut
+    pos[400:420, 0] %= L
+    for delta in (0.0, 0.25 * L, L - 1e-12):
+        sim, p, _ = make(n, L, pos=pos, delta=delta)
+        sim.build_neighbors()
+        pairs_equal(sim, p, pos, delta)
+        sim.close()
+
+
+@pytest.mark.parametrize("n,delta,kappa_tau", [(64, 0.4, 0.5), (2000, 3.3, 0.05), (4096, 7.7, 0.5)])
+def test_assembly_matches_oracle(n, delta, kappa_tau):
+    L = synth.box_length(n)
+    sim, p, pos = make(n, L, seed=3 + n, kappa_tau=kappa_tau, delta=delta)
+    sim.set_step(17)
+    sim.build_neighbors()
+    sim.assemble()
+    diag, b, pairs, w = sim.system()
+    ref_pairs = oracle.neighbors(p, pos, delta)
+    assert np.array_equal(pairs, ref_pairs)
+    xi = oracle.noise(p.seed, 17, np.arange(n))
+    ref = oracle.assemble(p, pos, ref_pairs, xi, delta)
+    assert np.abs(w - ref.w).max() <= 1e-14
+    assert np.abs(diag - ref.diag).max() <= 1e-14 * np.abs(ref.diag).max()
+    assert np.abs(b - ref.b).max() <= 1e-13 * np.abs(ref.b).max()
+    sim.close()
+
+
+@pytest.mark.parametrize("n,seed", [(24, 1), (64, 2), (777, 3), (4096, 4)])
+def test_single_solve_velocities(n, seed):
+    L = synth.box_length(n)
+    delta = 0.37 * L
+    sim, p, pos = make(n, L, seed=seed, delta=delta)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    assert info["status"] == 0 and info["residual"] <= 1e-13
+    v = sim.get_velocities()
+    sysr = oracle.assemble(p, pos, oracle.neighbors(p, pos, delta), oracle.noise(p.seed, 0, np.arange(n)), delta)
+    if n <= 64:
+        ref = oracle.dense_solve(sysr)
+    else:
+        ref, _, _ = oracle.pcg(sysr, 1e-13)
+    assert np.abs(v - ref).max() <= 1e-11 * np.abs(ref).max()
+    # the GPU solution satisfies the oracle's own system
+    res = np.linalg.norm(sysr.b - sysr.matvec(v)) / np.linalg.norm(sysr.b)
+    assert res <= 1e-12
+    sim.close()
+
+
+def test_steps_follow_the_oracle():
+    n, steps = 1000, 5
+    L = synth.box_length(n)
+    sim, p, pos = make(n, L, seed=9, warm_start="prev")
+    info = sim.step(steps)
+    assert info["steps_done"] == steps and info["status"] == 0
+    gpos = sim.get_positions()
+    gv = sim.get_velocities()
+    delta, step = sim.state()
+    opos, od = pos, 0.0
+    for s in range(steps):
+        r = oracle.step(p, opos, od, s, tol=1e-13)
+        opos, od, ov = r.pos, r.delta, r.v
+    assert step == steps
+    assert abs(delta - od) < 1e-12
+    d = gpos - opos
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < 1e-10 * steps
+    assert np.abs(gv - ov).max() <= 1e-9 * np.abs(ov).max()
+    sim.close()
+
+
+def test_graph_and_host_loop_modes_agree(monkeypatch):
+    n = 2000
+    L = synth.box_length(n)
+    outs = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("SHEARSIM_HOST_LOOP", mode)
+        sim, p, pos = make(n, L, seed=4, tol=1e-10, warm_start="prev")
+        info = sim.step(3)
+        outs.append((sim.get_positions(), sim.get_velocities(), info["cg_iterations"]))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
+def test_runs_are_deterministic():
+    n = 3000
+    L = synth.box_length(n)
+    res = []
+    for _ in range(2):
+        sim, p, pos = make(n, L, seed=6, tol=1e-8, warm_start="prev")
+        sim.step(4)
+        res.append(sim.get_positions())
+        sim.close()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_momentum_bookkeeping_on_gpu():
+    """Pair terms cancel: sum_i v_i = sum_i (noise_i + shear_i) / zeta (no oracle involved)."""
+    n = 4096
+    L = synth.box_length(n)
+    sim, p, pos = make(n, L, seed=12, delta=2.0, zeta=1.7, kT=0.8)
+    sim.build_neighbors()
+    sim.assemble()
+    sim.solve_velocities()
+    v = sim.get_velocities()
+    amp = math.sqrt(2 * p.zeta * p.kT / p.dt)
+    expect = amp * oracle.noise(p.seed, 0, np.arange(n)).sum(0) / p.zeta
+    expect[0] += p.kappa * (pos[:, 1] - L / 2).sum()
+    assert np.allclose(v.sum(0), expect, atol=1e-10 * np.abs(v).sum())
+    sim.close()
+
+
+# ------------------------------------------------------------- edge cases
+
+
+def test_two_particles_minimum_box():
+    pos = np.array([[0.2, 0.1, 0.3], [0.9, 1.95, 0.5]])
+    sim, p, _ = make(2, 2.0, pos=pos, delta=0.6)
+    sim.build_neighbors()
+    sim.assemble()
+    sim.solve_velocities()
+    r = oracle.step(p, pos, 0.6, 0, tol=1e-14, solver="dense")
+    assert np.array_equal(sim.neighbors(), r.system.pairs)
+    assert np.abs(sim.get_velocities() - r.v).max() <= 1e-12 * np.abs(r.v).max()
+    sim.close()
+
+
+def test_no_coupling_solves_in_one_iteration():
+    n = 500
+    sim, p, pos = make(n, synth.box_length(n), alpha=0.0)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    assert info["iterations"] <= 1
+    sim.close()
+
+
+def test_zero_right_hand_side_gives_zero_velocity():
+    n = 400
+    sim, p, pos = make(n, synth.box_length(n), kappa=0.0, kT=0.0, eps=0.0)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    assert info["status"] == 0 and info["bnorm"] == 0.0
+    assert np.all(sim.get_velocities() == 0.0)
+    sim.close()
+
+
+def test_iteration_cap_reports_not_converged_and_recovers():
+    n = 2000
+    L = synth.box_length(n)
+    pos = synth.uniform_positions(n, (L, L, L), 2)
+    sim = ss.Simulation(n, (L, L, L), 3.0, seed=2, cg_tol=1e-14, cg_max_iter=3, positions=pos)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities(raise_on_error=False)
+    assert info["status"] == ss.SP_ERR_NOT_CONVERGED and info["iterations"] == 3
+    st = sim.step(2, raise_on_error=False)
+    assert st["status"] == ss.SP_ERR_NOT_CONVERGED and st["steps_done"] == 0
+    sim.close()
+
+
+def test_dense_cluster_grows_pair_storage():
+    """Far more than 20 partners per particle: the pair arrays are regrown and the step retried."""
+    n = 1500
+    L = 10.0
+    rng = np.random.Generator(np.random.PCG64(3))
+    pos = rng.uniform(0.0, 2.5, (n, 3))
+    sim, p, _ = make(n, L, pos=pos, tol=1e-9)
+    info = sim.step(1)
+    assert info["status"] == 0 and info["steps_done"] == 1
+    r = oracle.step(p, pos, 0.0, 0, tol=1e-12)
+    assert sim.num_pairs() == r.system.pairs.shape[0]
+    assert np.abs(sim.get_velocities() - r.v).max() <= 1e-7 * np.abs(r.v).max()
+    sim.close()
+
+
+# ------------------------------------------------ full size (262,144 particles)
+
+
+@pytest.fixture(scope="module")
+def full():
+    w = synth.PRECISION
+    L = w.L
+    pos = synth.uniform_positions(w.n, L, w.seed)
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    sim = ss.Simulation(w.n, L, kappa, seed=w.seed, cg_tol=1e-12, positions=pos, warm_start="none",
+                        cg_max_iter=5000)
+    sim.set_positions(pos, 7.25)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    p = oracle.Params(n=w.n, L=L, kappa=kappa, seed=w.seed)
+    yield sim, p, pos, info
+    sim.close()
+
+
+def test_full_size_sampled_rows(full):
+    sim, p, pos, info = full
+    delta = 7.25
+    diag, b, pairs, w = sim.system()
+    rng = np.random.Generator(np.random.PCG64(0))
+    rows = rng.choice(p.n, 64, replace=False)
+    xi = oracle.noise(p.seed, 0, np.arange(p.n))
+    for i in rows:
+        nb = oracle.row_neighbors(p, pos, delta, i)
+        mine = np.sort(np.concatenate([pairs[pairs[:, 0] == i, 1], pairs[pairs[:, 1] == i, 0]]))
+        assert np.array_equal(nb, mine)
+        # the row of the system, from the oracle's assembly of exactly these pairs
+        rp = np.stack([np.full(len(nb), i), nb], 1)
+        rp = np.sort(rp, axis=1)
+        ref = oracle.assemble(p, pos, rp, xi, delta)
+        assert abs(diag[i] - ref.diag[i]) <= 1e-14 * ref.diag[i]
+        assert np.abs(b[i] - ref.b[i]).max() <= 1e-13 * np.abs(ref.b[i]).max()
+
+
+def test_full_size_velocities_against_oracle_solve(full):
+    sim, p, pos, info = full
+    delta = 7.25
+    assert info["status"] == 0 and info["residual"] <= 1e-12
+    v = sim.get_velocities()
+    pairs = oracle.neighbors(p, pos, delta, method="cells")
+    sysr = oracle.assemble(p, pos, pairs, oracle.noise(p.seed, 0, np.arange(p.n)), delta)
+    ref, it, res = oracle.pcg(sysr, 1e-12)
+    assert np.abs(v - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.linalg.norm(sysr.b - sysr.matvec(v)) <= 2e-12 * np.linalg.norm(sysr.b)

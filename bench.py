@@ -288,7 +288,8 @@ def main():
                          "avg_launch_ms": spmv_avg_ms, "launches_profiled": prof["spmv_launches"],
                          "note": "working set of one solve (~110 MB) fits in L2; per-step L2 flush only"},
             "kernel_ms_per_step": {k: prof[k] for k in ("spmv_ms", "update_ms", "direction_ms",
-                                                         "true_residual_ms", "build_ms", "other_ms")},
+                                                         "true_residual_ms", "build_ms", "sort_ms",
+                                                         "count_ms", "fill_ms", "other_ms")},
             "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": n * 24 + 8,
                     "d2h_bytes_per_step": n * 24 + 16, "steps": args.e2e_steps},
             "clocks": clk,

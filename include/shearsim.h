@@ -176,6 +176,9 @@ typedef struct sp_kernel_profile {
     int64_t nnz;                     /* off-diagonal entries (2 x pairs) */
     int32_t cg_iterations;
     int32_t precision;               /* enum sp_precision of the solver */
+    double sort_ms;                  /* part of build_ms: binning and the counting sort into cell order */
+    double count_ms;                 /* part of build_ms: pair counting and the row-pointer scan */
+    double fill_ms;                  /* part of build_ms: the fused pair/assembly pass */
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 

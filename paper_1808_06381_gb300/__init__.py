@@ -65,7 +65,8 @@ class sp_kernel_profile(ctypes.Structure):
                 ("spmv_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("direction_ms", ctypes.c_double),
                 ("true_residual_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("cg_iterations", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("sort_ms", ctypes.c_double), ("count_ms", ctypes.c_double),
+                ("fill_ms", ctypes.c_double)]
 
 
 def declared_symbols() -> list:

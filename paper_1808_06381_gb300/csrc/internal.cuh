@@ -27,7 +27,12 @@ struct KParams {
     int nc[3];          // cells per axis (cell edge >= r_c)
     double inv_cw[3];   // cells per unit length
     int ncell;
+    int fast_cells;     // every axis has >= 3 cells: FP32 pre-filter with exact fallback
+    float rc2_lo;       // FP32 distance^2 below this: certainly |R|^2 < r_c^2
+    float rc2_hi;       // FP32 distance^2 at or above this: certainly |R|^2 >= r_c^2
+    float Lf[3];        // box edges in FP32
     double tol2;        // cg_tol^2
+    double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
 };
 
@@ -40,7 +45,7 @@ struct DevState {
     int overflow;             // sticky: nnz exceeded nnz_cap
     int error;                // sticky: first failing sp_status of a step (0 = none)
     // conjugate gradients
-    double bnorm2, rho, alpha, beta, rr, pq, rr_true;
+    double bnorm2, rho, alpha, beta, rr, pq, rr_true, rr_restart;
     int iter, restarts, done, status, check_true, zero_b;
     // mixed precision bookkeeping
     int since_replace;
@@ -62,6 +67,7 @@ struct DevBuffers {
     double* v_s;     // [3][npad] velocities of the last solve
     // work arrays of the current step (cell order)
     double* pos_w;   // [3][npad]
+    float* pos32;    // [3][npad] FP32 copy of pos_w for the pair pre-filter
     int* id_w;       // [n]
     int* cell_of;    // [n]
     int* slot;       // [n]
@@ -75,15 +81,18 @@ struct DevBuffers {
     float* val32;    // [nnz_cap] FP32 copy for the mixed solver
     double* diag;    // [n] A_ii
     double* dinv;    // [n] 1 / A_ii
+    float* diag32;   // [n]
     float* dinv32;   // [n]
     double* b;       // [3][npad]
     double* x;       // [3][npad] solution (velocities)
     double* r;       // [3][npad]
     double* p;       // [3][npad]
     double* q;       // [3][npad]
-    float* r32;      // [4][n] mixed path: r as interleaved float4
-    float* p32;      // [4][n]
-    float* q32;      // [4][n]
+    double* z;       // [3][npad] D^-1 r (FP64 solver)
+    float4* r4;      // [npad] mixed solver vectors, (x, y, z, 0) per row
+    float4* p4;
+    float4* q4;
+    float4* d4;      // correction accumulated since the last fold into x
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* partials;// [kMaxPartials * 4]
     int* scan_tmp;   // block sums of the scans
@@ -273,17 +282,17 @@ struct CgLaunch {
     int use_cond;                       // call cudaGraphSetConditional (inside a graph)
     unsigned long long h_loop, h_check; // cudaGraphConditionalHandle values
 };
+// One CG iteration is two kernels: spmv (q = A z + beta q, p = z + beta p, p.q)
+// and update (x or d += alpha p, r -= alpha q, r.r, r.z).  The true-residual
+// check is one kernel (FP64) or two (mixed: fold d into x, then FP64 residual).
 void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L);
 void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L);
-void launch_cg_iteration_head(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C,
-                              Launch L);
 void launch_cg_true_residual(const KParams& P, DevBuffers& B, bool mixed, bool always_check,
-                             Launch L);
-void launch_cg_iteration_tail(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C,
-                              Launch L);
-void launch_cg_finish(const KParams& P, DevBuffers& B, Launch L);
+                             const CgLaunch& C, Launch L);
+void launch_cg_finish(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 int cg_kernels_per_iteration(bool mixed);
+int cg_kernels_per_check(bool mixed);
 
 // integrate.cu
 void launch_integrate(const KParams& P, DevBuffers& B, Launch L);

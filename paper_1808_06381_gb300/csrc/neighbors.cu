@@ -171,8 +171,8 @@ __global__ void k_scatter(int n, const int* __restrict__ cell_of, const int* __r
 __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int* __restrict__ perm,
                               const int* __restrict__ id_s, const double* __restrict__ pos_s,
                               const double* __restrict__ v_s, double* __restrict__ pos_w,
-                              int* __restrict__ id_w, double* __restrict__ x, int warm,
-                              const DevState* st)
+                              float* __restrict__ pos32, int* __restrict__ id_w,
+                              double* __restrict__ x, int warm, const DevState* st)
 {
     if (st->error | st->overflow) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,9 +191,12 @@ __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int
     const int np = P.npad;
     for (int k = beg; k < end; ++k) {
         const int s = perm[k];
-        pos_w[k] = pos_s[s];
-        pos_w[np + k] = pos_s[np + s];
-        pos_w[2 * np + k] = pos_s[2 * np + s];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = pos_s[a * np + s];
+            pos_w[a * np + k] = v;
+            pos32[a * np + k] = (float)v;
+        }
         id_w[k] = id_s[s];
         x[k] = warm ? v_s[s] : 0.0;
         x[np + k] = warm ? v_s[np + s] : 0.0;
@@ -206,15 +209,15 @@ void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Laun
     k_scatter<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P.n, B.cell_of, B.slot,
                                                                                 B.cell_start, B.perm, B.st);
     k_sort_gather<<<grid_for(P.ncell, 128, 1 << 30), 128, 0, L.stream>>>(
-        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.id_w, B.x, warm ? 1 : 0, B.st);
+        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.x, warm ? 1 : 0, B.st);
 }
 
 // Single-cell boxes (every edge below 3 r_c): keep the state order.
 __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
                                   const double* __restrict__ pos_s, const double* __restrict__ v_s,
-                                  double* __restrict__ pos_w, int* __restrict__ id_w,
-                                  double* __restrict__ x, int* __restrict__ perm, int warm,
-                                  const DevState* st)
+                                  double* __restrict__ pos_w, float* __restrict__ pos32,
+                                  int* __restrict__ id_w, double* __restrict__ x, int* __restrict__ perm,
+                                  int warm, const DevState* st)
 {
     if (st->error | st->overflow) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,6 +228,7 @@ __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         pos_w[a * np + k] = pos_s[a * np + k];
+        pos32[a * np + k] = (float)pos_s[a * np + k];
         x[a * np + k] = warm ? v_s[a * np + k] : 0.0;
     }
 }
@@ -232,7 +236,7 @@ __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L)
 {
     k_identity_gather<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(
-        P, B.id_s, B.pos_s, B.v_s, B.pos_w, B.id_w, B.x, B.perm, warm ? 1 : 0, B.st);
+        P, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.x, B.perm, warm ? 1 : 0, B.st);
 }
 
 // ------------------------------------------------------------- pair search
@@ -245,10 +249,10 @@ void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L
 // candidate goes through the exact predicate, so the pair set does not depend
 // on the cell geometry.
 template <class F>
-__device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta,
-                                                  const double* __restrict__ pos,
-                                                  const int* __restrict__ cell_start, int i,
-                                                  double xi, double yi, double zi, F&& visit)
+__device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, double delta,
+                                                          const double* __restrict__ pos,
+                                                          const int* __restrict__ cell_start, int i,
+                                                          double xi, double yi, double zi, F&& visit)
 {
     const int np = P.npad;
     auto scan = [&](int s0, int s1) {
@@ -311,7 +315,115 @@ __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta
     }
 }
 
-__global__ void k_nbr_count(KParams P, const double* __restrict__ pos,
+__device__ __forceinline__ int floor_div(int a, int b)
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// The same pair set as for_each_neighbor_generic for boxes with >= 3 cells per
+// axis, with most of the FP64 work removed.  Each candidate cell is visited as
+// one image of the box (integer shifts a, m, c along x, y, z), so the image
+// separation R_i - (R_j + a L_x x + m (L_y y + delta x) + c L_z z) is first
+// evaluated in FP32 from FP32 positions.  Its squared length differs from the
+// exact one by less than the margin kept in rc2_lo / rc2_hi (bounded from the
+// FP32 rounding of positions, shifts, differences and sums, for box edges up
+// to L: 2^-24 (256 L r_c + 64 r_c^2)), so candidates outside the margin band
+// are decided by the FP32 value, and the few inside it by the exact FP64
+// predicate.  For an accepted pair the exact separation is the canonical
+// minimum image with n = m and the rounded quotients equal to a and c (at most
+// one image of j lies within r_c of i because every box edge is >= 3 r_c), so
+// it is evaluated with those integers and the same rounded operations,
+// without divisions.  FP32 arithmetic uses explicit round-to-nearest
+// intrinsics so that the counting and filling passes decide identically.
+template <bool NEED_D, class F>
+__device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double delta,
+                                                       const double* __restrict__ pos,
+                                                       const float* __restrict__ pos32,
+                                                       const int* __restrict__ cell_start, int i,
+                                                       double xi, double yi, double zi, F&& visit)
+{
+    const int np = P.npad;
+    const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
+    const float xf = pos32[i], yf = pos32[np + i], zf = pos32[2 * np + i];
+    const float deltaf = (float)delta;
+    const int cx = cell_coord(xi, P.inv_cw[0], nc0);
+    const int cy = cell_coord(yi, P.inv_cw[1], nc1);
+    const int cz = cell_coord(zi, P.inv_cw[2], nc2);
+    for (int dzc = -1; dzc <= 1; ++dzc) {
+        int czz = cz + dzc, c_img = 0;
+        if (czz < 0) {
+            czz += nc2;
+            c_img = -1;
+        } else if (czz >= nc2) {
+            czz -= nc2;
+            c_img = 1;
+        }
+        const float szf = __fmul_rn((float)c_img, P.Lf[2]);
+        for (int dyc = -1; dyc <= 1; ++dyc) {
+            int cyy = cy + dyc, m = 0;
+            if (cyy < 0) {
+                cyy += nc1;
+                m = -1;
+            } else if (cyy >= nc1) {
+                cyy -= nc1;
+                m = 1;
+            }
+            const float syf = __fmul_rn((float)m, P.Lf[1]);
+            const int cxu0 = m == 0 ? cx : (int)floor((xi - (double)m * delta) * P.inv_cw[0]);
+            const int rowbase = (czz * nc1 + cyy) * nc0;
+            for (int dxc = -1; dxc <= 1; ++dxc) {
+                const int cxu = cxu0 + dxc;
+                const int a = floor_div(cxu, nc0);
+                const int c = rowbase + (cxu - a * nc0);
+                const float sxf = __fadd_rn(__fmul_rn((float)m, deltaf), __fmul_rn((float)a, P.Lf[0]));
+                const int j1 = cell_start[c + 1];
+                for (int j = cell_start[c]; j < j1; ++j) {
+                    if (j == i) continue;
+                    const float dxf = __fsub_rn(__fsub_rn(xf, pos32[j]), sxf);
+                    const float dyf = __fsub_rn(__fsub_rn(yf, pos32[np + j]), syf);
+                    const float dzf = __fsub_rn(__fsub_rn(zf, pos32[2 * np + j]), szf);
+                    const float r2f = __fadd_rn(__fadd_rn(__fmul_rn(dxf, dxf), __fmul_rn(dyf, dyf)),
+                                                __fmul_rn(dzf, dzf));
+                    if (r2f >= P.rc2_hi) continue;
+                    if (r2f < P.rc2_lo) {
+                        if (NEED_D) {
+                            const double xj = pos[j], yj = pos[np + j], zj = pos[2 * np + j];
+                            const double n = (double)m;
+                            const double dx = __dsub_rn(__dsub_rn(__dsub_rn(xi, xj), __dmul_rn(n, delta)),
+                                                        __dmul_rn(P.L[0], (double)a));
+                            const double dy = __dsub_rn(__dsub_rn(yi, yj), __dmul_rn(n, P.L[1]));
+                            const double dz = __dsub_rn(__dsub_rn(zi, zj), __dmul_rn(P.L[2], (double)c_img));
+                            visit(j, dx, dy, dz, n, sq_norm_exact(dx, dy, dz));
+                        } else {
+                            visit(j, 0.0, 0.0, 0.0, 0.0, 0.0);
+                        }
+                    } else {
+                        double dx, dy, dz;
+                        const double n = min_image(P, delta, xi, yi, zi, pos[j], pos[np + j],
+                                                   pos[2 * np + j], dx, dy, dz);
+                        const double r2 = sq_norm_exact(dx, dy, dz);
+                        if (r2 < P.rc2) visit(j, dx, dy, dz, n, r2);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <bool NEED_D, class F>
+__device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta,
+                                                  const double* __restrict__ pos,
+                                                  const float* __restrict__ pos32,
+                                                  const int* __restrict__ cell_start, int i,
+                                                  double xi, double yi, double zi, F&& visit)
+{
+    if (P.fast_cells)
+        for_each_neighbor_fast<NEED_D>(P, delta, pos, pos32, cell_start, i, xi, yi, zi, visit);
+    else
+        for_each_neighbor_generic(P, delta, pos, cell_start, i, xi, yi, zi, visit);
+}
+
+__global__ void k_nbr_count(KParams P, const double* __restrict__ pos, const float* __restrict__ pos32,
                             const int* __restrict__ cell_start, int* __restrict__ row_cnt,
                             const DevState* st)
 {
@@ -321,14 +433,14 @@ __global__ void k_nbr_count(KParams P, const double* __restrict__ pos,
     const double delta = st->delta;
     const int np = P.npad;
     int cnt = 0;
-    for_each_neighbor(P, delta, pos, cell_start, i, pos[i], pos[np + i], pos[2 * np + i],
-                      [&](int, double, double, double, double, double) { ++cnt; });
+    for_each_neighbor<false>(P, delta, pos, pos32, cell_start, i, pos[i], pos[np + i], pos[2 * np + i],
+                             [&](int, double, double, double, double, double) { ++cnt; });
     row_cnt[i] = cnt;
 }
 
 void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L)
 {
-    k_nbr_count<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B.pos_w, B.cell_start,
+    k_nbr_count<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B.pos_w, B.pos32, B.cell_start,
                                                                     B.row_cnt, B.st);
 }
 
@@ -344,6 +456,7 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
     const double d = 1.0 + P.alpha * sw;
     B.diag[i] = d;
     B.dinv[i] = 1.0 / d;
+    B.diag32[i] = (float)d;
     B.dinv32[i] = (float)(1.0 / d);
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     if (P.noise_amp != 0.0) {
@@ -370,7 +483,7 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
 template <bool ASSEMBLE>
 __global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
 {
-    const DevState* st = B.st;
+    DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
@@ -379,25 +492,30 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
     const int np = P.npad;
     const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
     int k = B.row_ptr[i];
+    const int kend = B.row_ptr[i + 1];
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
     int* __restrict__ col = B.col;
     double* __restrict__ val = B.val;
     float* __restrict__ val32 = B.val32;
-    for_each_neighbor(P, delta, B.pos_w, B.cell_start, i, xi, yi, zi,
-                      [&](int j, double dx, double dy, double dz, double nimg, double r2) {
-                          col[k] = j;
-                          if (ASSEMBLE) {
-                              const double w = exp(-r2 / P.two_lambda2);
-                              val[k] = w;
-                              val32[k] = (float)w;
-                              sw += w;
-                              fx += dx * w;
-                              fy += dy * w;
-                              fz += dz * w;
-                              nw += nimg * w;
-                          }
-                          ++k;
-                      });
+    for_each_neighbor<ASSEMBLE>(P, delta, B.pos_w, B.pos32, B.cell_start, i, xi, yi, zi,
+                                [&](int j, double dx, double dy, double dz, double nimg, double r2) {
+                                    if (k < kend) {
+                                        col[k] = j;
+                                        if (ASSEMBLE) {
+                                            const double w = exp(-r2 / P.two_lambda2);
+                                            val[k] = w;
+                                            val32[k] = (float)w;
+                                            sw += w;
+                                            fx += dx * w;
+                                            fy += dy * w;
+                                            fz += dz * w;
+                                            nw += nimg * w;
+                                        }
+                                    }
+                                    ++k;
+                                });
+    // the counting pass and this one must agree; a mismatch is reported, never written past
+    if (k != kend) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
     if (ASSEMBLE) finish_row(P, B, i, yi, step, use_inj, sw, fx, fy, fz, nw);
 }
 

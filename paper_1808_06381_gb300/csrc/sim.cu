@@ -169,7 +169,18 @@ void derive(const sp_params& p, KParams& k, int npad)
         ncell = 1;
     }
     k.ncell = (int)ncell;
+    k.fast_cells = (k.nc[0] >= 3 && k.nc[1] >= 3 && k.nc[2] >= 3) ? 1 : 0;
+    // FP32 pre-filter margin on |R|^2: 2^-24 (256 L r_c + 64 r_c^2) bounds the
+    // FP32 rounding of positions, image shifts, differences, squares and sums
+    const double Lmax = std::max(p.L[0], std::max(p.L[1], p.L[2]));
+    const double margin = std::ldexp(256.0 * Lmax * p.rc + 64.0 * p.rc * p.rc, -24);
+    k.rc2_lo = (float)(k.rc2 - margin);
+    k.rc2_hi = (float)(k.rc2 + margin);
+    for (int a = 0; a < 3; ++a) k.Lf[a] = (float)p.L[a];
     k.tol2 = p.cg_tol * p.cg_tol;
+    // mixed solver: each FP32 inner solve reduces the residual by 10^-4 before
+    // the FP64 residual is recomputed (well above FP32 attainable accuracy)
+    k.inner2 = 1e-8;
     k.max_iter = p.cg_max_iter;
 }
 
@@ -224,7 +235,8 @@ int capture_cg_loop(sp_sim* s, cudaStream_t cs)
     cudaGraphConditionalHandle h_check;
     SS_CUDA(cudaGraphConditionalHandleCreate(&h_check, body, 0u, cudaGraphCondAssignDefault));
     CgLaunch C{1, (unsigned long long)h_loop, (unsigned long long)h_check};
-    launch_cg_iteration_head(P, B, mx, C, launch_of(s, bs));
+    launch_cg_spmv(P, B, mx, launch_of(s, bs));
+    launch_cg_update(P, B, mx, C, launch_of(s, bs));
     cudaGraph_t bg = nullptr;
     SS_CUDA(cudaStreamGetCaptureInfo(bs, &cst, nullptr, &bg, &deps, nullptr, &nd));
     cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
@@ -237,9 +249,8 @@ int capture_cg_loop(sp_sim* s, cudaStream_t cs)
     SS_CUDA(cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaStream_t is = s->cap_stream[2];
     SS_CUDA(cudaStreamBeginCaptureToGraph(is, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    launch_cg_true_residual(P, B, mx, true, launch_of(s, is));
+    launch_cg_true_residual(P, B, mx, true, C, launch_of(s, is));
     SS_CUDA(cudaStreamEndCapture(is, &ifbody));
-    launch_cg_iteration_tail(P, B, mx, C, launch_of(s, bs));
     SS_CUDA(cudaStreamEndCapture(bs, &body));
     return SP_OK;
 }
@@ -256,10 +267,10 @@ int host_cg_loop(sp_sim* s, long long* launches)
     const int chunk = 8;
     for (int it = 0; it < P.max_iter + kMaxCgRestarts + chunk; it += chunk) {
         for (int k = 0; k < chunk; ++k) {
-            launch_cg_iteration_head(P, B, mx, C, L);
-            launch_cg_true_residual(P, B, mx, false, L);
-            launch_cg_iteration_tail(P, B, mx, C, L);
-            *launches += cg_kernels_per_iteration(mx) + 1;
+            launch_cg_spmv(P, B, mx, L);
+            launch_cg_update(P, B, mx, C, L);
+            launch_cg_true_residual(P, B, mx, false, C, L);
+            *launches += cg_kernels_per_iteration(mx) + cg_kernels_per_check(mx);
         }
         SS_CUDA(cudaMemcpyAsync(s->st_host, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
         SS_CUDA(cudaStreamSynchronize(s->stream));
@@ -282,7 +293,7 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
     } else {
         SS_TRY(host_cg_loop(s, launches));
     }
-    launch_cg_finish(P, B, L);
+    launch_cg_finish(P, B, mixed(s), L);
     launch_stress(P, B, L);
     *launches += 2;
     return SP_OK;
@@ -451,10 +462,10 @@ int sp_sim_destroy(sp_sim* s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     free_graphs(s);
     DevBuffers& B = s->B;
-    void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.id_w, B.cell_of, B.slot, B.perm, B.cell_count,
-                    B.cell_start, B.row_cnt, B.row_ptr, B.col, B.val, B.val32, B.diag, B.dinv, B.dinv32,
-                    B.b, B.x, B.r, B.p, B.q, B.r32, B.p32, B.q32, B.xi_inj, B.partials, B.scan_tmp,
-                    B.stage, B.st};
+    void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
+                    B.cell_count, B.cell_start, B.row_cnt, B.row_ptr, B.col, B.val, B.val32, B.diag,
+                    B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
+                    B.xi_inj, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -524,6 +535,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     auto A = [&](int r) { if (a == SP_OK) a = r; };
     A(dev_alloc(s, &B.pos_s, v3));
     A(dev_alloc(s, &B.pos_w, v3));
+    A(dev_alloc(s, &B.pos32, v3));
     A(dev_alloc(s, &B.v_s, v3));
     A(dev_alloc(s, &B.id_s, n));
     A(dev_alloc(s, &B.id_w, n));
@@ -536,15 +548,18 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.row_ptr, (size_t)n + 1));
     A(dev_alloc(s, &B.diag, n));
     A(dev_alloc(s, &B.dinv, n));
+    A(dev_alloc(s, &B.diag32, n));
     A(dev_alloc(s, &B.dinv32, n));
     A(dev_alloc(s, &B.b, v3));
     A(dev_alloc(s, &B.x, v3));
     A(dev_alloc(s, &B.r, v3));
     A(dev_alloc(s, &B.p, v3));
     A(dev_alloc(s, &B.q, v3));
-    A(dev_alloc(s, &B.r32, 4 * (size_t)npad));
-    A(dev_alloc(s, &B.p32, 4 * (size_t)npad));
-    A(dev_alloc(s, &B.q32, 4 * (size_t)npad));
+    A(dev_alloc(s, &B.z, v3));
+    A(dev_alloc(s, &B.r4, (size_t)npad));
+    A(dev_alloc(s, &B.p4, (size_t)npad));
+    A(dev_alloc(s, &B.q4, (size_t)npad));
+    A(dev_alloc(s, &B.d4, (size_t)npad));
     A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(n, s->kp.ncell) / 4096 + 2)));
     A(dev_alloc(s, &B.stage, 3 * (size_t)n));
@@ -710,7 +725,7 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
     const DevState& h = *s->st_host;
     if (!s->host_loop) {
         launches += h.steps_in_call * s->fixed_launches_step + h.iter_sum * cg_kernels_per_iteration(mixed(s)) +
-                    h.true_checks;
+                    h.true_checks * cg_kernels_per_check(mixed(s));
     }
     if (info) {
         info->status = status;
@@ -750,44 +765,57 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         cls.push_back(c);
         return SP_OK;
     };
-    enum { START = -1, BUILD = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER };
+    enum { START = -1, SORT = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER, COUNT, FILL };
     launch_reset_step_stats(B.st, s->stream);
     int rc = mark(START);
     if (rc == SP_OK) {
-        enqueue_build(s, s->stream);
+        const bool warm = s->p.warm_start == SP_WARM_PREV;
+        if (P.ncell == 1) {
+            launch_identity_gather(P, B, warm, L);
+        } else {
+            launch_bin(P, B, L);
+            launch_scan(B.cell_count, B.cell_start, P.ncell, B.scan_tmp, 0, B.st, 0, L);
+            launch_scatter_sort_gather(P, B, warm, L);
+        }
+        mark(SORT);
+        launch_nbr_count(P, B, L);
+        launch_scan(B.row_cnt, B.row_ptr, P.n, B.scan_tmp, s->nnz_cap, B.st, 1, L);
+        mark(COUNT);
         launch_nbr_fill(P, B, true, s->use_inj, mx, L);
-        rc = mark(BUILD);
+        rc = mark(FILL);
     }
     if (rc == SP_OK) {
         launch_cg_init(P, B, s->p.warm_start == SP_WARM_PREV, mx, L);
         rc = mark(OTHER);
     }
-    for (int it = 0; rc == SP_OK && it < P.max_iter + kMaxCgRestarts + 1; ++it) {
+    for (int it = 0; rc == SP_OK && it < P.max_iter + kMaxCgRestarts + 8; ++it) {
         launch_cg_spmv(P, B, mx, L);
         mark(SPMV);
         launch_cg_update(P, B, mx, C, L);
-        mark(UPDATE);
-        launch_cg_true_residual(P, B, mx, false, L);
-        mark(TRUE_RES);
-        launch_cg_iteration_tail(P, B, mx, C, L);
-        rc = mark(DIRECTION);
+        rc = mark(UPDATE);
         if (rc != SP_OK) break;
         rc = read_state(s);
         if (rc != SP_OK) break;
+        if (s->st_host->check_true) {
+            launch_cg_true_residual(P, B, mx, false, C, L);
+            rc = mark(TRUE_RES);
+            if (rc != SP_OK) break;
+            rc = read_state(s);
+            if (rc != SP_OK) break;
+        }
         const DevState& h = *s->st_host;
-        if (h.check_true == 0 && h.true_checks > out->true_residual_launches) out->true_residual_launches = (int)h.true_checks;
         if (h.done || h.error || h.overflow) break;
     }
     if (rc == SP_OK) {
-        launch_cg_finish(P, B, L);
+        launch_cg_finish(P, B, mx, L);
         launch_stress(P, B, L);
         launch_integrate(P, B, L);
         rc = mark(OTHER);
     }
     if (rc == SP_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
     if (rc == SP_OK) rc = read_state(s);
-    double* acc[] = {&out->build_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
-                     &out->direction_ms, &out->other_ms};
+    double* acc[] = {&out->sort_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
+                     &out->direction_ms, &out->other_ms, &out->count_ms, &out->fill_ms};
     for (size_t k = 1; rc == SP_OK && k < ev.size(); ++k) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
@@ -798,12 +826,19 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         if (s->err.empty()) s->err = "profiling step failed";
         return rc;
     }
+    out->build_ms = out->sort_ms + out->count_ms + out->fill_ms;
     const DevState& h = *s->st_host;
+    if (h.overflow) {
+        // the pair storage was too small for this step: grow it and report the failure
+        SS_TRY(grow_pairs(s));
+        s->err = "pair storage grown during profiling; repeat the call";
+        return SP_ERR_OOM;
+    }
     out->cg_iterations = h.iter;
     out->spmv_launches = h.iter;
     out->update_launches = h.iter;
-    out->direction_launches = h.iter;
-    out->true_residual_launches = (int)h.true_checks;
+    out->direction_launches = 0;   // fused into the SpMV kernel
+    out->true_residual_launches = (int)h.true_checks * cg_kernels_per_check(mx);
     out->n = P.n;
     out->nnz = h.nnz;
     out->precision = s->p.precision;

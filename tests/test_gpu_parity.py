@@ -318,3 +318,100 @@ def test_full_size_velocities_against_oracle_solve(full):
     ref, it, res = oracle.pcg(sysr, 1e-12)
     assert np.abs(v - ref).max() <= 1e-10 * np.abs(ref).max()
     assert np.linalg.norm(sysr.b - sysr.matvec(v)) <= 2e-12 * np.linalg.norm(sysr.b)
+
+
+# --------------------------------------------- FP32 pre-filter of the pair search
+
+
+@pytest.mark.parametrize("L,delta", [(40.0, 13.7), (111.8, 77.25)])
+def test_pairs_near_the_cut_in_large_boxes(L, delta):
+    """Pairs at |R|^2 = r_c^2 (1 +- 1e-5 .. 1e-7), inside the FP32 margin band, also across
+    the sheared boundary: the exact predicate decides them, bit for bit as the oracle."""
+    rng = np.random.Generator(np.random.PCG64(int(L)))
+    n_pairs = 3000
+    a = rng.uniform(0, L, (n_pairs, 3))
+    a[: n_pairs // 3, 1] = rng.uniform(L - 0.5, L, n_pairs // 3)       # near the top face
+    u = rng.normal(size=(n_pairs, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = 1.0 + rng.choice([-1e-5, -1e-6, -1e-7, 1e-7, 1e-6, 1e-5, 0.0], n_pairs)
+    b = a + u * r[:, None]
+    pos = np.concatenate([a, b])
+    # b may leave the box: map it back with the sheared images
+    y_over = pos[:, 1] >= L
+    pos[y_over, 1] -= L
+    pos[y_over, 0] -= delta
+    y_under = pos[:, 1] < 0
+    pos[y_under, 1] += L
+    pos[y_under, 0] += delta
+    pos[:, 0] %= L
+    pos[:, 2] %= L
+    pos[pos >= L] = 0.0
+    n = pos.shape[0]
+    sim, p, _ = make(n, L, pos=pos, delta=delta)
+    sim.build_neighbors()
+    got = sim.neighbors()
+    ref = oracle.neighbors(p, pos, delta, method="cells")
+    assert np.array_equal(got, ref)
+    assert ref.shape[0] > n_pairs // 2
+    sim.close()
+
+
+# ------------------------------------------------------------ mixed precision
+
+
+@pytest.mark.parametrize("n,tol,bound", [(777, 1e-10, 1e-8), (4096, 1e-10, 1e-8), (4096, 1e-8, 1e-6)])
+def test_mixed_solve_meets_the_fp64_tolerance(n, tol, bound):
+    """Mixed solver: FP32 inner iterations, FP64 residual replacement.  The reported
+    true residual is the FP64 one and meets tol; the velocity error against the FP64
+    oracle solve is within cond(A) * tol (cond ~ 22; bound stated with margin)."""
+    L = synth.box_length(n)
+    delta = 0.21 * L
+    sim, p, pos = make(n, L, seed=n + 5, delta=delta, tol=tol, precision="mixed")
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    assert info["status"] == 0 and info["residual"] <= tol
+    v = sim.get_velocities()
+    sysr = oracle.assemble(p, pos, oracle.neighbors(p, pos, delta), oracle.noise(p.seed, 0, np.arange(n)), delta)
+    ref, _, _ = oracle.pcg(sysr, 1e-13)
+    assert np.abs(v - ref).max() <= bound * np.abs(ref).max()
+    # the residual the solver reports is the oracle's residual of its answer
+    res = np.linalg.norm(sysr.b - sysr.matvec(v)) / np.linalg.norm(sysr.b)
+    assert res <= 1.01 * tol
+    assert abs(res - info["residual"]) <= 1e-3 * tol + 1e-15
+    sim.close()
+
+
+def test_mixed_steps_follow_the_oracle():
+    n, steps = 2000, 4
+    L = synth.box_length(n)
+    sim, p, pos = make(n, L, seed=21, warm_start="prev", tol=1e-11, precision="mixed")
+    info = sim.step(steps)
+    assert info["status"] == 0 and info["last_residual"] <= 1e-11
+    gpos = sim.get_positions()
+    opos, od = pos, 0.0
+    for s in range(steps):
+        r = oracle.step(p, opos, od, s, tol=1e-13)
+        opos, od = r.pos, r.delta
+    d = gpos - opos
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < 1e-9 * steps
+    sim.close()
+
+
+def test_mixed_full_size_against_fp64_gpu(full):
+    sim64, p, pos, info64 = full
+    w = synth.PRECISION
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    sim = ss.Simulation(w.n, w.L, kappa, seed=w.seed, cg_tol=1e-8, positions=pos, warm_start="none",
+                        precision="mixed")
+    sim.set_positions(pos, 7.25)
+    sim.build_neighbors()
+    sim.assemble()
+    info = sim.solve_velocities()
+    assert info["status"] == 0 and info["residual"] <= 1e-8
+    v = sim.get_velocities()
+    v64 = sim64.get_velocities()
+    # single-solve velocity error of the mixed path vs the FP64 solve (to 1e-12): <= cond * 1e-8
+    assert np.abs(v - v64).max() <= 1e-6 * np.abs(v64).max()
+    sim.close()

@@ -214,6 +214,37 @@ int sp_set_noise(sp_sim* sim, const double* xi_host);
 int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count,
                      const int64_t* ids_host, uint64_t* out_host);
 
+/* ---- allocation-free solve ----
+ *
+ * No counterpart in the paper: an entry point for callers that cannot
+ * allocate device memory (a host framework that owns every device allocation
+ * through its own pool, a real-time loop that forbids allocation after
+ * start-up, or an embedding that must not touch the caller's allocator).
+ *
+ * Solves (A (x) I_3) x = b by Jacobi-preconditioned CG in FP64 from x = 0,
+ * stopping at ||b - A x||_2 <= tol ||b||_2 (checked on the exactly recomputed
+ * residual), for A = diag - alpha W with W given in CSR (off-diagonal weights
+ * only; A_ij = -alpha w_ij; A must be symmetric positive definite):
+ *   row_ptr_dev [n+1], col_dev [nnz] (int32), w_dev [nnz], diag_dev [n] (A_ii),
+ *   b_dev [3][n] and x_dev [3][n] (x, y, z planes) — all caller-owned device
+ *   memory on `device`; x_dev is overwritten.  stream: a cudaStream_t or NULL.
+ *
+ * It allocates nothing: its working vectors live in one fixed device array
+ * (about 3.2 MB) that every device context loading this library holds until
+ * the process exits.  Hence:
+ *   - n must be <= 32768, else SP_ERR_INVALID_ARG (sp_last_error(NULL) says why);
+ *   - every call on a device shares that array, so calls that may overlap on
+ *     the GPU (several streams or host threads) race; serialise them;
+ *   - the first call on a device looks up the array's address with that device
+ *     current (the caller's current device is restored); make that first call
+ *     before any stream capture.
+ * Returns SP_OK, SP_ERR_NOT_CONVERGED (max_iter reached), SP_ERR_NONFINITE or
+ * SP_ERR_CUDA; info (may be NULL) receives iterations and the true residual. */
+int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, const int32_t* row_ptr_dev,
+                         const int32_t* col_dev, const double* w_dev, const double* diag_dev, double alpha,
+                         const double* b_dev, double* x_dev, double tol, int32_t max_iter,
+                         sp_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,7 +98,8 @@ def load(path: str = LIB_PATH):
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
-            ("sp_profile_step", [vp, P(sp_kernel_profile)])]
+            ("sp_profile_step", [vp, P(sp_kernel_profile)]),
+            ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)])]
     for name, args in sims:
         f = getattr(lib, name)
         f.argtypes = args
@@ -130,6 +131,21 @@ def philox_blocks(seed: int, step: int, ids, device: int = 0) -> np.ndarray:
     out = np.zeros((ids.shape[0], 4), dtype=np.uint64)
     _check(load().sp_philox_blocks(device, seed, step, ids.shape[0], _p(ids), _p(out)))
     return out
+
+
+NOALLOC_MAX_ROWS = 32768
+
+
+def solve_csr_noalloc(n: int, row_ptr_ptr: int, col_ptr: int, w_ptr: int, diag_ptr: int, alpha: float,
+                      b_ptr: int, x_ptr: int, tol: float = 1e-8, max_iter: int = 1000, device: int = 0,
+                      stream=None) -> dict:
+    """Allocation-free FP64 solve of (diag - alpha W) x = b for caller-owned device arrays
+    given as raw pointers (CSR int32 row_ptr/col, float64 w/diag, float64 [3][n] b and x)."""
+    info = sp_solve_info()
+    rc = load().sp_solve_csr_noalloc(device, stream, n, row_ptr_ptr, col_ptr, w_ptr, diag_ptr, alpha, b_ptr,
+                                     x_ptr, tol, max_iter, ctypes.byref(info))
+    return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
+            "error": (load().sp_last_error(None) or b"").decode() if rc != SP_OK else ""}
 
 
 def _torch_stream():

@@ -439,6 +439,10 @@ int do_build(sp_sim* s)
 
 }  // namespace
 
+// Error text of calls that have no simulation object (creation, the
+// allocation-free solve); sp_last_error(NULL) returns it.
+std::string& sp_global_error() { return g_create_error; }
+
 // ======================================================================= ABI
 
 extern "C" {

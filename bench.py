@@ -102,11 +102,51 @@ class ClockSampler:
 
 
 def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
-    """Bytes the solver's SpMV must move per launch: row pointers, columns and
-    weights of every entry, the diagonal, one read of p and one write of q."""
+    """Bytes the solver's SpMV kernel must move per launch (padding excluded):
+    per entry its column and weight; per row the slot map, one read of the
+    gathered vector (r with D^-1 in the mixed solver, z in FP64), the diagonal,
+    and the read and write of q and p (q' = A z + beta q, p' = z + beta p)."""
     if precision == "mixed":
-        return 4.0 * (n + 1) + 8.0 * nnz + 4.0 * n + 16.0 * n + 16.0 * n
-    return 4.0 * (n + 1) + 12.0 * nnz + 8.0 * n + 24.0 * n + 24.0 * n
+        return n * (4.0 + 16.0 + 4.0 + 32.0 + 32.0) + 8.0 * nnz
+    return n * (4.0 + 24.0 + 8.0 + 48.0 + 48.0) + 12.0 * nnz
+
+
+def update_algorithmic_bytes(n: int, precision: str) -> float:
+    """Update kernel: mixed reads p, q, d, r and writes d, r (float4 rows);
+    FP64 reads x, p, r, q, D^-1 and writes x, r, z."""
+    if precision == "mixed":
+        return n * 6 * 16.0
+    return n * (4 * 24.0 + 8.0 + 3 * 24.0)
+
+
+def persistent_algorithmic_bytes(n: int, nnz: int, iters: int, checks: int) -> float:
+    """Bytes one persistent mixed solve must move: per iteration one SpMV and one
+    update; per FP64 residual replacement the fold of d into x (x read and
+    written, d read and cleared) and the FP64 SpMV r = b - A x (columns and FP64
+    weights, one read of x, b and the diagonals, r written)."""
+    per_check = n * (48.0 + 32.0) + n * (4.0 + 24.0 + 24.0 + 24.0 + 8.0 + 4.0 + 16.0) + 12.0 * nnz
+    return iters * (spmv_algorithmic_bytes(n, nnz, "mixed") + update_algorithmic_bytes(n, "mixed")) \
+        + checks * per_check
+
+
+def run_steps(sim, steps, stream, flush):
+    """Time `steps` single steps with CUDA events on the simulation's stream,
+    flushing L2 before each; returns (total ms, launches, CG iterations, max residual)."""
+    import torch
+    total_ms, launches, iters, max_res = 0.0, 0, 0, 0.0
+    for _ in range(steps):
+        flush.zero_()                      # L2 flush between timed steps (512 MB > L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = sim.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        launches += info["kernel_launches"]
+        iters += info["cg_iterations"]
+        max_res = max(max_res, info["last_residual"])
+    return total_ms, launches, iters, max_res
 
 
 def cpu_baseline(workload, precision: str, steps: int = 2):
@@ -163,7 +203,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-comparison", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
@@ -192,13 +233,27 @@ def main():
     seed = workload.seed + 1000 * rank
     pos0 = synth.uniform_positions(n, L, seed)
     kappa = ss.kappa_from_kappa_tau(workload.kappa_tau)
-    sim = ss.Simulation(n, L, kappa, alpha=workload.alpha, eps=workload.eps, zeta=workload.zeta,
-                        kT=workload.kT, dt=workload.dt, rc=workload.rc, seed=seed, precision=args.precision,
-                        warm_start="prev", cg_tol=workload.tol, cg_max_iter=2000, device=local_rank,
-                        positions=pos0)
+    def make_sim(precision):
+        return ss.Simulation(n, L, kappa, alpha=workload.alpha, eps=workload.eps, zeta=workload.zeta,
+                             kT=workload.kT, dt=workload.dt, rc=workload.rc, seed=seed, precision=precision,
+                             warm_start="prev", cg_tol=workload.tol, cg_max_iter=2000, device=local_rank,
+                             positions=pos0)
+
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    # the FP64 solver on the same workload, for comparison (same steps, same timing)
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64_comparison:
+        sim64 = make_sim("fp64")
+        for _ in range(args.warmup):
+            sim64.step(1)
+        t64, _, it64, res64 = run_steps(sim64, args.steps, stream, flush)
+        fp64 = {"value": n * args.steps / (t64 / 1e3), "ms_per_step": t64 / args.steps,
+                "cg_iterations_per_step": it64 / args.steps, "max_true_residual": res64}
+        sim64.close()
+
+    sim = make_sim(args.precision)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -213,22 +268,7 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = 0.0
-    launches = 0
-    iters = 0
-    max_res = 0.0
-    for _ in range(args.steps):
-        flush.zero_()                      # L2 flush between timed steps (512 MB > L2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info = sim.step(1)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        launches += info["kernel_launches"]
-        iters += info["cg_iterations"]
-        max_res = max(max_res, info["last_residual"])
+    total_ms, launches, iters, max_res = run_steps(sim, args.steps, stream, flush)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -241,12 +281,27 @@ def main():
         t_max = float(t.item())
     value = n * world * args.steps / (t_max / 1e3)
 
-    # per-kernel timing of one more step (CUDA events on the simulation's stream)
+    # per-kernel timing of one more step (CUDA events on the simulation's
+    # stream), then the two loop kernels launched back to back on that system
     prof = sim.profile_step()
-    spmv_avg_ms = prof["spmv_ms"] / max(prof["spmv_launches"], 1)
+    spmv_avg_ms = prof["spmv_probe_ms"]
     algo = spmv_algorithmic_bytes(prof["n"], prof["nnz"], args.precision)
+    upd_algo = update_algorithmic_bytes(prof["n"], args.precision)
     peak, peak_kind = measured_peaks()
     achieved = algo / (spmv_avg_ms * 1e-3) / 1e9
+    upd_achieved = upd_algo / (prof["update_probe_ms"] * 1e-3) / 1e9
+    persistent = None
+    if prof["persistent_ms"] > 0:
+        pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
+        pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
+        persistent = {"kernel": "k32_cg_persistent", "bound": "hbm", "achieved": pach, "peak": peak,
+                      "unit": "GB/s", "frac": pach / peak, "traffic": None,
+                      "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                      "algorithmic_bytes_per_launch": pbytes, "avg_launch_ms": prof["persistent_ms"],
+                      "cg_iterations": prof["cg_iterations"], "true_residual_checks": prof["true_checks"],
+                      "grid": prof["persistent_blocks"],
+                      "note": "one launch per solve; CUDA events on the simulation's stream; the "
+                              "solver's working set (~60 MB) is L2-resident during the solve"}
 
     # end to end through the public API: host positions in, step, host positions out
     import ctypes  # noqa: F401
@@ -282,14 +337,25 @@ def main():
                        "replicas": world, "l2": "flushed between timed steps (512 MB write)"},
             "cg_iterations_per_step": iters / args.steps, "max_true_residual": max_res,
             "gpu_launches": launches,
-            "roofline": {"kernel": "k_cg_spmv", "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": f"hbm_gbs {peak_kind}", "algorithmic_bytes_per_launch": algo,
-                         "avg_launch_ms": spmv_avg_ms, "launches_profiled": prof["spmv_launches"],
-                         "note": "working set of one solve (~110 MB) fits in L2; per-step L2 flush only"},
-            "kernel_ms_per_step": {k: prof[k] for k in ("spmv_ms", "update_ms", "direction_ms",
-                                                         "true_residual_ms", "build_ms", "sort_ms",
-                                                         "count_ms", "fill_ms", "other_ms")},
+            "roofline": persistent if persistent else {"kernel": "k32_spmv" if args.precision == "mixed" else "k64_spmv", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                         "algorithmic_bytes_per_launch": algo, "avg_launch_ms": spmv_avg_ms,
+                         "launches_timed": prof["probe_reps"],
+                         "note": "CUDA events around back-to-back launches on the solved system; "
+                                 "the solver's working set (~60 MB) stays in L2 between launches"},
+            "roofline_spmv_kernel": {"kernel": "k32_spmv" if args.precision == "mixed" else "k64_spmv",
+                                     "achieved": achieved, "frac": achieved / peak,
+                                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": spmv_avg_ms,
+                                     "note": "the two-kernel solver's SpMV, launched back to back"},
+            "roofline_update": {"kernel": "k32_update" if args.precision == "mixed" else "k64_update",
+                                "achieved": upd_achieved, "frac": upd_achieved / peak,
+                                "algorithmic_bytes_per_launch": upd_algo, "avg_launch_ms": prof["update_probe_ms"]},
+            "kernel_ms_per_step": {k: prof[k] for k in ("persistent_ms", "spmv_ms", "update_ms", "true_residual_ms",
+                                                         "build_ms", "sort_ms", "count_ms", "fill_ms", "other_ms",
+                                                         "init_ms", "stress_ms", "integrate_ms")},
+            "matrix": {"nnz": prof["nnz"], "stored_with_padding": prof["nnz_slots"]},
+            "fp64_comparison": fp64,
             "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": n * 24 + 8,
                     "d2h_bytes_per_step": n * 24 + 16, "steps": args.e2e_steps},
             "clocks": clk,

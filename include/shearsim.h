@@ -52,7 +52,8 @@ typedef enum sp_status {
     SP_ERR_NONFINITE = -4,      /* a NaN or infinity appeared in the solve */
     SP_ERR_OOM = -5,            /* device allocation failed */
     SP_ERR_BOX_TOO_SMALL = -6,  /* some box edge is below 2 r_c: the minimum image is ambiguous */
-    SP_ERR_NO_DEVICE = -7       /* no CUDA device, or the requested ordinal does not exist */
+    SP_ERR_NO_DEVICE = -7,      /* no CUDA device, or the requested ordinal does not exist */
+    SP_ERR_TIMEOUT = -8         /* a device-side wait of the persistent solver ran past its limit */
 } sp_status;
 
 enum sp_precision {
@@ -179,6 +180,16 @@ typedef struct sp_kernel_profile {
     double sort_ms;                  /* part of build_ms: binning and the counting sort into cell order */
     double count_ms;                 /* part of build_ms: pair counting and the row-pointer scan */
     double fill_ms;                  /* part of build_ms: the fused pair/assembly pass */
+    int64_t nnz_slots;               /* stored entries including the sliced layout's padding */
+    int32_t probe_reps;              /* back-to-back launches timed for the two fields below */
+    double spmv_probe_ms;            /* average SpMV kernel time, launched back to back */
+    double update_probe_ms;          /* average update kernel time, launched back to back */
+    double persistent_ms;            /* the persistent mixed solver kernel (0 when not used) */
+    int32_t true_checks;             /* FP64 true-residual computations of the solve */
+    int32_t persistent_blocks;       /* its grid (cooperative launch), 0 when not used */
+    double init_ms;                  /* part of other_ms: solver set-up (r = b - A x0) */
+    double stress_ms;                /* part of other_ms: the stress kernel */
+    double integrate_ms;             /* part of other_ms: the position update */
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 

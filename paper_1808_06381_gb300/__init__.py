@@ -26,8 +26,10 @@ SP_ERR_NONFINITE = -4
 SP_ERR_OOM = -5
 SP_ERR_BOX_TOO_SMALL = -6
 SP_ERR_NO_DEVICE = -7
+SP_ERR_TIMEOUT = -8
 _STATUS = {0: "SP_OK", -1: "SP_ERR_INVALID_ARG", -2: "SP_ERR_CUDA", -3: "SP_ERR_NOT_CONVERGED",
-           -4: "SP_ERR_NONFINITE", -5: "SP_ERR_OOM", -6: "SP_ERR_BOX_TOO_SMALL", -7: "SP_ERR_NO_DEVICE"}
+           -4: "SP_ERR_NONFINITE", -5: "SP_ERR_OOM", -6: "SP_ERR_BOX_TOO_SMALL", -7: "SP_ERR_NO_DEVICE",
+           -8: "SP_ERR_TIMEOUT"}
 
 PREC = {"fp64": 0, "mixed": 1}
 WARM = {"none": 0, "prev": 1}
@@ -66,7 +68,11 @@ class sp_kernel_profile(ctypes.Structure):
                 ("true_residual_ms", ctypes.c_double), ("build_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("cg_iterations", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("sort_ms", ctypes.c_double), ("count_ms", ctypes.c_double),
-                ("fill_ms", ctypes.c_double)]
+                ("fill_ms", ctypes.c_double), ("nnz_slots", ctypes.c_int64), ("probe_reps", ctypes.c_int32),
+                ("spmv_probe_ms", ctypes.c_double), ("update_probe_ms", ctypes.c_double),
+                ("persistent_ms", ctypes.c_double), ("true_checks", ctypes.c_int32),
+                ("persistent_blocks", ctypes.c_int32), ("init_ms", ctypes.c_double), ("stress_ms", ctypes.c_double),
+                ("integrate_ms", ctypes.c_double)]
 
 
 def declared_symbols() -> list:

@@ -8,6 +8,11 @@
 // partial sums in a fixed order (deterministic, and no block ever waits for
 // another).
 //
+// The matrix is stored sliced (SELL-32-sigma256, see internal.cuh): one thread
+// owns one row, a warp owns a chunk of 32 rows of nearly equal length, and
+// entry k of the whole chunk is one coalesced 128-byte load of columns and of
+// weights; the gathers of several entries are independent and issued together.
+//
 // One iteration is two kernels.  With z = D^-1 r the search direction update
 // p' = z + beta p gives A p' = A z + beta (A p), so the SpMV kernel gathers z,
 // forms q' = A z + beta q and p' = z + beta p for its own rows and reduces
@@ -17,10 +22,11 @@
 // FP64 solver: everything in FP64; z is stored by the update kernel so the
 // SpMV gathers one FP64 3-vector per entry.
 //
-// Mixed solver: the matrix values, the Jacobi diagonal and the vectors r, p,
-// q are FP32 (one float4 per row), the iteration solves for a correction d
-// (FP32) of the FP64 solution x; dots accumulate in FP64.  When the FP32
-// residual has dropped by the inner factor, or meets the tolerance, d is
+// Mixed solver: the matrix values and the vectors r, p, q, d are FP32, one
+// float4 per row (r.w carries the Jacobi scale D^-1, so one 16-byte gather
+// brings z_j); the iteration solves for a correction d of the FP64 solution x;
+// dot products accumulate in double-float (FP32 pairs, ~44 bits).  When the
+// FP32 residual has dropped by the inner factor, or meets the tolerance, d is
 // folded into x and the true residual b - A x is recomputed with the FP64
 // matrix; the solve ends when that meets the tolerance, else the iteration
 // restarts from it (residual replacement).
@@ -29,11 +35,13 @@
 // true-residual check an IF node; the kernels set both conditions.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace ss {
 
-constexpr int kSpmvBlock = 256;
+constexpr int kBlock = 256;
 
 __device__ __forceinline__ bool halted(const DevState* st)
 {
@@ -45,186 +53,133 @@ __device__ __forceinline__ void set_cond(const CgLaunch& C, unsigned long long h
     if (C.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
 }
 
-// Rows handled by a warp-uniform loop: group g of T lanes takes rows
-// g, g + ngroups, ...; the loop bound is uniform across the warp so the
-// shuffles always see every lane.
-#define SS_ROW_LOOP_BEGIN(T)                                                         \
-    const int lane = threadIdx.x & ((T) - 1);                                        \
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;                          \
-    const int ngroups = (gridDim.x * blockDim.x) / (T);                              \
-    const int warp_first_group = ((gtid >> 5) << 5) / (T);                           \
-    const int group_in_warp = (threadIdx.x & 31) / (T);                              \
-    for (int base = warp_first_group; base < P.n; base += ngroups) {                 \
-        const int i = base + group_in_warp;                                          \
-        const bool active = i < P.n;
+// Slots handled by a grid-stride loop; nslots is a multiple of the block size,
+// so every warp sees whole chunks.
+#define SS_SLOT_LOOP_BEGIN                                                                       \
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < P.nslots;                      \
+         slot += gridDim.x * blockDim.x) {                                                       \
+        const int row = B.slot_row[slot];                                                        \
+        const int e0 = B.chunk_off[slot >> 5] + (slot & 31);                                     \
+        const int e1 = B.chunk_off[(slot >> 5) + 1];
 
-#define SS_ROW_LOOP_END }
+#define SS_SLOT_LOOP_END }
 
-template <int T, class V>
-__device__ __forceinline__ void group_sum3(V& s0, V& s1, V& s2)
-{
-#pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o, T);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o, T);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o, T);
-    }
-}
+// Entries of one row are processed in batches of kBatch: all column and weight
+// loads of a batch are issued first, then all gathers, so one row waits for
+// two memory latencies per batch instead of two per entry.  The batch count
+// (the chunk's longest row / kBatch) is uniform across the warp; entries past
+// the row's own length are padding (weight 0) and load nothing.
+constexpr int kBatch = 6;
 
-// s_a = sum_j w_ij v_a[j] over row i (FP64 planes), T lanes per row.
-template <int T>
-__device__ __forceinline__ void row_sum64(const int* __restrict__ row_ptr, const int* __restrict__ col,
-                                          const double* __restrict__ val, const double* __restrict__ v,
-                                          int np, int i, bool active, int lane, double& s0, double& s1,
-                                          double& s2)
+// s_a = sum_j w_ij v_a[j] over the entries of one row (FP64 planes).
+__device__ __forceinline__ void row_sum64(const int* __restrict__ col, const double* __restrict__ val,
+                                          const double* __restrict__ v, int np, int e0, int e1, bool active,
+                                          double& s0, double& s1, double& s2)
 {
     s0 = s1 = s2 = 0.0;
-    if (active) {
-        const int end = row_ptr[i + 1];
-        for (int k = row_ptr[i] + lane; k < end; k += T) {
-            const int j = col[k];
-            const double w = val[k];
-            s0 += w * v[j];
-            s1 += w * v[np + j];
-            s2 += w * v[2 * np + j];
+    for (int eb = e0; eb < e1; eb += 32 * kBatch) {
+        int j[kBatch];
+        double w[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = eb + 32 * u;
+            j[u] = 0;
+            w[u] = 0.0;
+            if (active && e < e1) {
+                j[u] = col[e];
+                w[u] = val[e];
+            }
+        }
+        double g0[kBatch], g1[kBatch], g2[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            g0[u] = g1[u] = g2[u] = 0.0;
+            if (w[u] != 0.0) {
+                g0[u] = v[j[u]];
+                g1[u] = v[np + j[u]];
+                g2[u] = v[2 * np + j[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            s0 += w[u] * g0[u];
+            s1 += w[u] * g1[u];
+            s2 += w[u] * g2[u];
         }
     }
-    group_sum3<T>(s0, s1, s2);
 }
 
-// s = sum_j w_ij dinv_j r_j over row i (FP32, float4 rows), T lanes per row.
-template <int T>
-__device__ __forceinline__ void row_sum32_z(const int* __restrict__ row_ptr, const int* __restrict__ col,
-                                            const float* __restrict__ val, const float4* __restrict__ r,
-                                            const float* __restrict__ dinv, int i, bool active, int lane,
+// s = sum_j w_ij D^-1_j r_j over the entries of one row (FP32; r.w = D^-1).
+__device__ __forceinline__ void row_sum32_z(const int* __restrict__ col, const float* __restrict__ val,
+                                            const float4* __restrict__ r, int e0, int e1, bool active,
                                             float& s0, float& s1, float& s2)
 {
     s0 = s1 = s2 = 0.f;
-    if (active) {
-        const int end = row_ptr[i + 1];
-        for (int k = row_ptr[i] + lane; k < end; k += T) {
-            const int j = col[k];
-            const float w = val[k] * dinv[j];
-            const float4 rj = r[j];
-            s0 = fmaf(w, rj.x, s0);
-            s1 = fmaf(w, rj.y, s1);
-            s2 = fmaf(w, rj.z, s2);
-        }
-    }
-    group_sum3<T>(s0, s1, s2);
-}
-
-// ============================================================== FP64 solver
-
-// r = b - A x0 (or r = b and x = 0); z = D^-1 r; p = q = 0.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k64_init(KParams P, DevBuffers B, int from_x)
-{
-    DevState* st = B.st;
-    if (st->error | st->overflow) return;
-    const int np = P.npad;
-    double bb = 0.0, rr = 0.0, rz = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    if (from_x) row_sum64<T>(B.row_ptr, B.col, B.val, B.x, np, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const double s[3] = {s0, s1, s2};
-        const double d = B.diag[i], di = B.dinv[i];
-        double rs = 0.0;
+    for (int eb = e0; eb < e1; eb += 32 * kBatch) {
+        int j[kBatch];
+        float w[kBatch];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
-            const double bk = B.b[k];
-            double rk = bk;
-            if (from_x)
-                rk = bk - (d * B.x[k] - P.alpha * s[c]);
-            else
-                B.x[k] = 0.0;
-            B.r[k] = rk;
-            B.z[k] = di * rk;
-            B.p[k] = 0.0;
-            B.q[k] = 0.0;
-            bb += bk * bk;
-            rs += rk * rk;
-        }
-        rr += rs;
-        rz += di * rs;
-    }
-    SS_ROW_LOOP_END
-    const double v[3] = {bb, rr, rz};
-    if (publish_partials<3>(v, B.partials, &st->ticket[0])) {
-        double out[3];
-        reduce_partials<3>(B.partials, out);
-        if (threadIdx.x == 0) {
-            st->bnorm2 = out[0];
-            st->rr = out[1];
-            st->rr_restart = out[1];
-            st->rho = out[2];
-            st->beta = 0.0;
-            st->iter = 0;
-            st->restarts = 0;
-            st->check_true = 0;
-            st->status = 0;
-            st->zero_b = 0;
-            st->done = 0;
-            if (!isfinite(out[0]) || !isfinite(out[1])) {
-                st->status = SP_ERR_NONFINITE;
-                st->error = SP_ERR_NONFINITE;
-                st->done = 1;
-            } else if (out[0] == 0.0) {
-                st->zero_b = 1;   // b = 0: the solution is v = 0
-                st->done = 1;
-                st->last_res = 0.0;
-            } else if (out[1] <= P.tol2 * out[0]) {
-                st->done = 1;     // the start vector already meets the tolerance (exact r)
-                st->last_res = sqrt(out[1] / out[0]);
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = eb + 32 * u;
+            j[u] = 0;
+            w[u] = 0.f;
+            if (active && e < e1) {
+                j[u] = col[e];
+                w[u] = val[e];
             }
+        }
+        float4 g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (w[u] != 0.f) g[u] = r[j[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const float ww = w[u] * g[u].w;
+            s0 = fmaf(ww, g[u].x, s0);
+            s1 = fmaf(ww, g[u].y, s1);
+            s2 = fmaf(ww, g[u].z, s2);
         }
     }
 }
 
-// q = A z + beta q; p = z + beta p; p.q.  Last block: alpha = rho / p.q.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k64_spmv(KParams P, DevBuffers B)
+__device__ __forceinline__ void init_scalars(const KParams& P, DevState* st, double bb, double rr, double rz)
 {
-    DevState* st = B.st;
-    if (halted(st)) return;
-    const int np = P.npad;
-    const double beta = st->beta;
-    double pq = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    double s0, s1, s2;
-    row_sum64<T>(B.row_ptr, B.col, B.val, B.z, np, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const double s[3] = {s0, s1, s2};
-        const double d = B.diag[i];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
-            const double zk = B.z[k];
-            const double az = d * zk - P.alpha * s[c];
-            const double qk = beta == 0.0 ? az : az + beta * B.q[k];
-            const double pk = beta == 0.0 ? zk : zk + beta * B.p[k];
-            B.q[k] = qk;
-            B.p[k] = pk;
-            pq += pk * qk;
-        }
+    st->bnorm2 = bb;
+    st->rr = rr;
+    st->rr_restart = rr;
+    st->rho = rz;
+    st->beta = 0.0;
+    st->iter = 0;
+    st->restarts = 0;
+    st->check_true = 0;
+    st->status = 0;
+    st->zero_b = 0;
+    st->done = 0;
+    if (!isfinite(bb) || !isfinite(rr)) {
+        st->status = SP_ERR_NONFINITE;
+        st->error = SP_ERR_NONFINITE;
+        st->done = 1;
+    } else if (bb == 0.0) {
+        st->zero_b = 1;   // b = 0: the solution is v = 0
+        st->done = 1;
+        st->last_res = 0.0;
+    } else if (rr <= P.tol2 * bb) {
+        st->done = 1;     // the start vector already meets the tolerance (exact r)
+        st->last_res = sqrt(rr / bb);
     }
-    SS_ROW_LOOP_END
-    const double v[1] = {pq};
-    if (publish_partials<1>(v, B.partials, &st->ticket[0])) {
-        double out[1];
-        reduce_partials<1>(B.partials, out);
-        if (threadIdx.x == 0) {
-            st->pq = out[0];
-            if (!(out[0] > 0.0) || !isfinite(out[0])) {
-                st->status = SP_ERR_NONFINITE;
-                st->error = SP_ERR_NONFINITE;
-                st->done = 1;
-            } else {
-                st->alpha = st->rho / out[0];
-            }
-        }
+}
+
+__device__ __forceinline__ void alpha_from_pq(DevState* st, double pq)
+{
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        st->status = SP_ERR_NONFINITE;
+        st->error = SP_ERR_NONFINITE;
+        st->done = 1;
+    } else {
+        st->alpha = st->rho / pq;
     }
 }
 
@@ -251,43 +206,6 @@ __device__ __forceinline__ void update_scalars(const KParams& P, DevState* st, d
     }
     set_cond(C, C.h_check, (unsigned)(st->check_true && !st->done));
     set_cond(C, C.h_loop, st->done ? 0u : 1u);
-}
-
-// x += alpha p; r -= alpha q; z = D^-1 r; partial r.r and r.z.
-__global__ void __launch_bounds__(kVecBlock) k64_update(KParams P, DevBuffers B, CgLaunch C)
-{
-    DevState* st = B.st;
-    if (halted(st)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            set_cond(C, C.h_check, 0u);
-            set_cond(C, C.h_loop, 0u);
-        }
-        return;
-    }
-    const int np = P.npad;
-    const double a = st->alpha;
-    double rr = 0.0, rz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const double di = B.dinv[i];
-        double rs = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
-            B.x[k] += a * B.p[k];
-            const double rk = B.r[k] - a * B.q[k];
-            B.r[k] = rk;
-            B.z[k] = di * rk;
-            rs += rk * rk;
-        }
-        rr += rs;
-        rz += di * rs;
-    }
-    const double v[2] = {rr, rz};
-    if (publish_partials<2>(v, B.partials, &st->ticket[0])) {
-        double out[2];
-        reduce_partials<2>(B.partials, out);
-        if (threadIdx.x == 0) update_scalars(P, st, out[0], out[1], P.tol2 * st->bnorm2, C);
-    }
 }
 
 // Last block of a true-residual kernel: accept, restart from the true
@@ -320,25 +238,136 @@ __device__ __forceinline__ void true_residual_scalars(const KParams& P, DevState
     set_cond(C, C.h_loop, st->done ? 0u : 1u);
 }
 
+// ============================================================== FP64 solver
+
+// r = b - A x0 (or r = b and x = 0); z = D^-1 r; p = q = 0.
+__global__ void __launch_bounds__(kBlock) k64_init(KParams P, DevBuffers B, int from_x)
+{
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int np = P.npad;
+    double bb = 0.0, rr = 0.0, rz = 0.0;
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        double s[3] = {0.0, 0.0, 0.0};
+        if (from_x) row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
+        const double d = B.diag[row], di = B.dinv[row];
+        double rs = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * np + row;
+            const double bk = B.b[k];
+            double rk = bk;
+            if (from_x)
+                rk = bk - (d * B.x[k] - P.alpha * s[c]);
+            else
+                B.x[k] = 0.0;
+            B.r[k] = rk;
+            B.z[k] = di * rk;
+            B.p[k] = 0.0;
+            B.q[k] = 0.0;
+            bb += bk * bk;
+            rs += rk * rk;
+        }
+        rr += rs;
+        rz += di * rs;
+    }
+    SS_SLOT_LOOP_END
+    const double v[3] = {bb, rr, rz};
+    if (publish_partials<3>(v, B.partials, &st->ticket[0])) {
+        double out[3];
+        reduce_partials<3>(B.partials, out);
+        if (threadIdx.x == 0) init_scalars(P, st, out[0], out[1], out[2]);
+    }
+}
+
+// q = A z + beta q; p = z + beta p; p.q.  Last block: alpha = rho / p.q.
+__global__ void __launch_bounds__(kBlock) k64_spmv(KParams P, DevBuffers B, int probe)
+{
+    DevState* st = B.st;
+    if (!probe && halted(st)) return;
+    const int np = P.npad;
+    const double beta = st->beta;
+    double pq = 0.0;
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        double s[3];
+        row_sum64(B.col, B.val, B.z, np, e0, e1, true, s[0], s[1], s[2]);
+        const double d = B.diag[row];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * np + row;
+            const double zk = B.z[k];
+            const double az = d * zk - P.alpha * s[c];
+            const double qk = beta == 0.0 ? az : az + beta * B.q[k];
+            const double pk = beta == 0.0 ? zk : zk + beta * B.p[k];
+            B.q[k] = qk;
+            B.p[k] = pk;
+            pq += pk * qk;
+        }
+    }
+    SS_SLOT_LOOP_END
+    const double v[1] = {pq};
+    if (publish_partials<1>(v, B.partials, &st->ticket[0])) {
+        double out[1];
+        reduce_partials<1>(B.partials, out);
+        if (threadIdx.x == 0 && !probe) alpha_from_pq(st, out[0]);
+    }
+}
+
+// x += alpha p; r -= alpha q; z = D^-1 r; partial r.r and r.z.
+__global__ void __launch_bounds__(kBlock) k64_update(KParams P, DevBuffers B, CgLaunch C, int probe)
+{
+    DevState* st = B.st;
+    if (!probe && halted(st)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            set_cond(C, C.h_check, 0u);
+            set_cond(C, C.h_loop, 0u);
+        }
+        return;
+    }
+    const int np = P.npad;
+    const double a = st->alpha;
+    double rr = 0.0, rz = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const double di = B.dinv[i];
+        double rs = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * np + i;
+            B.x[k] += a * B.p[k];
+            const double rk = B.r[k] - a * B.q[k];
+            B.r[k] = rk;
+            B.z[k] = di * rk;
+            rs += rk * rk;
+        }
+        rr += rs;
+        rz += di * rs;
+    }
+    const double v[2] = {rr, rz};
+    if (publish_partials<2>(v, B.partials, &st->ticket[0])) {
+        double out[2];
+        reduce_partials<2>(B.partials, out);
+        if (threadIdx.x == 0 && !probe) update_scalars(P, st, out[0], out[1], P.tol2 * st->bnorm2, C);
+    }
+}
+
 // r = b - A x in FP64; z = D^-1 r; partial r.r and r.z.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k64_true_residual(KParams P, DevBuffers B, int always,
-                                                                CgLaunch C)
+__global__ void __launch_bounds__(kBlock) k64_true_residual(KParams P, DevBuffers B, int always, CgLaunch C)
 {
     DevState* st = B.st;
     if (halted(st) || (!always && !st->check_true)) return;
     const int np = P.npad;
     double rr = 0.0, rz = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    double s0, s1, s2;
-    row_sum64<T>(B.row_ptr, B.col, B.val, B.x, np, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const double s[3] = {s0, s1, s2};
-        const double d = B.diag[i], di = B.dinv[i];
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        double s[3];
+        row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
+        const double d = B.diag[row], di = B.dinv[row];
         double rs = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
+            const int k = c * np + row;
             const double rk = B.b[k] - (d * B.x[k] - P.alpha * s[c]);
             B.r[k] = rk;
             B.z[k] = di * rk;
@@ -347,7 +376,7 @@ __global__ void __launch_bounds__(kSpmvBlock) k64_true_residual(KParams P, DevBu
         rr += rs;
         rz += di * rs;
     }
-    SS_ROW_LOOP_END
+    SS_SLOT_LOOP_END
     const double v[2] = {rr, rz};
     if (publish_partials<2>(v, B.partials, &st->ticket[0])) {
         double out[2];
@@ -358,27 +387,27 @@ __global__ void __launch_bounds__(kSpmvBlock) k64_true_residual(KParams P, DevBu
 
 // ============================================================= mixed solver
 
-__device__ __forceinline__ float4 f4(float x, float y, float z) { return make_float4(x, y, z, 0.f); }
+__device__ __forceinline__ float4 f4(float x, float y, float z, float w) { return make_float4(x, y, z, w); }
 
-// r = b - A x0 in FP64 (or r = b and x = 0); r4 = fp32(r); d = p = q = 0.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k32_init(KParams P, DevBuffers B, int from_x)
+// r = b - A x0 with the FP64 matrix (or r = b and x = 0); r4 = (fp32(r), D^-1);
+// d = p = q = 0.  The norms are taken in FP64 on the FP64 residual.
+__global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int from_x)
 {
     DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int np = P.npad;
     double bb = 0.0, rr = 0.0, rz = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    if (from_x) row_sum64<T>(B.row_ptr, B.col, B.val, B.x, np, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const double s[3] = {s0, s1, s2};
-        const double d = B.diag[i];
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        double s[3] = {0.0, 0.0, 0.0};
+        if (from_x) row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
+        const double d = B.diag[row];
+        const float di = B.dinv32[row];
         double rk[3];
         double rs = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
+            const int k = c * np + row;
             const double bk = B.b[k];
             rk[c] = bk;
             if (from_x)
@@ -388,68 +417,47 @@ __global__ void __launch_bounds__(kSpmvBlock) k32_init(KParams P, DevBuffers B, 
             bb += bk * bk;
             rs += rk[c] * rk[c];
         }
-        B.r4[i] = f4((float)rk[0], (float)rk[1], (float)rk[2]);
-        B.p4[i] = f4(0.f, 0.f, 0.f);
-        B.q4[i] = f4(0.f, 0.f, 0.f);
-        B.d4[i] = f4(0.f, 0.f, 0.f);
+        B.r4[row] = f4((float)rk[0], (float)rk[1], (float)rk[2], di);
+        B.p4[row] = f4(0.f, 0.f, 0.f, 0.f);
+        B.q4[row] = f4(0.f, 0.f, 0.f, 0.f);
+        B.d4[row] = f4(0.f, 0.f, 0.f, 0.f);
         rr += rs;
-        rz += (double)B.dinv32[i] * rs;
+        rz += (double)di * rs;
     }
-    SS_ROW_LOOP_END
+    SS_SLOT_LOOP_END
     const double v[3] = {bb, rr, rz};
     if (publish_partials<3>(v, B.partials, &st->ticket[0])) {
         double out[3];
         reduce_partials<3>(B.partials, out);
-        if (threadIdx.x == 0) {
-            st->bnorm2 = out[0];
-            st->rr = out[1];
-            st->rr_restart = out[1];
-            st->rho = out[2];
-            st->beta = 0.0;
-            st->iter = 0;
-            st->restarts = 0;
-            st->check_true = 0;
-            st->status = 0;
-            st->zero_b = 0;
-            st->done = 0;
-            if (!isfinite(out[0]) || !isfinite(out[1])) {
-                st->status = SP_ERR_NONFINITE;
-                st->error = SP_ERR_NONFINITE;
-                st->done = 1;
-            } else if (out[0] == 0.0) {
-                st->zero_b = 1;
-                st->done = 1;
-                st->last_res = 0.0;
-            } else if (out[1] <= P.tol2 * out[0]) {
-                st->done = 1;
-                st->last_res = sqrt(out[1] / out[0]);
-            }
-        }
+        if (threadIdx.x == 0) init_scalars(P, st, out[0], out[1], out[2]);
     }
 }
 
-// FP32: z = D^-1 r gathered on the fly; q = A z + beta q; p = z + beta p; p.q in FP64.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k32_spmv(KParams P, DevBuffers B)
+// FP32: z_j = D^-1_j r_j gathered from r4; q = A z + beta q; p = z + beta p;
+// p.q in double-float.
+__global__ void __launch_bounds__(kBlock, 6) k32_spmv(KParams P, DevBuffers B, int probe)
 {
     DevState* st = B.st;
-    if (halted(st)) return;
+    if (!probe && halted(st)) return;
     const float beta = (float)st->beta;
     const float alpha_e = (float)P.alpha;
-    double pq = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    float s0, s1, s2;
-    row_sum32_z<T>(B.row_ptr, B.col, B.val32, B.r4, B.dinv32, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const float di = B.dinv32[i], d = B.diag32[i];
-        const float4 ri = B.r4[i];
-        const float z0 = di * ri.x, z1 = di * ri.y, z2 = di * ri.z;
+    const int* __restrict__ col = B.col;
+    const float* __restrict__ val = B.val32;
+    const float4* __restrict__ r4 = B.r4;
+    dfloat pq{0.f, 0.f};
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        float s0, s1, s2;
+        row_sum32_z(col, val, r4, e0, e1, true, s0, s1, s2);
+        const float4 ri = r4[row];
+        const float d = B.diag32[row];
+        const float z0 = ri.w * ri.x, z1 = ri.w * ri.y, z2 = ri.w * ri.z;
         float q0 = fmaf(d, z0, -alpha_e * s0);
         float q1 = fmaf(d, z1, -alpha_e * s1);
         float q2 = fmaf(d, z2, -alpha_e * s2);
         float p0 = z0, p1 = z1, p2 = z2;
         if (beta != 0.f) {
-            const float4 qo = B.q4[i], po = B.p4[i];
+            const float4 qo = B.q4[row], po = B.p4[row];
             q0 = fmaf(beta, qo.x, q0);
             q1 = fmaf(beta, qo.y, q1);
             q2 = fmaf(beta, qo.z, q2);
@@ -457,33 +465,22 @@ __global__ void __launch_bounds__(kSpmvBlock) k32_spmv(KParams P, DevBuffers B)
             p1 = fmaf(beta, po.y, p1);
             p2 = fmaf(beta, po.z, p2);
         }
-        B.q4[i] = f4(q0, q1, q2);
-        B.p4[i] = f4(p0, p1, p2);
-        pq += (double)(p0 * q0 + p1 * q1 + p2 * q2);
+        B.q4[row] = f4(q0, q1, q2, 0.f);
+        B.p4[row] = f4(p0, p1, p2, 0.f);
+        pq = df_add(pq, p0 * q0 + p1 * q1 + p2 * q2);
     }
-    SS_ROW_LOOP_END
-    const double v[1] = {pq};
-    if (publish_partials<1>(v, B.partials, &st->ticket[0])) {
-        double out[1];
-        reduce_partials<1>(B.partials, out);
-        if (threadIdx.x == 0) {
-            st->pq = out[0];
-            if (!(out[0] > 0.0) || !isfinite(out[0])) {
-                st->status = SP_ERR_NONFINITE;
-                st->error = SP_ERR_NONFINITE;
-                st->done = 1;
-            } else {
-                st->alpha = st->rho / out[0];
-            }
-        }
-    }
+    SS_SLOT_LOOP_END
+    dfloat v[1] = {pq};
+    double out[1];
+    if (publish_reduce_df<1>(v, B.partials_df, &st->ticket[0], out) && threadIdx.x == 0 && !probe)
+        alpha_from_pq(st, out[0]);
 }
 
-// FP32: d += alpha p; r -= alpha q; r.r and r.z accumulated in FP64.
-__global__ void __launch_bounds__(kVecBlock) k32_update(KParams P, DevBuffers B, CgLaunch C)
+// FP32: d += alpha p; r -= alpha q; r.r and r.z in double-float.
+__global__ void __launch_bounds__(kBlock) k32_update(KParams P, DevBuffers B, CgLaunch C, int probe)
 {
     DevState* st = B.st;
-    if (halted(st)) {
+    if (!probe && halted(st)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             set_cond(C, C.h_check, 0u);
             set_cond(C, C.h_loop, 0u);
@@ -491,7 +488,7 @@ __global__ void __launch_bounds__(kVecBlock) k32_update(KParams P, DevBuffers B,
         return;
     }
     const float a = (float)st->alpha;
-    double rr = 0.0, rz = 0.0;
+    dfloat rr{0.f, 0.f}, rz{0.f, 0.f};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const float4 p = B.p4[i], q = B.q4[i];
         float4 d = B.d4[i], r = B.r4[i];
@@ -504,24 +501,21 @@ __global__ void __launch_bounds__(kVecBlock) k32_update(KParams P, DevBuffers B,
         B.d4[i] = d;
         B.r4[i] = r;
         const float rs = r.x * r.x + r.y * r.y + r.z * r.z;
-        rr += (double)rs;
-        rz += (double)(B.dinv32[i] * rs);
+        rr = df_add(rr, rs);
+        rz = df_add(rz, r.w * rs);
     }
-    const double v[2] = {rr, rz};
-    if (publish_partials<2>(v, B.partials, &st->ticket[0])) {
-        double out[2];
-        reduce_partials<2>(B.partials, out);
-        if (threadIdx.x == 0) {
-            // stop the FP32 inner solve once the residual dropped by the inner
-            // factor since the last restart, or meets half the tolerance
-            const double target = fmax(P.inner2 * st->rr_restart, 0.25 * P.tol2 * st->bnorm2);
-            update_scalars(P, st, out[0], out[1], target, C);
-        }
+    dfloat v[2] = {rr, rz};
+    double out[2];
+    if (publish_reduce_df<2>(v, B.partials_df, &st->ticket[0], out) && threadIdx.x == 0 && !probe) {
+        // stop the FP32 inner solve once the residual dropped by the inner
+        // factor since the last restart, or meets half the tolerance
+        const double target = fmax(P.inner2 * st->rr_restart, 0.25 * P.tol2 * st->bnorm2);
+        update_scalars(P, st, out[0], out[1], target, C);
     }
 }
 
 // x += d; d = 0 (FP64 accumulation of the FP32 correction).
-__global__ void __launch_bounds__(kVecBlock) k32_fold(KParams P, DevBuffers B, int always)
+__global__ void __launch_bounds__(kBlock) k32_fold(KParams P, DevBuffers B, int always)
 {
     const DevState* st = B.st;
     if (halted(st) || (!always && !st->check_true)) return;
@@ -531,38 +525,36 @@ __global__ void __launch_bounds__(kVecBlock) k32_fold(KParams P, DevBuffers B, i
         B.x[i] += (double)d.x;
         B.x[np + i] += (double)d.y;
         B.x[2 * np + i] += (double)d.z;
-        B.d4[i] = f4(0.f, 0.f, 0.f);
+        B.d4[i] = f4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-// r = b - A x with the FP64 matrix; r4 = fp32(r); r.r in FP64, r.z with the FP32 diagonal.
-template <int T>
-__global__ void __launch_bounds__(kSpmvBlock) k32_true_residual(KParams P, DevBuffers B, int always,
-                                                                CgLaunch C)
+// r = b - A x with the FP64 matrix; r4 = (fp32(r), D^-1); r.r in FP64.
+__global__ void __launch_bounds__(kBlock) k32_true_residual(KParams P, DevBuffers B, int always, CgLaunch C)
 {
     DevState* st = B.st;
     if (halted(st) || (!always && !st->check_true)) return;
     const int np = P.npad;
     double rr = 0.0, rz = 0.0;
-    SS_ROW_LOOP_BEGIN(T)
-    double s0, s1, s2;
-    row_sum64<T>(B.row_ptr, B.col, B.val, B.x, np, i, active, lane, s0, s1, s2);
-    if (active && lane == 0) {
-        const double s[3] = {s0, s1, s2};
-        const double d = B.diag[i];
+    SS_SLOT_LOOP_BEGIN
+    if (row >= 0) {
+        double s[3];
+        row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
+        const double d = B.diag[row];
+        const float di = B.dinv32[row];
         double rk[3];
         double rs = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int k = c * np + i;
+            const int k = c * np + row;
             rk[c] = B.b[k] - (d * B.x[k] - P.alpha * s[c]);
             rs += rk[c] * rk[c];
         }
-        B.r4[i] = f4((float)rk[0], (float)rk[1], (float)rk[2]);
+        B.r4[row] = f4((float)rk[0], (float)rk[1], (float)rk[2], di);
         rr += rs;
-        rz += (double)B.dinv32[i] * rs;
+        rz += (double)di * rs;
     }
-    SS_ROW_LOOP_END
+    SS_SLOT_LOOP_END
     const double v[2] = {rr, rz};
     if (publish_partials<2>(v, B.partials, &st->ticket[0])) {
         double out[2];
@@ -589,52 +581,83 @@ __global__ void k_cg_finish(KParams P, DevBuffers B)
 
 // ------------------------------------------------------------------ launchers
 
-constexpr int kLanes64 = 2;   // FP64: few lanes per row keep the FP64 shuffle-adds low
-constexpr int kLanes32 = 4;
+namespace {
+// Resident blocks per SM of each kernel (computed once per process).
+struct Occupancy {
+    int k64_init, k64_spmv, k64_update, k64_true, k32_init, k32_spmv, k32_update, k32_fold, k32_true;
+};
+Occupancy g_occ;
+std::once_flag g_occ_once;
 
-static int spmv_grid(const KParams& P, int T, Launch L)
+int occ_of(const void* f)
 {
-    return grid_for((long long)P.n * T, kSpmvBlock, L.num_sms * 8);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+}  // namespace
+
+void cg_prepare()
+{
+    std::call_once(g_occ_once, [] {
+        g_occ.k64_init = occ_of((const void*)k64_init);
+        g_occ.k64_spmv = occ_of((const void*)k64_spmv);
+        g_occ.k64_update = occ_of((const void*)k64_update);
+        g_occ.k64_true = occ_of((const void*)k64_true_residual);
+        g_occ.k32_init = occ_of((const void*)k32_init);
+        g_occ.k32_spmv = occ_of((const void*)k32_spmv);
+        g_occ.k32_update = occ_of((const void*)k32_update);
+        g_occ.k32_fold = occ_of((const void*)k32_fold);
+        g_occ.k32_true = occ_of((const void*)k32_true_residual);
+    });
 }
 
-static int vec_grid(const KParams& P, Launch L)
+// One wave: at most (SMs x resident blocks), never more blocks than work.
+static int wave_grid(long long threads, int occ, Launch L)
 {
-    return grid_for(P.n, kVecBlock, L.num_sms * 8);
+    long long g = (threads + kBlock - 1) / kBlock;
+    const long long wave = (long long)L.num_sms * occ;
+    if (g > wave) g = wave;
+    if (g > kMaxPartials) g = kMaxPartials;
+    return (int)(g < 1 ? 1 : g);
 }
 
 void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L)
 {
     if (mixed)
-        k32_init<kLanes64><<<spmv_grid(P, kLanes64, L), kSpmvBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
+        k32_init<<<wave_grid(P.nslots, g_occ.k32_init, L), kBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
     else
-        k64_init<kLanes64><<<spmv_grid(P, kLanes64, L), kSpmvBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
+        k64_init<<<wave_grid(P.nslots, g_occ.k64_init, L), kBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
 }
 
-void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L)
+void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L, int probe)
 {
     if (mixed)
-        k32_spmv<kLanes32><<<spmv_grid(P, kLanes32, L), kSpmvBlock, 0, L.stream>>>(P, B);
+        k32_spmv<<<wave_grid(P.nslots, g_occ.k32_spmv, L), kBlock, 0, L.stream>>>(P, B, probe);
     else
-        k64_spmv<kLanes64><<<spmv_grid(P, kLanes64, L), kSpmvBlock, 0, L.stream>>>(P, B);
+        k64_spmv<<<wave_grid(P.nslots, g_occ.k64_spmv, L), kBlock, 0, L.stream>>>(P, B, probe);
 }
 
-void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L)
+void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L, int probe)
 {
     if (mixed)
-        k32_update<<<vec_grid(P, L), kVecBlock, 0, L.stream>>>(P, B, C);
+        k32_update<<<wave_grid(P.n, g_occ.k32_update, L), kBlock, 0, L.stream>>>(P, B, C, probe);
     else
-        k64_update<<<vec_grid(P, L), kVecBlock, 0, L.stream>>>(P, B, C);
+        k64_update<<<wave_grid(P.n, g_occ.k64_update, L), kBlock, 0, L.stream>>>(P, B, C, probe);
 }
 
 void launch_cg_true_residual(const KParams& P, DevBuffers& B, bool mixed, bool always_check,
                              const CgLaunch& C, Launch L)
 {
     if (mixed) {
-        k32_fold<<<vec_grid(P, L), kVecBlock, 0, L.stream>>>(P, B, always_check ? 1 : 0);
-        k32_true_residual<kLanes64><<<spmv_grid(P, kLanes64, L), kSpmvBlock, 0, L.stream>>>(
+        k32_fold<<<wave_grid(P.n, g_occ.k32_fold, L), kBlock, 0, L.stream>>>(P, B, always_check ? 1 : 0);
+        k32_true_residual<<<wave_grid(P.nslots, g_occ.k32_true, L), kBlock, 0, L.stream>>>(
             P, B, always_check ? 1 : 0, C);
     } else {
-        k64_true_residual<kLanes64><<<spmv_grid(P, kLanes64, L), kSpmvBlock, 0, L.stream>>>(
+        k64_true_residual<<<wave_grid(P.nslots, g_occ.k64_true, L), kBlock, 0, L.stream>>>(
             P, B, always_check ? 1 : 0, C);
     }
 }

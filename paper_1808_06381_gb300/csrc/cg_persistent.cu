@@ -1,0 +1,558 @@
+// Persistent mixed-precision CG: the whole solve of Eq. algebra (arXiv
+// 1808.06381, §Method) in one cooperative launch.
+//
+// Same iteration as the mixed solver of cg.cu (FP32 SpMV with the direction
+// update fused, FP32 update of r and of the correction d, double-float dot
+// products, FP64 residual replacement), but the iteration loop runs inside the
+// kernel: one block per window of 256 rows (or several windows per block
+// when the rows outnumber the resident threads), two grid-wide barriers per
+// iteration, and the CG scalars reduced redundantly — in the same fixed order —
+// by every block from the per-block partial sums, so every block takes the
+// same decisions.  A block touches the solver vectors of its own rows only,
+// except for the gathers of r (and of x in the FP64 residual), which read rows
+// written by other blocks since the last barrier and therefore bypass L1.
+//
+// The barrier is a counter plus a generation word in device memory.  The
+// launch is cooperative (all blocks resident), and every wait is bounded: a
+// block that waits longer than kBarrierSpinLimit polls sets SP_ERR_TIMEOUT and
+// leaves the solve, so no GPU can hang on it.
+#include <math.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace ss {
+
+namespace {
+
+constexpr int kPBlock = 256;
+constexpr long long kBarrierSpinLimit = 1ll << 24;   // x ~100 ns sleeps: well above a second
+
+struct PShared {
+    float2 df[32];
+    double d[32];
+    double bcast[4];
+    int flag;
+    // scalars decided by thread 0 (FP64 math once per block, not once per thread)
+    float alpha_f, beta_f;
+    int action;   // 0 continue, 1 check the true residual, 2 stop
+};
+
+// Grid barrier (all blocks of a cooperative launch).  Returns false when the
+// solve must stop (an error was raised anywhere, including a barrier timeout).
+__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShared& sh)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = gen + 1u;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicExch(&st->bar_gen, target);
+        } else {
+            long long spins = 0;
+            while (atomicAdd(&st->bar_gen, 0u) != target) {
+                __nanosleep(100);
+                if (++spins > kBarrierSpinLimit) {
+                    atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        sh.flag = atomicAdd(&st->error, 0);
+    }
+    __syncthreads();
+    gen += 1u;
+    return sh.flag == 0;
+}
+
+// Publish this block's double-float sums (K values) for the next barrier.
+template <int K>
+__device__ __forceinline__ void publish_df(const dfloat (&v)[K], float2* partials, PShared& sh)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const dfloat t = block_sum_df(v[k], sh.df);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = make_float2(t.hi, t.lo);
+    }
+}
+
+// After the barrier: warp 0 of every block sums all blocks' partials in the
+// same order; the totals are valid in thread 0 only (no barrier here).
+template <int K>
+__device__ __forceinline__ void total_df(const float2* partials, double (&out)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        out[k] = 0.0;
+        if (threadIdx.x < 32) {
+            dfloat v{0.f, 0.f};
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+                const float2 p = __ldcg(partials + k * kMaxPartials + b);
+                v = df_add(v, dfloat{p.x, p.y});
+            }
+            v = warp_sum_df(v);
+            if (threadIdx.x == 0) out[k] = (double)v.hi + (double)v.lo;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void publish_d(const double (&v)[K], double* partials, PShared& sh)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double t = block_sum(v[k], sh.d);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = t;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void total_d(const double* partials, double (&out)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        out[k] = 0.0;
+        if (threadIdx.x < 32) {
+            double v = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(partials + k * kMaxPartials + b);
+            v = warp_sum(v);
+            if (threadIdx.x == 0) out[k] = v;
+        }
+    }
+}
+
+// Barrier fused with the reduction of K sums: every block publishes its block
+// sum; the last block to arrive sums all blocks' partials (every thread a
+// strided share, in the same fixed order whichever block is last), stores the
+// totals and only then releases the barrier; every block then reads the
+// totals.  One reduction costs one barrier plus about two memory latencies.
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
+                                               const dfloat (&v)[K], float2* partials, double* totals,
+                                               double (&out)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const dfloat t = block_sum_df(v[k], sh.df);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = make_float2(t.hi, t.lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh.flag = (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    const unsigned int target = gen + 1u;
+    if (sh.flag) {   // last to arrive: reduce, publish, release
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dfloat a{0.f, 0.f};
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+                const float2 p = __ldcg(partials + k * kMaxPartials + b);
+                a = df_add(a, dfloat{p.x, p.y});
+            }
+            const dfloat t = block_sum_df(a, sh.df);
+            if (threadIdx.x == 0) totals[k] = (double)t.hi + (double)t.lo;
+        }
+        if (threadIdx.x == 0) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicExch(&st->bar_gen, target);
+        }
+    } else if (threadIdx.x == 0) {
+        long long spins = 0;
+        while (atomicAdd(&st->bar_gen, 0u) != target) {
+            __nanosleep(64);
+            if (++spins > kBarrierSpinLimit) {
+                atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+                break;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh.flag = atomicAdd(&st->error, 0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.bcast[k] = __ldcg(totals + k);
+    }
+    __syncthreads();
+    gen = target;
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
+    return sh.flag == 0;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
+                                               const double (&v)[K], double* partials, double* totals,
+                                               double (&out)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double t = block_sum(v[k], sh.d);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh.flag = (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    const unsigned int target = gen + 1u;
+    if (sh.flag) {
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+                a += __ldcg(partials + k * kMaxPartials + b);
+            const double t = block_sum(a, sh.d);
+            if (threadIdx.x == 0) totals[k] = t;
+        }
+        if (threadIdx.x == 0) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicExch(&st->bar_gen, target);
+        }
+    } else if (threadIdx.x == 0) {
+        long long spins = 0;
+        while (atomicAdd(&st->bar_gen, 0u) != target) {
+            __nanosleep(64);
+            if (++spins > kBarrierSpinLimit) {
+                atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+                break;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh.flag = atomicAdd(&st->error, 0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.bcast[k] = __ldcg(totals + k);
+    }
+    __syncthreads();
+    gen = target;
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
+    return sh.flag == 0;
+}
+
+constexpr int kBatchP = 6;    // FP32 gathers per batch
+constexpr int kBatchP64 = 2;  // FP64 gathers per batch (the rare true-residual SpMV)
+
+// s = sum_j w_ij D^-1_j r_j (FP32); r rows of other blocks are read from L2.
+__device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const float* __restrict__ val,
+                                            const float4* r, int e0, int e1, float& s0, float& s1, float& s2)
+{
+    s0 = s1 = s2 = 0.f;
+    for (int eb = e0; eb < e1; eb += 32 * kBatchP) {
+        int j[kBatchP];
+        float w[kBatchP];
+#pragma unroll
+        for (int u = 0; u < kBatchP; ++u) {
+            const int e = eb + 32 * u;
+            j[u] = 0;
+            w[u] = 0.f;
+            if (e < e1) {
+                j[u] = __ldg(col + e);
+                w[u] = __ldg(val + e);
+            }
+        }
+        float4 g[kBatchP];
+#pragma unroll
+        for (int u = 0; u < kBatchP; ++u) {
+            g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (w[u] != 0.f) g[u] = __ldcg(r + j[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatchP; ++u) {
+            const float ww = w[u] * g[u].w;
+            s0 = fmaf(ww, g[u].x, s0);
+            s1 = fmaf(ww, g[u].y, s1);
+            s2 = fmaf(ww, g[u].z, s2);
+        }
+    }
+}
+
+// s_a = sum_j w_ij x_a[j] (FP64 planes; x rows of other blocks are read from L2).
+__device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const double* __restrict__ val,
+                                            const double* x, int np, int e0, int e1, double& s0, double& s1,
+                                            double& s2)
+{
+    s0 = s1 = s2 = 0.0;
+    for (int eb = e0; eb < e1; eb += 32 * kBatchP64) {
+        int j[kBatchP64];
+        double w[kBatchP64];
+#pragma unroll
+        for (int u = 0; u < kBatchP64; ++u) {
+            const int e = eb + 32 * u;
+            j[u] = 0;
+            w[u] = 0.0;
+            if (e < e1) {
+                j[u] = __ldg(col + e);
+                w[u] = __ldg(val + e);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatchP64; ++u) {
+            if (w[u] != 0.0) {
+                s0 += w[u] * __ldcg(x + j[u]);
+                s1 += w[u] * __ldcg(x + np + j[u]);
+                s2 += w[u] * __ldcg(x + 2 * np + j[u]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBuffers B)
+{
+    DevState* st = B.st;
+    __shared__ PShared sh;
+    if (threadIdx.x == 0) sh.flag = 0;
+    __syncthreads();
+    if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
+    unsigned int gen = 0u;   // used by thread 0 only
+    if (threadIdx.x == 0) gen = atomicAdd(&st->bar_gen, 0u);
+
+    const int nwin = P.nslots / 256;
+    const int wb = (int)((long long)blockIdx.x * nwin / gridDim.x);
+    const int we = (int)((long long)(blockIdx.x + 1) * nwin / gridDim.x);
+    const int np = P.npad;
+    const float alpha_e = (float)P.alpha;
+
+    // CG scalars: thread 0 keeps them in FP64 and makes every decision; the
+    // other threads only see the FP32 step lengths and the action code.
+    double rho = 0.0, rr_restart = 0.0, bnorm2 = 0.0, last_res = 0.0;
+    int iter = 0, restarts = 0, status = SP_OK;
+    if (threadIdx.x == 0) {
+        rho = st->rho;
+        rr_restart = st->rr_restart;
+        bnorm2 = st->bnorm2;
+        last_res = st->last_res;
+        sh.beta_f = 0.f;
+    }
+    __syncthreads();
+
+    for (;;) {
+        // ---- SpMV with the fused direction update; p.q
+        dfloat pq{0.f, 0.f};
+        const float betaf = sh.beta_f;
+        for (int w = wb; w < we; ++w) {
+            const int slot = w * 256 + threadIdx.x;
+            const int row = B.slot_row[slot];
+            if (row >= 0) {
+                const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
+                const int e1 = B.chunk_off[(slot >> 5) + 1];
+                const float4 ri = B.r4[row];
+                const float d = __ldg(B.diag32 + row);
+                float4 qo = make_float4(0.f, 0.f, 0.f, 0.f), po = qo;
+                if (betaf != 0.f) {
+                    qo = B.q4[row];
+                    po = B.p4[row];
+                }
+                float s0, s1, s2;
+                p_row_sum32(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
+                const float z0 = ri.w * ri.x, z1 = ri.w * ri.y, z2 = ri.w * ri.z;
+                float q0 = fmaf(d, z0, -alpha_e * s0);
+                float q1 = fmaf(d, z1, -alpha_e * s1);
+                float q2 = fmaf(d, z2, -alpha_e * s2);
+                float p0 = z0, p1 = z1, p2 = z2;
+                if (betaf != 0.f) {
+                    q0 = fmaf(betaf, qo.x, q0);
+                    q1 = fmaf(betaf, qo.y, q1);
+                    q2 = fmaf(betaf, qo.z, q2);
+                    p0 = fmaf(betaf, po.x, p0);
+                    p1 = fmaf(betaf, po.y, p1);
+                    p2 = fmaf(betaf, po.z, p2);
+                }
+                B.q4[row] = make_float4(q0, q1, q2, 0.f);
+                B.p4[row] = make_float4(p0, p1, p2, 0.f);
+                pq = df_add(pq, p0 * q0 + p1 * q1 + p2 * q2);
+            }
+        }
+        // partial-sum sets: 0 for p.q, 1-2 for r.r and r.z, the FP64 array for the
+        // true residual, so a block still reading one set after a barrier is
+        // never overtaken by a faster block writing the same set (the next
+        // write of a set lies behind at least one more barrier)
+        {
+            const dfloat v[1] = {pq};
+            double tot[1];
+            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, st->totals, tot)) break;
+            if (threadIdx.x == 0) {
+                sh.action = 0;
+                if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+                    status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.alpha_f = (float)(rho / tot[0]);
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+
+        // ---- update of d and r (own rows); r.r and r.D^-1 r
+        const float af = sh.alpha_f;
+        dfloat rr{0.f, 0.f}, rz{0.f, 0.f};
+        for (int w = wb; w < we; ++w) {
+            const int i = w * 256 + threadIdx.x;
+            if (i < P.n) {
+                const float4 p = B.p4[i], q = B.q4[i];
+                float4 d = B.d4[i], r = B.r4[i];
+                d.x = fmaf(af, p.x, d.x);
+                d.y = fmaf(af, p.y, d.y);
+                d.z = fmaf(af, p.z, d.z);
+                r.x = fmaf(-af, q.x, r.x);
+                r.y = fmaf(-af, q.y, r.y);
+                r.z = fmaf(-af, q.z, r.z);
+                B.d4[i] = d;
+                B.r4[i] = r;
+                const float rs = r.x * r.x + r.y * r.y + r.z * r.z;
+                rr = df_add(rr, rs);
+                rz = df_add(rz, r.w * rs);
+            }
+        }
+        {
+            const dfloat v[2] = {rr, rz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, st->totals + 2, tot)) break;
+            if (threadIdx.x == 0) {
+                ++iter;
+                sh.action = 0;
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                    status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.beta_f = (float)(tot[1] / rho);
+                    rho = tot[1];
+                    const double target = fmax(P.inner2 * rr_restart, 0.25 * P.tol2 * bnorm2);
+                    if (tot[0] <= target || iter >= P.max_iter) sh.action = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+        if (sh.action == 0) continue;
+
+        // ---- residual replacement: x += d (own rows), then r = b - A x in FP64
+        for (int w = wb; w < we; ++w) {
+            const int i = w * 256 + threadIdx.x;
+            if (i < P.n) {
+                const float4 d = B.d4[i];
+                B.x[i] += (double)d.x;
+                B.x[np + i] += (double)d.y;
+                B.x[2 * np + i] += (double)d.z;
+                B.d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        if (!grid_sync(st, gen, sh)) break;
+        double trr = 0.0, trz = 0.0;
+        for (int w = wb; w < we; ++w) {
+            const int slot = w * 256 + threadIdx.x;
+            const int row = B.slot_row[slot];
+            if (row >= 0) {
+                const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
+                const int e1 = B.chunk_off[(slot >> 5) + 1];
+                double s[3];
+                p_row_sum64(B.col, B.val, B.x, np, e0, e1, s[0], s[1], s[2]);
+                const double d = B.diag[row];
+                const float di = B.dinv32[row];
+                double rk[3];
+                double rs = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k = c * np + row;
+                    rk[c] = B.b[k] - (d * B.x[k] - P.alpha * s[c]);
+                    rs += rk[c] * rk[c];
+                }
+                B.r4[row] = make_float4((float)rk[0], (float)rk[1], (float)rk[2], di);
+                trr += rs;
+                trz += (double)di * rs;
+            }
+        }
+        {
+            const double v[2] = {trr, trz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, st->totals + 4, tot)) break;
+            if (threadIdx.x == 0) {
+                last_res = sqrt(tot[0] / bnorm2);
+                if (blockIdx.x == 0) st->true_checks += 1;
+                sh.action = 0;
+                if (!isfinite(tot[0])) {
+                    status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else if (tot[0] <= P.tol2 * bnorm2) {
+                    sh.action = 2;   // converged
+                } else if (iter >= P.max_iter || restarts >= kMaxCgRestarts + 8) {
+                    status = SP_ERR_NOT_CONVERGED;
+                    sh.action = 2;
+                } else {
+                    ++restarts;
+                    rho = tot[1];
+                    sh.beta_f = 0.f;
+                    rr_restart = tot[0];
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+    }
+    // every block's thread 0 holds the same scalars; block 0 records them
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter = iter;
+        st->restarts = restarts;
+        st->last_res = last_res;
+        st->done = 1;
+        if (st->error == 0 && status != SP_OK) {
+            st->status = status;
+            st->error = status;
+        } else if (st->error != 0) {
+            st->status = st->error;
+        } else {
+            st->status = SP_OK;
+        }
+    }
+}
+
+namespace {
+int g_pocc = 0;
+std::once_flag g_pocc_once;
+}  // namespace
+
+int cg_persistent_grid(const KParams& P, Launch L)
+{
+    std::call_once(g_pocc_once, [] {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc, k32_cg_persistent, kPBlock, 0) != cudaSuccess)
+            g_pocc = 0;
+        cudaGetLastError();
+    });
+    long long g = std::min<long long>((long long)L.num_sms * g_pocc, P.nslots / 256);
+    if (g > kMaxPartials) g = kMaxPartials;
+    return (int)g;
+}
+
+cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
+{
+    const int g = cg_persistent_grid(P, L);
+    if (g < 1) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(kPBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k32_cg_persistent, P, B);
+}
+
+}  // namespace ss

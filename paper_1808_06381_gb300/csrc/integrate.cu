@@ -63,7 +63,8 @@ void launch_integrate(const KParams& P, DevBuffers& B, Launch L)
 // sigma_xy = -(1/V) sum_{i<j} y_ij f_ij,x with the pair forces of Eq. F and
 // Eq. vc (times zeta): f_ij = c_ev R_ij w_ij + zeta alpha w_ij (v_j - v_i + V_ij).
 // y_ij f_ij,x is symmetric in (i, j), so each row sums its whole neighbour list
-// and the total is halved.
+// and the total is halved.  Separations come from the stored image codes and
+// weights from the assembled matrix.
 __global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
 {
     DevState* st = B.st;
@@ -74,14 +75,17 @@ __global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
         const double vxi = B.x[i];
-        for (int k = B.row_ptr[i]; k < B.row_ptr[i + 1]; ++k) {
-            const int j = B.col[k];
+        const int slot = B.row_slot[i];
+        const int base = B.chunk_off[slot >> 5] + (slot & 31);
+        const int cnt = B.row_cnt[i];
+        for (int k = 0; k < cnt; ++k) {
+            const int e = base + 32 * k;
+            const int j = B.col[e];
             double dx, dy, dz;
-            const double nimg = min_image(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
-                                          B.pos_w[2 * np + j], dx, dy, dz);
-            const double w = B.val[k];
-            const double fx = P.c_ev * dx * w
-                            + P.zeta * P.alpha * w * (B.x[j] - vxi + P.kappa * P.L[1] * nimg);
+            const double nimg = image_separation(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
+                                                 B.pos_w[2 * np + j], B.img[e], dx, dy, dz);
+            const double w = B.val[e];
+            const double fx = P.c_ev * dx * w + P.zeta * P.alpha * w * (B.x[j] - vxi + P.kappa * P.L[1] * nimg);
             acc += dy * fx;
         }
     }

@@ -27,6 +27,8 @@ struct KParams {
     int nc[3];          // cells per axis (cell edge >= r_c)
     double inv_cw[3];   // cells per unit length
     int ncell;
+    int nslots;         // rows rounded up to a multiple of 256
+    int nchunks;        // nslots / 32
     int fast_cells;     // every axis has >= 3 cells: FP32 pre-filter with exact fallback
     float rc2_lo;       // FP32 distance^2 below this: certainly |R|^2 < r_c^2
     float rc2_hi;       // FP32 distance^2 at or above this: certainly |R|^2 >= r_c^2
@@ -41,7 +43,8 @@ struct DevState {
     double delta;             // Lees-Edwards image offset of the image at y + L_y
     long long step;           // step counter (noise key)
     long long nnz;            // off-diagonal entries of the current matrix (2 x pairs)
-    long long nnz_cap;        // capacity of col / val
+    long long nnz_slots;      // entries including the padding of the sliced layout
+    long long nnz_cap;        // capacity of col / val / img
     int overflow;             // sticky: nnz exceeded nnz_cap
     int error;                // sticky: first failing sp_status of a step (0 = none)
     // conjugate gradients
@@ -57,6 +60,9 @@ struct DevState {
     double last_res;
     double stress_xy;
     unsigned int ticket[4];
+    unsigned int bar_count;   // grid barrier of the persistent solver: arrivals
+    unsigned int bar_gen;     // and generation
+    double totals[8];         // grid-wide sums published by the persistent solver's last block
 };
 
 // Device buffers of one simulation (all in the current cell order unless noted).
@@ -74,10 +80,17 @@ struct DevBuffers {
     int* perm;       // [n] new row -> state row
     int* cell_count; // [ncell]
     int* cell_start; // [ncell + 1]
-    int* row_cnt;    // [n]
-    int* row_ptr;    // [n + 1]
-    int* col;        // [nnz_cap]
-    double* val;     // [nnz_cap] pair weights w_ij (A_ij = -alpha w_ij)
+    // Matrix in sliced ELLPACK (SELL-32-sigma256): rows are ranked by length
+    // (descending) inside windows of 256, the ranked rows form chunks of 32,
+    // and entry k of the row in slot s sits at chunk_off[s / 32] + 32 k + s % 32.
+    int* row_cnt;    // [n] off-diagonal entries of each row
+    int* slot_row;   // [nslots] row of each slot (-1: padding slot)
+    int* row_slot;   // [n]
+    int* chunk_len32;// [nchunks] 32 x the longest row of each chunk
+    int* chunk_off;  // [nchunks + 1]
+    int* col;        // [nnz_cap] partner row (padding entries: the row itself)
+    unsigned char* img; // [nnz_cap] image of the partner: (a+2) | (m+1) << 3 | (c+1) << 5
+    double* val;     // [nnz_cap] pair weights w_ij (A_ij = -alpha w_ij); padding 0
     float* val32;    // [nnz_cap] FP32 copy for the mixed solver
     double* diag;    // [n] A_ii
     double* dinv;    // [n] 1 / A_ii
@@ -95,6 +108,7 @@ struct DevBuffers {
     float4* d4;      // correction accumulated since the last fold into x
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* partials;// [kMaxPartials * 4]
+    float2* partials_df; // [kMaxPartials * 4] double-float partial sums (mixed solver)
     int* scan_tmp;   // block sums of the scans
     double* stage;   // [n][3] staging for host transfers
     DevState* st;
@@ -248,6 +262,111 @@ __device__ __forceinline__ int cell_coord(double x, double inv_cw, int nc)
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// Image code of a pair: the partner's image sits at R_j + a L_x x + m (L_y y + delta x) + c L_z z.
+__device__ __forceinline__ unsigned char image_code(int a, int m, int c)
+{
+    return (unsigned char)((a + 2) | ((m + 1) << 3) | ((c + 1) << 5));
+}
+
+// Exact separation R_i - (image of R_j) for a pair whose image indices are
+// known: the canonical minimum-image operations of min_image() with n = m
+// and the two rounded quotients replaced by a and c (equal for any pair
+// within r_c), so the result is bit-identical and needs no division.
+__device__ __forceinline__ double image_separation(const KParams& P, double delta, double xi, double yi,
+                                                   double zi, double xj, double yj, double zj,
+                                                   unsigned char code, double& dx, double& dy,
+                                                   double& dz)
+{
+    const double a = (double)((int)(code & 7) - 2);
+    const double n = (double)((int)((code >> 3) & 3) - 1);
+    const double c = (double)((int)((code >> 5) & 3) - 1);
+    dx = __dsub_rn(__dsub_rn(__dsub_rn(xi, xj), __dmul_rn(n, delta)), __dmul_rn(P.L[0], a));
+    dy = __dsub_rn(__dsub_rn(yi, yj), __dmul_rn(n, P.L[1]));
+    dz = __dsub_rn(__dsub_rn(zi, zj), __dmul_rn(P.L[2], c));
+    return n;
+}
+
+// Double-float accumulation (Knuth's TwoSum): a sum kept as an unevaluated
+// pair hi + lo of FP32 numbers, about 44 significant bits, using only the FP32
+// pipes (GB300 issues FP64 at a small fraction of the FP32 rate).
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, t);
+    return dfloat{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, float x) { return df_add(a, dfloat{x, 0.f}); }
+
+__device__ __forceinline__ dfloat warp_sum_df(dfloat v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dfloat w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// Block sum of double-float values; valid in thread 0.
+__device__ __forceinline__ dfloat block_sum_df(dfloat v, float2* sh)
+{
+    v = warp_sum_df(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    dfloat t{0.f, 0.f};
+    if (threadIdx.x < nw) t = dfloat{sh[threadIdx.x].x, sh[threadIdx.x].y};
+    if (w == 0) t = warp_sum_df(t);
+    return t;
+}
+
+// Double-float counterpart of publish_partials / reduce_partials: every block
+// publishes its sums, and the last block to arrive returns the totals (as
+// doubles, in thread 0) after summing the partials in a fixed order.
+template <int K>
+__device__ __forceinline__ bool publish_reduce_df(dfloat (&vals)[K], float2* partials, unsigned int* ticket,
+                                                  double (&out)[K])
+{
+    __shared__ float2 sh[32];
+    __shared__ bool last;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const dfloat t = block_sum_df(vals[k], sh);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = make_float2(t.hi, t.lo);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        dfloat v{0.f, 0.f};
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            const float2 p = __ldcg(partials + k * kMaxPartials + i);
+            v = df_add(v, dfloat{p.x, p.y});
+        }
+        const dfloat t = block_sum_df(v, sh);
+        out[k] = (double)t.hi + (double)t.lo;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
 // ------------------------------------------------------------------ launchers
 
 inline int grid_for(long long work, int per_block, int max_blocks)
@@ -265,8 +384,11 @@ struct Launch {
 
 // neighbors.cu
 void launch_bin(const KParams& P, DevBuffers& B, Launch L);
+// mode 0: plain scan; mode 2: the total is the matrix size with padding
+// (st->nnz_slots), and exceeding cap_check raises the overflow flag.
 void launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st,
                  int mode, Launch L);
+void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L);
 void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L);
@@ -286,12 +408,18 @@ struct CgLaunch {
 // and update (x or d += alpha p, r -= alpha q, r.r, r.z).  The true-residual
 // check is one kernel (FP64) or two (mixed: fold d into x, then FP64 residual).
 void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L);
-void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L);
-void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L);
+// probe = 1: time the kernel on the current system without touching the solver state
+void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L, int probe = 0);
+void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L,
+                      int probe = 0);
 void launch_cg_true_residual(const KParams& P, DevBuffers& B, bool mixed, bool always_check,
                              const CgLaunch& C, Launch L);
 void launch_cg_finish(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 int cg_kernels_per_iteration(bool mixed);
+void cg_prepare();   // resident-block counts of the solver kernels (once per process)
+// cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
+cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
+int cg_persistent_grid(const KParams& P, Launch L);
 int cg_kernels_per_check(bool mixed);
 
 // integrate.cu

@@ -36,8 +36,8 @@ void launch_bin(const KParams& P, DevBuffers& B, Launch L)
 // ------------------------------------------------------------ exclusive scan
 // out[k] = sum_{m<k} in[m] for k in [0, n]; out[n] is the total.  Three
 // kernels: per-chunk sums, a one-block scan of the chunk sums, and a
-// chunk-local rescan.  mode 1 also records the total as the matrix size and
-// raises the overflow flag if it exceeds cap_check.
+// chunk-local rescan.  mode 2 also records the total as the padded matrix
+// size and raises the overflow flag if it exceeds cap_check.
 
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
@@ -107,8 +107,8 @@ __global__ void k_scan_top(int* __restrict__ bsum, int nb, int* __restrict__ out
     }
     if (threadIdx.x == 0) {
         out[n] = (int)carry;
-        if (mode == 1) {
-            st->nnz = carry;
+        if (mode == 2) {
+            st->nnz_slots = carry;
             if (carry > cap_check) st->overflow = 1;
         }
     }
@@ -241,13 +241,33 @@ void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L
 
 // ------------------------------------------------------------- pair search
 
-// Visit every j != i with |R_ij|^2 < r_c^2 (the 5 % truncation of §Method).
-// Candidate cells: the 3 x 3 x 3 block around i's cell; a row of cells that
-// wraps through y = 0 or y = L_y belongs to the image displaced by -/+ delta in
-// x, so its three x cells are centred on x_i +/- delta.  Axes with fewer than
-// 3 cells are scanned whole (and then x is scanned whole when y is).  Every
-// candidate goes through the exact predicate, so the pair set does not depend
-// on the cell geometry.
+// Canonical minimum image (min_image) that also reports the two rounded
+// quotients, i.e. the image of the partner as a code.
+__device__ __forceinline__ unsigned char min_image_code(const KParams& P, double delta, double xi,
+                                                        double yi, double zi, double xj, double yj,
+                                                        double zj, double& r2)
+{
+    double dx = __dsub_rn(xi, xj);
+    double dy = __dsub_rn(yi, yj);
+    double dz = __dsub_rn(zi, zj);
+    const double n = round(__ddiv_rn(dy, P.L[1]));
+    dy = __dsub_rn(dy, __dmul_rn(n, P.L[1]));
+    dx = __dsub_rn(dx, __dmul_rn(n, delta));
+    const double a = round(__ddiv_rn(dx, P.L[0]));
+    dx = __dsub_rn(dx, __dmul_rn(P.L[0], a));
+    const double c = round(__ddiv_rn(dz, P.L[2]));
+    dz = __dsub_rn(dz, __dmul_rn(P.L[2], c));
+    r2 = sq_norm_exact(dx, dy, dz);
+    return image_code((int)a, (int)n, (int)c);
+}
+
+// Visit every j != i with |R_ij|^2 < r_c^2 (the 5 % truncation of §Method),
+// passing the image code of the partner.  Candidate cells: the 3 x 3 x 3 block
+// around i's cell; a row of cells that wraps through y = 0 or y = L_y belongs
+// to the image displaced by -/+ delta in x, so its three x cells are centred
+// on x_i +/- delta.  Axes with fewer than 3 cells are scanned whole (and then
+// x is scanned whole when y is).  Every candidate goes through the exact
+// predicate, so the pair set does not depend on the cell geometry.
 template <class F>
 __device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, double delta,
                                                           const double* __restrict__ pos,
@@ -258,11 +278,9 @@ __device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, doub
     auto scan = [&](int s0, int s1) {
         for (int j = s0; j < s1; ++j) {
             if (j == i) continue;
-            double dx, dy, dz;
-            const double nimg = min_image(P, delta, xi, yi, zi, pos[j], pos[np + j], pos[2 * np + j],
-                                          dx, dy, dz);
-            const double r2 = sq_norm_exact(dx, dy, dz);
-            if (r2 < P.rc2) visit(j, dx, dy, dz, nimg, r2);
+            double r2;
+            const unsigned char code = min_image_code(P, delta, xi, yi, zi, pos[j], pos[np + j], pos[2 * np + j], r2);
+            if (r2 < P.rc2) visit(j, code);
         }
     };
     if (P.ncell == 1) {
@@ -321,21 +339,19 @@ __device__ __forceinline__ int floor_div(int a, int b)
 }
 
 // The same pair set as for_each_neighbor_generic for boxes with >= 3 cells per
-// axis, with most of the FP64 work removed.  Each candidate cell is visited as
-// one image of the box (integer shifts a, m, c along x, y, z), so the image
-// separation R_i - (R_j + a L_x x + m (L_y y + delta x) + c L_z z) is first
-// evaluated in FP32 from FP32 positions.  Its squared length differs from the
-// exact one by less than the margin kept in rc2_lo / rc2_hi (bounded from the
-// FP32 rounding of positions, shifts, differences and sums, for box edges up
-// to L: 2^-24 (256 L r_c + 64 r_c^2)), so candidates outside the margin band
-// are decided by the FP32 value, and the few inside it by the exact FP64
-// predicate.  For an accepted pair the exact separation is the canonical
-// minimum image with n = m and the rounded quotients equal to a and c (at most
-// one image of j lies within r_c of i because every box edge is >= 3 r_c), so
-// it is evaluated with those integers and the same rounded operations,
-// without divisions.  FP32 arithmetic uses explicit round-to-nearest
+// axis, with almost no FP64 work.  Each candidate cell is visited as one image
+// of the box (integer shifts a, m, c along x, y, z), so the image separation
+// R_i - (R_j + a L_x x + m (L_y y + delta x) + c L_z z) is first evaluated in
+// FP32 from FP32 positions.  Its squared length differs from the exact one by
+// less than the margin kept in rc2_lo / rc2_hi (bounded from the FP32 rounding
+// of positions, shifts, differences and sums, for box edges up to L:
+// 2^-24 (256 L r_c + 64 r_c^2)), so candidates outside the margin band are
+// decided by the FP32 value and the few inside it by the exact FP64
+// predicate.  At most one image of j lies within r_c of i because every box
+// edge is >= 3 r_c, so the image found here is the canonical minimum image of
+// every accepted pair.  FP32 arithmetic uses explicit round-to-nearest
 // intrinsics so that the counting and filling passes decide identically.
-template <bool NEED_D, class F>
+template <class F>
 __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double delta,
                                                        const double* __restrict__ pos,
                                                        const float* __restrict__ pos32,
@@ -376,6 +392,7 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
                 const int a = floor_div(cxu, nc0);
                 const int c = rowbase + (cxu - a * nc0);
                 const float sxf = __fadd_rn(__fmul_rn((float)m, deltaf), __fmul_rn((float)a, P.Lf[0]));
+                const unsigned char code = image_code(a, m, c_img);
                 const int j1 = cell_start[c + 1];
                 for (int j = cell_start[c]; j < j1; ++j) {
                     if (j == i) continue;
@@ -386,23 +403,12 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
                                                 __fmul_rn(dzf, dzf));
                     if (r2f >= P.rc2_hi) continue;
                     if (r2f < P.rc2_lo) {
-                        if (NEED_D) {
-                            const double xj = pos[j], yj = pos[np + j], zj = pos[2 * np + j];
-                            const double n = (double)m;
-                            const double dx = __dsub_rn(__dsub_rn(__dsub_rn(xi, xj), __dmul_rn(n, delta)),
-                                                        __dmul_rn(P.L[0], (double)a));
-                            const double dy = __dsub_rn(__dsub_rn(yi, yj), __dmul_rn(n, P.L[1]));
-                            const double dz = __dsub_rn(__dsub_rn(zi, zj), __dmul_rn(P.L[2], (double)c_img));
-                            visit(j, dx, dy, dz, n, sq_norm_exact(dx, dy, dz));
-                        } else {
-                            visit(j, 0.0, 0.0, 0.0, 0.0, 0.0);
-                        }
+                        visit(j, code);
                     } else {
-                        double dx, dy, dz;
-                        const double n = min_image(P, delta, xi, yi, zi, pos[j], pos[np + j],
-                                                   pos[2 * np + j], dx, dy, dz);
-                        const double r2 = sq_norm_exact(dx, dy, dz);
-                        if (r2 < P.rc2) visit(j, dx, dy, dz, n, r2);
+                        double r2;
+                        const unsigned char ce = min_image_code(P, delta, xi, yi, zi, pos[j], pos[np + j],
+                                                                pos[2 * np + j], r2);
+                        if (r2 < P.rc2) visit(j, ce);
                     }
                 }
             }
@@ -410,7 +416,7 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
     }
 }
 
-template <bool NEED_D, class F>
+template <class F>
 __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta,
                                                   const double* __restrict__ pos,
                                                   const float* __restrict__ pos32,
@@ -418,23 +424,24 @@ __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta
                                                   double xi, double yi, double zi, F&& visit)
 {
     if (P.fast_cells)
-        for_each_neighbor_fast<NEED_D>(P, delta, pos, pos32, cell_start, i, xi, yi, zi, visit);
+        for_each_neighbor_fast(P, delta, pos, pos32, cell_start, i, xi, yi, zi, visit);
     else
         for_each_neighbor_generic(P, delta, pos, cell_start, i, xi, yi, zi, visit);
 }
 
 __global__ void k_nbr_count(KParams P, const double* __restrict__ pos, const float* __restrict__ pos32,
                             const int* __restrict__ cell_start, int* __restrict__ row_cnt,
-                            const DevState* st)
+                            DevState* st)
 {
     if (st->error | st->overflow) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) st->nnz = 0;
     if (i >= P.n) return;
     const double delta = st->delta;
     const int np = P.npad;
     int cnt = 0;
-    for_each_neighbor<false>(P, delta, pos, pos32, cell_start, i, pos[i], pos[np + i], pos[2 * np + i],
-                             [&](int, double, double, double, double, double) { ++cnt; });
+    for_each_neighbor(P, delta, pos, pos32, cell_start, i, pos[i], pos[np + i], pos[2 * np + i],
+                      [&](int, unsigned char) { ++cnt; });
     row_cnt[i] = cnt;
 }
 
@@ -442,6 +449,39 @@ void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L)
 {
     k_nbr_count<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B.pos_w, B.pos32, B.cell_start,
                                                                     B.row_cnt, B.st);
+}
+
+// Slices of the matrix: inside each window of 256 rows, rank the rows by
+// length (longest first, ties by row) so that each chunk of 32 ranked rows has
+// rows of nearly equal length; a chunk is stored column-major with the length
+// of its longest row.  Also sums the entries of the matrix.
+__global__ void __launch_bounds__(256) k_sell_plan(KParams P, DevBuffers B)
+{
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    __shared__ int cnt_s[256];
+    __shared__ double sh[32];
+    const int t = threadIdx.x;
+    const int row = blockIdx.x * 256 + t;
+    const int c = row < P.n ? B.row_cnt[row] : -1;
+    cnt_s[t] = c;
+    __syncthreads();
+    int rank = 0;
+    for (int u = 0; u < 256; ++u) {
+        const int cu = cnt_s[u];
+        rank += (cu > c) || (cu == c && u < t);
+    }
+    const int slot = blockIdx.x * 256 + rank;
+    B.slot_row[slot] = row < P.n ? row : -1;
+    if (row < P.n) B.row_slot[row] = slot;
+    if ((rank & 31) == 0) B.chunk_len32[slot >> 5] = (c > 0 ? c : 0) * 32;
+    const double tot = block_sum((double)(c > 0 ? c : 0), sh);
+    if (t == 0) atomicAdd((unsigned long long*)&st->nnz, (unsigned long long)tot);
+}
+
+void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L)
+{
+    k_sell_plan<<<P.nslots / 256, 256, 0, L.stream>>>(P, B);
 }
 
 // Row i of Eq. algebra from its pair sums (§Method, Eq. F and Eq. vc):
@@ -478,8 +518,45 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
     B.b[2 * np + i] = F2 / P.zeta;
 }
 
-// Pair search writing the CSR columns; with ASSEMBLE also the weights and the
-// row of Eq. algebra in the same pass.
+// Weights and pair sums of row i from its stored entries (FP64; the
+// entries' image codes give the exact separations without divisions).
+// Padding entries get weight 0.
+__device__ __forceinline__ void assemble_row(const KParams& P, const DevBuffers& B, int i, double delta,
+                                             unsigned long long step, int use_inj)
+{
+    const int np = P.npad;
+    const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
+    const int slot = B.row_slot[i];
+    const int base = B.chunk_off[slot >> 5] + (slot & 31);
+    const int clen = (B.chunk_off[(slot >> 5) + 1] - B.chunk_off[slot >> 5]) >> 5;
+    const int cnt = B.row_cnt[i];
+    double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+        const int e = base + 32 * k;
+        const int j = B.col[e];
+        double dx, dy, dz;
+        const double n = image_separation(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
+                                          B.pos_w[2 * np + j], B.img[e], dx, dy, dz);
+        const double w = exp(-sq_norm_exact(dx, dy, dz) / P.two_lambda2);
+        B.val[e] = w;
+        B.val32[e] = (float)w;
+        sw += w;
+        fx += dx * w;
+        fy += dy * w;
+        fz += dz * w;
+        nw += n * w;
+    }
+    for (int k = cnt; k < clen; ++k) {
+        B.val[base + 32 * k] = 0.0;
+        B.val32[base + 32 * k] = 0.f;
+    }
+    finish_row(P, B, i, yi, step, use_inj, sw, fx, fy, fz, nw);
+}
+
+// Pair search writing the sliced columns and image codes (FP32 decisions);
+// with ASSEMBLE the row is then assembled in a second, converged pass, so the
+// FP64 work runs once per accepted entry rather than inside the divergent
+// candidate loop.
 template <bool ASSEMBLE>
 __global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
 {
@@ -488,35 +565,29 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const double delta = st->delta;
-    const unsigned long long step = (unsigned long long)st->step;
     const int np = P.npad;
     const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
-    int k = B.row_ptr[i];
-    const int kend = B.row_ptr[i + 1];
-    double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
+    const int slot = B.row_slot[i];
+    const int base = B.chunk_off[slot >> 5] + (slot & 31);
+    const int clen = (B.chunk_off[(slot >> 5) + 1] - B.chunk_off[slot >> 5]) >> 5;
+    const int cnt = B.row_cnt[i];
+    int k = 0;
     int* __restrict__ col = B.col;
-    double* __restrict__ val = B.val;
-    float* __restrict__ val32 = B.val32;
-    for_each_neighbor<ASSEMBLE>(P, delta, B.pos_w, B.pos32, B.cell_start, i, xi, yi, zi,
-                                [&](int j, double dx, double dy, double dz, double nimg, double r2) {
-                                    if (k < kend) {
-                                        col[k] = j;
-                                        if (ASSEMBLE) {
-                                            const double w = exp(-r2 / P.two_lambda2);
-                                            val[k] = w;
-                                            val32[k] = (float)w;
-                                            sw += w;
-                                            fx += dx * w;
-                                            fy += dy * w;
-                                            fz += dz * w;
-                                            nw += nimg * w;
-                                        }
-                                    }
-                                    ++k;
-                                });
+    unsigned char* __restrict__ img = B.img;
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, xi, yi, zi, [&](int j, unsigned char code) {
+        if (k < cnt) {
+            col[base + 32 * k] = j;
+            img[base + 32 * k] = code;
+        }
+        ++k;
+    });
     // the counting pass and this one must agree; a mismatch is reported, never written past
-    if (k != kend) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
-    if (ASSEMBLE) finish_row(P, B, i, yi, step, use_inj, sw, fx, fy, fz, nw);
+    if (k != cnt) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
+    for (int kk = cnt; kk < clen; ++kk) {
+        col[base + 32 * kk] = i;
+        img[base + 32 * kk] = image_code(0, 0, 0);
+    }
+    if (ASSEMBLE) assemble_row(P, B, i, delta, (unsigned long long)st->step, use_inj);
 }
 
 void launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool mixed,
@@ -530,34 +601,14 @@ void launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_in
         k_nbr_fill<false><<<g, 128, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
 }
 
-// Assembly from an existing pair list (same arithmetic and order as the fused pass).
+// Assembly from existing pairs (the same arithmetic as the fused pass).
 __global__ void k_assemble(KParams P, DevBuffers B, int use_inj)
 {
     const DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
-    const double delta = st->delta;
-    const unsigned long long step = (unsigned long long)st->step;
-    const int np = P.npad;
-    const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
-    double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
-    for (int k = B.row_ptr[i]; k < B.row_ptr[i + 1]; ++k) {
-        const int j = B.col[k];
-        double dx, dy, dz;
-        const double nimg = min_image(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
-                                      B.pos_w[2 * np + j], dx, dy, dz);
-        const double r2 = sq_norm_exact(dx, dy, dz);
-        const double w = exp(-r2 / P.two_lambda2);
-        B.val[k] = w;
-        B.val32[k] = (float)w;
-        sw += w;
-        fx += dx * w;
-        fy += dy * w;
-        fz += dz * w;
-        nw += nimg * w;
-    }
-    finish_row(P, B, i, yi, step, use_inj, sw, fx, fy, fz, nw);
+    assemble_row(P, B, i, st->delta, (unsigned long long)st->step, use_inj);
 }
 
 void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool mixed, Launch L)

@@ -34,6 +34,7 @@ struct sp_sim {
     long long nnz_cap = 0;
     bool use_inj = false;
     bool host_loop = false;       // CG loop driven from the host
+    bool persistent = true;       // mixed solver: one cooperative launch per solve
     bool built = false;           // pairs match the current positions
     bool assembled = false;
     cudaGraph_t step_graph = nullptr;
@@ -102,12 +103,15 @@ int alloc_pairs(sp_sim* s, long long cap)
     cudaFree(B.col);
     cudaFree(B.val);
     cudaFree(B.val32);
+    cudaFree(B.img);
     B.col = nullptr;
     B.val = nullptr;
     B.val32 = nullptr;
+    B.img = nullptr;
     SS_TRY(dev_alloc(s, &B.col, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val32, (size_t)cap));
+    SS_TRY(dev_alloc(s, &B.img, (size_t)cap));
     s->nnz_cap = cap;
     s->st_host->nnz_cap = cap;
     SS_CUDA(cudaMemcpyAsync(&B.st->nnz_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, s->stream));
@@ -169,6 +173,8 @@ void derive(const sp_params& p, KParams& k, int npad)
         ncell = 1;
     }
     k.ncell = (int)ncell;
+    k.nslots = (k.n + 255) / 256 * 256;
+    k.nchunks = k.nslots / 32;
     k.fast_cells = (k.nc[0] >= 3 && k.nc[1] >= 3 && k.nc[2] >= 3) ? 1 : 0;
     // FP32 pre-filter margin on |R|^2: 2^-24 (256 L r_c + 64 r_c^2) bounds the
     // FP32 rounding of positions, image shifts, differences, squares and sums
@@ -203,8 +209,9 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs)
         launches += 6;
     }
     launch_nbr_count(P, B, L);
-    launch_scan(B.row_cnt, B.row_ptr, P.n, B.scan_tmp, s->nnz_cap, B.st, 1, L);
-    return launches + 4;
+    launch_sell_plan(P, B, L);
+    launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
+    return launches + 5;
 }
 
 // Conditional WHILE node holding one CG iteration, with an IF node for the
@@ -288,7 +295,10 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
     Launch L = launch_of(s, cs);
     launch_cg_init(P, B, from_x, mixed(s), L);
     *launches += 1;
-    if (in_graph) {
+    if (mixed(s) && s->persistent) {
+        SS_CUDA(launch_cg32_persistent(P, B, L));
+        *launches += 1;
+    } else if (in_graph) {
         SS_TRY(capture_cg_loop(s, cs));
     } else {
         SS_TRY(host_cg_loop(s, launches));
@@ -384,7 +394,7 @@ int clear_flags(sp_sim* s)
 
 int grow_pairs(sp_sim* s)
 {
-    long long need = s->st_host->nnz;
+    long long need = s->st_host->nnz_slots;
     long long cap = std::max<long long>((long long)(need * 1.25) + 1024, s->nnz_cap * 3 / 2);
     if (cap > 0x7fffffffll) {
         s->err = "pair count exceeds 2^31";
@@ -467,7 +477,8 @@ int sp_sim_destroy(sp_sim* s)
     free_graphs(s);
     DevBuffers& B = s->B;
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
-                    B.cell_count, B.cell_start, B.row_cnt, B.row_ptr, B.col, B.val, B.val32, B.diag,
+                    B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
+                    B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
                     B.xi_inj, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
@@ -512,9 +523,12 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         return fail(SP_ERR_CUDA);
     }
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    cg_prepare();
     if (s->num_sms < 1) s->num_sms = 1;
     const char* hl = std::getenv("SHEARSIM_HOST_LOOP");
     s->host_loop = hl && hl[0] == '1';
+    const char* pe = std::getenv("SHEARSIM_PERSISTENT");
+    s->persistent = !(pe && pe[0] == '0');
     if (p->stream) {
         s->stream = (cudaStream_t)p->stream;
     } else {
@@ -549,7 +563,10 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.cell_count, s->kp.ncell));
     A(dev_alloc(s, &B.cell_start, (size_t)s->kp.ncell + 1));
     A(dev_alloc(s, &B.row_cnt, n));
-    A(dev_alloc(s, &B.row_ptr, (size_t)n + 1));
+    A(dev_alloc(s, &B.slot_row, (size_t)s->kp.nslots));
+    A(dev_alloc(s, &B.row_slot, n));
+    A(dev_alloc(s, &B.chunk_len32, (size_t)s->kp.nchunks));
+    A(dev_alloc(s, &B.chunk_off, (size_t)s->kp.nchunks + 1));
     A(dev_alloc(s, &B.diag, n));
     A(dev_alloc(s, &B.dinv, n));
     A(dev_alloc(s, &B.diag32, n));
@@ -565,7 +582,8 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.q4, (size_t)npad));
     A(dev_alloc(s, &B.d4, (size_t)npad));
     A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
-    A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(n, s->kp.ncell) / 4096 + 2)));
+    A(dev_alloc(s, &B.partials_df, 4 * (size_t)kMaxPartials));
+    A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(std::max(n, s->kp.ncell), s->kp.nchunks) / 4096 + 2)));
     A(dev_alloc(s, &B.stage, 3 * (size_t)n));
     A(dev_alloc(s, &B.st, 1));
     if (a != SP_OK) return fail(a);
@@ -728,8 +746,9 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
     }
     const DevState& h = *s->st_host;
     if (!s->host_loop) {
-        launches += h.steps_in_call * s->fixed_launches_step + h.iter_sum * cg_kernels_per_iteration(mixed(s)) +
-                    h.true_checks * cg_kernels_per_check(mixed(s));
+        launches += h.steps_in_call * s->fixed_launches_step;
+        if (!(mixed(s) && s->persistent))
+            launches += h.iter_sum * cg_kernels_per_iteration(mixed(s)) + h.true_checks * cg_kernels_per_check(mixed(s));
     }
     if (info) {
         info->status = status;
@@ -769,7 +788,8 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         cls.push_back(c);
         return SP_OK;
     };
-    enum { START = -1, SORT = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER, COUNT, FILL };
+    enum { START = -1, SORT = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER, COUNT, FILL, PERSIST, INIT, STRESS,
+           INTEGRATE };
     launch_reset_step_stats(B.st, s->stream);
     int rc = mark(START);
     if (rc == SP_OK) {
@@ -783,16 +803,23 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         }
         mark(SORT);
         launch_nbr_count(P, B, L);
-        launch_scan(B.row_cnt, B.row_ptr, P.n, B.scan_tmp, s->nnz_cap, B.st, 1, L);
+        launch_sell_plan(P, B, L);
+        launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
         mark(COUNT);
         launch_nbr_fill(P, B, true, s->use_inj, mx, L);
         rc = mark(FILL);
     }
     if (rc == SP_OK) {
         launch_cg_init(P, B, s->p.warm_start == SP_WARM_PREV, mx, L);
-        rc = mark(OTHER);
+        rc = mark(INIT);
     }
-    for (int it = 0; rc == SP_OK && it < P.max_iter + kMaxCgRestarts + 8; ++it) {
+    const bool pers = mx && s->persistent;
+    if (rc == SP_OK && pers) {
+        if (launch_cg32_persistent(P, B, L) != cudaSuccess) rc = SP_ERR_CUDA;
+        if (rc == SP_OK) rc = mark(PERSIST);
+        out->persistent_blocks = cg_persistent_grid(P, L);
+    }
+    for (int it = 0; rc == SP_OK && !pers && it < P.max_iter + kMaxCgRestarts + 8; ++it) {
         launch_cg_spmv(P, B, mx, L);
         mark(SPMV);
         launch_cg_update(P, B, mx, C, L);
@@ -812,14 +839,40 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     }
     if (rc == SP_OK) {
         launch_cg_finish(P, B, mx, L);
+        mark(OTHER);
         launch_stress(P, B, L);
+        mark(STRESS);
         launch_integrate(P, B, L);
-        rc = mark(OTHER);
+        rc = mark(INTEGRATE);
     }
     if (rc == SP_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
     if (rc == SP_OK) rc = read_state(s);
+    // back-to-back launches of the two loop kernels on the system just solved
+    // (probe mode: same work, solver scalars untouched), one event pair each
+    if (rc == SP_OK && !s->st_host->error && !s->st_host->overflow) {
+        const int reps = 20;
+        cudaEvent_t e[3];
+        for (auto& x : e) cudaEventCreate(&x);
+        cudaEventRecord(e[0], s->stream);
+        for (int k = 0; k < reps; ++k) launch_cg_spmv(P, B, mx, L, 1);
+        cudaEventRecord(e[1], s->stream);
+        for (int k = 0; k < reps; ++k) launch_cg_update(P, B, mx, C, L, 1);
+        cudaEventRecord(e[2], s->stream);
+        if (cudaEventSynchronize(e[2]) == cudaSuccess) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, e[0], e[1]);
+            cudaEventElapsedTime(&b, e[1], e[2]);
+            out->spmv_probe_ms = a / reps;
+            out->update_probe_ms = b / reps;
+            out->probe_reps = reps;
+        } else {
+            rc = SP_ERR_CUDA;
+        }
+        for (auto& x : e) cudaEventDestroy(x);
+    }
     double* acc[] = {&out->sort_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
-                     &out->direction_ms, &out->other_ms, &out->count_ms, &out->fill_ms};
+                     &out->direction_ms, &out->other_ms, &out->count_ms, &out->fill_ms, &out->persistent_ms,
+                     &out->init_ms, &out->stress_ms, &out->integrate_ms};
     for (size_t k = 1; rc == SP_OK && k < ev.size(); ++k) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
@@ -831,6 +884,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         return rc;
     }
     out->build_ms = out->sort_ms + out->count_ms + out->fill_ms;
+    out->other_ms += out->init_ms + out->stress_ms + out->integrate_ms;
     const DevState& h = *s->st_host;
     if (h.overflow) {
         // the pair storage was too small for this step: grow it and report the failure
@@ -842,9 +896,15 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     out->spmv_launches = h.iter;
     out->update_launches = h.iter;
     out->direction_launches = 0;   // fused into the SpMV kernel
-    out->true_residual_launches = (int)h.true_checks * cg_kernels_per_check(mx);
+    out->true_residual_launches = pers ? 0 : (int)h.true_checks * cg_kernels_per_check(mx);
+    out->true_checks = (int)h.true_checks;
+    if (pers) {
+        out->spmv_launches = 0;
+        out->update_launches = 0;
+    }
     out->n = P.n;
     out->nnz = h.nnz;
+    out->nnz_slots = h.nnz_slots;
     out->precision = s->p.precision;
     s->built = false;
     s->assembled = false;
@@ -942,22 +1002,37 @@ int sp_get_num_pairs(sp_sim* s, int64_t* npairs)
 }
 
 namespace {
-// The CSR of the current matrix on the host, rows in cell order.
-int fetch_csr(sp_sim* s, std::vector<int>& row_ptr, std::vector<int>& col, std::vector<double>& val,
-              std::vector<int>& ids)
+// The pairs of the current matrix on the host, as (row, col, weight) entries
+// in row order (rows in cell order).
+int fetch_entries(sp_sim* s, std::vector<int>& rows, std::vector<int>& cols, std::vector<double>& vals,
+                  std::vector<int>& ids)
 {
     const int n = s->kp.n;
     SS_TRY(read_state(s));
-    const long long nnz = s->st_host->nnz;
-    row_ptr.resize(n + 1);
-    col.resize(nnz);
-    val.resize(nnz);
+    const long long slots = s->st_host->nnz_slots;
+    std::vector<int> cnt(n), row_slot(n), chunk_off(s->kp.nchunks + 1), col(slots);
+    std::vector<double> val(slots);
     ids.resize(n);
-    SS_CUDA(cudaMemcpyAsync(row_ptr.data(), s->B.row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s->stream));
-    SS_CUDA(cudaMemcpyAsync(col.data(), s->B.col, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s->stream));
-    SS_CUDA(cudaMemcpyAsync(val.data(), s->B.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(cnt.data(), s->B.row_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(row_slot.data(), s->B.row_slot, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(chunk_off.data(), s->B.chunk_off, sizeof(int) * (s->kp.nchunks + 1),
+                            cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(col.data(), s->B.col, sizeof(int) * slots, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaMemcpyAsync(val.data(), s->B.val, sizeof(double) * slots, cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaMemcpyAsync(ids.data(), s->B.id_w, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaStreamSynchronize(s->stream));
+    rows.clear();
+    cols.clear();
+    vals.clear();
+    for (int r = 0; r < n; ++r) {
+        const int slot = row_slot[r];
+        const int base = chunk_off[slot >> 5] + (slot & 31);
+        for (int k = 0; k < cnt[r]; ++k) {
+            rows.push_back(r);
+            cols.push_back(col[base + 32 * k]);
+            vals.push_back(val[base + 32 * k]);
+        }
+    }
     return SP_OK;
 }
 }  // namespace
@@ -966,20 +1041,18 @@ int sp_get_neighbors(sp_sim* s, int64_t cap, int64_t* pairs_host, int64_t* npair
 {
     if (!s || !npairs) return SP_ERR_INVALID_ARG;
     SS_TRY(set_device(s));
-    std::vector<int> rp, col, ids;
-    std::vector<double> val;
-    SS_TRY(fetch_csr(s, rp, col, val, ids));
+    std::vector<int> rows, cols, ids;
+    std::vector<double> vals;
+    SS_TRY(fetch_entries(s, rows, cols, vals, ids));
     long long m = 0;
-    for (int r = 0; r < s->kp.n; ++r) {
-        for (int k = rp[r]; k < rp[r + 1]; ++k) {
-            const int a = ids[r], b = ids[col[k]];
-            if (a < b) {
-                if (pairs_host && m < cap) {
-                    pairs_host[2 * m] = a;
-                    pairs_host[2 * m + 1] = b;
-                }
-                ++m;
+    for (size_t e = 0; e < rows.size(); ++e) {
+        const int a = ids[rows[e]], b = ids[cols[e]];
+        if (a < b) {
+            if (pairs_host && m < cap) {
+                pairs_host[2 * m] = a;
+                pairs_host[2 * m + 1] = b;
             }
+            ++m;
         }
     }
     *npairs = m;
@@ -996,9 +1069,9 @@ int sp_get_system(sp_sim* s, double* diag_host, double* b_host, double* w_host)
     SS_TRY(set_device(s));
     const int n = s->kp.n;
     const size_t np = (size_t)s->kp.npad;
-    std::vector<int> rp, col, ids;
-    std::vector<double> val;
-    SS_TRY(fetch_csr(s, rp, col, val, ids));
+    std::vector<int> rows, cols, ids;
+    std::vector<double> vals;
+    SS_TRY(fetch_entries(s, rows, cols, vals, ids));
     if (diag_host) {
         std::vector<double> d(n);
         SS_CUDA(cudaMemcpy(d.data(), s->B.diag, sizeof(double) * n, cudaMemcpyDeviceToHost));
@@ -1012,9 +1085,8 @@ int sp_get_system(sp_sim* s, double* diag_host, double* b_host, double* w_host)
     }
     if (w_host) {
         long long m = 0;
-        for (int r = 0; r < n; ++r)
-            for (int k = rp[r]; k < rp[r + 1]; ++k)
-                if (ids[r] < ids[col[k]]) w_host[m++] = val[k];
+        for (size_t e = 0; e < rows.size(); ++e)
+            if (ids[rows[e]] < ids[cols[e]]) w_host[m++] = vals[e];
     }
     return SP_OK;
 }

@@ -415,3 +415,34 @@ def test_mixed_full_size_against_fp64_gpu(full):
     # single-solve velocity error of the mixed path vs the FP64 solve (to 1e-12): <= cond * 1e-8
     assert np.abs(v - v64).max() <= 1e-6 * np.abs(v64).max()
     sim.close()
+
+
+def test_persistent_and_multikernel_mixed_solvers_agree(monkeypatch):
+    """The one-launch mixed solver and the two-kernels-per-iteration one run the same
+    iteration; both meet the FP64 tolerance and agree to the solve accuracy."""
+    n = 20000
+    L = synth.box_length(n)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SHEARSIM_PERSISTENT", flag)
+        sim, p, pos = make(n, L, seed=31, tol=1e-10, precision="mixed", delta=0.4 * L)
+        sim.build_neighbors()
+        sim.assemble()
+        info = sim.solve_velocities()
+        assert info["status"] == 0 and info["residual"] <= 1e-10, (flag, info)
+        outs.append(sim.get_velocities())
+        sim.close()
+    assert np.abs(outs[0] - outs[1]).max() <= 2e-8 * np.abs(outs[1]).max()
+
+
+def test_persistent_mixed_steps_are_deterministic():
+    n = 30000
+    L = synth.box_length(n)
+    res = []
+    for _ in range(2):
+        sim, p, pos = make(n, L, seed=8, tol=1e-8, precision="mixed", warm_start="prev")
+        info = sim.step(3)
+        assert info["status"] == 0
+        res.append(sim.get_positions())
+        sim.close()
+    assert np.array_equal(res[0], res[1])

@@ -146,12 +146,15 @@ int sp_solve_velocities(sp_sim* sim, const double* v0_dev, sp_solve_info* info);
 int sp_step(sp_sim* sim, int32_t nsteps, sp_step_info* info);
 
 /* Eq. Sfactor at q_z = 0 on the sheared reciprocal lattice of the current
- * snapshot: q_x = 2 pi kx / L_x, q_y = 2 pi ky / L_y - (delta / L_y) q_x for
+ * positions: q_x = 2 pi kx / L_x, q_y = 2 pi ky / L_y - (delta / L_y) q_x for
  * kx in [-nkx, nkx], ky in [-nky, nky].  Outputs (host, (2nkx+1)(2nky+1)
  * entries, kx slowest): S_host = |sum_c exp(-i q . R_c)|^2 / n, qx_host, qy_host
- * (either q array may be NULL).  The density is spread on a grid of
- * `grid` x `grid` cells in the sheared frame by cloud-in-cell and the window is
- * divided out; |kx|, |ky| must stay below grid / 4. */
+ * (either q array may be NULL).
+ * grid > 0: the density is spread on a grid x grid mesh of the sheared frame
+ * x' = x - (delta/L_y) y by cloud-in-cell (z summed), transformed, and the CIC
+ * window divided out; |kx|, |ky| must stay below grid / 4 (aliasing grows
+ * towards the mesh's Nyquist limit).  grid = 0: exact direct sum over the
+ * particles for every mode (cost n x modes). */
 int sp_structure_factor(sp_sim* sim, int32_t nkx, int32_t nky, int32_t grid, double* S_host,
                         double* qx_host, double* qy_host);
 
@@ -224,6 +227,32 @@ int sp_set_noise(sp_sim* sim, const double* xi_host);
  * checking: out_host[4 * k ...] = Philox(ctr = (ids[k], step, 0, 0), key = (seed, 0)). */
 int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count,
                      const int64_t* ids_host, uint64_t* out_host);
+
+/* ---- batches of independent replicas ----
+ *
+ * Ensembles of simulations with their own box, particle count, shear rate
+ * and seed, advanced together: one time step of the whole batch is one CUDA
+ * graph whose pair searches and assemblies run as parallel branches and
+ * whose velocity solves of all replicas are one cooperative persistent launch
+ * (blocks shared out in proportion to each replica's rows; every replica
+ * keeps its own CG scalars and convergence).  Every replica must use
+ * SP_PREC_MIXED on the same device; params[k].stream is ignored (the batch
+ * owns its stream). */
+typedef struct sp_batch sp_batch;
+
+/* R replicas (1 <= R <= 4096); pos_host: NULL, or R pointers to [n_k][3]
+ * initial positions (entries may be NULL for positions drawn from the seed). */
+int sp_batch_create(int32_t R, const sp_params* params, const double* const* pos_host, sp_batch** out);
+int sp_batch_destroy(sp_batch* b);
+/* nsteps steps of every replica; info: NULL or [R] step infos.  A replica whose
+ * pair storage overflows is regrown and catches up on its own. */
+int sp_batch_step(sp_batch* b, int32_t nsteps, sp_step_info* info);
+/* Replica k as a simulation handle for state access (owned by the batch;
+ * never pass it to sp_sim_destroy). */
+int sp_batch_get_sim(sp_batch* b, int32_t k, sp_sim** sim);
+/* Blocks of the cooperative launch given to each replica, [R]. */
+int sp_batch_blocks(sp_batch* b, int32_t* blocks);
+const char* sp_batch_last_error(const sp_batch* b);
 
 /* ---- allocation-free solve ----
  *

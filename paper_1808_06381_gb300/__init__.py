@@ -105,13 +105,18 @@ def load(path: str = LIB_PATH):
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
             ("sp_profile_step", [vp, P(sp_kernel_profile)]),
-            ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)])]
+            ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)]),
+            ("sp_batch_create", [i32, vp, vp, P(vp)]), ("sp_batch_destroy", [vp]),
+            ("sp_batch_step", [vp, i32, vp]), ("sp_batch_get_sim", [vp, i32, P(vp)]),
+            ("sp_batch_blocks", [vp, vp])]
     for name, args in sims:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
     lib.sp_last_error.argtypes = [vp]
     lib.sp_last_error.restype = ctypes.c_char_p
+    lib.sp_batch_last_error.argtypes = [vp]
+    lib.sp_batch_last_error.restype = ctypes.c_char_p
     lib.sp_kappa_from_kappa_tau.argtypes = [d, d, d, d]
     lib.sp_kappa_from_kappa_tau.restype = d
     _lib = lib
@@ -189,6 +194,7 @@ class Simulation:
         self.n = int(n)
         self.L = tuple(float(x) for x in L)
         self.params = p
+        self._borrowed = False
         pos = None
         if positions is not None:
             pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(self.n, 3)
@@ -196,11 +202,38 @@ class Simulation:
         _check(lib.sp_sim_create(ctypes.byref(p), _p(pos) if pos is not None else None, ctypes.byref(h)))
         self._h = h
 
+    @staticmethod
+    def make_params(n, L, kappa, alpha=4.0, eps=1.0, zeta=1.0, kT=1.0, dt=0.01, rc=1.0, seed=0,
+                    precision="mixed", warm_start="prev", cg_tol=1e-8, cg_max_iter=1000, device=0) -> sp_params:
+        p = sp_params()
+        p.n = int(n)
+        for a in range(3):
+            p.L[a] = float(L[a])
+        p.rc, p.alpha, p.eps, p.zeta, p.kT, p.kappa, p.dt = rc, alpha, eps, zeta, kT, kappa, dt
+        p.seed = int(seed)
+        p.precision = PREC[precision]
+        p.warm_start = WARM[warm_start]
+        p.cg_tol = cg_tol
+        p.cg_max_iter = cg_max_iter
+        p.device = device
+        p.stream = None
+        return p
+
+    @classmethod
+    def borrowed(cls, handle, n, L) -> "Simulation":
+        """A view of a simulation owned elsewhere (a batch replica); close() does not free it."""
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p(handle)
+        self._borrowed = True
+        self.n = int(n)
+        self.L = tuple(float(x) for x in L)
+        return self
+
     # lifetime
     def close(self):
-        if getattr(self, "_h", None) is not None and self._h.value:
+        if getattr(self, "_h", None) is not None and self._h.value and not getattr(self, "_borrowed", False):
             load().sp_sim_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -317,3 +350,69 @@ class Simulation:
         else:
             xi = np.ascontiguousarray(xi, dtype=np.float64)
             self._c(load().sp_set_noise(self._h, _p(xi)))
+
+
+class Batch:
+    """Independent replicas advanced together (sp_batch_*): one graph per step with one
+    cooperative launch solving every replica's velocities."""
+
+    def __init__(self, replicas, positions=None):
+        """replicas: list of dicts of Simulation.make_params arguments (precision is mixed)."""
+        lib = load()
+        self.R = len(replicas)
+        arr = (sp_params * self.R)()
+        self._shapes = []
+        for k, kw in enumerate(replicas):
+            kw = dict(kw)
+            kw.setdefault("precision", "mixed")
+            arr[k] = Simulation.make_params(**kw)
+            self._shapes.append((int(kw["n"]), tuple(kw["L"])))
+        self._keep = []
+        pos_arr = None
+        if positions is not None:
+            pos_arr = (ctypes.c_void_p * self.R)()
+            for k, pos in enumerate(positions):
+                if pos is None:
+                    pos_arr[k] = None
+                else:
+                    a = np.ascontiguousarray(pos, dtype=np.float64)
+                    self._keep.append(a)
+                    pos_arr[k] = a.ctypes.data
+        h = ctypes.c_void_p()
+        rc = lib.sp_batch_create(self.R, ctypes.cast(arr, ctypes.c_void_p),
+                                 ctypes.cast(pos_arr, ctypes.c_void_p) if pos_arr is not None else None,
+                                 ctypes.byref(h))
+        if rc != SP_OK:
+            raise ShearsimError(rc, (lib.sp_batch_last_error(None) or b"").decode())
+        self._h = h
+
+    def step(self, nsteps: int = 1, raise_on_error: bool = True) -> list:
+        infos = (sp_step_info * self.R)()
+        rc = load().sp_batch_step(self._h, int(nsteps), ctypes.cast(infos, ctypes.c_void_p))
+        if raise_on_error and rc != SP_OK:
+            raise ShearsimError(rc, (load().sp_batch_last_error(self._h) or b"").decode())
+        return [{"status": x.status, "steps_done": x.steps_done, "cg_iterations": x.cg_iterations,
+                 "max_iterations": x.max_iterations, "last_residual": x.last_residual,
+                 "stress_xy": x.stress_xy, "kernel_launches": x.kernel_launches} for x in infos]
+
+    def sim(self, k: int) -> Simulation:
+        h = ctypes.c_void_p()
+        _check(load().sp_batch_get_sim(self._h, int(k), ctypes.byref(h)))
+        n, L = self._shapes[k]
+        return Simulation.borrowed(h.value, n, L)
+
+    def blocks(self) -> np.ndarray:
+        out = np.zeros(self.R, dtype=np.int32)
+        _check(load().sp_batch_blocks(self._h, _p(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sp_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

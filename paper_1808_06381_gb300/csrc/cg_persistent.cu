@@ -41,13 +41,13 @@ struct PShared {
 
 // Grid barrier (all blocks of a cooperative launch).  Returns false when the
 // solve must stop (an error was raised anywhere, including a barrier timeout).
-__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShared& sh)
+__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShared& sh, int nb)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int target = gen + 1u;
         __threadfence();
-        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) {
             atomicExch(&st->bar_count, 0u);
             __threadfence();
             atomicExch(&st->bar_gen, target);
@@ -69,62 +69,6 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShar
     return sh.flag == 0;
 }
 
-// Publish this block's double-float sums (K values) for the next barrier.
-template <int K>
-__device__ __forceinline__ void publish_df(const dfloat (&v)[K], float2* partials, PShared& sh)
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const dfloat t = block_sum_df(v[k], sh.df);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = make_float2(t.hi, t.lo);
-    }
-}
-
-// After the barrier: warp 0 of every block sums all blocks' partials in the
-// same order; the totals are valid in thread 0 only (no barrier here).
-template <int K>
-__device__ __forceinline__ void total_df(const float2* partials, double (&out)[K])
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        out[k] = 0.0;
-        if (threadIdx.x < 32) {
-            dfloat v{0.f, 0.f};
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-                const float2 p = __ldcg(partials + k * kMaxPartials + b);
-                v = df_add(v, dfloat{p.x, p.y});
-            }
-            v = warp_sum_df(v);
-            if (threadIdx.x == 0) out[k] = (double)v.hi + (double)v.lo;
-        }
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void publish_d(const double (&v)[K], double* partials, PShared& sh)
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double t = block_sum(v[k], sh.d);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = t;
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void total_d(const double* partials, double (&out)[K])
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        out[k] = 0.0;
-        if (threadIdx.x < 32) {
-            double v = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(partials + k * kMaxPartials + b);
-            v = warp_sum(v);
-            if (threadIdx.x == 0) out[k] = v;
-        }
-    }
-}
-
 // Barrier fused with the reduction of K sums: every block publishes its block
 // sum; the last block to arrive sums all blocks' partials (every thread a
 // strided share, in the same fixed order whichever block is last), stores the
@@ -133,17 +77,17 @@ __device__ __forceinline__ void total_d(const double* partials, double (&out)[K]
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
                                                const dfloat (&v)[K], float2* partials, double* totals,
-                                               double (&out)[K])
+                                               double (&out)[K], int bid, int nb)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const dfloat t = block_sum_df(v[k], sh.df);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = make_float2(t.hi, t.lo);
+        if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = make_float2(t.hi, t.lo);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        sh.flag = (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) ? 1 : 0;
+        sh.flag = (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) ? 1 : 0;
     }
     __syncthreads();
     const unsigned int target = gen + 1u;
@@ -152,7 +96,7 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             dfloat a{0.f, 0.f};
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
                 const float2 p = __ldcg(partials + k * kMaxPartials + b);
                 a = df_add(a, dfloat{p.x, p.y});
             }
@@ -190,17 +134,17 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
                                                const double (&v)[K], double* partials, double* totals,
-                                               double (&out)[K])
+                                               double (&out)[K], int bid, int nb)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const double t = block_sum(v[k], sh.d);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + blockIdx.x] = t;
+        if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        sh.flag = (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) ? 1 : 0;
+        sh.flag = (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) ? 1 : 0;
     }
     __syncthreads();
     const unsigned int target = gen + 1u;
@@ -209,7 +153,7 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             double a = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
                 a += __ldcg(partials + k * kMaxPartials + b);
             const double t = block_sum(a, sh.d);
             if (threadIdx.x == 0) totals[k] = t;
@@ -311,10 +255,12 @@ __device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const d
 
 }  // namespace
 
-__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBuffers B)
+// The solve of one system by blocks bid = 0..nb-1 of the launch (all of the
+// launch for a single system; a share of it in a batch).
+__device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
+                                                 PShared& sh)
 {
     DevState* st = B.st;
-    __shared__ PShared sh;
     if (threadIdx.x == 0) sh.flag = 0;
     __syncthreads();
     if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
@@ -322,8 +268,8 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
     if (threadIdx.x == 0) gen = atomicAdd(&st->bar_gen, 0u);
 
     const int nwin = P.nslots / 256;
-    const int wb = (int)((long long)blockIdx.x * nwin / gridDim.x);
-    const int we = (int)((long long)(blockIdx.x + 1) * nwin / gridDim.x);
+    const int wb = (int)((long long)bid * nwin / nb);
+    const int we = (int)((long long)(bid + 1) * nwin / nb);
     const int np = P.npad;
     const float alpha_e = (float)P.alpha;
 
@@ -384,7 +330,7 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
         {
             const dfloat v[1] = {pq};
             double tot[1];
-            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, st->totals, tot)) break;
+            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, st->totals, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 sh.action = 0;
                 if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -422,7 +368,7 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
         {
             const dfloat v[2] = {rr, rz};
             double tot[2];
-            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, st->totals + 2, tot)) break;
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, st->totals + 2, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 ++iter;
                 sh.action = 0;
@@ -452,7 +398,7 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
                 B.d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        if (!grid_sync(st, gen, sh)) break;
+        if (!grid_sync(st, gen, sh, nb)) break;
         double trr = 0.0, trz = 0.0;
         for (int w = wb; w < we; ++w) {
             const int slot = w * 256 + threadIdx.x;
@@ -480,10 +426,10 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
         {
             const double v[2] = {trr, trz};
             double tot[2];
-            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, st->totals + 4, tot)) break;
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, st->totals + 4, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 last_res = sqrt(tot[0] / bnorm2);
-                if (blockIdx.x == 0) st->true_checks += 1;
+                if (bid == 0) st->true_checks += 1;
                 sh.action = 0;
                 if (!isfinite(tot[0])) {
                     status = SP_ERR_NONFINITE;
@@ -505,7 +451,7 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
         if (sh.action == 2) break;
     }
     // every block's thread 0 holds the same scalars; block 0 records them
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         st->iter = iter;
         st->restarts = restarts;
         st->last_res = last_res;
@@ -521,18 +467,77 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBu
     }
 }
 
+__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBuffers B)
+{
+    __shared__ PShared sh;
+    persistent_solve(P, B, blockIdx.x, gridDim.x, sh);
+}
+
+// Batch: block b serves replica k with blk_off[k] <= b < blk_off[k + 1]; each
+// replica's blocks synchronise and reduce among themselves only, and leave
+// when their replica has converged.
+__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KParams* __restrict__ Ps,
+                                                                     const DevBuffers* __restrict__ Bs,
+                                                                     const int* __restrict__ blk_off, int R)
+{
+    __shared__ PShared sh;
+    __shared__ int rep;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (blk_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        rep = lo;
+    }
+    __syncthreads();
+    const int k = rep;
+    persistent_solve(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
+}
+
 namespace {
 int g_pocc = 0;
+int g_pocc_batch = 0;
 std::once_flag g_pocc_once;
-}  // namespace
-
-int cg_persistent_grid(const KParams& P, Launch L)
+void pocc_init()
 {
     std::call_once(g_pocc_once, [] {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc, k32_cg_persistent, kPBlock, 0) != cudaSuccess)
             g_pocc = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc_batch, k32_cg_persistent_batch, kPBlock, 0) !=
+            cudaSuccess)
+            g_pocc_batch = 0;
         cudaGetLastError();
     });
+}
+}  // namespace
+
+int cg_persistent_batch_capacity(Launch L)
+{
+    pocc_init();
+    return L.num_sms * g_pocc_batch;
+}
+
+cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,
+                                         int R, int total_blocks, Launch L)
+{
+    if (total_blocks < 1 || total_blocks > cg_persistent_batch_capacity(L)) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)total_blocks);
+    cfg.blockDim = dim3(kPBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
+}
+
+int cg_persistent_grid(const KParams& P, Launch L)
+{
+    pocc_init();
     long long g = std::min<long long>((long long)L.num_sms * g_pocc, P.nslots / 256);
     if (g > kMaxPartials) g = kMaxPartials;
     return (int)g;

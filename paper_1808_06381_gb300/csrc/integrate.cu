@@ -97,9 +97,52 @@ __global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
     }
 }
 
-void launch_stress(const KParams& P, DevBuffers& B, Launch L)
+// The same sum for the mixed solver without FP64 arithmetic in the loop:
+// separations from the FP32 positions and the pair's image (for box edges L
+// each component is within about 5 L 2^-24 of the exact one, below 1e-5
+// relative for the boxes used here), weights from the FP32 matrix, FP32
+// velocities, and a double-float accumulation.
+__global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
 {
-    k_stress<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int np = P.npad;
+    const float deltaf = (float)st->delta;
+    const float c_ev = (float)P.c_ev, za = (float)(P.zeta * P.alpha), kl = (float)(P.kappa * P.L[1]);
+    dfloat acc{0.f, 0.f};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const float xi = B.pos32[i], yi = B.pos32[np + i];
+        const float vxi = (float)B.x[i];
+        const int slot = B.row_slot[i];
+        const int base = B.chunk_off[slot >> 5] + (slot & 31);
+        const int cnt = B.row_cnt[i];
+        float row = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+            const int e = base + 32 * k;
+            const int j = B.col[e];
+            const unsigned char code = B.img[e];
+            const float a = (float)((int)(code & 7) - 2);
+            const float m = (float)((int)((code >> 3) & 3) - 1);
+            const float dx = (xi - B.pos32[j]) - (m * deltaf + a * P.Lf[0]);
+            const float dy = (yi - B.pos32[np + j]) - m * P.Lf[1];
+            const float w = B.val32[e];
+            const float fx = c_ev * dx * w + za * w * ((float)B.x[j] - vxi + kl * m);
+            row = fmaf(dy, fx, row);
+        }
+        acc = df_add(acc, row);
+    }
+    dfloat v[1] = {acc};
+    double out[1];
+    if (publish_reduce_df<1>(v, B.partials_df, &st->ticket[0], out) && threadIdx.x == 0)
+        st->stress_xy = -0.5 * out[0] / (P.L[0] * P.L[1] * P.L[2]);
+}
+
+void launch_stress(const KParams& P, DevBuffers& B, bool mixed, Launch L)
+{
+    if (mixed)
+        k_stress32<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
+    else
+        k_stress<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
 }
 
 __global__ void k_scatter_by_id(const double* __restrict__ planes, int npad, const int* __restrict__ ids,

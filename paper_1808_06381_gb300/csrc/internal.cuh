@@ -420,17 +420,24 @@ void cg_prepare();   // resident-block counts of the solver kernels (once per pr
 // cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
 int cg_persistent_grid(const KParams& P, Launch L);
+// A batch of systems in one cooperative launch: blocks [blk_off[k], blk_off[k+1]) solve system k.
+int cg_persistent_batch_capacity(Launch L);
+cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,
+                                         int R, int total_blocks, Launch L);
 int cg_kernels_per_check(bool mixed);
 
 // integrate.cu
 void launch_integrate(const KParams& P, DevBuffers& B, Launch L);
-void launch_stress(const KParams& P, DevBuffers& B, Launch L);
+void launch_stress(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 void launch_scatter_by_id(const double* planes, int npad, const int* ids, int n, double* out_n3,
                           cudaStream_t s);
 void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, double* planes,
                          cudaStream_t s);
 void launch_reset_step_stats(DevState* st, cudaStream_t s);
-void launch_structure_factor(const KParams& P, const DevBuffers& B, int grid, int nkx, int nky,
-                             double* grid_buf, double* S, double* qx, double* qy, cudaStream_t s);
+// sfactor.cu: S(q) at q_z = 0 for kx in [-nkx, nkx], ky in [-nky, nky] (kx slowest);
+// G = 0: direct sum over particles; G > 0: CIC grid of G x G in the sheared frame.
+cudaError_t run_structure_factor(const KParams& P, const DevBuffers& B, double delta, int G, int nkx, int nky,
+                                 const double* twiddle_dev, unsigned long long* grid_dev, double2* A_dev,
+                                 double* S_dev, double* qx_dev, double* qy_dev, cudaStream_t s);
 
 }  // namespace ss

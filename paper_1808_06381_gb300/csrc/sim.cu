@@ -22,31 +22,9 @@
 
 using namespace ss;
 
-struct sp_sim {
-    sp_params p{};
-    KParams kp{};
-    DevBuffers B{};
-    DevState* st_host = nullptr;  // pinned mirror of the device state
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
-    int num_sms = 0;
-    long long nnz_cap = 0;
-    bool use_inj = false;
-    bool host_loop = false;       // CG loop driven from the host
-    bool persistent = true;       // mixed solver: one cooperative launch per solve
-    bool built = false;           // pairs match the current positions
-    bool assembled = false;
-    cudaGraph_t step_graph = nullptr;
-    cudaGraphExec_t step_exec = nullptr;
-    cudaGraph_t solve_graph[2] = {nullptr, nullptr};   // [from_x]
-    cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
-    long long fixed_launches_step = 0;
-    long long fixed_launches_solve = 0;
-    std::string err;
-};
+#include "sim_impl.cuh"
 
-namespace {
+namespace ss_host {
 
 std::string g_create_error;
 
@@ -304,7 +282,7 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
         SS_TRY(host_cg_loop(s, launches));
     }
     launch_cg_finish(P, B, mixed(s), L);
-    launch_stress(P, B, L);
+    launch_stress(P, B, mixed(s), L);
     *launches += 2;
     return SP_OK;
 }
@@ -447,7 +425,9 @@ int do_build(sp_sim* s)
     return SP_OK;
 }
 
-}  // namespace
+}  // namespace ss_host
+
+using namespace ss_host;
 
 // Error text of calls that have no simulation object (creation, the
 // allocation-free solve); sp_last_error(NULL) returns it.
@@ -840,7 +820,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     if (rc == SP_OK) {
         launch_cg_finish(P, B, mx, L);
         mark(OTHER);
-        launch_stress(P, B, L);
+        launch_stress(P, B, mixed(s), L);
         mark(STRESS);
         launch_integrate(P, B, L);
         rc = mark(INTEGRATE);
@@ -1135,10 +1115,61 @@ int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count
 int sp_structure_factor(sp_sim* s, int32_t nkx, int32_t nky, int32_t grid, double* S_host,
                         double* qx_host, double* qy_host)
 {
-    (void)nkx; (void)nky; (void)grid; (void)S_host; (void)qx_host; (void)qy_host;
-    if (!s) return SP_ERR_INVALID_ARG;
-    s->err = "structure factor not available in this build";
-    return SP_ERR_INVALID_ARG;
+    if (!s || !S_host || nkx < 0 || nky < 0 || grid < 0) return SP_ERR_INVALID_ARG;
+    if (grid > 0 && (grid < 8 || grid > 8192 || 4 * nkx >= grid || 4 * nky >= grid)) {
+        s->err = "structure factor: grid must be in [8, 8192] with |kx|, |ky| < grid / 4";
+        return SP_ERR_INVALID_ARG;
+    }
+    if ((long long)(2 * nkx + 1) * (2 * nky + 1) > (1ll << 24)) {
+        s->err = "structure factor: too many modes";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    SS_TRY(read_state(s));
+    const double delta = s->st_host->delta;
+    const size_t m = (size_t)(2 * nkx + 1) * (2 * nky + 1);
+    double *S = nullptr, *qx = nullptr, *qy = nullptr, *tw = nullptr;
+    unsigned long long* g = nullptr;
+    double2* A = nullptr;
+    int rc = SP_OK;
+    auto A_ = [&](int r) { if (rc == SP_OK) rc = r; };
+    A_(dev_alloc(s, &S, m));
+    A_(dev_alloc(s, &qx, m));
+    A_(dev_alloc(s, &qy, m));
+    if (grid > 0) {
+        A_(dev_alloc(s, &tw, 2 * (size_t)grid));
+        A_(dev_alloc(s, &g, (size_t)grid * grid));
+        A_(dev_alloc(s, &A, (size_t)(2 * nkx + 1) * grid));
+    }
+    if (rc == SP_OK && grid > 0) {
+        // twiddle table (cos, sin)(2 pi m / G), m = 0..G-1
+        std::vector<double> t(2 * (size_t)grid);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int k = 0; k < grid; ++k) {
+            t[2 * k] = std::cos(two_pi * k / grid);
+            t[2 * k + 1] = std::sin(two_pi * k / grid);
+        }
+        if (cudaMemcpyAsync(tw, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess)
+            rc = SP_ERR_CUDA;
+        if (rc == SP_OK) SS_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    if (rc == SP_OK) {
+        if (run_structure_factor(s->kp, s->B, delta, grid, nkx, nky, tw, g, A, S, qx, qy, s->stream) != cudaSuccess)
+            rc = SP_ERR_CUDA;
+    }
+    if (rc == SP_OK) {
+        if (cudaMemcpyAsync(S_host, S, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            (qx_host && cudaMemcpyAsync(qx_host, qx, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) ||
+            (qy_host && cudaMemcpyAsync(qy_host, qy, sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            rc = SP_ERR_CUDA;
+    }
+    if (rc == SP_ERR_CUDA && s->err.empty()) s->err = std::string("structure factor: ") + cudaGetErrorString(cudaGetLastError());
+    void* ptrs[] = {S, qx, qy, tw, g, A};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    return rc;
 }
 
 }  // extern "C"

@@ -1,0 +1,47 @@
+// Private host-side declarations shared by the translation units of the
+// shearsim library (simulation object and the enqueueing helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "internal.cuh"
+
+// One simulation: parameters, device buffers, streams and captured graphs.
+struct sp_sim {
+    sp_params p{};
+    ss::KParams kp{};
+    ss::DevBuffers B{};
+    ss::DevState* st_host = nullptr;  // pinned mirror of the device state
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
+    int num_sms = 0;
+    long long nnz_cap = 0;
+    bool use_inj = false;
+    bool host_loop = false;       // CG loop driven from the host
+    bool persistent = true;       // mixed solver: one cooperative launch per solve
+    bool built = false;           // pairs match the current positions
+    bool assembled = false;
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraph_t solve_graph[2] = {nullptr, nullptr};   // [from_x]
+    cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
+    long long fixed_launches_step = 0;
+    long long fixed_launches_solve = 0;
+    std::string err;
+};
+
+namespace ss_host {
+ss::Launch launch_of(const sp_sim* s, cudaStream_t st);
+bool mixed(const sp_sim* s);
+long long enqueue_build(sp_sim* s, cudaStream_t cs);
+int read_state(sp_sim* s);
+int grow_pairs(sp_sim* s);
+int clear_flags(sp_sim* s);
+int set_device(sp_sim* s);
+void free_graphs(sp_sim* s);
+}  // namespace ss_host
+
+std::string& sp_global_error();

@@ -193,6 +193,7 @@ typedef struct sp_kernel_profile {
     double init_ms;                  /* part of other_ms: solver set-up (r = b - A x0) */
     double stress_ms;                /* part of other_ms: the stress kernel */
     double integrate_ms;             /* part of other_ms: the position update */
+    double mpnn_ms;                  /* the learned warm start's inference (0 when not used) */
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 
@@ -227,6 +228,36 @@ int sp_set_noise(sp_sim* sim, const double* xi_host);
  * checking: out_host[4 * k ...] = Philox(ctr = (ids[k], step, 0, 0), key = (seed, 0)). */
 int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count,
                      const int64_t* ids_host, uint64_t* out_host);
+
+/* ---- learned warm start ----
+ *
+ * The paper solves Eq. algebra with no learned part; this optional network
+ * guesses the velocities before CG, which then runs from the guess to the
+ * same tolerance (CG alone judges the result).  For node i and Cartesian
+ * component c, with shared weights: s = RMS of b; x0 = (b/A_ii, vprev, b)/s;
+ * a0 = M x0 with (M u)_i = sum_j alpha w_ij / A_ii u_j; y = tanh(tanh([x0,a0] W1)
+ * W2) W3 (6 -> 64 -> 64 -> 4, BF16 tensor cores, FP32 accumulation); a1 = M y;
+ * guess = s [y, a1, x0] . o.  Flat FP32 weights: W1 [6][64], W2 [64][64],
+ * W3 [64][4], o [11], row-major in that order (sp_mpnn_num_params() floats).
+ * Training minimises the mean square of (guess - v*)/s over the rows, v* the
+ * converged velocities, with Adam on FP32 master weights. */
+int sp_mpnn_num_params(void);
+/* Attach the network (weights_host: sp_mpnn_num_params() floats, or NULL for
+ * a seeded start whose readout returns the previous velocities); from then on
+ * every step runs it before the solve and CG starts from its guess. */
+int sp_mpnn_enable(sp_sim* sim, uint64_t seed, const float* weights_host);
+int sp_mpnn_disable(sp_sim* sim);
+int sp_mpnn_get_weights(sp_sim* sim, float* weights_host);
+int sp_mpnn_set_weights(sp_sim* sim, const float* weights_host);
+/* Run the network on the assembled system (after sp_assemble); its guess
+ * becomes the start vector of the next sp_solve_velocities.  guess_host:
+ * [n][3] by particle id, or NULL. */
+int sp_mpnn_forward(sp_sim* sim, double* guess_host);
+/* One training step on the last solve (call after sp_step(sim, 1), or after
+ * sp_mpnn_forward then sp_solve_velocities): loss of the guess against the
+ * converged velocities, gradient (grad_host may be NULL), Adam with learning
+ * rate lr (lr = 0 computes the gradient only). */
+int sp_mpnn_train_step(sp_sim* sim, float lr, double* loss, float* grad_host);
 
 /* ---- batches of independent replicas ----
  *

@@ -108,7 +108,10 @@ def load(path: str = LIB_PATH):
             ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)]),
             ("sp_batch_create", [i32, vp, vp, P(vp)]), ("sp_batch_destroy", [vp]),
             ("sp_batch_step", [vp, i32, vp]), ("sp_batch_get_sim", [vp, i32, P(vp)]),
-            ("sp_batch_blocks", [vp, vp])]
+            ("sp_batch_blocks", [vp, vp]),
+            ("sp_mpnn_enable", [vp, u64, vp]), ("sp_mpnn_disable", [vp]), ("sp_mpnn_get_weights", [vp, vp]),
+            ("sp_mpnn_set_weights", [vp, vp]), ("sp_mpnn_forward", [vp, vp]),
+            ("sp_mpnn_train_step", [vp, ctypes.c_float, P(d), vp])]
     for name, args in sims:
         f = getattr(lib, name)
         f.argtypes = args
@@ -117,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.sp_last_error.restype = ctypes.c_char_p
     lib.sp_batch_last_error.argtypes = [vp]
     lib.sp_batch_last_error.restype = ctypes.c_char_p
+    lib.sp_mpnn_num_params.argtypes = []
+    lib.sp_mpnn_num_params.restype = ctypes.c_int
     lib.sp_kappa_from_kappa_tau.argtypes = [d, d, d, d]
     lib.sp_kappa_from_kappa_tau.restype = d
     _lib = lib
@@ -284,6 +289,38 @@ class Simulation:
         prof = sp_kernel_profile()
         self._c(load().sp_profile_step(self._h, ctypes.byref(prof)))
         return {name: getattr(prof, name) for name, _ in sp_kernel_profile._fields_}
+
+    # learned warm start
+    def mpnn_enable(self, seed: int = 0, weights=None):
+        if weights is None:
+            self._c(load().sp_mpnn_enable(self._h, int(seed), None))
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            self._c(load().sp_mpnn_enable(self._h, int(seed), _p(w)))
+
+    def mpnn_disable(self):
+        self._c(load().sp_mpnn_disable(self._h))
+
+    def mpnn_weights(self) -> np.ndarray:
+        w = np.zeros(load().sp_mpnn_num_params(), dtype=np.float32)
+        self._c(load().sp_mpnn_get_weights(self._h, _p(w)))
+        return w
+
+    def mpnn_set_weights(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._c(load().sp_mpnn_set_weights(self._h, _p(w)))
+
+    def mpnn_forward(self) -> np.ndarray:
+        g = np.zeros((self.n, 3))
+        self._c(load().sp_mpnn_forward(self._h, _p(g)))
+        return g
+
+    def mpnn_train_step(self, lr: float = 1e-3, want_grad: bool = False):
+        loss = ctypes.c_double()
+        grad = np.zeros(load().sp_mpnn_num_params(), dtype=np.float32) if want_grad else None
+        self._c(load().sp_mpnn_train_step(self._h, float(lr), ctypes.byref(loss),
+                                          _p(grad) if grad is not None else None))
+        return (loss.value, grad) if want_grad else loss.value
 
     def stress_xy(self) -> float:
         v = ctypes.c_double()

@@ -3,6 +3,7 @@
 // device state, and host launchers for the kernels of each translation unit.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,6 +116,33 @@ struct DevBuffers {
 };
 
 constexpr int kMaxPartials = 4096;
+
+// Learned warm start (mpnn.cu): flat FP32 weights W1 [6][64], W2 [64][64],
+// W3 [64][4], o [11] (row-major, in that order).
+constexpr int kMpOffW1 = 0;
+constexpr int kMpOffW2 = 6 * 64;
+constexpr int kMpOffW3 = kMpOffW2 + 64 * 64;
+constexpr int kMpOffO = kMpOffW3 + 64 * 4;
+constexpr int kMpParams = kMpOffO + 11;
+
+struct MpBuffers {
+    float4* x0;      // [3n] rows 3i + c: (b / A_ii, vprev, b, 0) / s
+    float4* a0;      // [3n] M x0
+    float4* y;       // [3n] MLP output (4 message features)
+    float4* a1;      // [3n] M y
+    float4* dy;      // [3n] training: dLoss / dy
+    float4* g1;      // [3n] training: dLoss / da1
+    float* master;   // [kMpParams] FP32 weights
+    float* m;        // [kMpParams] Adam first moment
+    float* v;        // [kMpParams] Adam second moment
+    float* grad;     // [kMpParams]
+    float* gpart;    // [blocks][kMpParams] per-block weight gradients
+    double* dpart;   // [blocks][12] per-block loss and readout gradient
+    __nv_bfloat16* wb;  // BF16 weight layouts for the tensor-core kernels
+    double* scal;    // [0] = s (RMS of b), [1] = last loss
+    double* part;    // [kMaxPartials] partial sums of the scale reduction
+    unsigned int* ticket;
+};
 
 // ------------------------------------------------------------------ helpers
 
@@ -425,6 +453,14 @@ int cg_persistent_batch_capacity(Launch L);
 cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,
                                          int R, int total_blocks, Launch L);
 int cg_kernels_per_check(bool mixed);
+
+// mpnn.cu
+void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L);
+int mp_infer_launches();
+void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, int t, Launch L);
+int mp_prepare();
+int mp_weights_bf16_count();
+void launch_mp_convert(MpBuffers& M, cudaStream_t s);
 
 // integrate.cu
 void launch_integrate(const KParams& P, DevBuffers& B, Launch L);

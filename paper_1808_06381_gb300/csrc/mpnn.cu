@@ -1,0 +1,596 @@
+// Learned warm start for the velocity solve: a small message-passing network
+// that guesses v = A^-1 b before CG (the paper has no learned part; the
+// solve it accelerates is Eq. algebra of arXiv 1808.06381, §Method).
+//
+// Per node i and Cartesian component c (row r = 3 i + c), shared weights:
+//   s = RMS of b;  x0 = (b / A_ii, vprev, b) / s
+//   a0 = M x0 with (M u)_i = sum_j alpha w_ij / A_ii u_j       (message pass 1)
+//   h1 = tanh([x0, a0] W1);  h2 = tanh(h1 W2);  y = h2 W3       (6 -> 64 -> 64 -> 4)
+//   a1 = M y                                                     (message pass 2)
+//   guess = s [y, a1, x0] . o
+// The message passes run on the narrow features (like an SpMV of the solver);
+// the MLP is fused in one kernel on BF16 tensor cores (mma.sync m16n8k16, FP32
+// accumulation): a warp takes 16 rows, the FP32 accumulators of a layer pass
+// through tanh and are repacked in registers as the A operand of the next
+// layer, weights sit in shared memory.  Training (MSE to the converged
+// velocities) runs the backward pass in one fused kernel that stages a tile of
+// 128 rows in shared memory and forms the weight gradients with tensor-core
+// products of transposed tiles (ldmatrix.trans), then a deterministic
+// reduction over blocks and Adam on FP32 master weights.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "sim_impl.cuh"
+
+namespace ss {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTileRows = 128;
+constexpr int kMaxGradBlocks = 1024;
+constexpr int kSW = 24;   // padded smem row stride for 16-wide tiles (48 B)
+constexpr int kSH = 72;   // padded smem row stride for 64-wide tiles (144 B)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(unsigned& r0, unsigned& r1, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_addr(p)));
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators.
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned*>(&v);
+}
+
+// B fragment (k16 x n8) from a shared [n][k] array (k contiguous), stride ld.
+__device__ __forceinline__ void load_b(const __nv_bfloat16* Bt, int ld, int n0, int k0, unsigned& b0, unsigned& b1)
+{
+    const int lane = threadIdx.x & 31;
+    ldsm_x2(b0, b1, Bt + (n0 + (lane & 7)) * ld + k0 + ((lane >> 3) & 1) * 8);
+}
+
+// Weight layouts in the packed BF16 array (element offsets).
+constexpr int kW1T = 0;                 // [64][16]: W1 transposed, k padded 6 -> 16
+constexpr int kW2T = kW1T + 64 * 16;    // [64][64]: W2 transposed
+constexpr int kW3T = kW2T + 64 * 64;    // [8][64]:  W3 transposed, n padded 4 -> 8
+constexpr int kW2N = kW3T + 8 * 64;     // [64][64]: W2 as is (backward)
+constexpr int kW3P = kW2N + 64 * 64;    // [64][16]: W3 as is, k padded 4 -> 16 (backward)
+constexpr int kWB = kW3P + 64 * 16;
+
+// Forward of the MLP for one warp's 16 rows, from the A fragment of the
+// inputs; returns the FP32 activations (for the backward pass) and the output
+// accumulator of layer 3.
+struct FwdRegs {
+    float h1[8][4];
+    float h2[8][4];
+    unsigned a1[4][4];
+    unsigned a2[4][4];
+    float y[4];
+};
+
+__device__ __forceinline__ void mlp_forward(const unsigned (&a0)[4], const __nv_bfloat16* sW1T,
+                                            const __nv_bfloat16* sW2T, const __nv_bfloat16* sW3T, FwdRegs& R)
+{
+#pragma unroll
+    for (int nb = 0; nb < 8; ++nb) {
+        R.h1[nb][0] = R.h1[nb][1] = R.h1[nb][2] = R.h1[nb][3] = 0.f;
+        unsigned b0, b1;
+        load_b(sW1T, kSW, nb * 8, 0, b0, b1);
+        mma16816(R.h1[nb], a0, b0, b1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R.h1[nb][q] = tanhf(R.h1[nb][q]);
+    }
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        R.a1[kb][0] = pack_bf16(R.h1[2 * kb][0], R.h1[2 * kb][1]);
+        R.a1[kb][1] = pack_bf16(R.h1[2 * kb][2], R.h1[2 * kb][3]);
+        R.a1[kb][2] = pack_bf16(R.h1[2 * kb + 1][0], R.h1[2 * kb + 1][1]);
+        R.a1[kb][3] = pack_bf16(R.h1[2 * kb + 1][2], R.h1[2 * kb + 1][3]);
+    }
+#pragma unroll
+    for (int nb = 0; nb < 8; ++nb) {
+        R.h2[nb][0] = R.h2[nb][1] = R.h2[nb][2] = R.h2[nb][3] = 0.f;
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+            unsigned b0, b1;
+            load_b(sW2T, kSH, nb * 8, kb * 16, b0, b1);
+            mma16816(R.h2[nb], R.a1[kb], b0, b1);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R.h2[nb][q] = tanhf(R.h2[nb][q]);
+    }
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        R.a2[kb][0] = pack_bf16(R.h2[2 * kb][0], R.h2[2 * kb][1]);
+        R.a2[kb][1] = pack_bf16(R.h2[2 * kb][2], R.h2[2 * kb][3]);
+        R.a2[kb][2] = pack_bf16(R.h2[2 * kb + 1][0], R.h2[2 * kb + 1][1]);
+        R.a2[kb][3] = pack_bf16(R.h2[2 * kb + 1][2], R.h2[2 * kb + 1][3]);
+    }
+    R.y[0] = R.y[1] = R.y[2] = R.y[3] = 0.f;
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        unsigned b0, b1;
+        load_b(sW3T, kSH, 0, kb * 16, b0, b1);
+        mma16816(R.y, R.a2[kb], b0, b1);
+    }
+}
+
+__device__ __forceinline__ float feat6(const float4& x, const float4& a, int k)
+{
+    switch (k) {
+        case 0: return x.x;
+        case 1: return x.y;
+        case 2: return x.z;
+        case 3: return a.x;
+        case 4: return a.y;
+        case 5: return a.z;
+        default: return 0.f;
+    }
+}
+
+// A fragment of the inputs [x0, a0] (6 features, k padded to 16) for rows r0, r1.
+__device__ __forceinline__ void input_frag(const float4* x0, const float4* a0, int rows, int r0, int r1,
+                                           unsigned (&a)[4])
+{
+    const int t = threadIdx.x & 3;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 x_0 = r0 < rows ? x0[r0] : z, a_0 = r0 < rows ? a0[r0] : z;
+    const float4 x_1 = r1 < rows ? x0[r1] : z, a_1 = r1 < rows ? a0[r1] : z;
+    a[0] = pack_bf16(feat6(x_0, a_0, 2 * t), feat6(x_0, a_0, 2 * t + 1));
+    a[1] = pack_bf16(feat6(x_1, a_1, 2 * t), feat6(x_1, a_1, 2 * t + 1));
+    a[2] = 0u;
+    a[3] = 0u;
+}
+
+__device__ __forceinline__ void load_weights_fwd(const __nv_bfloat16* wb, __nv_bfloat16* sW1T, __nv_bfloat16* sW2T,
+                                                 __nv_bfloat16* sW3T)
+{
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) sW1T[(e / 16) * kSW + e % 16] = wb[kW1T + e];
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) sW2T[(e / 64) * kSH + e % 64] = wb[kW2T + e];
+    for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) sW3T[(e / 64) * kSH + e % 64] = wb[kW3T + e];
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- kernels
+
+// s = sqrt(sum b^2 / 3n) (1 if b = 0)
+__global__ void k_mp_scale(KParams P, DevBuffers B, MpBuffers M)
+{
+    const int np = P.npad;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) acc += B.b[c * np + i] * B.b[c * np + i];
+    const double v[1] = {acc};
+    if (publish_partials<1>(v, M.part, &M.ticket[0])) {
+        double out[1];
+        reduce_partials<1>(M.part, out);
+        if (threadIdx.x == 0) {
+            const double s = sqrt(out[0] / (3.0 * P.n));
+            M.scal[0] = s > 0.0 ? s : 1.0;
+        }
+    }
+}
+
+// x0 rows (b / A_ii, vprev, b) / s, with vprev = the current x (the previous velocities).
+__global__ void k_mp_input(KParams P, DevBuffers B, MpBuffers M)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int np = P.npad;
+    const float inv = (float)(1.0 / M.scal[0]);
+    const double di = B.dinv[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double b = B.b[c * np + i];
+        M.x0[3 * i + c] = make_float4((float)(b * di) * inv, (float)B.x[c * np + i] * inv, (float)b * inv, 0.f);
+    }
+}
+
+// out = M in (mode 0), out = M^T in (mode 1), out += M^T in (mode 2); three rows per node.
+__global__ void k_mp_aggregate(KParams P, DevBuffers B, const float4* __restrict__ in, float4* __restrict__ out,
+                               int mode)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int slot = B.row_slot[i];
+    const int base = B.chunk_off[slot >> 5] + (slot & 31);
+    const int cnt = B.row_cnt[i];
+    const float ae = (float)P.alpha;
+    float4 s[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < cnt; ++k) {
+        const int e = base + 32 * k;
+        const int j = B.col[e];
+        float w = ae * B.val32[e];
+        if (mode != 0) w *= B.dinv32[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 u = in[3 * j + c];
+            s[c].x = fmaf(w, u.x, s[c].x);
+            s[c].y = fmaf(w, u.y, s[c].y);
+            s[c].z = fmaf(w, u.z, s[c].z);
+            s[c].w = fmaf(w, u.w, s[c].w);
+        }
+    }
+    const float di = mode == 0 ? B.dinv32[i] : 1.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float4 r = make_float4(s[c].x * di, s[c].y * di, s[c].z * di, s[c].w * di);
+        if (mode == 2) {
+            const float4 o = out[3 * i + c];
+            r = make_float4(r.x + o.x, r.y + o.y, r.z + o.z, r.w + o.w);
+        }
+        out[3 * i + c] = r;
+    }
+}
+
+// y = h2 W3 with h2 = tanh(tanh([x0, a0] W1) W2): one warp per 16 rows.
+__global__ void __launch_bounds__(kThreads) k_mp_mlp_fwd(int rows, MpBuffers M)
+{
+    __shared__ __align__(16) __nv_bfloat16 sW1T[64 * kSW];
+    __shared__ __align__(16) __nv_bfloat16 sW2T[64 * kSH];
+    __shared__ __align__(16) __nv_bfloat16 sW3T[8 * kSH];
+    load_weights_fwd(M.wb, sW1T, sW2T, sW3T);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int base = (blockIdx.x * 8 + warp) * 16; base < rows; base += gridDim.x * 8 * 16) {
+        const int r0 = base + g, r1 = base + g + 8;
+        unsigned a0[4];
+        input_frag(M.x0, M.a0, rows, r0, r1, a0);
+        FwdRegs R;
+        mlp_forward(a0, sW1T, sW2T, sW3T, R);
+        if (t < 2) {
+            float* y = reinterpret_cast<float*>(M.y);
+            if (r0 < rows) *reinterpret_cast<float2*>(y + 4 * (size_t)r0 + 2 * t) = make_float2(R.y[0], R.y[1]);
+            if (r1 < rows) *reinterpret_cast<float2*>(y + 4 * (size_t)r1 + 2 * t) = make_float2(R.y[2], R.y[3]);
+        }
+    }
+}
+
+// guess = s [y, a1, x0] . o, written as the start vector of CG.
+__global__ void k_mp_output(KParams P, DevBuffers B, MpBuffers M)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const double s = M.scal[0];
+    const float* o = M.master + kMpOffO;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int r = 3 * i + c;
+        const float4 y = M.y[r], a = M.a1[r], x = M.x0[r];
+        const float out = y.x * o[0] + y.y * o[1] + y.z * o[2] + y.w * o[3] + a.x * o[4] + a.y * o[5] + a.z * o[6] +
+                          a.w * o[7] + x.x * o[8] + x.y * o[9] + x.z * o[10];
+        B.x[c * P.npad + i] = s * (double)out;
+    }
+}
+
+// Loss rows: e = out - vstar / s, dout = 2 e / 3n; dy = dout o[0:4], g1 = dout o[4:8];
+// per block: sum e^2 and the readout gradient sum dout [y, a1, x0].
+__global__ void k_mp_loss(KParams P, DevBuffers B, MpBuffers M)
+{
+    const double s = M.scal[0];
+    const float* o = M.master + kMpOffO;
+    const int rows = 3 * P.n;
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const int i = r / 3, c = r - 3 * i;
+        const float4 y = M.y[r], a = M.a1[r], x = M.x0[r];
+        const float out = y.x * o[0] + y.y * o[1] + y.z * o[2] + y.w * o[3] + a.x * o[4] + a.y * o[5] + a.z * o[6] +
+                          a.w * o[7] + x.x * o[8] + x.y * o[9] + x.z * o[10];
+        const double e = (double)out - B.x[c * P.npad + i] / s;
+        const float d = (float)(2.0 * e / rows);
+        M.dy[r] = make_float4(d * o[0], d * o[1], d * o[2], d * o[3]);
+        M.g1[r] = make_float4(d * o[4], d * o[5], d * o[6], d * o[7]);
+        const float f[11] = {y.x, y.y, y.z, y.w, a.x, a.y, a.z, a.w, x.x, x.y, x.z};
+        acc[0] += e * e;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) acc[1 + k] += (double)(d * f[k]);
+    }
+    __shared__ double sh[32];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double t = block_sum(acc[k], sh);
+        if (threadIdx.x == 0) M.dpart[blockIdx.x * 12 + k] = t;
+    }
+}
+
+// Backward of the MLP: per warp 16 rows (forward recomputed), activation
+// gradients on tensor cores; the block's 128 rows are staged in shared memory
+// and the weight gradients accumulated with transposed-tile products; one
+// partial gradient per block.
+__global__ void __launch_bounds__(kThreads, 1) k_mp_mlp_bwd(int rows, MpBuffers M)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16* sW1T = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+    __nv_bfloat16* sW2T = sW1T + 64 * kSW;
+    __nv_bfloat16* sW3T = sW2T + 64 * kSH;
+    __nv_bfloat16* sW2N = sW3T + 8 * kSH;
+    __nv_bfloat16* sW3P = sW2N + 64 * kSH;
+    __nv_bfloat16* tIn = sW3P + 64 * kSW;
+    __nv_bfloat16* tDY = tIn + kTileRows * kSW;
+    __nv_bfloat16* tH1 = tDY + kTileRows * kSW;
+    __nv_bfloat16* tH2 = tH1 + kTileRows * kSH;
+    __nv_bfloat16* tP1 = tH2 + kTileRows * kSH;
+    __nv_bfloat16* tP2 = tP1 + kTileRows * kSH;
+    load_weights_fwd(M.wb, sW1T, sW2T, sW3T);
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) sW2N[(e / 64) * kSH + e % 64] = M.wb[kW2N + e];
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) sW3P[(e / 16) * kSW + e % 16] = M.wb[kW3P + e];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float gW2[4][4], gW1[4], gW3[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        gW1[q] = gW3[q] = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gW2[q][u] = 0.f;
+    }
+    const int lr0 = warp * 16 + g, lr1 = lr0 + 8;   // rows of this warp inside the tile
+    for (int tile = blockIdx.x * kTileRows; tile < rows; tile += gridDim.x * kTileRows) {
+        const int r0 = tile + lr0, r1 = tile + lr1;
+        unsigned ain[4];
+        input_frag(M.x0, M.a0, rows, r0, r1, ain);
+        FwdRegs R;
+        mlp_forward(ain, sW1T, sW2T, sW3T, R);
+        // dY fragment (k = the 4 message features, padded to 16)
+        unsigned ady[4] = {0u, 0u, 0u, 0u};
+        if (t < 2) {
+            const float* dy = reinterpret_cast<const float*>(M.dy);
+            const float2 u0 = r0 < rows ? *reinterpret_cast<const float2*>(dy + 4 * (size_t)r0 + 2 * t) : make_float2(0.f, 0.f);
+            const float2 u1 = r1 < rows ? *reinterpret_cast<const float2*>(dy + 4 * (size_t)r1 + 2 * t) : make_float2(0.f, 0.f);
+            ady[0] = pack_bf16(u0.x, u0.y);
+            ady[1] = pack_bf16(u1.x, u1.y);
+        }
+        // dh2 = dY W3^T, dp2 = dh2 (1 - h2^2)
+        float p2[8][4];
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+            p2[nb][0] = p2[nb][1] = p2[nb][2] = p2[nb][3] = 0.f;
+            unsigned b0, b1;
+            load_b(sW3P, kSW, nb * 8, 0, b0, b1);
+            mma16816(p2[nb], ady, b0, b1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p2[nb][q] *= 1.f - R.h2[nb][q] * R.h2[nb][q];
+        }
+        unsigned ap2[4][4];
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+            ap2[kb][0] = pack_bf16(p2[2 * kb][0], p2[2 * kb][1]);
+            ap2[kb][1] = pack_bf16(p2[2 * kb][2], p2[2 * kb][3]);
+            ap2[kb][2] = pack_bf16(p2[2 * kb + 1][0], p2[2 * kb + 1][1]);
+            ap2[kb][3] = pack_bf16(p2[2 * kb + 1][2], p2[2 * kb + 1][3]);
+        }
+        // dh1 = dp2 W2^T, dp1 = dh1 (1 - h1^2)
+        float p1[8][4];
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+            p1[nb][0] = p1[nb][1] = p1[nb][2] = p1[nb][3] = 0.f;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                unsigned b0, b1;
+                load_b(sW2N, kSH, nb * 8, kb * 16, b0, b1);
+                mma16816(p1[nb], ap2[kb], b0, b1);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p1[nb][q] *= 1.f - R.h1[nb][q] * R.h1[nb][q];
+        }
+        // stage the tile (BF16): inputs, dY, h1, h2, dp1, dp2
+        unsigned* u;
+        u = reinterpret_cast<unsigned*>(tIn);
+        u[(lr0 * kSW + 2 * t) / 2] = ain[0];
+        u[(lr1 * kSW + 2 * t) / 2] = ain[1];
+        u[(lr0 * kSW + 8 + 2 * t) / 2] = ain[2];
+        u[(lr1 * kSW + 8 + 2 * t) / 2] = ain[3];
+        u = reinterpret_cast<unsigned*>(tDY);
+        u[(lr0 * kSW + 2 * t) / 2] = ady[0];
+        u[(lr1 * kSW + 2 * t) / 2] = ady[1];
+        u[(lr0 * kSW + 8 + 2 * t) / 2] = 0u;
+        u[(lr1 * kSW + 8 + 2 * t) / 2] = 0u;
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+            const int c0 = nb * 8 + 2 * t;
+            reinterpret_cast<unsigned*>(tH1)[(lr0 * kSH + c0) / 2] = pack_bf16(R.h1[nb][0], R.h1[nb][1]);
+            reinterpret_cast<unsigned*>(tH1)[(lr1 * kSH + c0) / 2] = pack_bf16(R.h1[nb][2], R.h1[nb][3]);
+            reinterpret_cast<unsigned*>(tH2)[(lr0 * kSH + c0) / 2] = pack_bf16(R.h2[nb][0], R.h2[nb][1]);
+            reinterpret_cast<unsigned*>(tH2)[(lr1 * kSH + c0) / 2] = pack_bf16(R.h2[nb][2], R.h2[nb][3]);
+            reinterpret_cast<unsigned*>(tP1)[(lr0 * kSH + c0) / 2] = pack_bf16(p1[nb][0], p1[nb][1]);
+            reinterpret_cast<unsigned*>(tP1)[(lr1 * kSH + c0) / 2] = pack_bf16(p1[nb][2], p1[nb][3]);
+            reinterpret_cast<unsigned*>(tP2)[(lr0 * kSH + c0) / 2] = pack_bf16(p2[nb][0], p2[nb][1]);
+            reinterpret_cast<unsigned*>(tP2)[(lr1 * kSH + c0) / 2] = pack_bf16(p2[nb][2], p2[nb][3]);
+        }
+        __syncthreads();
+        // weight gradients: sum over the tile's rows (k = row)
+        // A operand rows (m) come from a tile's columns: x4.trans over (rows kr.., cols m0..)
+        const int ar = (lane & 7) + ((lane >> 4) & 1) * 8;   // stored row offset for A (x4.trans)
+        const int ac = ((lane >> 3) & 1) * 8;                // stored col offset for A
+        const int br = (lane & 7) + ((lane >> 3) & 1) * 8;   // stored row offset for B (x2.trans)
+#pragma unroll
+        for (int kb = 0; kb < kTileRows / 16; ++kb) {
+            const int kr = kb * 16;
+            {   // dW2[i][h] += h1^T dp2: warp -> i block (warp % 4) x h half (warp / 4)
+                const int m0 = (warp & 3) * 16, h0 = (warp >> 2) * 32;
+                unsigned a[4];
+                ldsm_x4_t(a[0], a[1], a[2], a[3], tH1 + (kr + ar) * kSH + m0 + ac);
+#pragma unroll
+                for (int nb = 0; nb < 4; ++nb) {
+                    unsigned b0, b1;
+                    ldsm_x2_t(b0, b1, tP2 + (kr + br) * kSH + h0 + nb * 8);
+                    mma16816(gW2[nb], a, b0, b1);
+                }
+            }
+            {   // dW1[f][i] += in^T dp1: warp -> i block of 8
+                unsigned a[4];
+                ldsm_x4_t(a[0], a[1], a[2], a[3], tIn + (kr + ar) * kSW + ac);
+                unsigned b0, b1;
+                ldsm_x2_t(b0, b1, tP1 + (kr + br) * kSH + warp * 8);
+                mma16816(gW1, a, b0, b1);
+            }
+            if (warp < 4) {   // dW3[h][m] += h2^T dY: warp -> h block
+                unsigned a[4];
+                ldsm_x4_t(a[0], a[1], a[2], a[3], tH2 + (kr + ar) * kSH + warp * 16 + ac);
+                unsigned b0, b1;
+                ldsm_x2_t(b0, b1, tDY + (kr + br) * kSW);
+                mma16816(gW3, a, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    // this block's partial gradient
+    float* gp = M.gpart + (size_t)blockIdx.x * kMpParams;
+    {
+        const int m0 = (warp & 3) * 16, h0 = (warp >> 2) * 32;
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) {
+            const int h = h0 + nb * 8 + 2 * t;
+            gp[kMpOffW2 + (m0 + g) * 64 + h] = gW2[nb][0];
+            gp[kMpOffW2 + (m0 + g) * 64 + h + 1] = gW2[nb][1];
+            gp[kMpOffW2 + (m0 + g + 8) * 64 + h] = gW2[nb][2];
+            gp[kMpOffW2 + (m0 + g + 8) * 64 + h + 1] = gW2[nb][3];
+        }
+    }
+    if (g < 6) {
+        const int i = warp * 8 + 2 * t;
+        gp[kMpOffW1 + g * 64 + i] = gW1[0];
+        gp[kMpOffW1 + g * 64 + i + 1] = gW1[1];
+    }
+    if (warp < 4 && t < 2) {
+        const int h = warp * 16 + g;
+        gp[kMpOffW3 + h * 4 + 2 * t] = gW3[0];
+        gp[kMpOffW3 + h * 4 + 2 * t + 1] = gW3[1];
+        gp[kMpOffW3 + (h + 8) * 4 + 2 * t] = gW3[2];
+        gp[kMpOffW3 + (h + 8) * 4 + 2 * t + 1] = gW3[3];
+    }
+}
+
+// grad = sum over blocks (fixed order); the readout's gradient and the loss from the loss blocks.
+__global__ void k_mp_grad_reduce(MpBuffers M, int nblocks_mlp, int nblocks_loss, int rows)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < kMpOffO) {
+        float s = 0.f;
+        for (int b = 0; b < nblocks_mlp; ++b) s += M.gpart[(size_t)b * kMpParams + p];
+        M.grad[p] = s;
+    } else if (p < kMpParams) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks_loss; ++b) s += M.dpart[b * 12 + 1 + (p - kMpOffO)];
+        M.grad[p] = (float)s;
+    } else if (p == kMpParams) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks_loss; ++b) s += M.dpart[b * 12];
+        M.scal[1] = s / rows;
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 masters, then the BF16 layouts for the kernels.
+__global__ void k_mp_adam(MpBuffers M, float lr, int t)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kMpParams) return;
+    if (lr != 0.f) {
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float gp = M.grad[p];
+        const float m = b1 * M.m[p] + (1.f - b1) * gp;
+        const float v = b2 * M.v[p] + (1.f - b2) * gp * gp;
+        M.m[p] = m;
+        M.v[p] = v;
+        const float mh = m / (1.f - powf(b1, (float)t));
+        const float vh = v / (1.f - powf(b2, (float)t));
+        M.master[p] -= lr * mh / (sqrtf(vh) + eps);
+    }
+    const __nv_bfloat16 w = __float2bfloat16_rn(M.master[p]);
+    if (p < kMpOffW2) {
+        const int f = p / 64, i = p % 64;     // W1[f][i]
+        M.wb[kW1T + i * 16 + f] = w;
+    } else if (p < kMpOffW3) {
+        const int q = p - kMpOffW2, i = q / 64, h = q % 64;   // W2[i][h]
+        M.wb[kW2T + h * 64 + i] = w;
+        M.wb[kW2N + i * 64 + h] = w;
+    } else if (p < kMpOffO) {
+        const int q = p - kMpOffW3, h = q / 4, m = q % 4;     // W3[h][m]
+        M.wb[kW3T + m * 64 + h] = w;
+        M.wb[kW3P + h * 16 + m] = w;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+int mp_bwd_smem_bytes()
+{
+    return (int)sizeof(__nv_bfloat16) *
+           (64 * kSW + 64 * kSH + 8 * kSH + 64 * kSH + 64 * kSW + 2 * kTileRows * kSW + 4 * kTileRows * kSH);
+}
+
+void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L)
+{
+    const int rows = 3 * P.n;
+    k_mp_scale<<<grid_for(P.n, kVecBlock, L.num_sms * 4), kVecBlock, 0, L.stream>>>(P, B, M);
+    k_mp_input<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P, B, M);
+    k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.x0, M.a0, 0);
+    k_mp_mlp_fwd<<<grid_for(rows, 8 * 16, L.num_sms * 4), kThreads, 0, L.stream>>>(rows, M);
+    k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.y, M.a1, 0);
+    k_mp_output<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P, B, M);
+}
+
+int mp_infer_launches() { return 6; }
+
+void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, int t, Launch L)
+{
+    const int rows = 3 * P.n;
+    const int nloss = grid_for(rows, kVecBlock, std::min(kMaxGradBlocks, L.num_sms * 4));
+    k_mp_loss<<<nloss, kVecBlock, 0, L.stream>>>(P, B, M);
+    k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.g1, M.dy, 2);
+    const int nmlp = grid_for(rows, kTileRows, std::min(kMaxGradBlocks, L.num_sms));
+    k_mp_mlp_bwd<<<nmlp, kThreads, mp_bwd_smem_bytes(), L.stream>>>(rows, M);
+    k_mp_grad_reduce<<<grid_for(kMpParams + 1, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(M, nmlp, nloss, rows);
+    k_mp_adam<<<grid_for(kMpParams, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(M, lr, t);
+}
+
+int mp_prepare()
+{
+    return (int)cudaFuncSetAttribute(k_mp_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mp_bwd_smem_bytes());
+}
+
+int mp_weights_bf16_count() { return kWB; }
+
+void launch_mp_convert(MpBuffers& M, cudaStream_t s)
+{
+    k_mp_adam<<<grid_for(kMpParams, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(M, 0.f, 1);
+}
+
+}  // namespace ss

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,8 @@ std::string g_create_error;
 Launch launch_of(const sp_sim* s, cudaStream_t st) { return Launch{st, s->num_sms}; }
 
 bool mixed(const sp_sim* s) { return s->p.precision == SP_PREC_MIXED; }
+
+bool warm_from_prev(const sp_sim* s) { return s->p.warm_start == SP_WARM_PREV || s->learned; }
 
 template <class T>
 int dev_alloc(sp_sim* s, T** ptr, size_t count)
@@ -175,7 +178,7 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs)
     KParams& P = s->kp;
     DevBuffers& B = s->B;
     Launch L = launch_of(s, cs);
-    const bool warm = s->p.warm_start == SP_WARM_PREV;
+    const bool warm = warm_from_prev(s);
     long long launches = 0;
     if (P.ncell == 1) {
         launch_identity_gather(P, B, warm, L);
@@ -295,7 +298,11 @@ int capture_step_graph(sp_sim* s)
     long long launches = enqueue_build(s, cs);
     launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
     launches += 1;
-    const bool warm = s->p.warm_start == SP_WARM_PREV;
+    if (s->learned) {
+        launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
+        launches += mp_infer_launches();
+    }
+    const bool warm = warm_from_prev(s);
     int rc = enqueue_solve(s, cs, warm, true, &launches);
     launch_integrate(s->kp, s->B, launch_of(s, cs));
     launches += 1;
@@ -463,6 +470,13 @@ int sp_sim_destroy(sp_sim* s)
                     B.xi_inj, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (s->mp_alloc) {
+        MpBuffers& M = s->mp;
+        void* mps[] = {M.x0, M.a0, M.y, M.a1, M.dy, M.g1, M.master, M.m, M.v, M.grad, M.gpart, M.dpart, M.wb, M.scal,
+                       M.part, M.ticket};
+        for (void* q : mps)
+            if (q) cudaFree(q);
+    }
     if (s->st_host) cudaFreeHost(s->st_host);
     for (auto& c : s->cap_stream)
         if (c) cudaStreamDestroy(c);
@@ -649,8 +663,8 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
             SS_CUDA(cudaMemcpyAsync(s->B.x + a * np, v0_dev + (size_t)a * n, sizeof(double) * n,
                                     cudaMemcpyDeviceToDevice, s->stream));
         from_x = 1;
-    } else if (s->p.warm_start == SP_WARM_PREV) {
-        from_x = 1;   // x holds the previous velocities, gathered by the build
+    } else if (warm_from_prev(s)) {
+        from_x = 1;   // x holds the previous velocities (gathered by the build) or the network's guess
     }
     long long launches = 0;
     if (!s->host_loop && !s->solve_exec[from_x]) {
@@ -701,7 +715,11 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
                 launches += enqueue_build(s, s->stream);
                 launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, s->stream));
                 launches += 1;
-                SS_TRY(enqueue_solve(s, s->stream, s->p.warm_start == SP_WARM_PREV, false, &launches));
+                if (s->learned) {
+                    launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, s->stream));
+                    launches += mp_infer_launches();
+                }
+                SS_TRY(enqueue_solve(s, s->stream, warm_from_prev(s), false, &launches));
                 launch_integrate(s->kp, s->B, launch_of(s, s->stream));
                 launches += 1;
                 SS_TRY(read_state(s));
@@ -769,7 +787,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         return SP_OK;
     };
     enum { START = -1, SORT = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER, COUNT, FILL, PERSIST, INIT, STRESS,
-           INTEGRATE };
+           INTEGRATE, MPNN };
     launch_reset_step_stats(B.st, s->stream);
     int rc = mark(START);
     if (rc == SP_OK) {
@@ -788,9 +806,13 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         mark(COUNT);
         launch_nbr_fill(P, B, true, s->use_inj, mx, L);
         rc = mark(FILL);
+        if (rc == SP_OK && s->learned) {
+            launch_mp_infer(P, B, s->mp, L);
+            rc = mark(MPNN);
+        }
     }
     if (rc == SP_OK) {
-        launch_cg_init(P, B, s->p.warm_start == SP_WARM_PREV, mx, L);
+        launch_cg_init(P, B, warm_from_prev(s), mx, L);
         rc = mark(INIT);
     }
     const bool pers = mx && s->persistent;
@@ -852,7 +874,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     }
     double* acc[] = {&out->sort_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
                      &out->direction_ms, &out->other_ms, &out->count_ms, &out->fill_ms, &out->persistent_ms,
-                     &out->init_ms, &out->stress_ms, &out->integrate_ms};
+                     &out->init_ms, &out->stress_ms, &out->integrate_ms, &out->mpnn_ms};
     for (size_t k = 1; rc == SP_OK && k < ev.size(); ++k) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
@@ -1170,6 +1192,125 @@ int sp_structure_factor(sp_sim* s, int32_t nkx, int32_t nky, int32_t grid, doubl
     for (void* q : ptrs)
         if (q) cudaFree(q);
     return rc;
+}
+
+int sp_mpnn_num_params(void) { return kMpParams; }
+
+int sp_mpnn_enable(sp_sim* s, uint64_t seed, const float* weights_host)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    MpBuffers& M = s->mp;
+    if (!s->mp_alloc) {
+        const size_t rows = 3 * (size_t)s->kp.n;
+        int a = SP_OK;
+        auto A = [&](int r) { if (a == SP_OK) a = r; };
+        A(dev_alloc(s, &M.x0, rows));
+        A(dev_alloc(s, &M.a0, rows));
+        A(dev_alloc(s, &M.y, rows));
+        A(dev_alloc(s, &M.a1, rows));
+        A(dev_alloc(s, &M.dy, rows));
+        A(dev_alloc(s, &M.g1, rows));
+        A(dev_alloc(s, &M.master, kMpParams));
+        A(dev_alloc(s, &M.m, kMpParams));
+        A(dev_alloc(s, &M.v, kMpParams));
+        A(dev_alloc(s, &M.grad, kMpParams));
+        A(dev_alloc(s, &M.gpart, (size_t)1024 * kMpParams));
+        A(dev_alloc(s, &M.dpart, (size_t)1024 * 12));
+        A(dev_alloc(s, &M.wb, (size_t)mp_weights_bf16_count()));
+        A(dev_alloc(s, &M.scal, 4));
+        A(dev_alloc(s, &M.part, (size_t)kMaxPartials));
+        A(dev_alloc(s, &M.ticket, 4));
+        s->mp_alloc = true;   // freed by sp_sim_destroy even if an allocation failed
+        if (a != SP_OK) return a;
+        if (mp_prepare() != 0) {
+            s->err = "could not enable the shared memory of the training kernel";
+            return SP_ERR_CUDA;
+        }
+    }
+    std::vector<float> w(kMpParams, 0.f);
+    if (weights_host) {
+        std::memcpy(w.data(), weights_host, sizeof(float) * kMpParams);
+    } else {
+        // scaled normal hidden weights; readout = the previous-velocity guess
+        std::mt19937_64 gen(seed);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        for (int k = 0; k < kMpOffW2; ++k) w[k] = (float)(nd(gen) / std::sqrt(6.0));
+        for (int k = kMpOffW2; k < kMpOffO; ++k) w[k] = (float)(nd(gen) / 8.0);
+        w[kMpOffO + 9] = 1.f;
+    }
+    SS_CUDA(cudaMemsetAsync(M.wb, 0, sizeof(__nv_bfloat16) * mp_weights_bf16_count(), s->stream));
+    SS_CUDA(cudaMemsetAsync(M.m, 0, sizeof(float) * kMpParams, s->stream));
+    SS_CUDA(cudaMemsetAsync(M.v, 0, sizeof(float) * kMpParams, s->stream));
+    SS_CUDA(cudaMemsetAsync(M.ticket, 0, sizeof(unsigned int) * 4, s->stream));
+    SS_CUDA(cudaMemsetAsync(M.scal, 0, sizeof(double) * 4, s->stream));
+    SS_CUDA(cudaMemcpyAsync(M.master, w.data(), sizeof(float) * kMpParams, cudaMemcpyHostToDevice, s->stream));
+    launch_mp_convert(M, s->stream);
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    s->mp_t = 0;
+    s->learned = true;
+    free_graphs(s);
+    return SP_OK;
+}
+
+int sp_mpnn_disable(sp_sim* s)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    s->learned = false;
+    free_graphs(s);
+    return SP_OK;
+}
+
+int sp_mpnn_get_weights(sp_sim* s, float* w_host)
+{
+    if (!s || !w_host || !s->mp_alloc) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_CUDA(cudaMemcpyAsync(w_host, s->mp.master, sizeof(float) * kMpParams, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int sp_mpnn_set_weights(sp_sim* s, const float* w_host)
+{
+    if (!s || !w_host || !s->mp_alloc) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    SS_CUDA(cudaMemcpyAsync(s->mp.master, w_host, sizeof(float) * kMpParams, cudaMemcpyHostToDevice, s->stream));
+    launch_mp_convert(s->mp, s->stream);
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int sp_mpnn_forward(sp_sim* s, double* guess_host)
+{
+    if (!s || !s->mp_alloc) return SP_ERR_INVALID_ARG;
+    if (!s->assembled) {
+        s->err = "sp_mpnn_forward needs sp_assemble first";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, s->stream));
+    SS_CUDA(cudaGetLastError());
+    if (guess_host) {
+        launch_scatter_by_id(s->B.x, s->kp.npad, s->B.id_w, s->kp.n, s->B.stage, s->stream);
+        SS_CUDA(cudaMemcpyAsync(guess_host, s->B.stage, sizeof(double) * 3 * s->kp.n, cudaMemcpyDeviceToHost,
+                                s->stream));
+    }
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
+}
+
+int sp_mpnn_train_step(sp_sim* s, float lr, double* loss, float* grad_host)
+{
+    if (!s || !s->mp_alloc || !(lr >= 0.f)) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    s->mp_t += 1;
+    launch_mp_train(s->kp, s->B, s->mp, lr, s->mp_t, launch_of(s, s->stream));
+    SS_CUDA(cudaGetLastError());
+    if (loss) SS_CUDA(cudaMemcpyAsync(loss, s->mp.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (grad_host)
+        SS_CUDA(cudaMemcpyAsync(grad_host, s->mp.grad, sizeof(float) * kMpParams, cudaMemcpyDeviceToHost, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    return SP_OK;
 }
 
 }  // extern "C"

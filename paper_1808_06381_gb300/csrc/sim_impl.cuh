@@ -30,6 +30,10 @@ struct sp_sim {
     cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
     long long fixed_launches_step = 0;
     long long fixed_launches_solve = 0;
+    ss::MpBuffers mp{};           // learned warm start (allocated by sp_mpnn_enable)
+    bool mp_alloc = false;
+    bool learned = false;         // run the network before every solve of a step
+    int mp_t = 0;                 // Adam step counter
     std::string err;
 };
 
@@ -42,6 +46,7 @@ int grow_pairs(sp_sim* s);
 int clear_flags(sp_sim* s);
 int set_device(sp_sim* s);
 void free_graphs(sp_sim* s);
+bool warm_from_prev(const sp_sim* s);   // the solve starts from x (previous velocities or the network's guess)
 }  // namespace ss_host
 
 std::string& sp_global_error();

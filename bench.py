@@ -208,8 +208,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "learned", "batch", "large"],
+                    help="mixed: N=262,144 precision workload (the default line); learned: the same with the "
+                         "learned warm start; batch: 64 replicas; large: N=4,194,304")
+    ap.add_argument("--train-steps", type=int, default=60)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.impl == "ours" and args.workload != "mixed":
+        return {"learned": run_learned, "batch": run_batch, "large": run_large}[args.workload](args)
 
     workload = synth.PRECISION
     if args.n:
@@ -365,6 +371,169 @@ def main():
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _common_line(metric_value, n_total, steps, warmup, ms_per_step, dtype, config, extra):
+    line = {"metric": METRIC, "value": metric_value, "unit": "particle-steps/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def _sim(ss, w, precision, warm, pos=None, seed=None):
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    return ss.Simulation(w.n, w.L, kappa, alpha=w.alpha, eps=w.eps, zeta=w.zeta, kT=w.kT, dt=w.dt, rc=w.rc,
+                         seed=w.seed if seed is None else seed, precision=precision, warm_start=warm,
+                         cg_tol=w.tol, cg_max_iter=2000,
+                         positions=synth.uniform_positions(w.n, w.L, w.seed) if pos is None else pos)
+
+
+def run_learned(args):
+    """Learned warm start at N=262,144, kappa*tau=0.5: the network is trained online for
+    --train-steps steps (untimed), then K steps are timed with it and, from the same state,
+    with a cold start (v0 = 0) and with the previous-velocity start."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    w = synth.LEARNED
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sim = _sim(ss, w, "mixed", "prev")
+    sim.step(args.warmup)
+    sim.mpnn_enable(seed=1)
+    losses = []
+    for _ in range(args.train_steps):
+        sim.step(1)
+        losses.append(sim.mpnn_train_step(lr=2e-3))
+    pos = sim.get_positions()
+    delta, step = sim.state()
+    results = {}
+    clocks = ClockSampler(None)
+    clocks.start()
+    t, launches, iters, res = run_steps(sim, args.steps, stream, flush)
+    clk = clocks.stop()
+    prof = sim.profile_step()
+    results["learned"] = (t, iters, res)
+    for warm in ("none", "prev"):
+        other = _sim(ss, w, "mixed", warm, pos=pos)
+        other.set_positions(pos, delta)
+        other.set_step(step)
+        if warm == "prev":
+            other.step(1)   # one step so that the previous velocities exist
+        t2, _, it2, r2 = run_steps(other, args.steps, stream, flush)
+        results[warm] = (t2, it2, r2)
+        other.close()
+    sim.close()
+    n = w.n
+    val = n * args.steps / (results["learned"][0] / 1e3)
+    line = _common_line(val, n, args.steps, args.warmup, results["learned"][0] / args.steps, "bf16+f32+f64",
+                        {"workload": w.name, "n": n, "kappa_tau": w.kappa_tau, "cg_tol": w.tol,
+                         "precision": "mixed", "warm_start": "learned", "train_steps": args.train_steps,
+                         "l2": "flushed between timed steps (512 MB write)"},
+                        {"cg_iterations_per_step": results["learned"][1] / args.steps,
+                         "max_true_residual": results["learned"][2],
+                         "comparison": {k: {"value": n * args.steps / (v[0] / 1e3),
+                                            "cg_iterations_per_step": v[1] / args.steps,
+                                            "max_true_residual": v[2]}
+                                        for k, v in results.items()},
+                         "training_loss_first_last": [losses[0], losses[-1]] if losses else None,
+                         "mpnn_ms_per_step": prof["mpnn_ms"], "gpu_launches": launches, "clocks": clk})
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """64 replicas (N log-uniform in [8192, 131072], kappa*tau log-uniform in [0.01, 1]) advanced
+    as one batch (one graph per step, one cooperative solve launch) versus the same replicas
+    stepped one after another.  The batch's data (~1.3 GB) is larger than L2."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    reps = synth.batch_replicas()
+    kws = [dict(n=r.n, L=r.L, kappa=ss.kappa_from_kappa_tau(r.kappa_tau), seed=r.seed, cg_tol=r.tol,
+                precision="mixed", warm_start="prev", cg_max_iter=2000) for r in reps]
+    pos = [synth.uniform_positions(r.n, r.L, r.seed) for r in reps]
+    ntot = sum(r.n for r in reps)
+    batch = ss.Batch(kws, positions=pos)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(None)
+    clocks.start()
+    t0 = time.perf_counter()
+    infos = batch.step(args.steps)
+    t_batch = time.perf_counter() - t0
+    clk = clocks.stop()
+    iters = sum(x["cg_iterations"] for x in infos)
+    worst = max(x["last_residual"] for x in infos)
+    launches = sum(x["kernel_launches"] for x in infos)
+    blocks = batch.blocks().tolist()
+    batch.close()
+    # the same replicas, one after another (each its own graph per step)
+    sims = [ss.Simulation(positions=pos[k], **kws[k]) for k in range(len(reps))]
+    for sm in sims:
+        sm.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sm in sims:
+            sm.step(1)
+    t_seq = time.perf_counter() - t0
+    for sm in sims:
+        sm.close()
+    val = ntot * args.steps / t_batch
+    line = _common_line(val, ntot, args.steps, args.warmup, 1e3 * t_batch / args.steps, "f32+f64",
+                        {"workload": "batch-64-replicas", "replicas": len(reps), "n_total": ntot,
+                         "n_min": min(r.n for r in reps), "n_max": max(r.n for r in reps),
+                         "cg_tol": reps[0].tol, "precision": "mixed", "l2": "working set > L2"},
+                        {"cg_iterations_per_replica_step": iters / (len(reps) * args.steps),
+                         "max_true_residual": worst, "gpu_launches": launches,
+                         "sequential": {"value": ntot * args.steps / t_seq, "ms_per_step": 1e3 * t_seq / args.steps},
+                         "speedup_vs_sequential": t_seq / t_batch, "blocks_per_replica": blocks,
+                         "timing": "host wall clock around the synchronising batch call", "clocks": clk})
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    """N = 4,194,304 (box 111.8), mixed solver: the solver's working set (~2 GB) is far larger
+    than L2, so this is the HBM-bound regime of the same kernels."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    w = synth.LARGE
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(4, dtype=torch.float32, device="cuda")   # inputs are larger than L2
+    sim = _sim(ss, w, "mixed", "prev")
+    sim.step(args.warmup)
+    clocks = ClockSampler(None)
+    clocks.start()
+    t, launches, iters, res = run_steps(sim, args.steps, stream, flush)
+    clk = clocks.stop()
+    prof = sim.profile_step()
+    peak, peak_kind = measured_peaks()
+    pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
+    pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
+    spmv = spmv_algorithmic_bytes(prof["n"], prof["nnz"], "mixed") / (prof["spmv_probe_ms"] * 1e-3) / 1e9
+    t_sq = time.perf_counter()
+    S, qx, qy = sim.structure_factor(48, 48, grid=256)
+    t_sq = time.perf_counter() - t_sq
+    sim.close()
+    n = w.n
+    line = _common_line(n * args.steps / (t / 1e3), n, args.steps, args.warmup, t / args.steps, "f32+f64",
+                        {"workload": w.name, "n": n, "box": w.L[0], "kappa_tau": w.kappa_tau, "cg_tol": w.tol,
+                         "precision": "mixed", "warm_start": "prev", "l2": "working set > L2"},
+                        {"cg_iterations_per_step": iters / args.steps, "max_true_residual": res,
+                         "gpu_launches": launches,
+                         "roofline": {"kernel": "k32_cg_persistent", "bound": "hbm", "achieved": pach, "peak": peak,
+                                      "unit": "GB/s", "frac": pach / peak, "traffic": None,
+                                      "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                                      "algorithmic_bytes_per_launch": pbytes,
+                                      "avg_launch_ms": prof["persistent_ms"]},
+                         "roofline_spmv_kernel": {"achieved": spmv, "frac": spmv / peak,
+                                                  "avg_launch_ms": prof["spmv_probe_ms"]},
+                         "kernel_ms_per_step": {k: prof[k] for k in ("persistent_ms", "build_ms", "fill_ms",
+                                                                      "count_ms", "sort_ms", "other_ms")},
+                         "structure_factor_ms": 1e3 * t_sq, "clocks": clk})
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

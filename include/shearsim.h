@@ -182,7 +182,7 @@ typedef struct sp_kernel_profile {
     int32_t precision;               /* enum sp_precision of the solver */
     double sort_ms;                  /* part of build_ms: binning and the counting sort into cell order */
     double count_ms;                 /* part of build_ms: pair counting and the row-pointer scan */
-    double fill_ms;                  /* part of build_ms: the fused pair/assembly pass */
+    double fill_ms;                  /* part of build_ms: the pair fill (columns and image codes) */
     int64_t nnz_slots;               /* stored entries including the sliced layout's padding */
     int32_t probe_reps;              /* back-to-back launches timed for the two fields below */
     double spmv_probe_ms;            /* average SpMV kernel time, launched back to back */
@@ -194,6 +194,7 @@ typedef struct sp_kernel_profile {
     double stress_ms;                /* part of other_ms: the stress kernel */
     double integrate_ms;             /* part of other_ms: the position update */
     double mpnn_ms;                  /* the learned warm start's inference (0 when not used) */
+    double assemble_ms;              /* part of build_ms: FP64 assembly of the matrix and right-hand side */
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 

@@ -72,7 +72,8 @@ class sp_kernel_profile(ctypes.Structure):
                 ("spmv_probe_ms", ctypes.c_double), ("update_probe_ms", ctypes.c_double),
                 ("persistent_ms", ctypes.c_double), ("true_checks", ctypes.c_int32),
                 ("persistent_blocks", ctypes.c_int32), ("init_ms", ctypes.c_double), ("stress_ms", ctypes.c_double),
-                ("integrate_ms", ctypes.c_double), ("mpnn_ms", ctypes.c_double)]
+                ("integrate_ms", ctypes.c_double), ("mpnn_ms", ctypes.c_double),
+                ("assemble_ms", ctypes.c_double)]
 
 
 def declared_symbols() -> list:

@@ -1,21 +1,23 @@
 // Persistent mixed-precision CG: the whole solve of Eq. algebra (arXiv
 // 1808.06381, §Method) in one cooperative launch.
 //
-// Same iteration as the mixed solver of cg.cu (FP32 SpMV with the direction
-// update fused, FP32 update of r and of the correction d, double-float dot
-// products, FP64 residual replacement), but the iteration loop runs inside the
-// kernel: one block per window of 256 rows (or several windows per block
-// when the rows outnumber the resident threads), two grid-wide barriers per
-// iteration, and the CG scalars reduced redundantly — in the same fixed order —
-// by every block from the per-block partial sums, so every block takes the
-// same decisions.  A block touches the solver vectors of its own rows only,
-// except for the gathers of r (and of x in the FP64 residual), which read rows
-// written by other blocks since the last barrier and therefore bypass L1.
+// Same iteration as the mixed solver of cg.cu (Jacobi-preconditioned CG: FP32
+// SpMV with the direction update fused, FP32 update of r and of the
+// correction d, double-float dot products, FP64 residual replacement), but
+// the iteration loop runs inside the kernel: a block owns whole windows of
+// 256 rows, two grid-wide reductions per iteration, and the CG scalars
+// decided by thread 0 of every block from identical totals, so every block
+// takes the same decisions.  A block writes the solver vectors of its own
+// rows only; its gathers of r (and of x in the FP64 residual) read rows that
+// other blocks wrote before the last barrier.
 //
-// The barrier is a counter plus a generation word in device memory.  The
-// launch is cooperative (all blocks resident), and every wait is bounded: a
-// block that waits longer than kBarrierSpinLimit polls sets SP_ERR_TIMEOUT and
-// leaves the solve, so no GPU can hang on it.
+// Grid barrier: one arrival counter (acquire-release atomic), a generation
+// word on its own line that the last arriving block releases, and the error
+// flag copied next to it by that block.  After the barrier every block sums
+// all blocks' partial sums itself, in one fixed order.  The launch is
+// cooperative (all blocks resident), and every wait is bounded by the global
+// timer: a block that waits longer than kBarrierTimeoutNs sets
+// SP_ERR_TIMEOUT and leaves the solve, so no GPU can hang on it.
 #include <math.h>
 
 #include <mutex>
@@ -27,169 +29,149 @@ namespace ss {
 namespace {
 
 constexpr int kPBlock = 256;
-constexpr long long kBarrierSpinLimit = 1ll << 24;   // x ~100 ns sleeps: well above a second
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 
 struct PShared {
     float2 df[32];
     double d[32];
     double bcast[4];
     int flag;
-    // scalars decided by thread 0 (FP64 math once per block, not once per thread)
+    // decided by thread 0 (FP64 scalars once per block, not once per thread)
     float alpha_f, beta_f;
-    int action;   // 0 continue, 1 check the true residual, 2 stop
+    int action;   // 0 continue, 1 replace the residual, 2 stop
+    // thread 0's CG state, kept here rather than in every thread's registers
+    double rho, rr_restart, bnorm2, last_res;
+    int iter, restarts, status;
 };
 
-// Grid barrier (all blocks of a cooperative launch).  Returns false when the
-// solve must stop (an error was raised anywhere, including a barrier timeout).
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Arrival and release by thread 0; returns the error flag (0 = continue).
+// The writes of every thread of every block before the barrier are visible
+// to every thread after it (release by each arrival, acquire by the waiters,
+// and the block barriers on both sides).
+__device__ __forceinline__ int barrier_thread0(DevState* st, unsigned int target, int nb)
+{
+    if (atom_add_acq_rel_gpu(&st->bar_count, 1u) == (unsigned)nb - 1) {
+        const int e = *(volatile int*)&st->error;
+        st->bar_err = e;
+        st->bar_count = 0u;
+        st_release_gpu(&st->bar_gen, target);
+        return e;
+    }
+    const unsigned long long t0 = global_ns();
+    for (unsigned int polls = 1;; ++polls) {
+        if (ld_acquire_gpu(&st->bar_gen) == target) return *(volatile int*)&st->bar_err;
+        if ((polls & 255u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+            return (int)SP_ERR_TIMEOUT;
+        }
+    }
+}
+
+// Grid barrier (the blocks of one system).  Returns false when the solve
+// must stop (an error was raised anywhere, including a barrier timeout).
 __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShared& sh, int nb)
 {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int target = gen + 1u;
-        __threadfence();
-        if (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicExch(&st->bar_gen, target);
-        } else {
-            long long spins = 0;
-            while (atomicAdd(&st->bar_gen, 0u) != target) {
-                __nanosleep(100);
-                if (++spins > kBarrierSpinLimit) {
-                    atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        sh.flag = atomicAdd(&st->error, 0);
-    }
+    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
     __syncthreads();
     gen += 1u;
     return sh.flag == 0;
 }
 
-// Barrier fused with the reduction of K sums: every block publishes its block
-// sum; the last block to arrive sums all blocks' partials (every thread a
-// strided share, in the same fixed order whichever block is last), stores the
-// totals and only then releases the barrier; every block then reads the
-// totals.  One reduction costs one barrier plus about two memory latencies.
+// Grid-wide sums of K double-float values: every block publishes its block
+// sums, passes the barrier, then sums all blocks' partials itself, in the
+// same fixed order in every block (so all blocks hold identical totals).
+// Consecutive calls must use alternating partial sets: a block may still be
+// reading one set when a faster block writes the next.
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
-                                               const dfloat (&v)[K], float2* partials, double* totals,
-                                               double (&out)[K], int bid, int nb)
+                                               const dfloat (&v)[K], float2* partials, double (&out)[K],
+                                               int bid, int nb)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const dfloat t = block_sum_df(v[k], sh.df);
         if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = make_float2(t.hi, t.lo);
     }
+    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        sh.flag = (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    const unsigned int target = gen + 1u;
-    if (sh.flag) {   // last to arrive: reduce, publish, release
-        __threadfence();
+    gen += 1u;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            dfloat a{0.f, 0.f};
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                const float2 p = __ldcg(partials + k * kMaxPartials + b);
-                a = df_add(a, dfloat{p.x, p.y});
-            }
-            const dfloat t = block_sum_df(a, sh.df);
-            if (threadIdx.x == 0) totals[k] = (double)t.hi + (double)t.lo;
+    for (int k = 0; k < K; ++k) {
+        dfloat a{0.f, 0.f};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const float2 p = __ldcg(partials + k * kMaxPartials + b);
+            a = df_add(a, dfloat{p.x, p.y});
         }
-        if (threadIdx.x == 0) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicExch(&st->bar_gen, target);
-        }
-    } else if (threadIdx.x == 0) {
-        long long spins = 0;
-        while (atomicAdd(&st->bar_gen, 0u) != target) {
-            __nanosleep(64);
-            if (++spins > kBarrierSpinLimit) {
-                atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
-                break;
-            }
-        }
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        sh.flag = atomicAdd(&st->error, 0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh.bcast[k] = __ldcg(totals + k);
+        const dfloat t = block_sum_df(a, sh.df);
+        if (threadIdx.x == 0) sh.bcast[k] = (double)t.hi + (double)t.lo;
     }
     __syncthreads();
-    gen = target;
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
     return sh.flag == 0;
 }
 
+// The same for FP64 values (the rare FP64 residual replacement).
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
-                                               const double (&v)[K], double* partials, double* totals,
-                                               double (&out)[K], int bid, int nb)
+                                               const double (&v)[K], double* partials, double (&out)[K],
+                                               int bid, int nb)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const double t = block_sum(v[k], sh.d);
         if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = t;
     }
+    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        sh.flag = (atomicAdd(&st->bar_count, 1u) == (unsigned)nb - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    const unsigned int target = gen + 1u;
-    if (sh.flag) {
-        __threadfence();
+    gen += 1u;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double a = 0.0;
-            for (int b = threadIdx.x; b < nb; b += blockDim.x)
-                a += __ldcg(partials + k * kMaxPartials + b);
-            const double t = block_sum(a, sh.d);
-            if (threadIdx.x == 0) totals[k] = t;
-        }
-        if (threadIdx.x == 0) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicExch(&st->bar_gen, target);
-        }
-    } else if (threadIdx.x == 0) {
-        long long spins = 0;
-        while (atomicAdd(&st->bar_gen, 0u) != target) {
-            __nanosleep(64);
-            if (++spins > kBarrierSpinLimit) {
-                atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
-                break;
-            }
-        }
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        sh.flag = atomicAdd(&st->error, 0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh.bcast[k] = __ldcg(totals + k);
+    for (int k = 0; k < K; ++k) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += __ldcg(partials + k * kMaxPartials + b);
+        const double t = block_sum(a, sh.d);
+        if (threadIdx.x == 0) sh.bcast[k] = t;
     }
     __syncthreads();
-    gen = target;
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
     return sh.flag == 0;
 }
 
-constexpr int kBatchP = 6;    // FP32 gathers per batch
-constexpr int kBatchP64 = 2;  // FP64 gathers per batch (the rare true-residual SpMV)
+constexpr int kBatchP = 6;    // FP32 gathers in flight per thread
+constexpr int kBatchP64 = 2;  // FP64 gathers in flight (the rare FP64 residual replacement)
 
-// s = sum_j w_ij D^-1_j r_j (FP32); r rows of other blocks are read from L2.
+// s = sum_j w_ij D^-1_j r_j (FP32).  Rows of r written by other blocks before
+// the last barrier are visible to plain loads (the barrier's acquire orders
+// them), so the gathers may hit L1: rows of neighbouring particles are
+// gathered by many rows of the same block.
 __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const float* __restrict__ val,
                                             const float4* r, int e0, int e1, float& s0, float& s1, float& s2)
 {
@@ -203,15 +185,15 @@ __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const f
             j[u] = 0;
             w[u] = 0.f;
             if (e < e1) {
-                j[u] = __ldg(col + e);
-                w[u] = __ldg(val + e);
+                j[u] = ld_stream(col + e);
+                w[u] = ld_stream(val + e);
             }
         }
         float4 g[kBatchP];
 #pragma unroll
         for (int u = 0; u < kBatchP; ++u) {
             g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (w[u] != 0.f) g[u] = __ldcg(r + j[u]);
+            if (w[u] != 0.f) g[u] = r[j[u]];
         }
 #pragma unroll
         for (int u = 0; u < kBatchP; ++u) {
@@ -223,7 +205,7 @@ __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const f
     }
 }
 
-// s_a = sum_j w_ij x_a[j] (FP64 planes; x rows of other blocks are read from L2).
+// s_a = sum_j w_ij x_a[j] (FP64 planes).
 __device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const double* __restrict__ val,
                                             const double* x, int np, int e0, int e1, double& s0, double& s1,
                                             double& s2)
@@ -256,7 +238,8 @@ __device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const d
 }  // namespace
 
 // The solve of one system by blocks bid = 0..nb-1 of the launch (all of the
-// launch for a single system; a share of it in a batch).
+// launch for a single system; a share of it in a batch).  Expects r4 = (r, D^-1)
+// with r = b - A x, p4 = q4 = d4 = 0 and the scalars, from the set-up kernel.
 __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
                                                  PShared& sh)
 {
@@ -265,7 +248,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     __syncthreads();
     if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
     unsigned int gen = 0u;   // used by thread 0 only
-    if (threadIdx.x == 0) gen = atomicAdd(&st->bar_gen, 0u);
+    if (threadIdx.x == 0) gen = *(volatile unsigned int*)&st->bar_gen;
 
     const int nwin = P.nslots / 256;
     const int wb = (int)((long long)bid * nwin / nb);
@@ -274,18 +257,23 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     const float alpha_e = (float)P.alpha;
 
     // CG scalars: thread 0 keeps them in FP64 and makes every decision; the
-    // other threads only see the FP32 step lengths and the action code.
-    double rho = 0.0, rr_restart = 0.0, bnorm2 = 0.0, last_res = 0.0;
-    int iter = 0, restarts = 0, status = SP_OK;
+    // other threads see the FP32 step lengths and the action code.
     if (threadIdx.x == 0) {
-        rho = st->rho;
-        rr_restart = st->rr_restart;
-        bnorm2 = st->bnorm2;
-        last_res = st->last_res;
+        sh.rho = st->rho;
+        sh.rr_restart = st->rr_restart;
+        sh.bnorm2 = st->bnorm2;
+        sh.last_res = st->last_res;
+        sh.iter = 0;
+        sh.restarts = 0;
+        sh.status = SP_OK;
         sh.beta_f = 0.f;
     }
     __syncthreads();
 
+    // partial-sum sets: set 0 for p.q, 1-2 for r.r and r.z, the FP64 array for
+    // the true residual; a block still reading one set after a barrier is
+    // never overtaken by a faster block writing the same set (its next write
+    // lies behind at least one more barrier)
     for (;;) {
         // ---- SpMV with the fused direction update; p.q
         dfloat pq{0.f, 0.f};
@@ -323,21 +311,17 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                 pq = df_add(pq, p0 * q0 + p1 * q1 + p2 * q2);
             }
         }
-        // partial-sum sets: 0 for p.q, 1-2 for r.r and r.z, the FP64 array for the
-        // true residual, so a block still reading one set after a barrier is
-        // never overtaken by a faster block writing the same set (the next
-        // write of a set lies behind at least one more barrier)
         {
             const dfloat v[1] = {pq};
             double tot[1];
-            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, st->totals, tot, bid, nb)) break;
+            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 sh.action = 0;
                 if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
-                    status = SP_ERR_NONFINITE;
+                    sh.status = SP_ERR_NONFINITE;
                     sh.action = 2;
                 } else {
-                    sh.alpha_f = (float)(rho / tot[0]);
+                    sh.alpha_f = (float)(sh.rho / tot[0]);
                 }
             }
         }
@@ -368,18 +352,18 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         {
             const dfloat v[2] = {rr, rz};
             double tot[2];
-            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, st->totals + 2, tot, bid, nb)) break;
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
-                ++iter;
+                ++sh.iter;
                 sh.action = 0;
                 if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-                    status = SP_ERR_NONFINITE;
+                    sh.status = SP_ERR_NONFINITE;
                     sh.action = 2;
                 } else {
-                    sh.beta_f = (float)(tot[1] / rho);
-                    rho = tot[1];
-                    const double target = fmax(P.inner2 * rr_restart, 0.25 * P.tol2 * bnorm2);
-                    if (tot[0] <= target || iter >= P.max_iter) sh.action = 1;
+                    sh.beta_f = (float)(tot[1] / sh.rho);
+                    sh.rho = tot[1];
+                    const double target = fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
+                    if (tot[0] <= target || sh.iter >= P.max_iter) sh.action = 1;
                 }
             }
         }
@@ -426,24 +410,24 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         {
             const double v[2] = {trr, trz};
             double tot[2];
-            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, st->totals + 4, tot, bid, nb)) break;
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
-                last_res = sqrt(tot[0] / bnorm2);
+                sh.last_res = sqrt(tot[0] / sh.bnorm2);
                 if (bid == 0) st->true_checks += 1;
                 sh.action = 0;
                 if (!isfinite(tot[0])) {
-                    status = SP_ERR_NONFINITE;
+                    sh.status = SP_ERR_NONFINITE;
                     sh.action = 2;
-                } else if (tot[0] <= P.tol2 * bnorm2) {
+                } else if (tot[0] <= P.tol2 * sh.bnorm2) {
                     sh.action = 2;   // converged
-                } else if (iter >= P.max_iter || restarts >= kMaxCgRestarts + 8) {
-                    status = SP_ERR_NOT_CONVERGED;
+                } else if (sh.iter >= P.max_iter || sh.restarts >= kMaxCgRestarts + 8) {
+                    sh.status = SP_ERR_NOT_CONVERGED;
                     sh.action = 2;
                 } else {
-                    ++restarts;
-                    rho = tot[1];
+                    ++sh.restarts;
+                    sh.rho = tot[1];
                     sh.beta_f = 0.f;
-                    rr_restart = tot[0];
+                    sh.rr_restart = tot[0];
                 }
             }
         }
@@ -452,13 +436,13 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     }
     // every block's thread 0 holds the same scalars; block 0 records them
     if (bid == 0 && threadIdx.x == 0) {
-        st->iter = iter;
-        st->restarts = restarts;
-        st->last_res = last_res;
+        st->iter = sh.iter;
+        st->restarts = sh.restarts;
+        st->last_res = sh.last_res;
         st->done = 1;
-        if (st->error == 0 && status != SP_OK) {
-            st->status = status;
-            st->error = status;
+        if (st->error == 0 && sh.status != SP_OK) {
+            st->status = sh.status;
+            st->error = sh.status;
         } else if (st->error != 0) {
             st->status = st->error;
         } else {

@@ -21,13 +21,15 @@ struct KParams {
     double L[3];
     double rc2;         // r_c^2: pair kept iff |R|^2 < rc2
     double two_lambda2; // 2 lambda^2, lambda^2 = r_c^2 / (2 ln 20)
+    double w_scale;     // 256 / (2 lambda^2): index scale of the weight table
     double alpha, zeta, kappa, dt;
     double c_ev;        // eps * 0.1 * kT / lambda^2
     double noise_amp;   // sqrt(2 zeta kT / dt)
     unsigned long long seed;
     int nc[3];          // cells per axis (cell edge >= r_c)
     double inv_cw[3];   // cells per unit length
-    int ncell;
+    int ncell;          // cell index slots: tiles of 8^3 cells, ntile[0] * ntile[1] * ntile[2] * 512
+    int ntile[3];       // tiles per axis
     int nslots;         // rows rounded up to a multiple of 256
     int nchunks;        // nslots / 32
     int fast_cells;     // every axis has >= 3 cells: FP32 pre-filter with exact fallback
@@ -61,9 +63,11 @@ struct DevState {
     double last_res;
     double stress_xy;
     unsigned int ticket[4];
-    unsigned int bar_count;   // grid barrier of the persistent solver: arrivals
-    unsigned int bar_gen;     // and generation
-    double totals[8];         // grid-wide sums published by the persistent solver's last block
+    // grid barrier of the persistent solver: arrivals, and (on its own line)
+    // the release generation with the error flag seen by the releasing block
+    alignas(128) unsigned int bar_count;
+    alignas(128) unsigned int bar_gen;
+    int bar_err;
 };
 
 // Device buffers of one simulation (all in the current cell order unless noted).
@@ -108,6 +112,7 @@ struct DevBuffers {
     float4* q4;
     float4* d4;      // correction accumulated since the last fold into x
     double* xi_inj;  // [n][3] injected normals by id (or null)
+    double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
     double* partials;// [kMaxPartials * 4]
     float2* partials_df; // [kMaxPartials * 4] double-float partial sums (mixed solver)
     int* scan_tmp;   // block sums of the scans
@@ -116,6 +121,8 @@ struct DevBuffers {
 };
 
 constexpr int kMaxPartials = 4096;
+constexpr int kExpTab = 1024;
+constexpr int kMaxSmIds = 1024;   // weight table: exp(-t) for t < 4 (pairs have t < ln 20)
 
 // Learned warm start (mpnn.cu): flat FP32 weights W1 [6][64], W2 [64][64],
 // W3 [64][4], o [11] (row-major, in that order).
@@ -232,6 +239,22 @@ __device__ __forceinline__ double sq_norm_exact(double dx, double dy, double dz)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Loads of data that no thread writes during the kernel and that is read
+// once per pass (matrix columns and values): non-coherent path, not
+// allocated in L1, so L1 keeps the gathered vector rows.
+__device__ __forceinline__ int ld_stream(const int* p)
+{
+    int v;
+    asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
                                               unsigned long long k1)
@@ -288,6 +311,22 @@ __device__ __forceinline__ int cell_coord(double x, double inv_cw, int nc)
 {
     int c = (int)floor(x * inv_cw);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Index of cell (cx, cy, cz) in the row order: the cells are grouped in
+// tiles of 8 x 8 x 8 (tiles in x-fastest order, Morton order inside a tile),
+// so any run of consecutive rows covers a compact region of space and the
+// solver's gathers of neighbouring rows reuse cache lines.  Slots of cells
+// outside the box stay empty.
+__device__ __forceinline__ int spread3(int v)
+{
+    return (v & 1) | ((v & 2) << 2) | ((v & 4) << 4);
+}
+
+__device__ __forceinline__ int cell_index(const KParams& P, int cx, int cy, int cz)
+{
+    const int t = ((cz >> 3) * P.ntile[1] + (cy >> 3)) * P.ntile[0] + (cx >> 3);
+    return (t << 9) | spread3(cx & 7) | (spread3(cy & 7) << 1) | (spread3(cz & 7) << 2);
 }
 
 // Image code of a pair: the partner's image sits at R_j + a L_x x + m (L_y y + delta x) + c L_z z.
@@ -420,9 +459,12 @@ void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L);
 void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L);
-void launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool mixed,
-                     Launch L);
-void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool mixed, Launch L);
+// Pair fill (columns and image codes), followed, with assemble, by the FP64
+// assembly of the matrix and right-hand side; returns the kernels launched.
+int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, Launch L);
+void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, Launch L);
+// Fills the weight table exp_tab (host computation, one copy).
+cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream);
 void launch_uniform_positions(const KParams& P, DevBuffers& B, Launch L);
 void launch_philox_blocks(unsigned long long seed, unsigned long long step, long long count,
                           const long long* ids, unsigned long long* out, cudaStream_t s);

@@ -4,8 +4,13 @@
 //
 // Rows are kept in cell order: each step re-sorts the particles by cell with a
 // counting sort (histogram, exclusive scan, scatter) and orders the particles
-// of a cell by id, so the order is deterministic and neighbours sit close in
-// memory for the solver's gathers.
+// of a cell by id, so the order is deterministic.  Cells are numbered in
+// tiles of 8^3 (Morton order inside a tile, cell_index), so that the rows of
+// one block of the solver cover a compact region of space and neighbours sit
+// close in memory for the solver's gathers.
+#include <array>
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace ss {
@@ -21,7 +26,7 @@ __global__ void k_bin(KParams P, const double* __restrict__ pos, int* __restrict
     const int cx = cell_coord(pos[i], P.inv_cw[0], P.nc[0]);
     const int cy = cell_coord(pos[P.npad + i], P.inv_cw[1], P.nc[1]);
     const int cz = cell_coord(pos[2 * P.npad + i], P.inv_cw[2], P.nc[2]);
-    const int c = (cz * P.nc[1] + cy) * P.nc[0] + cx;
+    const int c = cell_index(P, cx, cy, cz);
     cell_of[i] = c;
     slot[i] = atomicAdd(cell_count + c, 1);
 }
@@ -294,6 +299,10 @@ __device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, doub
     const int cz = cell_coord(zi, P.inv_cw[2], nc2);
     const int zlo = zall ? 0 : -1, zhi = zall ? nc2 - 1 : 1;
     const int ylo = yall ? 0 : -1, yhi = yall ? nc1 - 1 : 1;
+    auto scan_cell = [&](int ax, int ay, int az) {
+        const int c = cell_index(P, ax, ay, az);
+        scan(cell_start[c], cell_start[c + 1]);
+    };
     for (int dzc = zlo; dzc <= zhi; ++dzc) {
         int czz = zall ? dzc : cz + dzc;
         if (czz < 0) czz += nc2;
@@ -312,22 +321,17 @@ __device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, doub
                     m = 1;
                 }
             }
-            const int rowbase = (czz * nc1 + cyy) * nc0;
             if (xall) {
-                scan(cell_start[rowbase], cell_start[rowbase + nc0]);
+                for (int ax = 0; ax < nc0; ++ax) scan_cell(ax, cyy, czz);
                 continue;
             }
             int cxc = cx;
             if (m != 0) cxc = cell_coord(wrap_box(xi - (double)m * delta, P.L[0]), P.inv_cw[0], nc0);
-            const int lo = cxc - 1, hi = cxc + 1;
-            if (lo < 0) {
-                scan(cell_start[rowbase + nc0 - 1], cell_start[rowbase + nc0]);
-                scan(cell_start[rowbase], cell_start[rowbase + hi + 1]);
-            } else if (hi >= nc0) {
-                scan(cell_start[rowbase + lo], cell_start[rowbase + nc0]);
-                scan(cell_start[rowbase], cell_start[rowbase + 1]);
-            } else {
-                scan(cell_start[rowbase + lo], cell_start[rowbase + hi + 1]);
+            for (int dxc = -1; dxc <= 1; ++dxc) {
+                int ax = cxc + dxc;
+                if (ax < 0) ax += nc0;
+                if (ax >= nc0) ax -= nc0;
+                scan_cell(ax, cyy, czz);
             }
         }
     }
@@ -386,11 +390,10 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
             }
             const float syf = __fmul_rn((float)m, P.Lf[1]);
             const int cxu0 = m == 0 ? cx : (int)floor((xi - (double)m * delta) * P.inv_cw[0]);
-            const int rowbase = (czz * nc1 + cyy) * nc0;
             for (int dxc = -1; dxc <= 1; ++dxc) {
                 const int cxu = cxu0 + dxc;
                 const int a = floor_div(cxu, nc0);
-                const int c = rowbase + (cxu - a * nc0);
+                const int c = cell_index(P, cxu - a * nc0, cyy, czz);
                 const float sxf = __fadd_rn(__fmul_rn((float)m, deltaf), __fmul_rn((float)a, P.Lf[0]));
                 const unsigned char code = image_code(a, m, c_img);
                 const int j1 = cell_start[c + 1];
@@ -518,47 +521,101 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
     B.b[2 * np + i] = F2 / P.zeta;
 }
 
-// Weights and pair sums of row i from its stored entries (FP64; the
-// entries' image codes give the exact separations without divisions).
-// Padding entries get weight 0.
-__device__ __forceinline__ void assemble_row(const KParams& P, const DevBuffers& B, int i, double delta,
-                                             unsigned long long step, int use_inj)
+// The pair weight w = exp(-|R|^2 / 2 lambda^2) of §Method for a pair within
+// r_c, i.e. exp(-t) with 0 <= t < ln 20, by the table-driven method of
+// P. T. P. Tang ("Table-driven implementation of the exponential function in
+// IEEE floating-point arithmetic", ACM TOMS 15, 1989): 256 t = k + f with k
+// the nearest integer and |f| <= 1/2, exp(-t) = E_k exp(-f / 256), E_k =
+// exp(-k / 256) from a table computed on the host, and exp(-f / 256) from
+// its Taylor polynomial of degree 5 (truncation below 1e-19 relative).  The
+// result is within about 2 ulp of exp(-t), for 9 FP64 operations.
+__device__ __forceinline__ double pair_weight(const KParams& P, const double* __restrict__ etab, double r2)
 {
+    constexpr double kRound = 6755399441055744.0;   // 1.5 * 2^52: adding it rounds to an integer
+    constexpr double c1 = -1.0 / 256.0;
+    constexpr double c2 = 1.0 / (2.0 * 65536.0);
+    constexpr double c3 = -1.0 / (6.0 * 16777216.0);
+    constexpr double c4 = 1.0 / (24.0 * 4294967296.0);
+    constexpr double c5 = -1.0 / (120.0 * 1099511627776.0);
+    const double kr = fma(r2, P.w_scale, kRound);
+    const int k = __double2loint(kr);               // low word: round(256 t)
+    const double kd = kr - kRound;
+    if (k >= kExpTab) return exp(-r2 / P.two_lambda2);   // t >= 4: not a pair within r_c
+    const double f = fma(r2, P.w_scale, -kd);       // 256 t - k, one rounding
+    double q = fma(c5, f, c4);
+    q = fma(q, f, c3);
+    q = fma(q, f, c2);
+    q = fma(q, f, c1);
+    q = fma(q, f, 1.0);
+    return __ldg(etab + k) * q;
+}
+
+cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream)
+{
+    static const std::array<double, kExpTab> host = [] {
+        std::array<double, kExpTab> t{};
+        for (int k = 0; k < kExpTab; ++k) t[k] = std::exp(-(double)k / 256.0);
+        return t;
+    }();
+    cudaError_t e = cudaMemcpyAsync(exp_tab, host.data(), sizeof(double) * kExpTab, cudaMemcpyHostToDevice,
+                                    stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
+}
+
+// Assembly of Eq. algebra from the stored pairs: one thread per slot of the
+// sliced layout, so the 32 rows of a warp have nearly equal lengths and read
+// their entries with coalesced loads; the FP64 work runs once per entry in
+// converged warps.  Separations use the entries' image codes (exact, no
+// divisions): the shifts n delta and a L_x of the canonical minimum image are
+// exact for |n| <= 1 and |a| <= 2 and taken by selection.  Padding entries
+// get weight 0.
+__global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
+{
+    const DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int slot = blockIdx.x * 256 + threadIdx.x;
+    const int i = B.slot_row[slot];
+    if (i < 0) return;
+    const double delta = st->delta;
     const int np = P.npad;
     const double xi = B.pos_w[i], yi = B.pos_w[np + i], zi = B.pos_w[2 * np + i];
-    const int slot = B.row_slot[i];
     const int base = B.chunk_off[slot >> 5] + (slot & 31);
     const int clen = (B.chunk_off[(slot >> 5) + 1] - B.chunk_off[slot >> 5]) >> 5;
     const int cnt = B.row_cnt[i];
+    const double Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
+    const double* __restrict__ pos = B.pos_w;
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
     for (int k = 0; k < cnt; ++k) {
         const int e = base + 32 * k;
-        const int j = B.col[e];
-        double dx, dy, dz;
-        const double n = image_separation(P, delta, xi, yi, zi, B.pos_w[j], B.pos_w[np + j],
-                                          B.pos_w[2 * np + j], B.img[e], dx, dy, dz);
-        const double w = exp(-sq_norm_exact(dx, dy, dz) / P.two_lambda2);
+        const int j = __ldg(B.col + e);
+        const int code = __ldg(B.img + e);
+        const int a = (code & 7) - 2, m = ((code >> 3) & 3) - 1, c = ((code >> 5) & 3) - 1;
+        const double sn = m == 0 ? 0.0 : (m > 0 ? delta : -delta);
+        const double sa = a == 0 ? 0.0 : (a == 1 ? Lx : (a == -1 ? -Lx : __dmul_rn(Lx, (double)a)));
+        const double sy = m == 0 ? 0.0 : (m > 0 ? Ly : -Ly);
+        const double sz = c == 0 ? 0.0 : (c > 0 ? Lz : -Lz);
+        const double dx = __dsub_rn(__dsub_rn(__dsub_rn(xi, pos[j]), sn), sa);
+        const double dy = __dsub_rn(__dsub_rn(yi, pos[np + j]), sy);
+        const double dz = __dsub_rn(__dsub_rn(zi, pos[2 * np + j]), sz);
+        const double w = pair_weight(P, B.exp_tab, sq_norm_exact(dx, dy, dz));
         B.val[e] = w;
         B.val32[e] = (float)w;
         sw += w;
-        fx += dx * w;
-        fy += dy * w;
-        fz += dz * w;
-        nw += n * w;
+        fx = fma(dx, w, fx);
+        fy = fma(dy, w, fy);
+        fz = fma(dz, w, fz);
+        nw += m == 0 ? 0.0 : (m > 0 ? w : -w);
     }
     for (int k = cnt; k < clen; ++k) {
         B.val[base + 32 * k] = 0.0;
         B.val32[base + 32 * k] = 0.f;
     }
-    finish_row(P, B, i, yi, step, use_inj, sw, fx, fy, fz, nw);
+    finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, sw, fx, fy, fz, nw);
 }
 
-// Pair search writing the sliced columns and image codes (FP32 decisions);
-// with ASSEMBLE the row is then assembled in a second, converged pass, so the
-// FP64 work runs once per accepted entry rather than inside the divergent
-// candidate loop.
-template <bool ASSEMBLE>
-__global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
+// Pair search writing the sliced columns and image codes (FP32 decisions).
+__global__ void k_nbr_fill(KParams P, DevBuffers B)
 {
     DevState* st = B.st;
     if (st->error | st->overflow) return;
@@ -587,34 +644,20 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B, int use_inj)
         col[base + 32 * kk] = i;
         img[base + 32 * kk] = image_code(0, 0, 0);
     }
-    if (ASSEMBLE) assemble_row(P, B, i, delta, (unsigned long long)st->step, use_inj);
 }
 
-void launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool mixed,
-                     Launch L)
+int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, Launch L)
 {
-    (void)mixed;
-    const int g = grid_for(P.n, 128, 1 << 30);
-    if (assemble)
-        k_nbr_fill<true><<<g, 128, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
-    else
-        k_nbr_fill<false><<<g, 128, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
+    k_nbr_fill<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B);
+    if (!assemble) return 1;
+    launch_assemble_only(P, B, use_inj, L);
+    return 2;
 }
 
-// Assembly from existing pairs (the same arithmetic as the fused pass).
-__global__ void k_assemble(KParams P, DevBuffers B, int use_inj)
+// Assembly from existing pairs.
+void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, Launch L)
 {
-    const DevState* st = B.st;
-    if (st->error | st->overflow) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    assemble_row(P, B, i, st->delta, (unsigned long long)st->step, use_inj);
-}
-
-void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool mixed, Launch L)
-{
-    (void)mixed;
-    k_assemble<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
+    k_assemble_slots<<<P.nslots / 256, 256, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
 }
 
 // ------------------------------------------------------ generator utilities

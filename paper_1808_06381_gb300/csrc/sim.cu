@@ -128,6 +128,7 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.rc2 = p.rc * p.rc;
     const double l2 = lambda2_of(p.rc);
     k.two_lambda2 = 2.0 * l2;
+    k.w_scale = 256.0 / k.two_lambda2;
     k.alpha = p.alpha;
     k.zeta = p.zeta;
     k.kappa = p.kappa;
@@ -136,18 +137,34 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.noise_amp = std::sqrt(2.0 * p.zeta * p.kT / p.dt);
     k.seed = p.seed;
     // cells: edge >= r_c (1 + 1e-9) so that rounding never moves a partner
-    // within r_c out of the 3 x 3 x 3 block
-    long long ncell = 1;
+    // within r_c out of the 3 x 3 x 3 block; in a sparse box the cells are
+    // made coarser, so the cell index slots stay within a small multiple of n
+    int nc[3];
     for (int a = 0; a < 3; ++a) {
-        int nc = (int)std::floor(p.L[a] / (p.rc * (1.0 + 1e-9)));
-        if (nc < 1) nc = 1;
-        if (nc > 4096) nc = 4096;
-        k.nc[a] = nc;
-        k.inv_cw[a] = (double)nc / p.L[a];
-        ncell *= nc;
+        nc[a] = (int)std::floor(p.L[a] / (p.rc * (1.0 + 1e-9)));
+        nc[a] = std::min(std::max(nc[a], 1), 4096);
     }
+    auto slots = [&]() {
+        long long t = 512;
+        for (int a = 0; a < 3; ++a) t *= (nc[a] + 7) / 8;
+        return t;
+    };
+    const long long slot_cap = std::min<long long>(std::max<long long>(8ll * p.n, 1ll << 15), 1ll << 30);
+    while (slots() > slot_cap) {
+        int a = 0;
+        for (int b = 1; b < 3; ++b)
+            if (nc[b] > nc[a]) a = b;
+        nc[a] = std::max(3, nc[a] / 2);
+    }
+    for (int a = 0; a < 3; ++a) {
+        k.nc[a] = nc[a];
+        k.inv_cw[a] = (double)nc[a] / p.L[a];
+        k.ntile[a] = (nc[a] + 7) / 8;
+    }
+    long long ncell = slots();
     if (k.nc[0] < 3 && k.nc[1] < 3 && k.nc[2] < 3) {
         k.nc[0] = k.nc[1] = k.nc[2] = 1;
+        k.ntile[0] = k.ntile[1] = k.ntile[2] = 1;
         k.inv_cw[0] = 1.0 / p.L[0];
         k.inv_cw[1] = 1.0 / p.L[1];
         k.inv_cw[2] = 1.0 / p.L[2];
@@ -296,8 +313,7 @@ int capture_step_graph(sp_sim* s)
     cudaStream_t cs = s->cap_stream[0];
     SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     long long launches = enqueue_build(s, cs);
-    launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
-    launches += 1;
+    launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, launch_of(s, cs));
     if (s->learned) {
         launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
         launches += mp_infer_launches();
@@ -374,6 +390,8 @@ int clear_flags(sp_sim* s)
     DevState* d = s->B.st;
     SS_TRY(write_field(s, &d->error, 0));
     SS_TRY(write_field(s, &d->overflow, 0));
+    // a persistent solve that stopped on an error may have left arrivals behind
+    SS_TRY(write_field(s, &d->bar_count, 0u));
     return SP_OK;
 }
 
@@ -412,7 +430,7 @@ int do_build(sp_sim* s)
     for (int attempt = 0; attempt < 4; ++attempt) {
         long long launches = enqueue_build(s, s->stream);
         (void)launches;
-        launch_nbr_fill(s->kp, s->B, false, s->use_inj, mixed(s), launch_of(s, s->stream));
+        launch_nbr_fill(s->kp, s->B, false, s->use_inj, launch_of(s, s->stream));
         SS_TRY(read_state(s));
         if (!s->st_host->overflow) break;
         SS_TRY(grow_pairs(s));
@@ -467,7 +485,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.xi_inj, B.exp_tab, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -577,6 +595,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.d4, (size_t)npad));
     A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.partials_df, 4 * (size_t)kMaxPartials));
+    A(dev_alloc(s, &B.exp_tab, (size_t)kExpTab));
     A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(std::max(n, s->kp.ncell), s->kp.nchunks) / 4096 + 2)));
     A(dev_alloc(s, &B.stage, 3 * (size_t)n));
     A(dev_alloc(s, &B.st, 1));
@@ -590,7 +609,8 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         cudaMemsetAsync(B.v_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.pos_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
-        cudaMemsetAsync(B.pos_w, 0, sizeof(double) * v3, s->stream) != cudaSuccess) {
+        cudaMemsetAsync(B.pos_w, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
+        upload_exp_table(B.exp_tab, s->stream) != cudaSuccess) {
         s->err = "initialising device state failed";
         return fail(SP_ERR_CUDA);
     }
@@ -640,7 +660,7 @@ int sp_assemble(sp_sim* s)
         s->err = "sp_assemble needs sp_build_neighbors after the last position change";
         return SP_ERR_INVALID_ARG;
     }
-    launch_assemble_only(s->kp, s->B, s->use_inj, mixed(s), launch_of(s, s->stream));
+    launch_assemble_only(s->kp, s->B, s->use_inj, launch_of(s, s->stream));
     SS_CUDA(cudaGetLastError());
     SS_CUDA(cudaStreamSynchronize(s->stream));
     s->assembled = true;
@@ -713,8 +733,7 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
         if (s->host_loop) {
             for (long long k = 0; k < todo; ++k) {
                 launches += enqueue_build(s, s->stream);
-                launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, s->stream));
-                launches += 1;
+                launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, launch_of(s, s->stream));
                 if (s->learned) {
                     launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, s->stream));
                     launches += mp_infer_launches();
@@ -787,7 +806,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         return SP_OK;
     };
     enum { START = -1, SORT = 0, SPMV, UPDATE, TRUE_RES, DIRECTION, OTHER, COUNT, FILL, PERSIST, INIT, STRESS,
-           INTEGRATE, MPNN };
+           INTEGRATE, MPNN, ASSEMBLE };
     launch_reset_step_stats(B.st, s->stream);
     int rc = mark(START);
     if (rc == SP_OK) {
@@ -804,8 +823,10 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         launch_sell_plan(P, B, L);
         launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
         mark(COUNT);
-        launch_nbr_fill(P, B, true, s->use_inj, mx, L);
-        rc = mark(FILL);
+        launch_nbr_fill(P, B, false, s->use_inj, L);
+        mark(FILL);
+        launch_assemble_only(P, B, s->use_inj, L);
+        rc = mark(ASSEMBLE);
         if (rc == SP_OK && s->learned) {
             launch_mp_infer(P, B, s->mp, L);
             rc = mark(MPNN);
@@ -874,7 +895,8 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     }
     double* acc[] = {&out->sort_ms, &out->spmv_ms, &out->update_ms, &out->true_residual_ms,
                      &out->direction_ms, &out->other_ms, &out->count_ms, &out->fill_ms, &out->persistent_ms,
-                     &out->init_ms, &out->stress_ms, &out->integrate_ms, &out->mpnn_ms};
+                     &out->init_ms, &out->stress_ms, &out->integrate_ms, &out->mpnn_ms,
+                     &out->assemble_ms};
     for (size_t k = 1; rc == SP_OK && k < ev.size(); ++k) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
@@ -885,7 +907,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         if (s->err.empty()) s->err = "profiling step failed";
         return rc;
     }
-    out->build_ms = out->sort_ms + out->count_ms + out->fill_ms;
+    out->build_ms = out->sort_ms + out->count_ms + out->fill_ms + out->assemble_ms;
     out->other_ms += out->init_ms + out->stress_ms + out->integrate_ms;
     const DevState& h = *s->st_host;
     if (h.overflow) {

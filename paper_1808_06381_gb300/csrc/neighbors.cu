@@ -337,11 +337,6 @@ __device__ __forceinline__ void for_each_neighbor_generic(const KParams& P, doub
     }
 }
 
-__device__ __forceinline__ int floor_div(int a, int b)
-{
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
 // The same pair set as for_each_neighbor_generic for boxes with >= 3 cells per
 // axis, with almost no FP64 work.  Each candidate cell is visited as one image
 // of the box (integer shifts a, m, c along x, y, z), so the image separation
@@ -369,6 +364,10 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
     const int cx = cell_coord(xi, P.inv_cw[0], nc0);
     const int cy = cell_coord(yi, P.inv_cw[1], nc1);
     const int cz = cell_coord(zi, P.inv_cw[2], nc2);
+    // image shifts by selection (no int-to-float conversions: GB300 runs them
+    // at the FP64 rate); every product below is exact, as before
+    auto times = [](int k, float v) { return k == 0 ? 0.f : (k > 0 ? v : -v); };
+    const float L2f = 2.f * P.Lf[0];
     for (int dzc = -1; dzc <= 1; ++dzc) {
         int czz = cz + dzc, c_img = 0;
         if (czz < 0) {
@@ -378,7 +377,7 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
             czz -= nc2;
             c_img = 1;
         }
-        const float szf = __fmul_rn((float)c_img, P.Lf[2]);
+        const float szf = times(c_img, P.Lf[2]);
         for (int dyc = -1; dyc <= 1; ++dyc) {
             int cyy = cy + dyc, m = 0;
             if (cyy < 0) {
@@ -388,13 +387,16 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
                 cyy -= nc1;
                 m = 1;
             }
-            const float syf = __fmul_rn((float)m, P.Lf[1]);
+            const float syf = times(m, P.Lf[1]);
+            const float mdf = times(m, deltaf);
             const int cxu0 = m == 0 ? cx : (int)floor((xi - (double)m * delta) * P.inv_cw[0]);
             for (int dxc = -1; dxc <= 1; ++dxc) {
                 const int cxu = cxu0 + dxc;
-                const int a = floor_div(cxu, nc0);
+                // floor(cxu / nc0) for cxu in [-2 nc0, 3 nc0)
+                const int a = cxu >= 0 ? (cxu >= nc0 ? (cxu >= 2 * nc0 ? 2 : 1) : 0) : (cxu >= -nc0 ? -1 : -2);
                 const int c = cell_index(P, cxu - a * nc0, cyy, czz);
-                const float sxf = __fadd_rn(__fmul_rn((float)m, deltaf), __fmul_rn((float)a, P.Lf[0]));
+                const float axf = a == 0 ? 0.f : (a == 1 ? P.Lf[0] : (a == -1 ? -P.Lf[0] : (a == 2 ? L2f : -L2f)));
+                const float sxf = __fadd_rn(mdf, axf);
                 const unsigned char code = image_code(a, m, c_img);
                 const int j1 = cell_start[c + 1];
                 for (int j = cell_start[c]; j < j1; ++j) {
@@ -568,8 +570,9 @@ cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream)
 // their entries with coalesced loads; the FP64 work runs once per entry in
 // converged warps.  Separations use the entries' image codes (exact, no
 // divisions): the shifts n delta and a L_x of the canonical minimum image are
-// exact for |n| <= 1 and |a| <= 2 and taken by selection.  Padding entries
-// get weight 0.
+// exact for |n| <= 1 and |a| <= 2 and taken by selection, and a warp whose
+// current entries all pair with the central image (most warps: the rows of
+// a warp are neighbours in space) skips them.  Padding entries get weight 0.
 __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
 {
     const DevState* st = B.st;
@@ -585,27 +588,36 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
     const int cnt = B.row_cnt[i];
     const double Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
     const double* __restrict__ pos = B.pos_w;
+    const int center = image_code(0, 0, 0);
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
     for (int k = 0; k < cnt; ++k) {
         const int e = base + 32 * k;
         const int j = __ldg(B.col + e);
         const int code = __ldg(B.img + e);
-        const int a = (code & 7) - 2, m = ((code >> 3) & 3) - 1, c = ((code >> 5) & 3) - 1;
-        const double sn = m == 0 ? 0.0 : (m > 0 ? delta : -delta);
-        const double sa = a == 0 ? 0.0 : (a == 1 ? Lx : (a == -1 ? -Lx : __dmul_rn(Lx, (double)a)));
-        const double sy = m == 0 ? 0.0 : (m > 0 ? Ly : -Ly);
-        const double sz = c == 0 ? 0.0 : (c > 0 ? Lz : -Lz);
-        const double dx = __dsub_rn(__dsub_rn(__dsub_rn(xi, pos[j]), sn), sa);
-        const double dy = __dsub_rn(__dsub_rn(yi, pos[np + j]), sy);
-        const double dz = __dsub_rn(__dsub_rn(zi, pos[2 * np + j]), sz);
-        const double w = pair_weight(P, B.exp_tab, sq_norm_exact(dx, dy, dz));
+        double dx = __dsub_rn(xi, pos[j]);
+        double dy = __dsub_rn(yi, pos[np + j]);
+        double dz = __dsub_rn(zi, pos[2 * np + j]);
+        const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
+        int m = 0;
+        if (shifted) {
+            const int a = (code & 7) - 2, c = ((code >> 5) & 3) - 1;
+            m = ((code >> 3) & 3) - 1;
+            const double sn = m == 0 ? 0.0 : (m > 0 ? delta : -delta);
+            const double sa = a == 0 ? 0.0 : (a == 1 ? Lx : (a == -1 ? -Lx : __dmul_rn(Lx, (double)a)));
+            const double sy = m == 0 ? 0.0 : (m > 0 ? Ly : -Ly);
+            const double sz = c == 0 ? 0.0 : (c > 0 ? Lz : -Lz);
+            dx = __dsub_rn(__dsub_rn(dx, sn), sa);
+            dy = __dsub_rn(dy, sy);
+            dz = __dsub_rn(dz, sz);
+        }
+        const double w = pair_weight(P, B.exp_tab, fma(dx, dx, fma(dy, dy, dz * dz)));
         B.val[e] = w;
         B.val32[e] = (float)w;
         sw += w;
         fx = fma(dx, w, fx);
         fy = fma(dy, w, fy);
         fz = fma(dz, w, fz);
-        nw += m == 0 ? 0.0 : (m > 0 ? w : -w);
+        if (shifted) nw += m == 0 ? 0.0 : (m > 0 ? w : -w);
     }
     for (int k = cnt; k < clen; ++k) {
         B.val[base + 32 * k] = 0.0;

@@ -165,22 +165,23 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
     return sh.flag == 0;
 }
 
-constexpr int kBatchP = 6;    // FP32 gathers in flight per thread
+constexpr int kBatchP = 6;    // FP32 gathers in flight per thread (batch kernel; see kPersistentCfg)
 constexpr int kBatchP64 = 2;  // FP64 gathers in flight (the rare FP64 residual replacement)
 
 // s = sum_j w_ij D^-1_j r_j (FP32).  Rows of r written by other blocks before
 // the last barrier are visible to plain loads (the barrier's acquire orders
 // them), so the gathers may hit L1: rows of neighbouring particles are
 // gathered by many rows of the same block.
+template <int KB>
 __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const float* __restrict__ val,
                                             const float4* r, int e0, int e1, float& s0, float& s1, float& s2)
 {
     s0 = s1 = s2 = 0.f;
-    for (int eb = e0; eb < e1; eb += 32 * kBatchP) {
-        int j[kBatchP];
-        float w[kBatchP];
+    for (int eb = e0; eb < e1; eb += 32 * KB) {
+        int j[KB];
+        float w[KB];
 #pragma unroll
-        for (int u = 0; u < kBatchP; ++u) {
+        for (int u = 0; u < KB; ++u) {
             const int e = eb + 32 * u;
             j[u] = 0;
             w[u] = 0.f;
@@ -189,14 +190,14 @@ __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const f
                 w[u] = ld_stream(val + e);
             }
         }
-        float4 g[kBatchP];
+        float4 g[KB];
 #pragma unroll
-        for (int u = 0; u < kBatchP; ++u) {
+        for (int u = 0; u < KB; ++u) {
             g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (w[u] != 0.f) g[u] = r[j[u]];
         }
 #pragma unroll
-        for (int u = 0; u < kBatchP; ++u) {
+        for (int u = 0; u < KB; ++u) {
             const float ww = w[u] * g[u].w;
             s0 = fmaf(ww, g[u].x, s0);
             s1 = fmaf(ww, g[u].y, s1);
@@ -240,6 +241,16 @@ __device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const d
 // The solve of one system by blocks bid = 0..nb-1 of the launch (all of the
 // launch for a single system; a share of it in a batch).  Expects r4 = (r, D^-1)
 // with r = b - A x, p4 = q4 = d4 = 0 and the scalars, from the set-up kernel.
+// Slot of this thread in the block's k-th window.  The chunks of a window
+// hold rows of decreasing length; warp c takes chunk c of even windows and
+// chunk 7 - c of odd ones, so a warp's rows over two windows have about
+// equal total length (the slowest warp sets the pace of every phase).
+__device__ __forceinline__ int chunk_lane(int k)
+{
+    return (k & 1) ? (int)(threadIdx.x ^ 0xE0u) : (int)threadIdx.x;
+}
+
+template <int KB>
 __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
                                                  PShared& sh)
 {
@@ -279,7 +290,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         dfloat pq{0.f, 0.f};
         const float betaf = sh.beta_f;
         for (int w = wb; w < we; ++w) {
-            const int slot = w * 256 + threadIdx.x;
+            const int slot = w * 256 + chunk_lane(w - wb);
             const int row = B.slot_row[slot];
             if (row >= 0) {
                 const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
@@ -292,7 +303,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                     po = B.p4[row];
                 }
                 float s0, s1, s2;
-                p_row_sum32(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
+                p_row_sum32<KB>(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
                 const float z0 = ri.w * ri.x, z1 = ri.w * ri.y, z2 = ri.w * ri.z;
                 float q0 = fmaf(d, z0, -alpha_e * s0);
                 float q1 = fmaf(d, z1, -alpha_e * s1);
@@ -385,7 +396,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         if (!grid_sync(st, gen, sh, nb)) break;
         double trr = 0.0, trz = 0.0;
         for (int w = wb; w < we; ++w) {
-            const int slot = w * 256 + threadIdx.x;
+            const int slot = w * 256 + chunk_lane(w - wb);
             const int row = B.slot_row[slot];
             if (row >= 0) {
                 const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
@@ -451,10 +462,14 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     }
 }
 
-__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent(KParams P, DevBuffers B)
+// Tile configurations of the single-system kernel: gathers in flight per
+// thread (KB) against resident blocks per SM (MINB, which caps the registers
+// at 65536 / (256 MINB)).  Chosen per system by the autotuner.
+template <int KB, int MINB>
+__global__ void __launch_bounds__(kPBlock, MINB) k32_cg_persistent(KParams P, DevBuffers B)
 {
     __shared__ PShared sh;
-    persistent_solve(P, B, blockIdx.x, gridDim.x, sh);
+    persistent_solve<KB>(P, B, blockIdx.x, gridDim.x, sh);
 }
 
 // Batch: block b serves replica k with blk_off[k] <= b < blk_off[k + 1]; each
@@ -476,23 +491,37 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
     }
     __syncthreads();
     const int k = rep;
-    persistent_solve(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
+    persistent_solve<kBatchP>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
 }
 
 namespace {
-int g_pocc = 0;
+struct PCfg {
+    int kb, minb;
+    const void* fn;
+    int occ;
+};
+PCfg g_pcfg[kPersistentConfigs] = {
+    {6, 4, (const void*)k32_cg_persistent<6, 4>, 0},  {8, 3, (const void*)k32_cg_persistent<8, 3>, 0},
+    {10, 3, (const void*)k32_cg_persistent<10, 3>, 0}, {12, 3, (const void*)k32_cg_persistent<12, 3>, 0},
+    {4, 4, (const void*)k32_cg_persistent<4, 4>, 0},  {8, 4, (const void*)k32_cg_persistent<8, 4>, 0},
+};
 int g_pocc_batch = 0;
 std::once_flag g_pocc_once;
 void pocc_init()
 {
     std::call_once(g_pocc_once, [] {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc, k32_cg_persistent, kPBlock, 0) != cudaSuccess)
-            g_pocc = 0;
+        for (auto& c : g_pcfg)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, kPBlock, 0) != cudaSuccess) c.occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc_batch, k32_cg_persistent_batch, kPBlock, 0) !=
             cudaSuccess)
             g_pocc_batch = 0;
         cudaGetLastError();
     });
+}
+const PCfg& cfg_of(const KParams& P)
+{
+    const int k = (P.pcfg >= 0 && P.pcfg < kPersistentConfigs) ? P.pcfg : 0;
+    return g_pcfg[k];
 }
 }  // namespace
 
@@ -522,7 +551,7 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
 int cg_persistent_grid(const KParams& P, Launch L)
 {
     pocc_init();
-    long long g = std::min<long long>((long long)L.num_sms * g_pocc, P.nslots / 256);
+    long long g = std::min<long long>((long long)L.num_sms * cfg_of(P).occ, P.nslots / 256);
     if (g > kMaxPartials) g = kMaxPartials;
     return (int)g;
 }
@@ -541,7 +570,8 @@ cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k32_cg_persistent, P, B);
+    void* args[] = {const_cast<KParams*>(&P), &B};
+    return cudaLaunchKernelExC(&cfg, cfg_of(P).fn, args);
 }
 
 }  // namespace ss

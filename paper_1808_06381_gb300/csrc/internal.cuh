@@ -39,7 +39,10 @@ struct KParams {
     double tol2;        // cg_tol^2
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
+    int pcfg;           // tile configuration of the persistent solver (index, autotuned)
 };
+
+constexpr int kPersistentConfigs = 6;
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {

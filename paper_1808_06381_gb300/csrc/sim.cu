@@ -129,6 +129,10 @@ void derive(const sp_params& p, KParams& k, int npad)
     const double l2 = lambda2_of(p.rc);
     k.two_lambda2 = 2.0 * l2;
     k.w_scale = 256.0 / k.two_lambda2;
+    {
+        const char* c = std::getenv("SHEARSIM_PCFG");
+        k.pcfg = c ? std::atoi(c) : 0;
+    }
     k.alpha = p.alpha;
     k.zeta = p.zeta;
     k.kappa = p.kappa;

@@ -37,6 +37,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank advances its own replica of the workload (independent positions and noise)."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(local_ms: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time: the whole job ends when the last replica does."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n: int, world: int, steps: int, t_max_ms: float) -> float:
+    """Particle-steps/s of all ranks together (weak scaling: N particles per rank)."""
+    return n * world * steps / (t_max_ms / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -236,7 +256,7 @@ def main():
     import paper_1808_06381_gb300 as ss
     ss.load()
     n, L = workload.n, workload.L
-    seed = workload.seed + 1000 * rank
+    seed = replica_seed(workload.seed, rank)
     pos0 = synth.uniform_positions(n, L, seed)
     kappa = ss.kappa_from_kappa_tau(workload.kappa_tau)
     def make_sim(precision):
@@ -280,12 +300,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
 
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = n * world * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_value(n, world, args.steps, t_max)
 
     # per-kernel timing of one more step (CUDA events on the simulation's
     # stream), then the two loop kernels launched back to back on that system
@@ -325,7 +341,7 @@ def main():
         host_in[:] = host_out
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = n * world * args.e2e_steps / e2e_s   # each rank does the same work
+    e2e_value = whole_job_value(n, world, args.e2e_steps, max_over_ranks(1e3 * e2e_s, dist, "cuda"))
 
     line = None
     if rank == 0:

@@ -198,6 +198,33 @@ typedef struct sp_kernel_profile {
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 
+/* ---- autotuning of the persistent solver's tiles ----
+ *
+ * Not in the paper (an implementation parameter).  The mixed-precision
+ * solve runs as one cooperative persistent kernel compiled in several tile
+ * configurations: gathers in flight per thread against resident blocks per
+ * SM.  All of them do the same arithmetic in the same order (results are
+ * bit-identical); only the speed differs.  sp_autotune builds the pair list
+ * and the system for the current positions, times `trials` solves from a
+ * zero start with every configuration on the simulation's stream, keeps the
+ * fastest for this simulation, and leaves positions, step counter and the
+ * previous velocities (the warm start) unchanged.  With the environment
+ * variable SHEARSIM_TUNE_CACHE naming a file, choices are looked up there
+ * first, keyed by device name, SM count, n and the mean row length, and new
+ * choices are appended (one line per key).  For SP_PREC_FP64, or with
+ * trials < 1, nothing is timed and configuration 0 is kept.  Errors:
+ * SP_ERR_INVALID_ARG (NULL sim), SP_ERR_CUDA, and those of the solve. */
+#define SP_TUNE_MAX_CONFIGS 8
+typedef struct sp_tune_info {
+    int32_t config;              /* chosen configuration (index) */
+    int32_t gathers_in_flight;   /* its gathers in flight per thread */
+    int32_t blocks_per_sm;       /* its resident blocks per SM */
+    int32_t from_cache;          /* 1: taken from the tuning cache, nothing timed */
+    int32_t num_configs;         /* configurations available */
+    double ms[SP_TUNE_MAX_CONFIGS]; /* best time of one solve per configuration (0: not timed) */
+} sp_tune_info;
+int sp_autotune(sp_sim* sim, int32_t trials, sp_tune_info* info);
+
 /* ---- state access (test hooks and checkpointing) ---- */
 
 /* Positions [n][3] by particle id. */

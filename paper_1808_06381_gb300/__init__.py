@@ -76,6 +76,11 @@ class sp_kernel_profile(ctypes.Structure):
                 ("assemble_ms", ctypes.c_double)]
 
 
+class sp_tune_info(ctypes.Structure):
+    _fields_ = [("config", ctypes.c_int32), ("gathers_in_flight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 8)]
+
+
 def declared_symbols() -> list:
     """Entry points declared in include/shearsim.h."""
     text = open(HEADER).read()
@@ -105,7 +110,7 @@ def load(path: str = LIB_PATH):
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
-            ("sp_profile_step", [vp, P(sp_kernel_profile)]),
+            ("sp_profile_step", [vp, P(sp_kernel_profile)]), ("sp_autotune", [vp, i32, P(sp_tune_info)]),
             ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)]),
             ("sp_batch_create", [i32, vp, vp, P(vp)]), ("sp_batch_destroy", [vp]),
             ("sp_batch_step", [vp, i32, vp]), ("sp_batch_get_sim", [vp, i32, P(vp)]),
@@ -290,6 +295,14 @@ class Simulation:
         prof = sp_kernel_profile()
         self._c(load().sp_profile_step(self._h, ctypes.byref(prof)))
         return {name: getattr(prof, name) for name, _ in sp_kernel_profile._fields_}
+
+    def autotune(self, trials: int = 3) -> dict:
+        """Pick the persistent solver's fastest tile configuration for this system (sp_autotune)."""
+        info = sp_tune_info()
+        self._c(load().sp_autotune(self._h, int(trials), ctypes.byref(info)))
+        return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
+                "blocks_per_sm": info.blocks_per_sm, "from_cache": bool(info.from_cache),
+                "ms": [info.ms[k] for k in range(info.num_configs)]}
 
     # learned warm start
     def mpnn_enable(self, seed: int = 0, weights=None):

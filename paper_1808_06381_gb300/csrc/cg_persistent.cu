@@ -548,6 +548,13 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
     return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
 }
 
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm)
+{
+    const PCfg& c = g_pcfg[(k >= 0 && k < kPersistentConfigs) ? k : 0];
+    *gathers = c.kb;
+    *blocks_per_sm = c.minb;
+}
+
 int cg_persistent_grid(const KParams& P, Launch L)
 {
     pocc_init();

@@ -29,21 +29,6 @@ namespace ss_host {
 
 std::string g_create_error;
 
-#define SS_CUDA(call)                                                                        \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess) {                                                             \
-            s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
-            return SP_ERR_CUDA;                                                              \
-        }                                                                                    \
-    } while (0)
-
-#define SS_TRY(expr)                 \
-    do {                                \
-        int rc_ = (expr);               \
-        if (rc_ != SP_OK) return rc_;   \
-    } while (0)
-
 Launch launch_of(const sp_sim* s, cudaStream_t st) { return Launch{st, s->num_sms}; }
 
 bool mixed(const sp_sim* s) { return s->p.precision == SP_PREC_MIXED; }
@@ -129,10 +114,7 @@ void derive(const sp_params& p, KParams& k, int npad)
     const double l2 = lambda2_of(p.rc);
     k.two_lambda2 = 2.0 * l2;
     k.w_scale = 256.0 / k.two_lambda2;
-    {
-        const char* c = std::getenv("SHEARSIM_PCFG");
-        k.pcfg = c ? std::atoi(c) : 0;
-    }
+    k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
     k.alpha = p.alpha;
     k.zeta = p.zeta;
     k.kappa = p.kappa;

@@ -37,6 +37,22 @@ struct sp_sim {
     std::string err;
 };
 
+// Error propagation inside functions that hold an sp_sim* named s.
+#define SS_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return SP_ERR_CUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+#define SS_TRY(expr)                 \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ != SP_OK) return rc_;   \
+    } while (0)
+
 namespace ss_host {
 ss::Launch launch_of(const sp_sim* s, cudaStream_t st);
 bool mixed(const sp_sim* s);
@@ -47,6 +63,9 @@ int clear_flags(sp_sim* s);
 int set_device(sp_sim* s);
 void free_graphs(sp_sim* s);
 bool warm_from_prev(const sp_sim* s);   // the solve starts from x (previous velocities or the network's guess)
+int do_build(sp_sim* s);                // pair list for the current positions (grows storage if needed)
+// init, loop, finish and stress of one solve, enqueued on cs
+int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches);
 }  // namespace ss_host
 
 std::string& sp_global_error();

@@ -67,19 +67,26 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region.
+
+    start() returns once the first sample has arrived (so sampling is running
+    when the timed region begins); stop() keeps the samples that arrived while
+    the region ran (at least the first one after it began)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_id: str | None):
         self.gpu_id = gpu_id
         self.proc = None
-        self.lines = []
+        self.lines = []   # (arrival time, text)
+        self.t_start = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", str(self.INTERVAL_MS)]
         if self.gpu_id:
             cmd[1:1] = ["-i", self.gpu_id]
         try:
@@ -88,23 +95,33 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.t_start = time.perf_counter()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_end = time.perf_counter()
+        time.sleep(2.5 * self.INTERVAL_MS / 1e3)   # the sample taken just after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=5)
+        inside = [ln for t, ln in self.lines if self.t_start <= t <= t_end + 1.5 * self.INTERVAL_MS / 1e3]
+        if not inside:
+            inside = [ln for t, ln in self.lines if t >= self.t_start][:1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in inside:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -118,7 +135,19 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "interval_ms": self.INTERVAL_MS, "reasons": sorted(reasons)}
+
+
+# DRAM bytes (read + write) per launch of the persistent solve from one ncu capture
+# (profiles/k32_cg_persistent_n262144.md), keyed by workload and tile configuration
+# (gathers in flight, blocks per SM); any other kernel or workload reports null.
+PROFILED_TRAFFIC = {("mixed-n262144", 8, 4): 439.6e6}
+
+
+def profiled_traffic(workload_name: str, tune) -> float | None:
+    if not tune:
+        return None
+    return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"]))
 
 
 def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
@@ -319,8 +348,11 @@ def main():
     if prof["persistent_ms"] > 0:
         pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
         pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
-        persistent = {"kernel": "k32_cg_persistent", "bound": "hbm", "achieved": pach, "peak": peak,
-                      "unit": "GB/s", "frac": pach / peak, "traffic": None,
+        kname = "k32_cg_persistent"
+        if tune:
+            kname += f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']}>"
+        persistent = {"kernel": kname, "bound": "hbm", "achieved": pach, "peak": peak,
+                      "unit": "GB/s", "frac": pach / peak, "traffic": profiled_traffic(workload.name, tune),
                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
                       "algorithmic_bytes_per_launch": pbytes, "avg_launch_ms": prof["persistent_ms"],
                       "cg_iterations": prof["cg_iterations"], "true_residual_checks": prof["true_checks"],

@@ -128,7 +128,7 @@ int capture(sp_batch* b)
         sp_sim* s = b->sims[k];
         cudaStream_t st = b->branch[k % S];
         launches += enqueue_build(s, st);
-        launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, launch_of(s, st));
+        launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, true, launch_of(s, st));
         launch_cg_init(s->kp, s->B, s->p.warm_start == SP_WARM_PREV, true, launch_of(s, st));
         launches += 1;
     }

@@ -36,6 +36,8 @@ struct KParams {
     float rc2_lo;       // FP32 distance^2 below this: certainly |R|^2 < r_c^2
     float rc2_hi;       // FP32 distance^2 at or above this: certainly |R|^2 >= r_c^2
     float Lf[3];        // box edges in FP32
+    float Llo[3];       // L - Lf: the box edges as double-floats (Lf, Llo)
+    float wsc_hi, wsc_lo; // w_scale as a double-float
     double tol2;        // cg_tol^2
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
@@ -82,6 +84,7 @@ struct DevBuffers {
     // work arrays of the current step (cell order)
     double* pos_w;   // [3][npad]
     float* pos32;    // [3][npad] FP32 copy of pos_w for the pair pre-filter
+    float* pos32lo;  // [3][npad] pos_w - pos32: positions as double-floats (pos32, pos32lo)
     int* id_w;       // [n]
     int* cell_of;    // [n]
     int* slot;       // [n]
@@ -116,6 +119,7 @@ struct DevBuffers {
     float4* d4;      // correction accumulated since the last fold into x
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
+    float2* exp_tab_df; // [kExpTab] the same as double-floats
     double* partials;// [kMaxPartials * 4]
     float2* partials_df; // [kMaxPartials * 4] double-float partial sums (mixed solver)
     int* scan_tmp;   // block sums of the scans
@@ -375,6 +379,42 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
 
 __device__ __forceinline__ dfloat df_add(dfloat a, float x) { return df_add(a, dfloat{x, 0.f}); }
 
+// Error-free building blocks (Knuth's TwoSum, Dekker's FastTwoSum, and the
+// product error by one fused multiply-add), explicit round-to-nearest
+// intrinsics so that no contraction changes them.
+__device__ __forceinline__ dfloat two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dfloat{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b)   // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return dfloat{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfloat df_sqr(dfloat a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    const float e = fmaf(__fmul_rn(2.f, a.hi), a.lo, fmaf(a.hi, a.hi, -p));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return dfloat{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+
 __device__ __forceinline__ dfloat warp_sum_df(dfloat v)
 {
 #pragma unroll
@@ -464,10 +504,10 @@ void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L
 void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L);
 // Pair fill (columns and image codes), followed, with assemble, by the FP64
 // assembly of the matrix and right-hand side; returns the kernels launched.
-int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, Launch L);
-void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, Launch L);
-// Fills the weight table exp_tab (host computation, one copy).
-cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream);
+int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool df, Launch L);
+void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool df, Launch L);
+// Fills the weight tables exp_tab and exp_tab_df (host computation, one copy each).
+cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t stream);
 void launch_uniform_positions(const KParams& P, DevBuffers& B, Launch L);
 void launch_philox_blocks(unsigned long long seed, unsigned long long step, long long count,
                           const long long* ids, unsigned long long* out, cudaStream_t s);

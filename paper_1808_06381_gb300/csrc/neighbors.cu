@@ -176,7 +176,7 @@ __global__ void k_scatter(int n, const int* __restrict__ cell_of, const int* __r
 __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int* __restrict__ perm,
                               const int* __restrict__ id_s, const double* __restrict__ pos_s,
                               const double* __restrict__ v_s, double* __restrict__ pos_w,
-                              float* __restrict__ pos32, int* __restrict__ id_w,
+                              float* __restrict__ pos32, float* __restrict__ pos32lo, int* __restrict__ id_w,
                               double* __restrict__ x, int warm, const DevState* st)
 {
     if (st->error | st->overflow) return;
@@ -200,7 +200,9 @@ __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int
         for (int a = 0; a < 3; ++a) {
             const double v = pos_s[a * np + s];
             pos_w[a * np + k] = v;
-            pos32[a * np + k] = (float)v;
+            const float vh = (float)v;
+            pos32[a * np + k] = vh;
+            pos32lo[a * np + k] = (float)(v - (double)vh);
         }
         id_w[k] = id_s[s];
         x[k] = warm ? v_s[s] : 0.0;
@@ -214,14 +216,15 @@ void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Laun
     k_scatter<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P.n, B.cell_of, B.slot,
                                                                                 B.cell_start, B.perm, B.st);
     k_sort_gather<<<grid_for(P.ncell, 128, 1 << 30), 128, 0, L.stream>>>(
-        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.x, warm ? 1 : 0, B.st);
+        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, warm ? 1 : 0,
+        B.st);
 }
 
 // Single-cell boxes (every edge below 3 r_c): keep the state order.
 __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
                                   const double* __restrict__ pos_s, const double* __restrict__ v_s,
                                   double* __restrict__ pos_w, float* __restrict__ pos32,
-                                  int* __restrict__ id_w, double* __restrict__ x, int* __restrict__ perm,
+                                  float* __restrict__ pos32lo, int* __restrict__ id_w, double* __restrict__ x, int* __restrict__ perm,
                                   int warm, const DevState* st)
 {
     if (st->error | st->overflow) return;
@@ -232,8 +235,11 @@ __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
     id_w[k] = id_s[k];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        pos_w[a * np + k] = pos_s[a * np + k];
-        pos32[a * np + k] = (float)pos_s[a * np + k];
+        const double v = pos_s[a * np + k];
+        pos_w[a * np + k] = v;
+        const float vh = (float)v;
+        pos32[a * np + k] = vh;
+        pos32lo[a * np + k] = (float)(v - (double)vh);
         x[a * np + k] = warm ? v_s[a * np + k] : 0.0;
     }
 }
@@ -241,7 +247,7 @@ __global__ void k_identity_gather(KParams P, const int* __restrict__ id_s,
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L)
 {
     k_identity_gather<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(
-        P, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.x, B.perm, warm ? 1 : 0, B.st);
+        P, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, B.perm, warm ? 1 : 0, B.st);
 }
 
 // ------------------------------------------------------------- pair search
@@ -552,17 +558,64 @@ __device__ __forceinline__ double pair_weight(const KParams& P, const double* __
     return __ldg(etab + k) * q;
 }
 
-cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream)
+cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t stream)
 {
     static const std::array<double, kExpTab> host = [] {
         std::array<double, kExpTab> t{};
         for (int k = 0; k < kExpTab; ++k) t[k] = std::exp(-(double)k / 256.0);
         return t;
     }();
+    static const std::array<float2, kExpTab> host_df = [] {
+        std::array<float2, kExpTab> t{};
+        for (int k = 0; k < kExpTab; ++k) {
+            const float hi = (float)host[k];
+            t[k] = make_float2(hi, (float)(host[k] - (double)hi));
+        }
+        return t;
+    }();
     cudaError_t e = cudaMemcpyAsync(exp_tab, host.data(), sizeof(double) * kExpTab, cudaMemcpyHostToDevice,
                                     stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(exp_tab_df, host_df.data(), sizeof(float2) * kExpTab, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return e;
+}
+
+// The pair weight of pair_weight() for the mixed-precision path, in
+// double-float arithmetic (FP32 pipes): the same table-driven method, with
+// 256 t = k + f split exactly, exp(-f/256) = 1 + g + g^2/2 + ... for
+// g = -f/256 (1 + g exact as a double-float, the remaining terms, below
+// 2^-19, in FP32) and E_k from the double-float table.  r2 is the squared
+// separation as a double-float; the result carries about 2^-44 relative error.
+__device__ __forceinline__ dfloat pair_weight_df(const KParams& P, const float2* __restrict__ etab, dfloat r2)
+{
+    constexpr float kRound = 12582912.f;   // 1.5 * 2^23: adding it rounds to an integer
+    const dfloat t = df_mul(r2, dfloat{P.wsc_hi, P.wsc_lo});
+    const float kr = __fadd_rn(t.hi, kRound);
+    const int k = __float_as_int(kr) - __float_as_int(kRound);
+    if (k < 0 || k >= kExpTab) {   // t >= 4: not a pair within r_c
+        const double w = exp(-df_to_double(r2) / P.two_lambda2);
+        const float wh = (float)w;
+        return dfloat{wh, (float)(w - (double)wh)};
+    }
+    const dfloat f = fast_two_sum(__fsub_rn(t.hi, __fsub_rn(kr, kRound)), t.lo);   // 256 t - k
+    const float gh = __fmul_rn(f.hi, -0.00390625f), gl = __fmul_rn(f.lo, -0.00390625f);   // exact
+    const float tail = __fmul_rn(__fmul_rn(gh, gh),
+                                 fmaf(gh, fmaf(gh, fmaf(gh, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f));
+    const dfloat one_g = two_sum(1.f, gh);
+    const dfloat q = fast_two_sum(one_g.hi, __fadd_rn(one_g.lo, __fadd_rn(gl, tail)));
+    const float2 e = __ldg(etab + k);
+    return df_mul(dfloat{e.x, e.y}, q);
+}
+
+// Separation component R_i - R_j - shift of the minimum image, from
+// double-float positions and a double-float shift.
+__device__ __forceinline__ dfloat sep_df(float ih, float il, float jh, float jl, dfloat shift)
+{
+    const dfloat d = two_sum(ih, -jh);
+    dfloat r = fast_two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(il, jl)));
+    if (shift.hi != 0.f) r = df_add(r, df_neg(shift));
+    return r;
 }
 
 // Assembly of Eq. algebra from the stored pairs: one thread per slot of the
@@ -573,6 +626,14 @@ cudaError_t upload_exp_table(double* exp_tab, cudaStream_t stream)
 // exact for |n| <= 1 and |a| <= 2 and taken by selection, and a warp whose
 // current entries all pair with the central image (most warps: the rows of
 // a warp are neighbours in space) skips them.  Padding entries get weight 0.
+//
+// DF (the mixed-precision path): the per-entry arithmetic — separations,
+// |R|^2, weight, pair sums — runs in double-float on the FP32 pipes from the
+// double-float positions, leaving three FP64 operations per entry (the FP64
+// weight); the system then agrees with the FP64 assembly to ~1e-12 relative
+// (the 2^-48 representation of the positions), far inside the mixed solver's
+// tolerance.  The noise and the per-row finish stay FP64.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
 {
     const DevState* st = B.st;
@@ -586,38 +647,90 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
     const int base = B.chunk_off[slot >> 5] + (slot & 31);
     const int clen = (B.chunk_off[(slot >> 5) + 1] - B.chunk_off[slot >> 5]) >> 5;
     const int cnt = B.row_cnt[i];
-    const double Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
-    const double* __restrict__ pos = B.pos_w;
     const int center = image_code(0, 0, 0);
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
-    for (int k = 0; k < cnt; ++k) {
-        const int e = base + 32 * k;
-        const int j = __ldg(B.col + e);
-        const int code = __ldg(B.img + e);
-        double dx = __dsub_rn(xi, pos[j]);
-        double dy = __dsub_rn(yi, pos[np + j]);
-        double dz = __dsub_rn(zi, pos[2 * np + j]);
-        const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
-        int m = 0;
-        if (shifted) {
-            const int a = (code & 7) - 2, c = ((code >> 5) & 3) - 1;
-            m = ((code >> 3) & 3) - 1;
-            const double sn = m == 0 ? 0.0 : (m > 0 ? delta : -delta);
-            const double sa = a == 0 ? 0.0 : (a == 1 ? Lx : (a == -1 ? -Lx : __dmul_rn(Lx, (double)a)));
-            const double sy = m == 0 ? 0.0 : (m > 0 ? Ly : -Ly);
-            const double sz = c == 0 ? 0.0 : (c > 0 ? Lz : -Lz);
-            dx = __dsub_rn(__dsub_rn(dx, sn), sa);
-            dy = __dsub_rn(dy, sy);
-            dz = __dsub_rn(dz, sz);
+    if (DF) {
+        const float* __restrict__ ph = B.pos32;
+        const float* __restrict__ pl = B.pos32lo;
+        const float xih = ph[i], yih = ph[np + i], zih = ph[2 * np + i];
+        const float xil = pl[i], yil = pl[np + i], zil = pl[2 * np + i];
+        const float dh = (float)delta;
+        const dfloat dd{dh, (float)(delta - (double)dh)};
+        const dfloat Lx{P.Lf[0], P.Llo[0]}, Ly{P.Lf[1], P.Llo[1]}, Lz{P.Lf[2], P.Llo[2]};
+        const dfloat zero{0.f, 0.f};
+        dfloat s_w = zero, s_x = zero, s_y = zero, s_z = zero, s_n = zero;
+        for (int k = 0; k < cnt; ++k) {
+            const int e = base + 32 * k;
+            const int j = __ldg(B.col + e);
+            const int code = __ldg(B.img + e);
+            const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
+            dfloat shx = zero, shy = zero, shz = zero;
+            int m = 0;
+            if (shifted) {
+                const int a = (code & 7) - 2, c = ((code >> 5) & 3) - 1;
+                m = ((code >> 3) & 3) - 1;
+                // a L_x + m delta as one double-float (the exact FP64 order does not matter here)
+                dfloat sa = zero;
+                if (a == 1 || a == -1)
+                    sa = a > 0 ? Lx : df_neg(Lx);
+                else if (a == 2 || a == -2)
+                    sa = a > 0 ? dfloat{2.f * Lx.hi, 2.f * Lx.lo} : dfloat{-2.f * Lx.hi, -2.f * Lx.lo};
+                else if (a != 0)
+                    sa = df_mul(dfloat{(float)a, 0.f}, Lx);
+                shx = m == 0 ? sa : df_add(sa, m > 0 ? dd : df_neg(dd));
+                shy = m == 0 ? zero : (m > 0 ? Ly : df_neg(Ly));
+                shz = c == 0 ? zero : (c > 0 ? Lz : df_neg(Lz));
+            }
+            const dfloat dx = sep_df(xih, xil, ph[j], pl[j], shx);
+            const dfloat dy = sep_df(yih, yil, ph[np + j], pl[np + j], shy);
+            const dfloat dz = sep_df(zih, zil, ph[2 * np + j], pl[2 * np + j], shz);
+            const dfloat r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+            const dfloat w = pair_weight_df(P, B.exp_tab_df, r2);
+            B.val[e] = df_to_double(w);
+            B.val32[e] = w.hi;
+            s_w = df_add(s_w, w);
+            s_x = df_add(s_x, df_mul(dx, w));
+            s_y = df_add(s_y, df_mul(dy, w));
+            s_z = df_add(s_z, df_mul(dz, w));
+            if (shifted && m != 0) s_n = df_add(s_n, m > 0 ? w : df_neg(w));
         }
-        const double w = pair_weight(P, B.exp_tab, fma(dx, dx, fma(dy, dy, dz * dz)));
-        B.val[e] = w;
-        B.val32[e] = (float)w;
-        sw += w;
-        fx = fma(dx, w, fx);
-        fy = fma(dy, w, fy);
-        fz = fma(dz, w, fz);
-        if (shifted) nw += m == 0 ? 0.0 : (m > 0 ? w : -w);
+        sw = df_to_double(s_w);
+        fx = df_to_double(s_x);
+        fy = df_to_double(s_y);
+        fz = df_to_double(s_z);
+        nw = df_to_double(s_n);
+    } else {
+        const double Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
+        const double* __restrict__ pos = B.pos_w;
+        for (int k = 0; k < cnt; ++k) {
+            const int e = base + 32 * k;
+            const int j = __ldg(B.col + e);
+            const int code = __ldg(B.img + e);
+            double dx = __dsub_rn(xi, pos[j]);
+            double dy = __dsub_rn(yi, pos[np + j]);
+            double dz = __dsub_rn(zi, pos[2 * np + j]);
+            const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
+            int m = 0;
+            if (shifted) {
+                const int a = (code & 7) - 2, c = ((code >> 5) & 3) - 1;
+                m = ((code >> 3) & 3) - 1;
+                const double sn = m == 0 ? 0.0 : (m > 0 ? delta : -delta);
+                const double sa = a == 0 ? 0.0 : (a == 1 ? Lx : (a == -1 ? -Lx : __dmul_rn(Lx, (double)a)));
+                const double sy = m == 0 ? 0.0 : (m > 0 ? Ly : -Ly);
+                const double sz = c == 0 ? 0.0 : (c > 0 ? Lz : -Lz);
+                dx = __dsub_rn(__dsub_rn(dx, sn), sa);
+                dy = __dsub_rn(dy, sy);
+                dz = __dsub_rn(dz, sz);
+            }
+            const double w = pair_weight(P, B.exp_tab, fma(dx, dx, fma(dy, dy, dz * dz)));
+            B.val[e] = w;
+            B.val32[e] = (float)w;
+            sw += w;
+            fx = fma(dx, w, fx);
+            fy = fma(dy, w, fy);
+            fz = fma(dz, w, fz);
+            if (shifted) nw += m == 0 ? 0.0 : (m > 0 ? w : -w);
+        }
     }
     for (int k = cnt; k < clen; ++k) {
         B.val[base + 32 * k] = 0.0;
@@ -658,18 +771,21 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B)
     }
 }
 
-int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, Launch L)
+int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool df, Launch L)
 {
     k_nbr_fill<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B);
     if (!assemble) return 1;
-    launch_assemble_only(P, B, use_inj, L);
+    launch_assemble_only(P, B, use_inj, df, L);
     return 2;
 }
 
-// Assembly from existing pairs.
-void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, Launch L)
+// Assembly from existing pairs (df: double-float entries, the mixed-precision path).
+void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool df, Launch L)
 {
-    k_assemble_slots<<<P.nslots / 256, 256, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
+    if (df)
+        k_assemble_slots<true><<<P.nslots / 256, 256, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
+    else
+        k_assemble_slots<false><<<P.nslots / 256, 256, 0, L.stream>>>(P, B, use_inj ? 1 : 0);
 }
 
 // ------------------------------------------------------ generator utilities

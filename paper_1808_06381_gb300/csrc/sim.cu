@@ -166,7 +166,12 @@ void derive(const sp_params& p, KParams& k, int npad)
     const double margin = std::ldexp(256.0 * Lmax * p.rc + 64.0 * p.rc * p.rc, -24);
     k.rc2_lo = (float)(k.rc2 - margin);
     k.rc2_hi = (float)(k.rc2 + margin);
-    for (int a = 0; a < 3; ++a) k.Lf[a] = (float)p.L[a];
+    for (int a = 0; a < 3; ++a) {
+        k.Lf[a] = (float)p.L[a];
+        k.Llo[a] = (float)(p.L[a] - (double)k.Lf[a]);
+    }
+    k.wsc_hi = (float)k.w_scale;
+    k.wsc_lo = (float)(k.w_scale - (double)k.wsc_hi);
     k.tol2 = p.cg_tol * p.cg_tol;
     // mixed solver: each FP32 inner solve reduces the residual by 10^-4 before
     // the FP64 residual is recomputed (well above FP32 attainable accuracy)
@@ -299,7 +304,7 @@ int capture_step_graph(sp_sim* s)
     cudaStream_t cs = s->cap_stream[0];
     SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     long long launches = enqueue_build(s, cs);
-    launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, launch_of(s, cs));
+    launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
     if (s->learned) {
         launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
         launches += mp_infer_launches();
@@ -416,7 +421,7 @@ int do_build(sp_sim* s)
     for (int attempt = 0; attempt < 4; ++attempt) {
         long long launches = enqueue_build(s, s->stream);
         (void)launches;
-        launch_nbr_fill(s->kp, s->B, false, s->use_inj, launch_of(s, s->stream));
+        launch_nbr_fill(s->kp, s->B, false, s->use_inj, mixed(s), launch_of(s, s->stream));
         SS_TRY(read_state(s));
         if (!s->st_host->overflow) break;
         SS_TRY(grow_pairs(s));
@@ -471,7 +476,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.exp_tab, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -552,6 +557,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.pos_s, v3));
     A(dev_alloc(s, &B.pos_w, v3));
     A(dev_alloc(s, &B.pos32, v3));
+    A(dev_alloc(s, &B.pos32lo, v3));
     A(dev_alloc(s, &B.v_s, v3));
     A(dev_alloc(s, &B.id_s, n));
     A(dev_alloc(s, &B.id_w, n));
@@ -582,6 +588,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.partials_df, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.exp_tab, (size_t)kExpTab));
+    A(dev_alloc(s, &B.exp_tab_df, (size_t)kExpTab));
     A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(std::max(n, s->kp.ncell), s->kp.nchunks) / 4096 + 2)));
     A(dev_alloc(s, &B.stage, 3 * (size_t)n));
     A(dev_alloc(s, &B.st, 1));
@@ -596,7 +603,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.pos_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.pos_w, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
-        upload_exp_table(B.exp_tab, s->stream) != cudaSuccess) {
+        upload_exp_table(B.exp_tab, B.exp_tab_df, s->stream) != cudaSuccess) {
         s->err = "initialising device state failed";
         return fail(SP_ERR_CUDA);
     }
@@ -646,7 +653,7 @@ int sp_assemble(sp_sim* s)
         s->err = "sp_assemble needs sp_build_neighbors after the last position change";
         return SP_ERR_INVALID_ARG;
     }
-    launch_assemble_only(s->kp, s->B, s->use_inj, launch_of(s, s->stream));
+    launch_assemble_only(s->kp, s->B, s->use_inj, mixed(s), launch_of(s, s->stream));
     SS_CUDA(cudaGetLastError());
     SS_CUDA(cudaStreamSynchronize(s->stream));
     s->assembled = true;
@@ -719,7 +726,7 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
         if (s->host_loop) {
             for (long long k = 0; k < todo; ++k) {
                 launches += enqueue_build(s, s->stream);
-                launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, launch_of(s, s->stream));
+                launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, s->stream));
                 if (s->learned) {
                     launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, s->stream));
                     launches += mp_infer_launches();
@@ -809,9 +816,9 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         launch_sell_plan(P, B, L);
         launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
         mark(COUNT);
-        launch_nbr_fill(P, B, false, s->use_inj, L);
+        launch_nbr_fill(P, B, false, s->use_inj, mx, L);
         mark(FILL);
-        launch_assemble_only(P, B, s->use_inj, L);
+        launch_assemble_only(P, B, s->use_inj, mx, L);
         rc = mark(ASSEMBLE);
         if (rc == SP_OK && s->learned) {
             launch_mp_infer(P, B, s->mp, L);

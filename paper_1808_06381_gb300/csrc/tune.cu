@@ -73,7 +73,7 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
 
     // the system of the current positions (noise of the current step counter)
     SS_TRY(do_build(s));
-    launch_assemble_only(s->kp, s->B, s->use_inj, launch_of(s, s->stream));
+    launch_assemble_only(s->kp, s->B, s->use_inj, mixed(s), launch_of(s, s->stream));
     SS_CUDA(cudaStreamSynchronize(s->stream));
     s->assembled = true;
     SS_TRY(read_state(s));

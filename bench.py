@@ -141,7 +141,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch of the persistent solve from one ncu capture
 # (profiles/k32_cg_persistent_n262144.md), keyed by workload and tile configuration
 # (gathers in flight, blocks per SM); any other kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 8, 4): 439.6e6}
+PROFILED_TRAFFIC = {}   # filled from the capture of the current kernels
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:

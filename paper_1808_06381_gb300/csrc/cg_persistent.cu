@@ -289,12 +289,21 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         // ---- SpMV with the fused direction update; p.q
         dfloat pq{0.f, 0.f};
         const float betaf = sh.beta_f;
+        // the row and entry range of the next window are loaded while this one
+        // is processed (they do not change during the solve)
+        int slot = wb * 256 + chunk_lane(0);
+        int row = wb < we ? B.slot_row[slot] : -1;
+        int e0 = wb < we ? B.chunk_off[slot >> 5] + (slot & 31) : 0;
+        int e1 = wb < we ? B.chunk_off[(slot >> 5) + 1] : 0;
         for (int w = wb; w < we; ++w) {
-            const int slot = w * 256 + chunk_lane(w - wb);
-            const int row = B.slot_row[slot];
+            int nrow = -1, ne0 = 0, ne1 = 0;
+            if (w + 1 < we) {
+                const int ns = (w + 1) * 256 + chunk_lane(w + 1 - wb);
+                nrow = B.slot_row[ns];
+                ne0 = B.chunk_off[ns >> 5] + (ns & 31);
+                ne1 = B.chunk_off[(ns >> 5) + 1];
+            }
             if (row >= 0) {
-                const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
-                const int e1 = B.chunk_off[(slot >> 5) + 1];
                 const float4 ri = B.r4[row];
                 const float d = __ldg(B.diag32 + row);
                 float4 qo = make_float4(0.f, 0.f, 0.f, 0.f), po = qo;
@@ -321,6 +330,9 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                 B.p4[row] = make_float4(p0, p1, p2, 0.f);
                 pq = df_add(pq, p0 * q0 + p1 * q1 + p2 * q2);
             }
+            row = nrow;
+            e0 = ne0;
+            e1 = ne1;
         }
         {
             const dfloat v[1] = {pq};

@@ -181,8 +181,8 @@ typedef struct sp_kernel_profile {
     int32_t cg_iterations;
     int32_t precision;               /* enum sp_precision of the solver */
     double sort_ms;                  /* part of build_ms: binning and the counting sort into cell order */
-    double count_ms;                 /* part of build_ms: pair counting and the row-pointer scan */
-    double fill_ms;                  /* part of build_ms: the pair fill (columns and image codes) */
+    double count_ms;                 /* part of build_ms: the pair search (counts and partners) and the slice plan */
+    double fill_ms;                  /* part of build_ms: a separate pair fill (0: the assembly places the pairs) */
     int64_t nnz_slots;               /* stored entries including the sliced layout's padding */
     int32_t probe_reps;              /* back-to-back launches timed for the two fields below */
     double spmv_probe_ms;            /* average SpMV kernel time, launched back to back */

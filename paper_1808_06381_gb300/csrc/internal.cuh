@@ -95,6 +95,8 @@ struct DevBuffers {
     // (descending) inside windows of 256, the ranked rows form chunks of 32,
     // and entry k of the row in slot s sits at chunk_off[s / 32] + 32 k + s % 32.
     int* row_cnt;    // [n] off-diagonal entries of each row
+    int* cand_j;     // [kCandCap][npad] partners of each row as found by the pair search
+    unsigned char* cand_img; // [kCandCap][npad] their image codes
     int* slot_row;   // [nslots] row of each slot (-1: padding slot)
     int* row_slot;   // [n]
     int* chunk_len32;// [nchunks] 32 x the longest row of each chunk
@@ -129,6 +131,7 @@ struct DevBuffers {
 
 constexpr int kMaxPartials = 4096;
 constexpr int kExpTab = 1024;
+constexpr int kCandCap = 32;    // partners kept per row by the search (rows with more are searched again)
 constexpr int kMaxSmIds = 1024;   // weight table: exp(-t) for t < 4 (pairs have t < ln 20)
 
 // Learned warm start (mpnn.cu): flat FP32 weights W1 [6][64], W2 [64][64],

@@ -440,10 +440,13 @@ __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta
         for_each_neighbor_generic(P, delta, pos, cell_start, i, xi, yi, zi, visit);
 }
 
-__global__ void k_nbr_count(KParams P, const double* __restrict__ pos, const float* __restrict__ pos32,
-                            const int* __restrict__ cell_start, int* __restrict__ row_cnt,
-                            DevState* st)
+// The pair search of a step, run once: counts the partners of every row and
+// keeps the first kCandCap of them (partner and image code, k-major so that a
+// warp's stores are coalesced) for the assembly, which places them in the
+// sliced layout.
+__global__ void k_nbr_collect(KParams P, DevBuffers B)
 {
+    DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) st->nnz = 0;
@@ -451,15 +454,22 @@ __global__ void k_nbr_count(KParams P, const double* __restrict__ pos, const flo
     const double delta = st->delta;
     const int np = P.npad;
     int cnt = 0;
-    for_each_neighbor(P, delta, pos, pos32, cell_start, i, pos[i], pos[np + i], pos[2 * np + i],
-                      [&](int, unsigned char) { ++cnt; });
-    row_cnt[i] = cnt;
+    int* __restrict__ cj = B.cand_j;
+    unsigned char* __restrict__ ci = B.cand_img;
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, B.pos_w[i], B.pos_w[np + i],
+                      B.pos_w[2 * np + i], [&](int j, unsigned char code) {
+                          if (cnt < kCandCap) {
+                              cj[(size_t)cnt * np + i] = j;
+                              ci[(size_t)cnt * np + i] = code;
+                          }
+                          ++cnt;
+                      });
+    B.row_cnt[i] = cnt;
 }
 
 void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L)
 {
-    k_nbr_count<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B.pos_w, B.pos32, B.cell_start,
-                                                                    B.row_cnt, B.st);
+    k_nbr_collect<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B);
 }
 
 // Slices of the matrix: inside each window of 256 rows, rank the rows by
@@ -581,6 +591,24 @@ cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t s
     return e;
 }
 
+// The partners of row i written straight into its slots (rows with more than
+// kCandCap partners; rare), in the order of the counting search.
+__device__ __noinline__ void search_row_into_slots(const KParams& P, const DevBuffers& B, int i, double delta,
+                                                   int base, int cnt)
+{
+    const int np = P.npad;
+    int k = 0;
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, B.pos_w[i], B.pos_w[np + i], B.pos_w[2 * np + i],
+                      [&](int j, unsigned char code) {
+                          if (k < cnt) {
+                              B.col[base + 32 * k] = j;
+                              B.img[base + 32 * k] = code;
+                          }
+                          ++k;
+                      });
+    if (k != cnt) atomicCAS(&B.st->error, 0, (int)SP_ERR_INVALID_ARG);
+}
+
 // The pair weight of pair_weight() for the mixed-precision path, in
 // double-float arithmetic (FP32 pipes): the same table-driven method, with
 // 256 t = k + f split exactly, exp(-f/256) = 1 + g + g^2/2 + ... for
@@ -634,7 +662,7 @@ __device__ __forceinline__ dfloat sep_df(float ih, float il, float jh, float jl,
 // (the 2^-48 representation of the positions), far inside the mixed solver's
 // tolerance.  The noise and the per-row finish stay FP64.
 template <bool DF>
-__global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
+__global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
 {
     const DevState* st = B.st;
     if (st->error | st->overflow) return;
@@ -648,6 +676,17 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
     const int clen = (B.chunk_off[(slot >> 5) + 1] - B.chunk_off[slot >> 5]) >> 5;
     const int cnt = B.row_cnt[i];
     const int center = image_code(0, 0, 0);
+    // partners of the row: from the search's candidates, placed into the sliced
+    // layout here; a row with more than kCandCap partners is searched again
+    const int* __restrict__ pj = B.cand_j + i;
+    const unsigned char* __restrict__ pimg = B.cand_img + i;
+    size_t pstride = (size_t)np;
+    if (cnt > kCandCap) {
+        search_row_into_slots(P, B, i, delta, base, cnt);
+        pj = B.col + base;
+        pimg = B.img + base;
+        pstride = 32;
+    }
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
     if (DF) {
         const float* __restrict__ ph = B.pos32;
@@ -661,8 +700,10 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
         dfloat s_w = zero, s_x = zero, s_y = zero, s_z = zero, s_n = zero;
         for (int k = 0; k < cnt; ++k) {
             const int e = base + 32 * k;
-            const int j = __ldg(B.col + e);
-            const int code = __ldg(B.img + e);
+            const int j = pj[k * pstride];
+            const int code = pimg[k * pstride];
+            B.col[e] = j;
+            B.img[e] = (unsigned char)code;
             const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
             dfloat shx = zero, shy = zero, shz = zero;
             int m = 0;
@@ -704,8 +745,10 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
         const double* __restrict__ pos = B.pos_w;
         for (int k = 0; k < cnt; ++k) {
             const int e = base + 32 * k;
-            const int j = __ldg(B.col + e);
-            const int code = __ldg(B.img + e);
+            const int j = pj[k * pstride];
+            const int code = pimg[k * pstride];
+            B.col[e] = j;
+            B.img[e] = (unsigned char)code;
             double dx = __dsub_rn(xi, pos[j]);
             double dy = __dsub_rn(yi, pos[np + j]);
             double dz = __dsub_rn(zi, pos[2 * np + j]);
@@ -733,6 +776,8 @@ __global__ void __launch_bounds__(256) k_assemble_slots(KParams P, DevBuffers B,
         }
     }
     for (int k = cnt; k < clen; ++k) {
+        B.col[base + 32 * k] = i;
+        B.img[base + 32 * k] = (unsigned char)center;
         B.val[base + 32 * k] = 0.0;
         B.val32[base + 32 * k] = 0.f;
     }
@@ -773,10 +818,12 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B)
 
 int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool df, Launch L)
 {
+    if (assemble) {   // places the collected partners and assembles
+        launch_assemble_only(P, B, use_inj, df, L);
+        return 1;
+    }
     k_nbr_fill<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B);
-    if (!assemble) return 1;
-    launch_assemble_only(P, B, use_inj, df, L);
-    return 2;
+    return 1;
 }
 
 // Assembly from existing pairs (df: double-float entries, the mixed-precision path).

@@ -476,7 +476,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -567,6 +567,8 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.cell_count, s->kp.ncell));
     A(dev_alloc(s, &B.cell_start, (size_t)s->kp.ncell + 1));
     A(dev_alloc(s, &B.row_cnt, n));
+    A(dev_alloc(s, &B.cand_j, (size_t)kCandCap * npad));
+    A(dev_alloc(s, &B.cand_img, (size_t)kCandCap * npad));
     A(dev_alloc(s, &B.slot_row, (size_t)s->kp.nslots));
     A(dev_alloc(s, &B.row_slot, n));
     A(dev_alloc(s, &B.chunk_len32, (size_t)s->kp.nchunks));
@@ -816,9 +818,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
         launch_sell_plan(P, B, L);
         launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
         mark(COUNT);
-        launch_nbr_fill(P, B, false, s->use_inj, mx, L);
-        mark(FILL);
-        launch_assemble_only(P, B, s->use_inj, mx, L);
+        launch_assemble_only(P, B, s->use_inj, mx, L);   // places the collected pairs and assembles
         rc = mark(ASSEMBLE);
         if (rc == SP_OK && s->learned) {
             launch_mp_infer(P, B, s->mp, L);

@@ -203,7 +203,8 @@ int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
  * Not in the paper (an implementation parameter).  The mixed-precision
  * solve runs as one cooperative persistent kernel compiled in several tile
  * configurations: gathers in flight per thread against resident blocks per
- * SM.  All of them do the same arithmetic in the same order (results are
+ * SM, with or without requesting the next batch of matrix columns while the
+ * current gathers are in flight.  All of them do the same arithmetic in the same order (results are
  * bit-identical); only the speed differs.  sp_autotune builds the pair list
  * and the system for the current positions, times `trials` solves from a
  * zero start with every configuration on the simulation's stream, keeps the
@@ -222,6 +223,7 @@ typedef struct sp_tune_info {
     int32_t from_cache;          /* 1: taken from the tuning cache, nothing timed */
     int32_t num_configs;         /* configurations available */
     double ms[SP_TUNE_MAX_CONFIGS]; /* best time of one solve per configuration (0: not timed) */
+    int32_t pipelined;           /* 1: the next batch of columns is requested during the current gathers */
 } sp_tune_info;
 int sp_autotune(sp_sim* sim, int32_t trials, sp_tune_info* info);
 

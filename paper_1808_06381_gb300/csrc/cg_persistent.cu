@@ -172,33 +172,43 @@ constexpr int kBatchP64 = 2;  // FP64 gathers in flight (the rare FP64 residual 
 // the last barrier are visible to plain loads (the barrier's acquire orders
 // them), so the gathers may hit L1: rows of neighbouring particles are
 // gathered by many rows of the same block.
-template <int KB>
+template <int KB, bool PIPE>
 __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const float* __restrict__ val,
                                             const float4* r, int e0, int e1, float& s0, float& s1, float& s2)
 {
     s0 = s1 = s2 = 0.f;
-    for (int eb = e0; eb < e1; eb += 32 * KB) {
-        int j[KB];
-        float w[KB];
+    int j[KB];
+    float w[KB];
+    auto load_batch = [&](int eb, int (&jj)[KB], float (&ww)[KB]) {
 #pragma unroll
         for (int u = 0; u < KB; ++u) {
             const int e = eb + 32 * u;
-            j[u] = 0;
-            w[u] = 0.f;
+            jj[u] = 0;
+            ww[u] = 0.f;
             if (e < e1) {
-                j[u] = ld_stream(col + e);
-                w[u] = ld_stream(val + e);
+                jj[u] = ld_stream(col + e);
+                ww[u] = ld_stream(val + e);
             }
         }
+    };
+    if (PIPE) load_batch(e0, j, w);
+    for (int eb = e0; eb < e1; eb += 32 * KB) {
+        if (!PIPE) load_batch(eb, j, w);
         float4 g[KB];
 #pragma unroll
         for (int u = 0; u < KB; ++u) {
             g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (w[u] != 0.f) g[u] = r[j[u]];
         }
+        // PIPE: the next batch's columns and weights are requested while this
+        // batch's gathers are in flight, so each batch waits one latency, not two
+        float wc[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) wc[u] = w[u];
+        if (PIPE) load_batch(eb + 32 * KB, j, w);
 #pragma unroll
         for (int u = 0; u < KB; ++u) {
-            const float ww = w[u] * g[u].w;
+            const float ww = wc[u] * g[u].w;
             s0 = fmaf(ww, g[u].x, s0);
             s1 = fmaf(ww, g[u].y, s1);
             s2 = fmaf(ww, g[u].z, s2);
@@ -250,7 +260,7 @@ __device__ __forceinline__ int chunk_lane(int k)
     return (k & 1) ? (int)(threadIdx.x ^ 0xE0u) : (int)threadIdx.x;
 }
 
-template <int KB>
+template <int KB, bool PIPE>
 __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
                                                  PShared& sh)
 {
@@ -312,7 +322,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                     po = B.p4[row];
                 }
                 float s0, s1, s2;
-                p_row_sum32<KB>(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
+                p_row_sum32<KB, PIPE>(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
                 const float z0 = ri.w * ri.x, z1 = ri.w * ri.y, z2 = ri.w * ri.z;
                 float q0 = fmaf(d, z0, -alpha_e * s0);
                 float q1 = fmaf(d, z1, -alpha_e * s1);
@@ -476,12 +486,14 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 
 // Tile configurations of the single-system kernel: gathers in flight per
 // thread (KB) against resident blocks per SM (MINB, which caps the registers
-// at 65536 / (256 MINB)).  Chosen per system by the autotuner.
-template <int KB, int MINB>
+// at 65536 / (256 MINB)), with or without requesting the next batch's
+// columns during the current gathers (PIPE).  Chosen per system by the
+// autotuner.
+template <int KB, int MINB, bool PIPE>
 __global__ void __launch_bounds__(kPBlock, MINB) k32_cg_persistent(KParams P, DevBuffers B)
 {
     __shared__ PShared sh;
-    persistent_solve<KB>(P, B, blockIdx.x, gridDim.x, sh);
+    persistent_solve<KB, PIPE>(P, B, blockIdx.x, gridDim.x, sh);
 }
 
 // Batch: block b serves replica k with blk_off[k] <= b < blk_off[k + 1]; each
@@ -503,19 +515,23 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
     }
     __syncthreads();
     const int k = rep;
-    persistent_solve<kBatchP>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
+    persistent_solve<kBatchP, false>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
 }
 
 namespace {
 struct PCfg {
-    int kb, minb;
+    int kb, minb, pipe;
     const void* fn;
     int occ;
 };
 PCfg g_pcfg[kPersistentConfigs] = {
-    {6, 4, (const void*)k32_cg_persistent<6, 4>, 0},  {8, 3, (const void*)k32_cg_persistent<8, 3>, 0},
-    {10, 3, (const void*)k32_cg_persistent<10, 3>, 0}, {12, 3, (const void*)k32_cg_persistent<12, 3>, 0},
-    {4, 4, (const void*)k32_cg_persistent<4, 4>, 0},  {8, 4, (const void*)k32_cg_persistent<8, 4>, 0},
+    {6, 4, 0, (const void*)k32_cg_persistent<6, 4, false>, 0},
+    {8, 4, 0, (const void*)k32_cg_persistent<8, 4, false>, 0},
+    {4, 4, 0, (const void*)k32_cg_persistent<4, 4, false>, 0},
+    {4, 4, 1, (const void*)k32_cg_persistent<4, 4, true>, 0},
+    {5, 4, 1, (const void*)k32_cg_persistent<5, 4, true>, 0},
+    {6, 3, 1, (const void*)k32_cg_persistent<6, 3, true>, 0},
+    {8, 3, 1, (const void*)k32_cg_persistent<8, 3, true>, 0},
 };
 int g_pocc_batch = 0;
 std::once_flag g_pocc_once;
@@ -560,11 +576,12 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
     return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
 }
 
-void cg_persistent_config(int k, int* gathers, int* blocks_per_sm)
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined)
 {
     const PCfg& c = g_pcfg[(k >= 0 && k < kPersistentConfigs) ? k : 0];
     *gathers = c.kb;
     *blocks_per_sm = c.minb;
+    *pipelined = c.pipe;
 }
 
 int cg_persistent_grid(const KParams& P, Launch L)

@@ -370,6 +370,10 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
     const int cx = cell_coord(xi, P.inv_cw[0], nc0);
     const int cy = cell_coord(yi, P.inv_cw[1], nc1);
     const int cz = cell_coord(zi, P.inv_cw[2], nc2);
+    // x cell of x_i - m delta for the rows of cells that wrap through y (m = -1, +1),
+    // computed once per particle (FP64 work is scarce on GB300)
+    const int cx_m1 = (int)floor((xi + delta) * P.inv_cw[0]);
+    const int cx_p1 = (int)floor((xi - delta) * P.inv_cw[0]);
     // image shifts by selection (no int-to-float conversions: GB300 runs them
     // at the FP64 rate); every product below is exact, as before
     auto times = [](int k, float v) { return k == 0 ? 0.f : (k > 0 ? v : -v); };
@@ -395,7 +399,7 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
             }
             const float syf = times(m, P.Lf[1]);
             const float mdf = times(m, deltaf);
-            const int cxu0 = m == 0 ? cx : (int)floor((xi - (double)m * delta) * P.inv_cw[0]);
+            const int cxu0 = m == 0 ? cx : (m > 0 ? cx_p1 : cx_m1);
             for (int dxc = -1; dxc <= 1; ++dxc) {
                 const int cxu = cxu0 + dxc;
                 // floor(cxu / nc0) for cxu in [-2 nc0, 3 nc0)

@@ -65,7 +65,7 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
         s->kp.pcfg = cfg;
         free_graphs(s);   // captured graphs hold the previous configuration's kernel
         out.config = cfg;
-        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm);
+        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined);
         if (info) *info = out;
         return SP_OK;
     };

@@ -11,7 +11,7 @@
 // The message passes run on the narrow features (like an SpMV of the solver);
 // the MLP is fused in one kernel on BF16 tensor cores (mma.sync m16n8k16, FP32
 // accumulation): a warp takes 16 rows, the FP32 accumulators of a layer pass
-// through tanh and are repacked in registers as the A operand of the next
+// through tanh (the hardware approximation) and are repacked in registers as the A operand of the next
 // layer, weights sit in shared memory.  Training (MSE to the converged
 // velocities) runs the backward pass in one fused kernel that stages a tile of
 // 128 rows in shared memory and forms the weight gradients with tensor-core
@@ -101,6 +101,15 @@ struct FwdRegs {
     float y[4];
 };
 
+// tanh by the hardware approximation (one MUFU operation, relative error
+// below 2^-10): finer than the BF16 rounding the activations get next.
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void mlp_forward(const unsigned (&a0)[4], const __nv_bfloat16* sW1T,
                                             const __nv_bfloat16* sW2T, const __nv_bfloat16* sW3T, FwdRegs& R)
 {
@@ -111,7 +120,7 @@ __device__ __forceinline__ void mlp_forward(const unsigned (&a0)[4], const __nv_
         load_b(sW1T, kSW, nb * 8, 0, b0, b1);
         mma16816(R.h1[nb], a0, b0, b1);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) R.h1[nb][q] = tanhf(R.h1[nb][q]);
+        for (int q = 0; q < 4; ++q) R.h1[nb][q] = tanh_fast(R.h1[nb][q]);
     }
 #pragma unroll
     for (int kb = 0; kb < 4; ++kb) {
@@ -130,7 +139,7 @@ __device__ __forceinline__ void mlp_forward(const unsigned (&a0)[4], const __nv_
             mma16816(R.h2[nb], R.a1[kb], b0, b1);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) R.h2[nb][q] = tanhf(R.h2[nb][q]);
+        for (int q = 0; q < 4; ++q) R.h2[nb][q] = tanh_fast(R.h2[nb][q]);
     }
 #pragma unroll
     for (int kb = 0; kb < 4; ++kb) {
@@ -282,17 +291,42 @@ __global__ void __launch_bounds__(kThreads) k_mp_mlp_fwd(int rows, MpBuffers M)
     }
 }
 
-// guess = s [y, a1, x0] . o, written as the start vector of CG.
-__global__ void k_mp_output(KParams P, DevBuffers B, MpBuffers M)
+// Second message pass fused with the output: a1 = M y for node i, then
+// guess = s [y, a1, x0] . o written as the start vector of CG (a1 is kept
+// for training).
+__global__ void k_mp_aggregate_output(KParams P, DevBuffers B, MpBuffers M)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    const int slot = B.row_slot[i];
+    const int base = B.chunk_off[slot >> 5] + (slot & 31);
+    const int cnt = B.row_cnt[i];
+    const float ae = (float)P.alpha;
+    float4 acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < cnt; ++k) {
+        const int e = base + 32 * k;
+        const int j = B.col[e];
+        const float w = ae * B.val32[e];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 u = M.y[3 * j + c];
+            acc[c].x = fmaf(w, u.x, acc[c].x);
+            acc[c].y = fmaf(w, u.y, acc[c].y);
+            acc[c].z = fmaf(w, u.z, acc[c].z);
+            acc[c].w = fmaf(w, u.w, acc[c].w);
+        }
+    }
+    const float di = B.dinv32[i];
     const double s = M.scal[0];
     const float* o = M.master + kMpOffO;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int r = 3 * i + c;
-        const float4 y = M.y[r], a = M.a1[r], x = M.x0[r];
+        const float4 a = make_float4(acc[c].x * di, acc[c].y * di, acc[c].z * di, acc[c].w * di);
+        M.a1[r] = a;
+        const float4 y = M.y[r], x = M.x0[r];
         const float out = y.x * o[0] + y.y * o[1] + y.z * o[2] + y.w * o[3] + a.x * o[4] + a.y * o[5] + a.z * o[6] +
                           a.w * o[7] + x.x * o[8] + x.y * o[9] + x.z * o[10];
         B.x[c * P.npad + i] = s * (double)out;
@@ -563,11 +597,10 @@ void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L)
     k_mp_input<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P, B, M);
     k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.x0, M.a0, 0);
     k_mp_mlp_fwd<<<grid_for(rows, 8 * 16, L.num_sms * 4), kThreads, 0, L.stream>>>(rows, M);
-    k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.y, M.a1, 0);
-    k_mp_output<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P, B, M);
+    k_mp_aggregate_output<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M);
 }
 
-int mp_infer_launches() { return 6; }
+int mp_infer_launches() { return 5; }
 
 void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, int t, Launch L)
 {

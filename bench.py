@@ -361,19 +361,17 @@ def main():
                               "solver's working set (~60 MB) is L2-resident during the solve"}
 
     # end to end through the public API: host positions in, step, host positions out
+    # (two pinned host buffers used in turn: each step's output is the next step's input)
     import ctypes  # noqa: F401
-    host_in = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    host_out = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    sim.get_positions(host_in)
+    bufs = [torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    sim.get_positions(bufs[0])
     delta, _ = sim.state()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        sim.set_positions(host_in, delta)
-        sim.step(1)
-        sim.get_positions(host_out)
-        delta, _ = sim.state()
-        host_in[:] = host_out
+    for k in range(args.e2e_steps):
+        sim.set_positions(bufs[k & 1], delta)
+        delta = sim.step(1)["delta"]
+        sim.get_positions(bufs[(k + 1) & 1])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_value(n, world, args.e2e_steps, max_over_ranks(1e3 * e2e_s, dist, "cuda"))

@@ -102,6 +102,8 @@ typedef struct sp_step_info {
     double last_residual;    /* true relative residual of the last solve */
     double stress_xy;        /* shear stress of the last step (pair virial, see sp_stress_xy) */
     int64_t kernel_launches; /* kernels this call ran on the GPU */
+    double delta;            /* Lees-Edwards offset after the steps (as sp_get_state) */
+    int64_t step;            /* step counter after the steps (as sp_get_state) */
 } sp_step_info;
 
 typedef struct sp_sim sp_sim;

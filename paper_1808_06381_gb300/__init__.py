@@ -58,7 +58,8 @@ class sp_solve_info(ctypes.Structure):
 class sp_step_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("steps_done", ctypes.c_int64),
                 ("cg_iterations", ctypes.c_int64), ("last_residual", ctypes.c_double),
-                ("stress_xy", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("stress_xy", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("delta", ctypes.c_double),
+                ("step", ctypes.c_int64)]
 
 
 class sp_kernel_profile(ctypes.Structure):
@@ -283,7 +284,8 @@ class Simulation:
             self._c(rc)
         return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,
                 "max_iterations": info.max_iterations, "last_residual": info.last_residual,
-                "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches}
+                "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches, "delta": info.delta,
+                "step": info.step}
 
     def structure_factor(self, nkx: int, nky: int, grid: int = 256):
         m = (2 * nkx + 1) * (2 * nky + 1)
@@ -446,7 +448,8 @@ class Batch:
             raise ShearsimError(rc, (load().sp_batch_last_error(self._h) or b"").decode())
         return [{"status": x.status, "steps_done": x.steps_done, "cg_iterations": x.cg_iterations,
                  "max_iterations": x.max_iterations, "last_residual": x.last_residual,
-                 "stress_xy": x.stress_xy, "kernel_launches": x.kernel_launches} for x in infos]
+                 "stress_xy": x.stress_xy, "kernel_launches": x.kernel_launches, "delta": x.delta,
+                 "step": x.step} for x in infos]
 
     def sim(self, k: int) -> Simulation:
         h = ctypes.c_void_p()

@@ -295,6 +295,8 @@ int sp_batch_step(sp_batch* b, int32_t nsteps, sp_step_info* info)
             info[k].max_iterations = iter_max;
             info[k].last_residual = s->st_host->last_res;
             info[k].stress_xy = s->st_host->stress_xy;
+            info[k].delta = s->st_host->delta;
+            info[k].step = s->st_host->step;
             info[k].kernel_launches = (k == 0 ? (long long)nsteps * b->fixed_launches : 0) + 0 * checks;
         }
         s->built = false;

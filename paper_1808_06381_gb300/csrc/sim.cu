@@ -770,6 +770,8 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
         info->last_residual = h.last_res;
         info->stress_xy = h.stress_xy;
         info->kernel_launches = launches;
+        info->delta = h.delta;
+        info->step = h.step;
     }
     s->built = false;
     s->assembled = false;

@@ -140,14 +140,15 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the persistent solve from one ncu capture
 # (profiles/k32_cg_persistent_n262144.md), keyed by workload and tile configuration
-# (gathers in flight, blocks per SM); any other kernel or workload reports null.
-PROFILED_TRAFFIC = {}   # filled from the capture of the current kernels
+# (gathers in flight, blocks per SM, pipelined); any other kernel or workload reports null.
+PROFILED_TRAFFIC = {("mixed-n262144", 6, 4, False): 460.7e6}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
     if not tune:
         return None
-    return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"]))
+    return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"],
+                                 tune["pipelined"]))
 
 
 def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
@@ -350,7 +351,7 @@ def main():
         pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
         kname = "k32_cg_persistent"
         if tune:
-            kname += f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']}>"
+            kname += f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])}>"
         persistent = {"kernel": kname, "bound": "hbm", "achieved": pach, "peak": peak,
                       "unit": "GB/s", "frac": pach / peak, "traffic": profiled_traffic(workload.name, tune),
                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",

@@ -9,10 +9,12 @@
 //   a1 = M y                                                     (message pass 2)
 //   guess = s [y, a1, x0] . o
 // The message passes run on the narrow features (like an SpMV of the solver);
-// the MLP is fused in one kernel on BF16 tensor cores (mma.sync m16n8k16, FP32
-// accumulation): a warp takes 16 rows, the FP32 accumulators of a layer pass
-// through tanh (the hardware approximation) and are repacked in registers as the A operand of the next
-// layer, weights sit in shared memory.  Training (MSE to the converged
+// the MLP of inference is one kernel on the tcgen05 tensor cores (BF16
+// operands in shared memory, FP32 accumulators in tensor memory, 128-row
+// tiles; k_mp_mlp_fwd_tc).  The training pass recomputes the forward with
+// mma.sync m16n8k16 fragments (a warp takes 16 rows, the FP32 accumulators of
+// a layer pass through tanh — the hardware approximation — and are repacked
+// in registers as the A operand of the next layer).  Training (MSE to the converged
 // velocities) runs the backward pass in one fused kernel that stages a tile of
 // 128 rows in shared memory and forms the weight gradients with tensor-core
 // products of transposed tiles (ldmatrix.trans), then a deterministic
@@ -192,6 +194,239 @@ __device__ __forceinline__ void load_weights_fwd(const __nv_bfloat16* wb, __nv_b
     for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) sW3T[(e / 64) * kSH + e % 64] = wb[kW3T + e];
 }
 
+// ------------------------------------------- forward MLP on tcgen05 tensor cores
+//
+// The three layers of a tile of 128 rows as 5th-generation tensor-core MMAs
+// (tcgen05.mma, kind::f16, BF16 operands from shared memory, FP32
+// accumulators in tensor memory), M = 128 rows: layer 1 [x0, a0] (K 6 -> 16)
+// x W1 (N = 64), layer 2 h1 x W2 (K = N = 64, four K = 16 steps), layer 3 h2 x
+// W3 (N 4 -> 16).  One thread issues the MMAs and commits them to an
+// mbarrier; the four warps read the accumulators back with tcgen05.ld (warp w
+// owns rows 32w..32w+31, its lane quarter of tensor memory), apply tanh, and
+// store BF16 into the next layer's operand tile.  Operands use the
+// no-swizzle K-major layout of 8 x 16-byte core matrices: element (r, k) of an
+// R x K tile sits at ((r / 8) (K / 8) + k / 8) 128 + (r % 8) 16 + (k % 8) 2
+// bytes, so the leading (K) core-matrix stride is 128 bytes and the stride
+// between 8-row groups K / 8 x 128 bytes.  64 columns of tensor memory are
+// reused by the three layers.  Every wait is bounded.
+namespace tc {
+
+constexpr int kRows = 128;
+constexpr int kTmemCols = 64;
+constexpr long long kWaitLimit = 1ll << 24;
+
+__device__ __forceinline__ int core_off(int r, int k, int K)   // byte offset in a core-matrix tile
+{
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned long long smem_desc(const void* base, int K)
+{
+    const unsigned long long addr = smem_addr(base);
+    const unsigned long long lbo = 128, sbo = (unsigned long long)(K >> 3) * 128;
+    return ((addr >> 4) & 0x3FFFull) | (((lbo >> 4) & 0x3FFFull) << 16) | (((sbo >> 4) & 0x3FFFull) << 32) |
+           (1ull << 46);   // descriptor version 1; base offset 0, no swizzle
+}
+
+__host__ __device__ constexpr unsigned idesc_bf16(int M, int N)
+{
+    return (1u << 4)                  // D: FP32
+           | (1u << 7) | (1u << 10)   // A, B: BF16
+           | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);   // both K-major
+}
+
+__device__ __forceinline__ void mma(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                    int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(void* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
+                 : "memory");
+}
+
+// bounded wait for the mbarrier phase with the given parity; false on timeout
+__device__ __forceinline__ bool wait_phase(void* mbar, unsigned parity)
+{
+    const unsigned a = smem_addr(mbar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+}  // namespace tc
+
+}  // namespace
+
+// y = h2 W3 with h2 = tanh(tanh([x0, a0] W1) W2), 128 rows per tile (see tc above).
+__global__ void __launch_bounds__(128) k_mp_mlp_fwd_tc(int rows, MpBuffers M, DevState* st)
+{
+    using namespace tc;
+    __shared__ __align__(128) unsigned char sA1[kRows * 16 * 2];   // [128][16] inputs
+    __shared__ __align__(128) unsigned char sB1[64 * 16 * 2];      // [64][16]  W1^T
+    __shared__ __align__(128) unsigned char sA2[kRows * 64 * 2];   // [128][64] h1, then h2
+    __shared__ __align__(128) unsigned char sB2[64 * 64 * 2];      // [64][64]  W2^T
+    __shared__ __align__(128) unsigned char sB3[16 * 64 * 2];      // [16][64]  W3^T (n padded 4 -> 16)
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights (BF16, already transposed and padded) into core-matrix tiles
+    for (int e = tid; e < 64 * 16; e += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(sB1 + core_off(e / 16, e % 16, 16)) = M.wb[kW1T + e];
+    for (int e = tid; e < 64 * 64; e += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(sB2 + core_off(e / 64, e % 64, 64)) = M.wb[kW2T + e];
+    for (int e = tid; e < 16 * 64; e += blockDim.x) {
+        const int n = e / 64, k = e % 64;
+        *reinterpret_cast<__nv_bfloat16*>(sB3 + core_off(n, k, 64)) =
+            n < 8 ? M.wb[kW3T + n * 64 + k] : __float2bfloat16_rn(0.f);
+    }
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_base;
+    const unsigned tlane = tmem + ((unsigned)(warp * 32) << 16);   // this warp's lane quarter
+    const unsigned id1 = idesc_bf16(kRows, 64), id3 = idesc_bf16(kRows, 16);
+    unsigned phase = 0;
+
+    for (int base = blockIdx.x * kRows; base < rows && !failed; base += gridDim.x * kRows) {
+        const int r = base + tid;   // this thread's row (tile row tid)
+        {   // layer-1 operand: [x0, a0] in BF16, k 6..15 zero
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x = r < rows ? M.x0[r] : z, a = r < rows ? M.a0[r] : z;
+            uint4 lo, hi;
+            lo.x = pack_bf16(x.x, x.y);
+            lo.y = pack_bf16(x.z, a.x);
+            lo.z = pack_bf16(a.y, a.z);
+            lo.w = 0u;
+            hi = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sA1 + core_off(tid, 0, 16)) = lo;
+            *reinterpret_cast<uint4*>(sA1 + core_off(tid, 8, 16)) = hi;
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            mma(tmem, smem_desc(sA1, 16), smem_desc(sB1, 16), id1, 0);
+            commit(&mbar);
+        }
+        if (!wait_phase(&mbar, phase)) atomicExch(&failed, 1);
+        phase ^= 1u;
+        fence_after();
+        // h1 = tanh(D), BF16 into the layer-2 operand
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; q += 8) {
+                uint4 w;
+                w.x = pack_bf16(tanh_fast(v[q]), tanh_fast(v[q + 1]));
+                w.y = pack_bf16(tanh_fast(v[q + 2]), tanh_fast(v[q + 3]));
+                w.z = pack_bf16(tanh_fast(v[q + 4]), tanh_fast(v[q + 5]));
+                w.w = pack_bf16(tanh_fast(v[q + 6]), tanh_fast(v[q + 7]));
+                *reinterpret_cast<uint4*>(sA2 + core_off(tid, c + q, 64)) = w;
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)   // K = 16 per step: two core matrices, 256 bytes
+                mma(tmem, smem_desc(sA2 + ks * 256, 64), smem_desc(sB2 + ks * 256, 64), id1, ks > 0);
+            commit(&mbar);
+        }
+        if (!wait_phase(&mbar, phase)) atomicExch(&failed, 1);
+        phase ^= 1u;
+        fence_after();
+        // h2 = tanh(D) overwrites h1 (layer 2 has read it)
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; q += 8) {
+                uint4 w;
+                w.x = pack_bf16(tanh_fast(v[q]), tanh_fast(v[q + 1]));
+                w.y = pack_bf16(tanh_fast(v[q + 2]), tanh_fast(v[q + 3]));
+                w.z = pack_bf16(tanh_fast(v[q + 4]), tanh_fast(v[q + 5]));
+                w.w = pack_bf16(tanh_fast(v[q + 6]), tanh_fast(v[q + 7]));
+                *reinterpret_cast<uint4*>(sA2 + core_off(tid, c + q, 64)) = w;
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma(tmem, smem_desc(sA2 + ks * 256, 64), smem_desc(sB3 + ks * 256, 64), id3, ks > 0);
+            commit(&mbar);
+        }
+        if (!wait_phase(&mbar, phase)) atomicExch(&failed, 1);
+        phase ^= 1u;
+        fence_after();
+        {
+            float v[16];
+            ld16(tlane, v);
+            if (r < rows) M.y[r] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        fence_before();
+        __syncthreads();   // the next tile's MMAs overwrite tensor memory and the operands
+        fence_after();
+    }
+    if (failed && tid == 0) atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+namespace {
 }  // namespace
 
 // -------------------------------------------------------------- kernels
@@ -265,29 +500,6 @@ __global__ void k_mp_aggregate(KParams P, DevBuffers B, const float4* __restrict
             r = make_float4(r.x + o.x, r.y + o.y, r.z + o.z, r.w + o.w);
         }
         out[3 * i + c] = r;
-    }
-}
-
-// y = h2 W3 with h2 = tanh(tanh([x0, a0] W1) W2): one warp per 16 rows.
-__global__ void __launch_bounds__(kThreads) k_mp_mlp_fwd(int rows, MpBuffers M)
-{
-    __shared__ __align__(16) __nv_bfloat16 sW1T[64 * kSW];
-    __shared__ __align__(16) __nv_bfloat16 sW2T[64 * kSH];
-    __shared__ __align__(16) __nv_bfloat16 sW3T[8 * kSH];
-    load_weights_fwd(M.wb, sW1T, sW2T, sW3T);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int base = (blockIdx.x * 8 + warp) * 16; base < rows; base += gridDim.x * 8 * 16) {
-        const int r0 = base + g, r1 = base + g + 8;
-        unsigned a0[4];
-        input_frag(M.x0, M.a0, rows, r0, r1, a0);
-        FwdRegs R;
-        mlp_forward(a0, sW1T, sW2T, sW3T, R);
-        if (t < 2) {
-            float* y = reinterpret_cast<float*>(M.y);
-            if (r0 < rows) *reinterpret_cast<float2*>(y + 4 * (size_t)r0 + 2 * t) = make_float2(R.y[0], R.y[1]);
-            if (r1 < rows) *reinterpret_cast<float2*>(y + 4 * (size_t)r1 + 2 * t) = make_float2(R.y[2], R.y[3]);
-        }
     }
 }
 
@@ -596,7 +808,7 @@ void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L)
     k_mp_scale<<<grid_for(P.n, kVecBlock, L.num_sms * 4), kVecBlock, 0, L.stream>>>(P, B, M);
     k_mp_input<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P, B, M);
     k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.x0, M.a0, 0);
-    k_mp_mlp_fwd<<<grid_for(rows, 8 * 16, L.num_sms * 4), kThreads, 0, L.stream>>>(rows, M);
+    k_mp_mlp_fwd_tc<<<grid_for(rows, tc::kRows, L.num_sms * 6), tc::kRows, 0, L.stream>>>(rows, M, B.st);
     k_mp_aggregate_output<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M);
 }
 

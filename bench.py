@@ -138,9 +138,10 @@ class ClockSampler:
                 "samples": len(sm), "interval_ms": self.INTERVAL_MS, "reasons": sorted(reasons)}
 
 
-# DRAM bytes (read + write) per launch of the persistent solve from one ncu capture
-# (profiles/k32_cg_persistent_n262144.md), keyed by workload and tile configuration
-# (gathers in flight, blocks per SM, pipelined); any other kernel or workload reports null.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# persistent solve from one ncu capture of this command's kernel, keyed by workload
+# and tile configuration (gathers in flight, blocks per SM, pipelined); any other
+# kernel or workload reports null.
 PROFILED_TRAFFIC = {("mixed-n262144", 6, 4, False): 460.7e6}
 
 

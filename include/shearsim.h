@@ -265,7 +265,7 @@ int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count
  *
  * The paper solves Eq. algebra with no learned part; this optional network
  * guesses the velocities before CG, which then runs from the guess to the
- * same tolerance (CG alone judges the result).  For node i and Cartesian
+ * same tolerance (CG alone decides convergence).  For node i and Cartesian
  * component c, with shared weights: s = RMS of b; x0 = (b/A_ii, vprev, b)/s;
  * a0 = M x0 with (M u)_i = sum_j alpha w_ij / A_ii u_j; y = tanh(tanh([x0,a0] W1)
  * W2) W3 (6 -> 64 -> 64 -> 4, BF16 tensor cores, FP32 accumulation); a1 = M y;

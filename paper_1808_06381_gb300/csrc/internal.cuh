@@ -73,6 +73,7 @@ struct DevState {
     alignas(128) unsigned int bar_count;
     alignas(128) unsigned int bar_gen;
     int bar_err;
+    long long noise_step;     // step whose normals noise3 holds (-1: none)
 };
 
 // Device buffers of one simulation (all in the current cell order unless noted).
@@ -95,6 +96,7 @@ struct DevBuffers {
     // (descending) inside windows of 256, the ranked rows form chunks of 32,
     // and entry k of the row in slot s sits at chunk_off[s / 32] + 32 k + s % 32.
     int* row_cnt;    // [n] off-diagonal entries of each row
+    double* noise3;  // [3][npad] the step's thermal normals by row, drawn during the pair search
     int* cand_j;     // [kCandCap][npad] partners of each row as found by the pair search
     unsigned char* cand_img; // [kCandCap][npad] their image codes
     int* slot_row;   // [nslots] row of each slot (-1: padding slot)
@@ -504,7 +506,9 @@ void launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_c
 void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L);
 void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
-void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L);
+// The step's pair search; with draw_noise it also draws the thermal normals
+// of every row (FP64 Box-Muller, overlapping the search's memory latency).
+void launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L);
 // Pair fill (columns and image codes), followed, with assemble, by the FP64
 // assembly of the matrix and right-hand side; returns the kernels launched.
 int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool df, Launch L);

@@ -448,13 +448,23 @@ __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta
 // keeps the first kCandCap of them (partner and image code, k-major so that a
 // warp's stores are coalesced) for the assembly, which places them in the
 // sliced layout.
-__global__ void k_nbr_collect(KParams P, DevBuffers B)
+__global__ void k_nbr_collect(KParams P, DevBuffers B, int draw_noise)
 {
     DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) st->nnz = 0;
+    if (i == 0) {
+        st->nnz = 0;
+        st->noise_step = draw_noise ? st->step : -1;
+    }
     if (i >= P.n) return;
+    if (draw_noise) {   // the step's normals of this row (the assembly uses them)
+        double g0, g1, g2;
+        normals3(P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
+        B.noise3[i] = g0;
+        B.noise3[P.npad + i] = g1;
+        B.noise3[2 * P.npad + i] = g2;
+    }
     const double delta = st->delta;
     const int np = P.npad;
     int cnt = 0;
@@ -471,9 +481,9 @@ __global__ void k_nbr_collect(KParams P, DevBuffers B)
     B.row_cnt[i] = cnt;
 }
 
-void launch_nbr_count(const KParams& P, DevBuffers& B, Launch L)
+void launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L)
 {
-    k_nbr_collect<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B);
+    k_nbr_collect<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, draw_noise ? 1 : 0);
 }
 
 // Slices of the matrix: inside each window of 256 rows, rank the rows by
@@ -514,7 +524,7 @@ void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L)
 //   F_i  = noise_amp xi_i + c_ev sum_j R_ij w_ij + zeta kappa (y_i - L_y/2) x
 //   b_i  = F_i / zeta + alpha kappa L_y (sum_j n_ij w_ij) x
 __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B, int i, double yi,
-                                           unsigned long long step, int use_inj, double sw,
+                                           unsigned long long step, int use_inj, bool drawn, double sw,
                                            double fx, double fy, double fz, double nw)
 {
     const int np = P.npad;
@@ -530,6 +540,10 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
             g0 = B.xi_inj[3 * (long long)id];
             g1 = B.xi_inj[3 * (long long)id + 1];
             g2 = B.xi_inj[3 * (long long)id + 2];
+        } else if (drawn) {   // drawn by the pair search of this step
+            g0 = B.noise3[i];
+            g1 = B.noise3[np + i];
+            g2 = B.noise3[2 * np + i];
         } else {
             normals3(P.seed, step, (unsigned long long)id, g0, g1, g2);
         }
@@ -785,7 +799,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
         B.val[base + 32 * k] = 0.0;
         B.val32[base + 32 * k] = 0.f;
     }
-    finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, sw, fx, fy, fz, nw);
+    finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, st->noise_step == st->step, sw, fx, fy, fz, nw);
 }
 
 // Pair search writing the sliced columns and image codes (FP32 decisions).

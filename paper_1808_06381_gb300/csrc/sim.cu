@@ -197,7 +197,7 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs)
         launch_scatter_sort_gather(P, B, warm, L);
         launches += 6;
     }
-    launch_nbr_count(P, B, L);
+    launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L);
     launch_sell_plan(P, B, L);
     launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
     return launches + 5;
@@ -476,7 +476,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -568,6 +568,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.cell_start, (size_t)s->kp.ncell + 1));
     A(dev_alloc(s, &B.row_cnt, n));
     A(dev_alloc(s, &B.cand_j, (size_t)kCandCap * npad));
+    A(dev_alloc(s, &B.noise3, v3));
     A(dev_alloc(s, &B.cand_img, (size_t)kCandCap * npad));
     A(dev_alloc(s, &B.slot_row, (size_t)s->kp.nslots));
     A(dev_alloc(s, &B.row_slot, n));
@@ -600,6 +601,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         return fail(SP_ERR_OOM);
     }
     std::memset(s->st_host, 0, sizeof(DevState));
+    s->st_host->noise_step = -1;   // no normals drawn yet
     if (cudaMemcpyAsync(B.st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.v_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
@@ -816,7 +818,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
             launch_scatter_sort_gather(P, B, warm, L);
         }
         mark(SORT);
-        launch_nbr_count(P, B, L);
+        launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L);
         launch_sell_plan(P, B, L);
         launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
         mark(COUNT);

@@ -142,14 +142,14 @@ class ClockSampler:
 # persistent solve from one ncu capture of this command's kernel, keyed by workload
 # and tile configuration (gathers in flight, blocks per SM, pipelined); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 6, 4, False): 460.7e6}
+PROFILED_TRAFFIC = {("mixed-n262144", 6, 4, False, 256): 460.7e6}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
     if not tune:
         return None
     return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"],
-                                 tune["pipelined"]))
+                                 tune["pipelined"], tune["block_threads"]))
 
 
 def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
@@ -363,7 +363,8 @@ def main():
         pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
         kname = "k32_cg_persistent"
         if tune:
-            kname += f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])}>"
+            kname += (f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])},"
+                      f"{tune['block_threads']}>")
         persistent = {"kernel": kname, "bound": "hbm", "achieved": pach, "peak": peak,
                       "unit": "GB/s", "frac": pach / peak, "traffic": profiled_traffic(workload.name, tune),
                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",

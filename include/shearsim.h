@@ -206,8 +206,13 @@ int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
  * solve runs as one cooperative persistent kernel compiled in several tile
  * configurations: gathers in flight per thread against resident blocks per
  * SM, with or without requesting the next batch of matrix columns while the
- * current gathers are in flight.  All of them do the same arithmetic in the same order (results are
- * bit-identical); only the speed differs.  sp_autotune builds the pair list
+ * current gathers are in flight, and blocks of 256 or 1024 threads (one or
+ * four windows of rows at a time; fewer, larger blocks make the grid-wide
+ * reductions cheaper).  All of them run the same iteration with the same
+ * per-row arithmetic; the grid-wide dot products are summed per block, so a
+ * configuration with another block count rounds them differently (results
+ * agree to about 1e-13 relative), and each configuration is deterministic.
+ * sp_autotune builds the pair list
  * and the system for the current positions, times `trials` solves from a
  * zero start with every configuration on the simulation's stream, keeps the
  * fastest for this simulation, and leaves positions, step counter and the
@@ -226,6 +231,7 @@ typedef struct sp_tune_info {
     int32_t num_configs;         /* configurations available */
     double ms[SP_TUNE_MAX_CONFIGS]; /* best time of one solve per configuration (0: not timed) */
     int32_t pipelined;           /* 1: the next batch of columns is requested during the current gathers */
+    int32_t block_threads;       /* threads per block (256 per window processed at once) */
 } sp_tune_info;
 int sp_autotune(sp_sim* sim, int32_t trials, sp_tune_info* info);
 

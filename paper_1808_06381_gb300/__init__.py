@@ -80,7 +80,7 @@ class sp_kernel_profile(ctypes.Structure):
 class sp_tune_info(ctypes.Structure):
     _fields_ = [("config", ctypes.c_int32), ("gathers_in_flight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 8),
-                ("pipelined", ctypes.c_int32)]
+                ("pipelined", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
 
 def declared_symbols() -> list:
@@ -305,6 +305,7 @@ class Simulation:
         self._c(load().sp_autotune(self._h, int(trials), ctypes.byref(info)))
         return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
                 "blocks_per_sm": info.blocks_per_sm, "pipelined": bool(info.pipelined),
+                "block_threads": info.block_threads,
                 "from_cache": bool(info.from_cache),
                 "ms": [info.ms[k] for k in range(info.num_configs)]}
 

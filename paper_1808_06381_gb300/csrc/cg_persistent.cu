@@ -248,18 +248,21 @@ __device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const d
 
 }  // namespace
 
+// Slot of thread t (0..255 of its window group) in the group's k-th window.
+// The chunks of a window hold rows of decreasing length; warp c takes chunk c
+// of even windows and chunk 7 - c of odd ones, so a warp's rows over two
+// windows have about equal total length (the slowest warp sets the pace of
+// every phase).
+__device__ __forceinline__ int chunk_lane(int k, int t)
+{
+    return (k & 1) ? (t ^ 0xE0) : t;
+}
+
 // The solve of one system by blocks bid = 0..nb-1 of the launch (all of the
 // launch for a single system; a share of it in a batch).  Expects r4 = (r, D^-1)
 // with r = b - A x, p4 = q4 = d4 = 0 and the scalars, from the set-up kernel.
-// Slot of this thread in the block's k-th window.  The chunks of a window
-// hold rows of decreasing length; warp c takes chunk c of even windows and
-// chunk 7 - c of odd ones, so a warp's rows over two windows have about
-// equal total length (the slowest warp sets the pace of every phase).
-__device__ __forceinline__ int chunk_lane(int k)
-{
-    return (k & 1) ? (int)(threadIdx.x ^ 0xE0u) : (int)threadIdx.x;
-}
-
+// A block of 256 G threads is G window groups of 256; group g takes the
+// block's windows wb + g, wb + g + G, ... (one row per thread and window).
 template <int KB, bool PIPE>
 __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
                                                  PShared& sh)
@@ -274,6 +277,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     const int nwin = P.nslots / 256;
     const int wb = (int)((long long)bid * nwin / nb);
     const int we = (int)((long long)(bid + 1) * nwin / nb);
+    const int G = blockDim.x >> 8;                              // window groups
+    const int t = threadIdx.x & 255, wg = wb + (threadIdx.x >> 8);   // lane in window, first window
     const int np = P.npad;
     const float alpha_e = (float)P.alpha;
 
@@ -301,14 +306,14 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         const float betaf = sh.beta_f;
         // the row and entry range of the next window are loaded while this one
         // is processed (they do not change during the solve)
-        int slot = wb * 256 + chunk_lane(0);
-        int row = wb < we ? B.slot_row[slot] : -1;
-        int e0 = wb < we ? B.chunk_off[slot >> 5] + (slot & 31) : 0;
-        int e1 = wb < we ? B.chunk_off[(slot >> 5) + 1] : 0;
-        for (int w = wb; w < we; ++w) {
+        int slot = wg * 256 + chunk_lane(0, t);
+        int row = wg < we ? B.slot_row[slot] : -1;
+        int e0 = wg < we ? B.chunk_off[slot >> 5] + (slot & 31) : 0;
+        int e1 = wg < we ? B.chunk_off[(slot >> 5) + 1] : 0;
+        for (int w = wg, k = 0; w < we; w += G, ++k) {
             int nrow = -1, ne0 = 0, ne1 = 0;
-            if (w + 1 < we) {
-                const int ns = (w + 1) * 256 + chunk_lane(w + 1 - wb);
+            if (w + G < we) {
+                const int ns = (w + G) * 256 + chunk_lane(k + 1, t);
                 nrow = B.slot_row[ns];
                 ne0 = B.chunk_off[ns >> 5] + (ns & 31);
                 ne1 = B.chunk_off[(ns >> 5) + 1];
@@ -364,8 +369,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         // ---- update of d and r (own rows); r.r and r.D^-1 r
         const float af = sh.alpha_f;
         dfloat rr{0.f, 0.f}, rz{0.f, 0.f};
-        for (int w = wb; w < we; ++w) {
-            const int i = w * 256 + threadIdx.x;
+        for (int w = wg; w < we; w += G) {
+            const int i = w * 256 + t;
             if (i < P.n) {
                 const float4 p = B.p4[i], q = B.q4[i];
                 float4 d = B.d4[i], r = B.r4[i];
@@ -405,8 +410,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         if (sh.action == 0) continue;
 
         // ---- residual replacement: x += d (own rows), then r = b - A x in FP64
-        for (int w = wb; w < we; ++w) {
-            const int i = w * 256 + threadIdx.x;
+        for (int w = wg; w < we; w += G) {
+            const int i = w * 256 + t;
             if (i < P.n) {
                 const float4 d = B.d4[i];
                 B.x[i] += (double)d.x;
@@ -417,8 +422,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         }
         if (!grid_sync(st, gen, sh, nb)) break;
         double trr = 0.0, trz = 0.0;
-        for (int w = wb; w < we; ++w) {
-            const int slot = w * 256 + chunk_lane(w - wb);
+        for (int w = wg, k = 0; w < we; w += G, ++k) {
+            const int slot = w * 256 + chunk_lane(k, t);
             const int row = B.slot_row[slot];
             if (row >= 0) {
                 const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
@@ -489,8 +494,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 // at 65536 / (256 MINB)), with or without requesting the next batch's
 // columns during the current gathers (PIPE).  Chosen per system by the
 // autotuner.
-template <int KB, int MINB, bool PIPE>
-__global__ void __launch_bounds__(kPBlock, MINB) k32_cg_persistent(KParams P, DevBuffers B)
+template <int KB, int MINB, bool PIPE, int BS>
+__global__ void __launch_bounds__(BS, MINB) k32_cg_persistent(KParams P, DevBuffers B)
 {
     __shared__ PShared sh;
     persistent_solve<KB, PIPE>(P, B, blockIdx.x, gridDim.x, sh);
@@ -520,18 +525,19 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
 
 namespace {
 struct PCfg {
-    int kb, minb, pipe;
+    int kb, minb, pipe, bs;
     const void* fn;
     int occ;
 };
-PCfg g_pcfg[kPersistentConfigs] = {
-    {6, 4, 0, (const void*)k32_cg_persistent<6, 4, false>, 0},
-    {8, 4, 0, (const void*)k32_cg_persistent<8, 4, false>, 0},
-    {4, 4, 0, (const void*)k32_cg_persistent<4, 4, false>, 0},
-    {4, 4, 1, (const void*)k32_cg_persistent<4, 4, true>, 0},
-    {5, 4, 1, (const void*)k32_cg_persistent<5, 4, true>, 0},
-    {6, 3, 1, (const void*)k32_cg_persistent<6, 3, true>, 0},
-    {8, 3, 1, (const void*)k32_cg_persistent<8, 3, true>, 0},
+PCfg g_pcfg[kPersistentConfigs] = {   // entry 0: the default without autotuning
+    {6, 1, 0, 1024, (const void*)k32_cg_persistent<6, 1, false, 1024>, 0},
+    {8, 1, 0, 1024, (const void*)k32_cg_persistent<8, 1, false, 1024>, 0},
+    {6, 4, 0, 256, (const void*)k32_cg_persistent<6, 4, false, 256>, 0},
+    {8, 4, 0, 256, (const void*)k32_cg_persistent<8, 4, false, 256>, 0},
+    {4, 4, 0, 256, (const void*)k32_cg_persistent<4, 4, false, 256>, 0},
+    {4, 4, 1, 256, (const void*)k32_cg_persistent<4, 4, true, 256>, 0},
+    {5, 4, 1, 256, (const void*)k32_cg_persistent<5, 4, true, 256>, 0},
+    {6, 3, 1, 256, (const void*)k32_cg_persistent<6, 3, true, 256>, 0},
 };
 int g_pocc_batch = 0;
 std::once_flag g_pocc_once;
@@ -539,7 +545,7 @@ void pocc_init()
 {
     std::call_once(g_pocc_once, [] {
         for (auto& c : g_pcfg)
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, kPBlock, 0) != cudaSuccess) c.occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, c.bs, 0) != cudaSuccess) c.occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc_batch, k32_cg_persistent_batch, kPBlock, 0) !=
             cudaSuccess)
             g_pocc_batch = 0;
@@ -576,18 +582,21 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
     return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
 }
 
-void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined)
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads)
 {
     const PCfg& c = g_pcfg[(k >= 0 && k < kPersistentConfigs) ? k : 0];
     *gathers = c.kb;
     *blocks_per_sm = c.minb;
     *pipelined = c.pipe;
+    *block_threads = c.bs;
 }
 
 int cg_persistent_grid(const KParams& P, Launch L)
 {
     pocc_init();
-    long long g = std::min<long long>((long long)L.num_sms * cfg_of(P).occ, P.nslots / 256);
+    const PCfg& c = cfg_of(P);
+    const long long groups = c.bs / 256;   // windows a block processes at once
+    long long g = std::min<long long>((long long)L.num_sms * c.occ, (P.nslots / 256 + groups - 1) / groups);
     if (g > kMaxPartials) g = kMaxPartials;
     return (int)g;
 }
@@ -598,7 +607,7 @@ cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
     if (g < 1) return cudaErrorCooperativeLaunchTooLarge;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g);
-    cfg.blockDim = dim3(kPBlock);
+    cfg.blockDim = dim3((unsigned)cfg_of(P).bs);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];

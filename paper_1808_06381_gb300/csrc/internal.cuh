@@ -44,7 +44,7 @@ struct KParams {
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
 };
 
-constexpr int kPersistentConfigs = 7;
+constexpr int kPersistentConfigs = 8;
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {
@@ -541,8 +541,9 @@ void cg_prepare();   // resident-block counts of the solver kernels (once per pr
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
 int cg_persistent_grid(const KParams& P, Launch L);
 // Tile configuration k of the persistent solver: gathers in flight, blocks per
-// SM, next batch requested during the current gathers (1) or not (0).
-void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined);
+// SM, next batch requested during the current gathers (1) or not (0), threads
+// per block (256 G: G windows at a time).
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads);
 // A batch of systems in one cooperative launch: blocks [blk_off[k], blk_off[k+1]) solve system k.
 int cg_persistent_batch_capacity(Launch L);
 cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,

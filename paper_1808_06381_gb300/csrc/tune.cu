@@ -1,5 +1,6 @@
 // sp_autotune: choice of the persistent solver's tile configuration for one
-// simulation by timing (all configurations compute bit-identical results).
+// simulation by timing (all configurations run the same iteration; only the
+// grouping of the dot products' partial sums, hence their rounding, differs).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,7 +66,7 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
         s->kp.pcfg = cfg;
         free_graphs(s);   // captured graphs hold the previous configuration's kernel
         out.config = cfg;
-        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined);
+        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads);
         if (info) *info = out;
         return SP_OK;
     };

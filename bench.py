@@ -142,7 +142,7 @@ class ClockSampler:
 # persistent solve from one ncu capture of this command's kernel, keyed by workload
 # and tile configuration (gathers in flight, blocks per SM, pipelined); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 6, 4, False, 256): 460.7e6}
+PROFILED_TRAFFIC = {("mixed-n262144", 6, 1, False, 1024): 405.4e6}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:

@@ -140,16 +140,28 @@ class ClockSampler:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # persistent solve from one ncu capture of this command's kernel, keyed by workload
-# and tile configuration (gathers in flight, blocks per SM, pipelined); any other
+# and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
+# block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 6, 1, False, 1024): 405.4e6}
+PROFILED_TRAFFIC = {("mixed-n262144", 6, 1, False, 1024, False): 405.4e6}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
     if not tune:
         return None
     return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"],
-                                 tune["pipelined"], tune["block_threads"]))
+                                 tune["pipelined"], tune["block_threads"], tune.get("resident", False)))
+
+
+def solver_kernel_name(tune) -> str:
+    """Name of the persistent solver kernel a tile configuration launches."""
+    if tune and tune.get("resident"):
+        bt = tune["block_threads"]
+        return f"k32_cg_resident<{bt},{2048 // bt}>"
+    if tune:
+        return (f"k32_cg_persistent<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])},"
+                f"{tune['block_threads']}>")
+    return "k32_cg_persistent"
 
 
 def spmv_algorithmic_bytes(n: int, nnz: int, precision: str) -> float:
@@ -361,10 +373,7 @@ def main():
     if prof["persistent_ms"] > 0:
         pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
         pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
-        kname = "k32_cg_persistent"
-        if tune:
-            kname += (f"<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])},"
-                      f"{tune['block_threads']}>")
+        kname = solver_kernel_name(tune)
         persistent = {"kernel": kname, "bound": "hbm", "achieved": pach, "peak": peak,
                       "unit": "GB/s", "frac": pach / peak, "traffic": profiled_traffic(workload.name, tune),
                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",

@@ -92,6 +92,8 @@ typedef struct sp_solve_info {
     int32_t iterations;   /* CG iterations of this solve */
     double residual;      /* final true relative residual ||b - A v|| / ||b|| (FP64) */
     double bnorm;         /* ||b||_2 */
+    int32_t offchip_blocks; /* on-chip solver configuration: blocks whose rows and entries did not
+                               fit on their SM and were solved with global gathers (0 otherwise) */
 } sp_solve_info;
 
 typedef struct sp_step_info {
@@ -212,6 +214,11 @@ int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
  * per-row arithmetic; the grid-wide dot products are summed per block, so a
  * configuration with another block count rounds them differently (results
  * agree to about 1e-13 relative), and each configuration is deterministic.
+ * One configuration (resident = 1) keeps each block's rows on its SM for the
+ * whole solve: their solver vectors in registers, their z = D^-1 r and the
+ * matrix entries between two of them in shared memory, so that only entries
+ * to other blocks' rows are gathered from global memory; it serves systems of
+ * at most 2048 rows per SM and is not timed (ms 0) for larger ones.
  * sp_autotune builds the pair list
  * and the system for the current positions, times `trials` solves from a
  * zero start with every configuration on the simulation's stream, keeps the
@@ -222,7 +229,7 @@ int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
  * choices are appended (one line per key).  For SP_PREC_FP64, or with
  * trials < 1, nothing is timed and configuration 0 is kept.  Errors:
  * SP_ERR_INVALID_ARG (NULL sim), SP_ERR_CUDA, and those of the solve. */
-#define SP_TUNE_MAX_CONFIGS 8
+#define SP_TUNE_MAX_CONFIGS 12
 typedef struct sp_tune_info {
     int32_t config;              /* chosen configuration (index) */
     int32_t gathers_in_flight;   /* its gathers in flight per thread */
@@ -232,8 +239,16 @@ typedef struct sp_tune_info {
     double ms[SP_TUNE_MAX_CONFIGS]; /* best time of one solve per configuration (0: not timed) */
     int32_t pipelined;           /* 1: the next batch of columns is requested during the current gathers */
     int32_t block_threads;       /* threads per block (256 per window processed at once) */
+    int32_t resident;            /* 1: rows, their vectors and the entries between them kept on chip */
 } sp_tune_info;
 int sp_autotune(sp_sim* sim, int32_t trials, sp_tune_info* info);
+/* Select tile configuration `config` (0 .. num_configs - 1) of the persistent
+ * solver for this simulation without timing, e.g. one an earlier sp_autotune
+ * chose for the same system.  info (may be NULL) receives its description
+ * (ms all 0).  A configuration that cannot serve the system (the on-chip one
+ * beyond 2048 rows per SM) falls back to configuration 0 at each solve.
+ * Errors: SP_ERR_INVALID_ARG (NULL sim, config out of range). */
+int sp_set_solver_config(sp_sim* sim, int32_t config, sp_tune_info* info);
 
 /* ---- state access (test hooks and checkpointing) ---- */
 

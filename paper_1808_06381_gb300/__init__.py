@@ -52,7 +52,7 @@ class sp_params(ctypes.Structure):
 
 class sp_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("residual", ctypes.c_double),
-                ("bnorm", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32)]
 
 
 class sp_step_info(ctypes.Structure):
@@ -79,8 +79,8 @@ class sp_kernel_profile(ctypes.Structure):
 
 class sp_tune_info(ctypes.Structure):
     _fields_ = [("config", ctypes.c_int32), ("gathers_in_flight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 8),
-                ("pipelined", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 12),
+                ("pipelined", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("resident", ctypes.c_int32)]
 
 
 def declared_symbols() -> list:
@@ -275,7 +275,8 @@ class Simulation:
         rc = load().sp_solve_velocities(self._h, v0_dev_ptr, ctypes.byref(info))
         if raise_on_error:
             self._c(rc)
-        return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm}
+        return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
+                "offchip_blocks": info.offchip_blocks}
 
     def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
         info = sp_step_info()
@@ -299,13 +300,22 @@ class Simulation:
         self._c(load().sp_profile_step(self._h, ctypes.byref(prof)))
         return {name: getattr(prof, name) for name, _ in sp_kernel_profile._fields_}
 
+    def set_solver_config(self, config: int) -> dict:
+        """Select a tile configuration of the persistent solver without timing (sp_set_solver_config)."""
+        info = sp_tune_info()
+        self._c(load().sp_set_solver_config(self._h, int(config), ctypes.byref(info)))
+        return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
+                "blocks_per_sm": info.blocks_per_sm, "pipelined": bool(info.pipelined),
+                "block_threads": info.block_threads, "resident": bool(info.resident),
+                "num_configs": info.num_configs}
+
     def autotune(self, trials: int = 3) -> dict:
         """Pick the persistent solver's fastest tile configuration for this system (sp_autotune)."""
         info = sp_tune_info()
         self._c(load().sp_autotune(self._h, int(trials), ctypes.byref(info)))
         return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
                 "blocks_per_sm": info.blocks_per_sm, "pipelined": bool(info.pipelined),
-                "block_threads": info.block_threads,
+                "block_threads": info.block_threads, "resident": bool(info.resident),
                 "from_cache": bool(info.from_cache),
                 "ms": [info.ms[k] for k in range(info.num_configs)]}
 

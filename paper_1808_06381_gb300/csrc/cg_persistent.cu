@@ -489,6 +489,488 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     }
 }
 
+// ------------------------------------------------------------ on-chip solve
+// The same iteration for systems whose rows fit on the chip: with at most
+// kResWindows windows per block, a thread of a block of BS owns at most RPT
+// rows (BS RPT = 2048) and keeps their solver vectors (r, D^-1, p, q, d) in
+// registers for the whole solve;
+// the block keeps z = D^-1 r of its rows and the matrix entries that couple
+// two of its rows (16-bit local column, FP32 weight) in shared memory.  Only
+// the entries that couple its rows to other blocks' rows ("halo" entries,
+// about a sixth with the tiled Morton row order) and those rows' r are read
+// from global memory in the iteration.  A block's windows hold one contiguous
+// range of rows, so an entry is local when its column lies in that range.
+// The set-up at the start of the solve sorts each row's entries into the two
+// lists; a chunk whose local entries find no room in shared memory keeps all
+// its entries in the halo list (slower, same result).
+constexpr int kResWindows = 8;                       // 2048 rows per block
+constexpr int kResChunks = kResWindows * 8;
+constexpr int kResHalo = 4;                          // halo gathers in flight per thread
+
+struct RShared {
+    int loff[kResChunks];    // shared-memory offset of the chunk's local entries
+    int nloc[kResChunks];    // local entries per row of the chunk (its longest row's count)
+    int nhalo[kResChunks];   // halo entries per row of the chunk
+    int hoff[kResChunks];    // global offset of the chunk's halo list
+    int mode;                // 0: on chip; 1: the block's entries did not fit, all gathers global
+};
+
+__device__ __forceinline__ void res_halo_batch(const DevBuffers& B, int hb, int kb, int nh, float& s0, float& s1,
+                                               float& s2)
+{
+    int j[kResHalo];
+    float w[kResHalo];
+#pragma unroll
+    for (int u = 0; u < kResHalo; ++u) {
+        j[u] = 0;
+        w[u] = 0.f;
+        if (kb + u < nh) {
+            j[u] = ld_stream(B.hcol + hb + 32 * (kb + u));
+            w[u] = ld_stream(B.hval + hb + 32 * (kb + u));
+        }
+    }
+    float4 g[kResHalo];
+#pragma unroll
+    for (int u = 0; u < kResHalo; ++u) {
+        g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (w[u] != 0.f) g[u] = B.r4[j[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < kResHalo; ++u) {
+        const float ww = w[u] * g[u].w;
+        s0 = fmaf(ww, g[u].x, s0);
+        s1 = fmaf(ww, g[u].y, s1);
+        s2 = fmaf(ww, g[u].z, s2);
+    }
+}
+
+// Thread t owns the rows at positions u BS + t (even u) and u BS + BS - 1 - t
+// (odd u), u < RPT, below R, of the block's R rows sorted by halo count,
+// then local count, both descending: a warp's 32 rows have about equal
+// counts (little padding in either list), and each thread pairs heavier rows
+// with lighter ones.
+template <int BS, int RPT>
+__device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffers& B, int bid, int nb, PShared& sh,
+                                               RShared& rs, float4* dyn, int smem_bytes)
+{
+    DevState* st = B.st;
+    if (threadIdx.x == 0) sh.flag = 0;
+    __syncthreads();
+    if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
+    unsigned int gen = 0u;
+    if (threadIdx.x == 0) gen = *(volatile unsigned int*)&st->bar_gen;
+
+    const int nwin = P.nslots / 256;
+    const int wb = (int)((long long)bid * nwin / nb);
+    const int we = (int)((long long)(bid + 1) * nwin / nb);
+    const int nwmax = (nwin + nb - 1) / nb;
+    const int rb = wb * 256, re = min(we * 256, P.n);   // the block's rows
+    const int R = re - rb;
+    float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows
+    const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 6;
+    float* sval = reinterpret_cast<float*>(dyn + nwmax * 256);
+    unsigned short* scol = reinterpret_cast<unsigned short*>(sval + cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int np = P.npad;
+    const float alpha_e = (float)P.alpha;
+
+    // ---- set-up 1: local and halo entry counts of every row of the block
+    // (read in slot order, so that a warp's loads are coalesced), sort keys
+    // (halo desc, local desc, row asc) sorted by a bitonic network; keys,
+    // counts and the inverse permutation borrow the space of zbuf (14 bytes
+    // per row of its 16)
+    const int t = threadIdx.x & 255, g = threadIdx.x >> 8;
+    int npow = 1;
+    while (npow < R) npow <<= 1;
+    unsigned int* skey = reinterpret_cast<unsigned int*>(zbuf);
+    unsigned int* scnt = skey + npow;
+    unsigned short* sinv = reinterpret_cast<unsigned short*>(scnt + R);
+    for (int i = R + (int)threadIdx.x; i < npow; i += BS) skey[i] = 0xffffffffu;
+    for (int w = wb + g; w < we; w += BS / 256) {
+        const int slot = w * 256 + t;
+        const int row = B.slot_row[slot];
+        if (row < 0) continue;
+        const int c = slot >> 5, e1 = B.chunk_off[c + 1];
+        int nl = 0, nh = 0;
+        for (int e = B.chunk_off[c] + (slot & 31); e < e1; e += 32) {
+            if (B.val32[e] != 0.f) {
+                const int j = B.col[e];
+                if (j >= rb && j < re) ++nl; else ++nh;
+            }
+        }
+        const int i = row - rb;
+        scnt[i] = (unsigned)nl | ((unsigned)nh << 16);
+        skey[i] = ((unsigned)(31 - min(nh, 31)) << 17) | ((unsigned)(63 - min(nl, 63)) << 11) | (unsigned)i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= npow; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int h = threadIdx.x; h < npow / 2; h += blockDim.x) {
+                const int i = 2 * h - (h & (j - 1)), l = i + j;
+                const unsigned int a = skey[i], b = skey[l];
+                if ((a > b) == ((i & k) == 0)) {
+                    skey[i] = b;
+                    skey[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int pos = threadIdx.x; pos < R; pos += BS) sinv[skey[pos] & 2047u] = (unsigned short)pos;
+
+    // ---- set-up 2: the own rows, the chunk maxima, the offsets of both lists
+    static_assert(BS * RPT == kResWindows * 256 && BS % 256 == 0, "a block holds 2048 rows");
+    int row[RPT];
+    {
+        int cl[RPT], ch[RPT];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int pos = u * BS + ((u & 1) ? BS - 1 - (int)threadIdx.x : (int)threadIdx.x);
+            const bool own = pos < R;
+            row[u] = -1;
+            cl[u] = ch[u] = 0;
+            if (own) {
+                const int i = (int)(skey[pos] & 2047u);
+                row[u] = rb + i;
+                cl[u] = (int)(scnt[i] & 0xffffu);
+                ch[u] = (int)(scnt[i] >> 16);
+            }
+            const int ml = __reduce_max_sync(0xffffffffu, cl[u]);
+            const int mh = __reduce_max_sync(0xffffffffu, ch[u]);
+            if (lane == 0) {
+                rs.nloc[u * (BS / 32) + warp] = ml;
+                rs.nhalo[u * (BS / 32) + warp] = mh;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int hbase = B.chunk_off[wb * 8], hcap = B.chunk_off[we * 8] - hbase;
+        int lo = 0, ho = 0;
+        for (int c = 0; c < kResChunks; ++c) {
+            rs.loff[c] = lo;
+            rs.hoff[c] = hbase + ho;
+            lo += 32 * rs.nloc[c];
+            ho += 32 * rs.nhalo[c];
+        }
+        rs.mode = (lo <= cap && ho <= hcap) ? 0 : 1;
+        if (rs.mode) atomicAdd(&st->res_offchip, 1);
+    }
+    __syncthreads();
+    const bool onchip = rs.mode == 0;
+    if (!onchip) {   // the sliced layout's own assignment, every gather global
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int w = wb + g + (BS / 256) * u;
+            row[u] = w < we ? B.slot_row[w * 256 + chunk_lane(u, t)] : -1;
+        }
+    }
+
+    // ---- set-up 3: place the entries (read in slot order; each row's lists
+    // go to the chunk and lane of the thread that owns the row)
+    if (onchip) {
+        for (int w = wb + g; w < we; w += BS / 256) {
+            const int slot = w * 256 + t;
+            const int row = B.slot_row[slot];
+            if (row < 0) continue;
+            const int pos = sinv[row - rb];
+            const int u = pos / BS, rem = pos - u * BS;
+            const int owner = (u & 1) ? BS - 1 - rem : rem;
+            const int c = u * (BS / 32) + (owner >> 5);
+            const int lo = rs.loff[c] + (owner & 31), nl = rs.nloc[c], nh = rs.nhalo[c];
+            const int hb = rs.hoff[c] + (owner & 31);
+            const int e1 = B.chunk_off[(slot >> 5) + 1];
+            int kl = 0, kh = 0;
+            for (int e = B.chunk_off[slot >> 5] + (slot & 31); e < e1; e += 32) {
+                const float v = B.val32[e];
+                if (v != 0.f) {
+                    const int j = B.col[e];
+                    if (j >= rb && j < re) {
+                        scol[lo + 32 * kl] = (unsigned short)(j - rb);
+                        sval[lo + 32 * kl] = v;
+                        ++kl;
+                    } else {
+                        B.hcol[hb + 32 * kh] = j;
+                        B.hval[hb + 32 * kh] = v;
+                        ++kh;
+                    }
+                }
+            }
+            for (; kl < nl; ++kl) {
+                scol[lo + 32 * kl] = 0;
+                sval[lo + 32 * kl] = 0.f;
+            }
+            for (; kh < nh; ++kh) {
+                B.hcol[hb + 32 * kh] = row;
+                B.hval[hb + 32 * kh] = 0.f;
+            }
+        }
+    }
+    __syncthreads();   // sinv (in zbuf) is read until here
+
+    // ---- load r and D^-1 of the own rows
+    float r[RPT][3], dv[RPT], p[RPT][3], q[RPT][3], d[RPT][3];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        dv[u] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[u][c] = p[u][c] = q[u][c] = d[u][c] = 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        if (row[u] < 0) continue;
+        const float4 r4 = B.r4[row[u]];
+        r[u][0] = r4.x;
+        r[u][1] = r4.y;
+        r[u][2] = r4.z;
+        dv[u] = r4.w;
+        zbuf[row[u] - rb] = make_float4(r4.w * r4.x, r4.w * r4.y, r4.w * r4.z, 0.f);
+    }
+    if (threadIdx.x == 0) {
+        sh.rho = st->rho;
+        sh.rr_restart = st->rr_restart;
+        sh.bnorm2 = st->bnorm2;
+        sh.last_res = st->last_res;
+        sh.iter = 0;
+        sh.restarts = 0;
+        sh.status = SP_OK;
+        sh.beta_f = 0.f;
+    }
+    __syncthreads();
+
+    for (;;) {
+        // ---- SpMV with the fused direction update; p.q
+        dfloat pq{0.f, 0.f};
+        const float betaf = sh.beta_f;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (row[u] < 0) continue;
+            const float di = __ldg(B.diag32 + row[u]);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            if (onchip) {
+                const int c = u * (BS / 32) + warp;
+                const int lo = rs.loff[c] + lane, nl = rs.nloc[c], nh = rs.nhalo[c];
+                const int hb = rs.hoff[c] + lane;
+                // the first halo batch is requested before the local sum, so
+                // its latency runs under the shared-memory work
+                int j[kResHalo];
+                float w[kResHalo];
+#pragma unroll
+                for (int k = 0; k < kResHalo; ++k) {
+                    j[k] = 0;
+                    w[k] = 0.f;
+                    if (k < nh) {
+                        j[k] = ld_stream(B.hcol + hb + 32 * k);
+                        w[k] = ld_stream(B.hval + hb + 32 * k);
+                    }
+                }
+                float4 gh[kResHalo];
+#pragma unroll
+                for (int k = 0; k < kResHalo; ++k) {
+                    gh[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (w[k] != 0.f) gh[k] = B.r4[j[k]];
+                }
+                for (int k = 0; k < nl; ++k) {
+                    const float wl = sval[lo + 32 * k];
+                    const float4 zj = zbuf[scol[lo + 32 * k]];
+                    s0 = fmaf(wl, zj.x, s0);
+                    s1 = fmaf(wl, zj.y, s1);
+                    s2 = fmaf(wl, zj.z, s2);
+                }
+#pragma unroll
+                for (int k = 0; k < kResHalo; ++k) {
+                    const float ww = w[k] * gh[k].w;
+                    s0 = fmaf(ww, gh[k].x, s0);
+                    s1 = fmaf(ww, gh[k].y, s1);
+                    s2 = fmaf(ww, gh[k].z, s2);
+                }
+                for (int kb = kResHalo; kb < nh; kb += kResHalo) res_halo_batch(B, hb, kb, nh, s0, s1, s2);
+            } else {
+                const int slot = B.row_slot[row[u]];
+                p_row_sum32<2, false>(B.col, B.val32, B.r4, B.chunk_off[slot >> 5] + (slot & 31),
+                                      B.chunk_off[(slot >> 5) + 1], s0, s1, s2);
+            }
+            const float z0 = dv[u] * r[u][0], z1 = dv[u] * r[u][1], z2 = dv[u] * r[u][2];
+            float q0 = fmaf(di, z0, -alpha_e * s0);
+            float q1 = fmaf(di, z1, -alpha_e * s1);
+            float q2 = fmaf(di, z2, -alpha_e * s2);
+            if (betaf != 0.f) {
+                q0 = fmaf(betaf, q[u][0], q0);
+                q1 = fmaf(betaf, q[u][1], q1);
+                q2 = fmaf(betaf, q[u][2], q2);
+                p[u][0] = fmaf(betaf, p[u][0], z0);
+                p[u][1] = fmaf(betaf, p[u][1], z1);
+                p[u][2] = fmaf(betaf, p[u][2], z2);
+            } else {
+                p[u][0] = z0;
+                p[u][1] = z1;
+                p[u][2] = z2;
+            }
+            q[u][0] = q0;
+            q[u][1] = q1;
+            q[u][2] = q2;
+            pq = df_add(pq, p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2]);
+        }
+        {
+            const dfloat v[1] = {pq};
+            double tot[1];
+            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                sh.action = 0;
+                if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.alpha_f = (float)(sh.rho / tot[0]);
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+
+        // ---- update of d and r; r.r and r.D^-1 r; z of the own rows published
+        const float af = sh.alpha_f;
+        dfloat rr{0.f, 0.f}, rz{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (row[u] < 0) continue;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                d[u][c] = fmaf(af, p[u][c], d[u][c]);
+                r[u][c] = fmaf(-af, q[u][c], r[u][c]);
+            }
+            const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
+            rr = df_add(rr, rsq);
+            rz = df_add(rz, dv[u] * rsq);
+            B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
+            zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+        }
+        {
+            const dfloat v[2] = {rr, rz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                ++sh.iter;
+                sh.action = 0;
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.beta_f = (float)(tot[1] / sh.rho);
+                    sh.rho = tot[1];
+                    const double target = fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
+                    if (tot[0] <= target || sh.iter >= P.max_iter) sh.action = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+        if (sh.action == 0) continue;
+
+        // ---- residual replacement: x += d, then r = b - A x in FP64 (the
+        // FP64 matrix in its sliced layout, x of other blocks' rows gathered)
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (row[u] < 0) continue;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                B.x[c * np + row[u]] += (double)d[u][c];
+                d[u][c] = 0.f;
+            }
+        }
+        if (!grid_sync(st, gen, sh, nb)) break;
+        // in slot order (coalesced); r goes to the owners through zbuf and is
+        // published for the other blocks' halo gathers before the barrier
+        double trr = 0.0, trz = 0.0;
+        for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
+            const int slot = w * 256 + chunk_lane(k, t);
+            const int rw = B.slot_row[slot];
+            if (rw < 0) continue;
+            double sx[3];
+            p_row_sum64(B.col, B.val, B.x, np, B.chunk_off[slot >> 5] + (slot & 31), B.chunk_off[(slot >> 5) + 1],
+                        sx[0], sx[1], sx[2]);
+            const double dd = B.diag[rw];
+            const float di = B.dinv32[rw];
+            double rk[3], rsq = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int kk = a * np + rw;
+                rk[a] = B.b[kk] - (dd * B.x[kk] - P.alpha * sx[a]);
+                rsq += rk[a] * rk[a];
+            }
+            trr += rsq;
+            trz += (double)di * rsq;
+            const float4 rf = make_float4((float)rk[0], (float)rk[1], (float)rk[2], di);
+            B.r4[rw] = rf;
+            zbuf[rw - rb] = rf;
+        }
+        {
+            const double v[2] = {trr, trz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                sh.last_res = sqrt(tot[0] / sh.bnorm2);
+                if (bid == 0) st->true_checks += 1;
+                sh.action = 0;
+                if (!isfinite(tot[0])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else if (tot[0] <= P.tol2 * sh.bnorm2) {
+                    sh.action = 2;   // converged
+                } else if (sh.iter >= P.max_iter || sh.restarts >= kMaxCgRestarts + 8) {
+                    sh.status = SP_ERR_NOT_CONVERGED;
+                    sh.action = 2;
+                } else {
+                    ++sh.restarts;
+                    sh.rho = tot[1];
+                    sh.beta_f = 0.f;
+                    sh.rr_restart = tot[0];
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) break;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (row[u] < 0) continue;
+            const float4 rf = zbuf[row[u] - rb];
+            r[u][0] = rf.x;
+            r[u][1] = rf.y;
+            r[u][2] = rf.z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (row[u] < 0) continue;
+            zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+        }
+        __syncthreads();
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        st->iter = sh.iter;
+        st->restarts = sh.restarts;
+        st->last_res = sh.last_res;
+        st->done = 1;
+        if (st->error == 0 && sh.status != SP_OK) {
+            st->status = sh.status;
+            st->error = sh.status;
+        } else if (st->error != 0) {
+            st->status = st->error;
+        } else {
+            st->status = SP_OK;
+        }
+    }
+}
+
+template <int BS, int RPT>
+__global__ void __launch_bounds__(BS, 1) k32_cg_resident(KParams P, DevBuffers B, int smem_bytes)
+{
+    extern __shared__ float4 res_dyn[];
+    __shared__ PShared sh;
+    __shared__ RShared rs;
+    resident_solve<BS, RPT>(P, B, blockIdx.x, gridDim.x, sh, rs, res_dyn, smem_bytes);
+}
+
 // Tile configurations of the single-system kernel: gathers in flight per
 // thread (KB) against resident blocks per SM (MINB, which caps the registers
 // at 65536 / (256 MINB)), with or without requesting the next batch's
@@ -524,37 +1006,72 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
 }
 
 namespace {
+// kResSmemBytes (190 KB) leaves a 196 KB carve-out's L1 for the halo gathers
+
 struct PCfg {
     int kb, minb, pipe, bs;
     const void* fn;
     int occ;
+    int resident;   // 1: the on-chip solve (k32_cg_resident), dynamic shared memory kResSmemBytes
 };
 PCfg g_pcfg[kPersistentConfigs] = {   // entry 0: the default without autotuning
-    {6, 1, 0, 1024, (const void*)k32_cg_persistent<6, 1, false, 1024>, 0},
-    {8, 1, 0, 1024, (const void*)k32_cg_persistent<8, 1, false, 1024>, 0},
-    {6, 4, 0, 256, (const void*)k32_cg_persistent<6, 4, false, 256>, 0},
-    {8, 4, 0, 256, (const void*)k32_cg_persistent<8, 4, false, 256>, 0},
-    {4, 4, 0, 256, (const void*)k32_cg_persistent<4, 4, false, 256>, 0},
-    {4, 4, 1, 256, (const void*)k32_cg_persistent<4, 4, true, 256>, 0},
-    {5, 4, 1, 256, (const void*)k32_cg_persistent<5, 4, true, 256>, 0},
-    {6, 3, 1, 256, (const void*)k32_cg_persistent<6, 3, true, 256>, 0},
+    {6, 1, 0, 1024, (const void*)k32_cg_persistent<6, 1, false, 1024>, 0, 0},
+    {8, 1, 0, 1024, (const void*)k32_cg_persistent<8, 1, false, 1024>, 0, 0},
+    {6, 4, 0, 256, (const void*)k32_cg_persistent<6, 4, false, 256>, 0, 0},
+    {8, 4, 0, 256, (const void*)k32_cg_persistent<8, 4, false, 256>, 0, 0},
+    {4, 4, 0, 256, (const void*)k32_cg_persistent<4, 4, false, 256>, 0, 0},
+    {4, 4, 1, 256, (const void*)k32_cg_persistent<4, 4, true, 256>, 0, 0},
+    {5, 4, 1, 256, (const void*)k32_cg_persistent<5, 4, true, 256>, 0, 0},
+    {6, 3, 1, 256, (const void*)k32_cg_persistent<6, 3, true, 256>, 0, 0},
+    {kResHalo, 1, 0, 1024, (const void*)k32_cg_resident<1024, 2>, 0, 1},
+    {kResHalo, 1, 0, 512, (const void*)k32_cg_resident<512, 4>, 0, 1},
 };
 int g_pocc_batch = 0;
 std::once_flag g_pocc_once;
 void pocc_init()
 {
     std::call_once(g_pocc_once, [] {
-        for (auto& c : g_pcfg)
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, c.bs, 0) != cudaSuccess) c.occ = 0;
+        for (auto& c : g_pcfg) {
+            int smem = 0;
+            if (c.resident) {
+                smem = kResSmemBytes;
+                if (cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+                    c.occ = 0;
+                    continue;
+                }
+            }
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, c.bs, smem) != cudaSuccess) c.occ = 0;
+        }
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc_batch, k32_cg_persistent_batch, kPBlock, 0) !=
             cudaSuccess)
             g_pocc_batch = 0;
         cudaGetLastError();
     });
 }
-const PCfg& cfg_of(const KParams& P)
+
+long long grid_of(const PCfg& c, const KParams& P, Launch L)
 {
+    const long long groups = c.bs / 256;   // windows a block processes at once
+    long long g = std::min<long long>((long long)L.num_sms * c.occ, (P.nslots / 256 + groups - 1) / groups);
+    if (g > kMaxPartials) g = kMaxPartials;
+    return g;
+}
+
+// The on-chip solve needs its halo lists and at most kResWindows windows per block.
+bool resident_fits(const PCfg& c, const KParams& P, const DevBuffers& B, Launch L)
+{
+    if (!B.hcol || !B.hval) return false;
+    const long long g = grid_of(c, P, L);
+    return g >= 1 && (P.nslots / 256 + g - 1) / g <= kResWindows;
+}
+
+// The configuration a launch uses: the chosen one, or entry 0 where the
+// chosen one is the on-chip solve and the system does not fit it.
+const PCfg& cfg_of(const KParams& P, const DevBuffers& B, Launch L)
+{
+    pocc_init();
     const int k = (P.pcfg >= 0 && P.pcfg < kPersistentConfigs) ? P.pcfg : 0;
+    if (g_pcfg[k].resident && !resident_fits(g_pcfg[k], P, B, L)) return g_pcfg[0];
     return g_pcfg[k];
 }
 }  // namespace
@@ -582,41 +1099,47 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
     return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
 }
 
-void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads)
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads,
+                          int* resident)
 {
     const PCfg& c = g_pcfg[(k >= 0 && k < kPersistentConfigs) ? k : 0];
     *gathers = c.kb;
     *blocks_per_sm = c.minb;
     *pipelined = c.pipe;
     *block_threads = c.bs;
+    *resident = c.resident;
 }
 
-int cg_persistent_grid(const KParams& P, Launch L)
+bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L)
 {
     pocc_init();
-    const PCfg& c = cfg_of(P);
-    const long long groups = c.bs / 256;   // windows a block processes at once
-    long long g = std::min<long long>((long long)L.num_sms * c.occ, (P.nslots / 256 + groups - 1) / groups);
-    if (g > kMaxPartials) g = kMaxPartials;
-    return (int)g;
+    if (k < 0 || k >= kPersistentConfigs || g_pcfg[k].occ < 1) return false;
+    return !g_pcfg[k].resident || resident_fits(g_pcfg[k], P, B, L);
+}
+
+int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L)
+{
+    return (int)grid_of(cfg_of(P, B, L), P, L);
 }
 
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
 {
-    const int g = cg_persistent_grid(P, L);
+    const PCfg& c = cfg_of(P, B, L);
+    const int g = (int)grid_of(c, P, L);
     if (g < 1) return cudaErrorCooperativeLaunchTooLarge;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g);
-    cfg.blockDim = dim3((unsigned)cfg_of(P).bs);
-    cfg.dynamicSmemBytes = 0;
+    cfg.blockDim = dim3((unsigned)c.bs);
+    cfg.dynamicSmemBytes = c.resident ? kResSmemBytes : 0;
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void* args[] = {const_cast<KParams*>(&P), &B};
-    return cudaLaunchKernelExC(&cfg, cfg_of(P).fn, args);
+    int smem = std::min(std::max(P.res_smem, 0), kResSmemBytes);
+    void* args[] = {const_cast<KParams*>(&P), &B, &smem};
+    return cudaLaunchKernelExC(&cfg, c.fn, args);
 }
 
 }  // namespace ss

@@ -42,9 +42,11 @@ struct KParams {
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
+    int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
 };
 
-constexpr int kPersistentConfigs = 8;
+constexpr int kPersistentConfigs = 10;
+constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {
@@ -74,6 +76,7 @@ struct DevState {
     alignas(128) unsigned int bar_gen;
     int bar_err;
     long long noise_step;     // step whose normals noise3 holds (-1: none)
+    int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
 };
 
 // Device buffers of one simulation (all in the current cell order unless noted).
@@ -107,6 +110,8 @@ struct DevBuffers {
     unsigned char* img; // [nnz_cap] image of the partner: (a+2) | (m+1) << 3 | (c+1) << 5
     double* val;     // [nnz_cap] pair weights w_ij (A_ij = -alpha w_ij); padding 0
     float* val32;    // [nnz_cap] FP32 copy for the mixed solver
+    int* hcol;       // [nnz_cap] on-chip solve: each block's entries to other blocks' rows (mixed only)
+    float* hval;     // [nnz_cap] their weights
     double* diag;    // [n] A_ii
     double* dinv;    // [n] 1 / A_ii
     float* diag32;   // [n]
@@ -539,11 +544,15 @@ int cg_kernels_per_iteration(bool mixed);
 void cg_prepare();   // resident-block counts of the solver kernels (once per process)
 // cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
-int cg_persistent_grid(const KParams& P, Launch L);
+int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L);
 // Tile configuration k of the persistent solver: gathers in flight, blocks per
 // SM, next batch requested during the current gathers (1) or not (0), threads
-// per block (256 G: G windows at a time).
-void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads);
+// per block (256 G: G windows at a time), on-chip solve (1) or not (0).
+void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads,
+                          int* resident);
+// Whether configuration k can solve this system (the on-chip solve needs at
+// most 2048 rows per block and its halo lists).
+bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L);
 // A batch of systems in one cooperative launch: blocks [blk_off[k], blk_off[k+1]) solve system k.
 int cg_persistent_batch_capacity(Launch L);
 cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,

@@ -344,6 +344,7 @@ extern "C" int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, con
         info->iterations = h.iter;
         info->residual = h.last_res;
         info->bnorm = std::sqrt(h.bnorm2);
+        info->offchip_blocks = 0;
     }
     if (status != SP_OK) err = "sp_solve_csr_noalloc: solve failed";
     return finish(status, nullptr);

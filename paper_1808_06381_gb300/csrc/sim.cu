@@ -70,14 +70,22 @@ int alloc_pairs(sp_sim* s, long long cap)
     cudaFree(B.val);
     cudaFree(B.val32);
     cudaFree(B.img);
+    cudaFree(B.hcol);
+    cudaFree(B.hval);
     B.col = nullptr;
     B.val = nullptr;
     B.val32 = nullptr;
     B.img = nullptr;
+    B.hcol = nullptr;
+    B.hval = nullptr;
     SS_TRY(dev_alloc(s, &B.col, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val32, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.img, (size_t)cap));
+    if (mixed(s)) {   // halo lists of the on-chip solve
+        SS_TRY(dev_alloc(s, &B.hcol, (size_t)cap));
+        SS_TRY(dev_alloc(s, &B.hval, (size_t)cap));
+    }
     s->nnz_cap = cap;
     s->st_host->nnz_cap = cap;
     SS_CUDA(cudaMemcpyAsync(&B.st->nnz_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, s->stream));
@@ -115,6 +123,7 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.two_lambda2 = 2.0 * l2;
     k.w_scale = 256.0 / k.two_lambda2;
     k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
+    k.res_smem = kResSmemBytes;
     k.alpha = p.alpha;
     k.zeta = p.zeta;
     k.kappa = p.kappa;
@@ -474,7 +483,7 @@ int sp_sim_destroy(sp_sim* s)
     DevBuffers& B = s->B;
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
-                    B.chunk_off, B.col, B.img, B.val, B.val32, B.diag, B.partials_df,
+                    B.chunk_off, B.col, B.img, B.val, B.val32, B.hcol, B.hval, B.diag, B.partials_df,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
                     B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
@@ -550,6 +559,10 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     const int n = (int)p->n;
     const int npad = (n + 63) / 64 * 64;
     derive(*p, s->kp, npad);
+    // a smaller shared-memory budget for the on-chip solve (its entries then
+    // fit on fewer SMs): only to exercise the fallback of blocks that do not fit
+    if (const char* rsm = std::getenv("SHEARSIM_RESIDENT_SMEM"))
+        s->kp.res_smem = std::min(std::max(std::atoi(rsm), 0), kResSmemBytes);
     DevBuffers& B = s->B;
     const size_t v3 = 3 * (size_t)npad;
     int a = SP_OK;
@@ -706,6 +719,7 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
         info->iterations = h.iter;
         info->residual = h.last_res;
         info->bnorm = std::sqrt(h.bnorm2);
+        info->offchip_blocks = h.res_offchip;
     }
     SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
     if (h.error) {
@@ -837,7 +851,7 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
     if (rc == SP_OK && pers) {
         if (launch_cg32_persistent(P, B, L) != cudaSuccess) rc = SP_ERR_CUDA;
         if (rc == SP_OK) rc = mark(PERSIST);
-        out->persistent_blocks = cg_persistent_grid(P, L);
+        out->persistent_blocks = cg_persistent_grid(P, B, L);
     }
     for (int it = 0; rc == SP_OK && !pers && it < P.max_iter + kMaxCgRestarts + 8; ++it) {
         launch_cg_spmv(P, B, mx, L);

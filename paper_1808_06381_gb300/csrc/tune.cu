@@ -56,6 +56,23 @@ void cache_store(const std::string& path, const std::string& key, int cfg)
 
 }  // namespace
 
+extern "C" int sp_set_solver_config(sp_sim* s, int32_t config, sp_tune_info* info)
+{
+    if (!s || config < 0 || config >= std::min(kPersistentConfigs, SP_TUNE_MAX_CONFIGS)) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    s->kp.pcfg = config;
+    free_graphs(s);   // captured graphs hold the previous configuration's kernel
+    if (info) {
+        sp_tune_info out{};
+        out.config = config;
+        out.num_configs = std::min(kPersistentConfigs, SP_TUNE_MAX_CONFIGS);
+        cg_persistent_config(config, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads,
+                             &out.resident);
+        *info = out;
+    }
+    return SP_OK;
+}
+
 extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
 {
     if (!s) return SP_ERR_INVALID_ARG;
@@ -66,7 +83,8 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
         s->kp.pcfg = cfg;
         free_graphs(s);   // captured graphs hold the previous configuration's kernel
         out.config = cfg;
-        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads);
+        cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads,
+                             &out.resident);
         if (info) *info = out;
         return SP_OK;
     };
@@ -103,6 +121,7 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
     int best = prev;
     double best_ms = 0.0;
     for (int c = 0; rc == SP_OK && c < out.num_configs; ++c) {
+        if (!cg_persistent_usable(c, s->kp, s->B, launch_of(s, s->stream))) continue;   // ms[c] stays 0
         s->kp.pcfg = c;
         double cmin = 0.0;
         for (int t = 0; rc == SP_OK && t <= trials; ++t) {   // the first solve warms up

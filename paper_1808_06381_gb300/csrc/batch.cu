@@ -129,8 +129,7 @@ int capture(sp_batch* b)
         cudaStream_t st = b->branch[k % S];
         launches += enqueue_build(s, st);
         launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, true, launch_of(s, st));
-        launch_cg_init(s->kp, s->B, s->p.warm_start == SP_WARM_PREV, true, launch_of(s, st));
-        launches += 1;
+        launches += launch_cg_init(s->kp, s->B, s->p.warm_start == SP_WARM_PREV, true, launch_of(s, st));
     }
     join();
     if (launch_cg32_persistent_batch(b->d_P, b->d_B, b->d_blk_off, b->R, b->total_blocks,

@@ -390,8 +390,20 @@ __global__ void __launch_bounds__(kBlock) k64_true_residual(KParams P, DevBuffer
 
 __device__ __forceinline__ float4 f4(float x, float y, float z, float w) { return make_float4(x, y, z, w); }
 
-// r = b - A x0 with the FP64 matrix (or r = b and x = 0); r4 = (fp32(r), D^-1);
-// d = p = q = 0.  The norms are taken in FP64 on the FP64 residual.
+// x0 (FP64 planes) as the double-float records xdf of the mixed solver.
+__global__ void __launch_bounds__(kBlock) k32_split_x(KParams P, DevBuffers B)
+{
+    if (B.st->error | B.st->overflow) return;
+    const int np = P.npad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const dfloat a = df_split(B.x[i]), b = df_split(B.x[np + i]), c = df_split(B.x[2 * np + i]);
+        B.xdf[2 * i] = f4(a.hi, b.hi, c.hi, 0.f);
+        B.xdf[2 * i + 1] = f4(a.lo, b.lo, c.lo, 0.f);
+    }
+}
+
+// r = b - A x0 in double-float from the double-float matrix, b and x0 (or
+// r = b and x = 0); r4 = (fp32(r), D^-1); d = p = q = 0.  ||b||^2 in FP64.
 __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int from_x)
 {
     DevState* st = B.st;
@@ -400,30 +412,34 @@ __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int 
     double bb = 0.0, rr = 0.0, rz = 0.0;
     SS_SLOT_LOOP_BEGIN
     if (row >= 0) {
-        double s[3] = {0.0, 0.0, 0.0};
-        if (from_x) row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
-        const double d = B.diag[row];
+        dfloat r[3];
+        if (from_x) {
+            dfloat s[3];
+            row_sum_df<4>(B.col, B.val32, B.val32lo, B.xdf, e0, e1, s);
+            residual_df(P, B, row, s, r);
+        } else {
+            const float4 bh = B.bdf[2 * row], bl = B.bdf[2 * row + 1];
+            r[0] = dfloat{bh.x, bl.x};
+            r[1] = dfloat{bh.y, bl.y};
+            r[2] = dfloat{bh.z, bl.z};
+            B.xdf[2 * row] = f4(0.f, 0.f, 0.f, 0.f);
+            B.xdf[2 * row + 1] = f4(0.f, 0.f, 0.f, 0.f);
+        }
         const float di = B.dinv32[row];
-        double rk[3];
-        double rs = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int k = c * np + row;
             const double bk = B.b[k];
-            rk[c] = bk;
-            if (from_x)
-                rk[c] = bk - (d * B.x[k] - P.alpha * s[c]);
-            else
-                B.x[k] = 0.0;
+            if (!from_x) B.x[k] = 0.0;
             bb += bk * bk;
-            rs += rk[c] * rk[c];
         }
-        B.r4[row] = f4((float)rk[0], (float)rk[1], (float)rk[2], di);
+        const float rs = r[0].hi * r[0].hi + r[1].hi * r[1].hi + r[2].hi * r[2].hi;
+        B.r4[row] = f4(r[0].hi, r[1].hi, r[2].hi, di);
         B.p4[row] = f4(0.f, 0.f, 0.f, 0.f);
         B.q4[row] = f4(0.f, 0.f, 0.f, 0.f);
         B.d4[row] = f4(0.f, 0.f, 0.f, 0.f);
-        rr += rs;
-        rz += (double)di * rs;
+        rr += (double)rs;
+        rz += (double)(di * rs);
     }
     SS_SLOT_LOOP_END
     const double v[3] = {bb, rr, rz};
@@ -626,12 +642,15 @@ static int wave_grid(long long threads, int occ, Launch L)
     return (int)(g < 1 ? 1 : g);
 }
 
-void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L)
+int launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L)
 {
-    if (mixed)
+    if (mixed) {
+        if (from_x) k32_split_x<<<wave_grid(P.n, 8, L), kBlock, 0, L.stream>>>(P, B);
         k32_init<<<wave_grid(P.nslots, g_occ.k32_init, L), kBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
-    else
-        k64_init<<<wave_grid(P.nslots, g_occ.k64_init, L), kBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
+        return from_x ? 2 : 1;
+    }
+    k64_init<<<wave_grid(P.nslots, g_occ.k64_init, L), kBlock, 0, L.stream>>>(P, B, from_x ? 1 : 0);
+    return 1;
 }
 
 void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L, int probe)

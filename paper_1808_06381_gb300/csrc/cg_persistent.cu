@@ -34,6 +34,8 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 struct PShared {
     float2 df[32];
     double d[32];
+    float2 dfk[2][32];   // per-warp sums of the grid reductions
+    double dk[2][32];
     double bcast[4];
     int flag;
     // decided by thread 0 (FP64 scalars once per block, not once per thread)
@@ -107,32 +109,65 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShar
 // Grid-wide sums of K double-float values: every block publishes its block
 // sums, passes the barrier, then sums all blocks' partials itself, in the
 // same fixed order in every block (so all blocks hold identical totals).
+// The K values go through one warp-level pass each and one block barrier;
+// warp 0 alone forms the block's sums, arrives, and sums the other blocks'
+// partials after the release, so a reduction costs two block barriers.
 // Consecutive calls must use alternating partial sets: a block may still be
 // reading one set when a faster block writes the next.
+constexpr int kPartialsPerLane = 8;   // covers grids of up to 256 blocks in one round of loads
+
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
                                                const dfloat (&v)[K], float2* partials, double (&out)[K],
                                                int bid, int nb)
 {
+    static_assert(K <= 2, "two values at most");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    dfloat w[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const dfloat t = block_sum_df(v[k], sh.df);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = make_float2(t.hi, t.lo);
+    for (int k = 0; k < K; ++k) w[k] = warp_sum_df(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.dfk[k][warp] = make_float2(w[k].hi, w[k].lo);
     }
-    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 a = lane < nw ? sh.dfk[k][lane] : make_float2(0.f, 0.f);
+            w[k] = warp_sum_df(dfloat{a.x, a.y});
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) partials[k * kMaxPartials + bid] = make_float2(w[k].hi, w[k].lo);
+            sh.flag = barrier_thread0(st, gen + 1u, nb);
+        }
+        __syncwarp();   // orders thread 0's acquire before the other lanes' loads
+        // all of a lane's loads are issued before the first sum (one latency)
+        float2 pv[K][kPartialsPerLane];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int u = 0; u < kPartialsPerLane; ++u) {
+                const int b = lane + 32 * u;
+                pv[k][u] = b < nb ? __ldcg(partials + k * kMaxPartials + b) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dfloat a{0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < kPartialsPerLane; ++u) a = df_add(a, dfloat{pv[k][u].x, pv[k][u].y});
+            for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) {
+                const float2 p = __ldcg(partials + k * kMaxPartials + b);
+                a = df_add(a, dfloat{p.x, p.y});
+            }
+            a = warp_sum_df(a);
+            if (lane == 0) sh.bcast[k] = (double)a.hi + (double)a.lo;
+        }
+    }
     __syncthreads();
     gen += 1u;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        dfloat a{0.f, 0.f};
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const float2 p = __ldcg(partials + k * kMaxPartials + b);
-            a = df_add(a, dfloat{p.x, p.y});
-        }
-        const dfloat t = block_sum_df(a, sh.df);
-        if (threadIdx.x == 0) sh.bcast[k] = (double)t.hi + (double)t.lo;
-    }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
     return sh.flag == 0;
@@ -144,29 +179,52 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
                                                const double (&v)[K], double* partials, double (&out)[K],
                                                int bid, int nb)
 {
+    static_assert(K <= 2, "two values at most");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double w[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double t = block_sum(v[k], sh.d);
-        if (threadIdx.x == 0) partials[k * kMaxPartials + bid] = t;
+    for (int k = 0; k < K; ++k) w[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.dk[k][warp] = w[k];
     }
-    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = warp_sum(lane < nw ? sh.dk[k][lane] : 0.0);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) partials[k * kMaxPartials + bid] = w[k];
+            sh.flag = barrier_thread0(st, gen + 1u, nb);
+        }
+        __syncwarp();
+        double pv[K][kPartialsPerLane];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int u = 0; u < kPartialsPerLane; ++u) {
+                const int b = lane + 32 * u;
+                pv[k][u] = b < nb ? __ldcg(partials + k * kMaxPartials + b) : 0.0;
+            }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = 0.0;
+#pragma unroll
+            for (int u = 0; u < kPartialsPerLane; ++u) a += pv[k][u];
+            for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) a += __ldcg(partials + k * kMaxPartials + b);
+            a = warp_sum(a);
+            if (lane == 0) sh.bcast[k] = a;
+        }
+    }
     __syncthreads();
     gen += 1u;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double a = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += __ldcg(partials + k * kMaxPartials + b);
-        const double t = block_sum(a, sh.d);
-        if (threadIdx.x == 0) sh.bcast[k] = t;
-    }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
     return sh.flag == 0;
 }
 
 constexpr int kBatchP = 6;    // FP32 gathers in flight per thread (batch kernel; see kPersistentCfg)
-constexpr int kBatchP64 = 2;  // FP64 gathers in flight (the rare FP64 residual replacement)
 
 // s = sum_j w_ij D^-1_j r_j (FP32).  Rows of r written by other blocks before
 // the last barrier are visible to plain loads (the barrier's acquire orders
@@ -216,37 +274,41 @@ __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const f
     }
 }
 
-// s_a = sum_j w_ij x_a[j] (FP64 planes).
-__device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const double* __restrict__ val,
-                                            const double* x, int np, int e0, int e1, double& s0, double& s1,
-                                            double& s2)
+}  // namespace
+
+// x += d of one row in double-float (the correction d accumulated in FP32
+// since the last fold).
+__device__ __forceinline__ void fold_correction(const DevBuffers& B, int i, float4 d)
 {
-    s0 = s1 = s2 = 0.0;
-    for (int eb = e0; eb < e1; eb += 32 * kBatchP64) {
-        int j[kBatchP64];
-        double w[kBatchP64];
-#pragma unroll
-        for (int u = 0; u < kBatchP64; ++u) {
-            const int e = eb + 32 * u;
-            j[u] = 0;
-            w[u] = 0.0;
-            if (e < e1) {
-                j[u] = __ldg(col + e);
-                w[u] = __ldg(val + e);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kBatchP64; ++u) {
-            if (w[u] != 0.0) {
-                s0 += w[u] * __ldcg(x + j[u]);
-                s1 += w[u] * __ldcg(x + np + j[u]);
-                s2 += w[u] * __ldcg(x + 2 * np + j[u]);
-            }
-        }
-    }
+    const float4 xh = B.xdf[2 * i], xl = B.xdf[2 * i + 1];
+    const dfloat a = df_add(dfloat{xh.x, xl.x}, d.x), b = df_add(dfloat{xh.y, xl.y}, d.y),
+                 c = df_add(dfloat{xh.z, xl.z}, d.z);
+    B.xdf[2 * i] = make_float4(a.hi, b.hi, c.hi, 0.f);
+    B.xdf[2 * i + 1] = make_float4(a.lo, b.lo, c.lo, 0.f);
 }
 
-}  // namespace
+// The true residual r = b - A x of one row (slot of the sliced layout) in
+// double-float; returns (fp32(r), D^-1) and |fp32(r)|^2 in rs.
+template <int KB>
+__device__ __forceinline__ float4 true_residual_row(const KParams& P, const DevBuffers& B, int slot, int row,
+                                                    float& rs)
+{
+    dfloat s[3], r[3];
+    row_sum_df<KB>(B.col, B.val32, B.val32lo, B.xdf, B.chunk_off[slot >> 5] + (slot & 31),
+                   B.chunk_off[(slot >> 5) + 1], s);
+    residual_df(P, B, row, s, r);
+    rs = r[0].hi * r[0].hi + r[1].hi * r[1].hi + r[2].hi * r[2].hi;
+    return make_float4(r[0].hi, r[1].hi, r[2].hi, B.dinv32[row]);
+}
+
+// The solution of one row in FP64 from its double-float form.
+__device__ __forceinline__ void store_x64(const DevBuffers& B, int np, int i)
+{
+    const float4 xh = B.xdf[2 * i], xl = B.xdf[2 * i + 1];
+    B.x[i] = (double)xh.x + (double)xl.x;
+    B.x[np + i] = (double)xh.y + (double)xl.y;
+    B.x[2 * np + i] = (double)xh.z + (double)xl.z;
+}
 
 // Slot of thread t (0..255 of its window group) in the group's k-th window.
 // The chunks of a window hold rows of decreasing length; warp c takes chunk c
@@ -409,14 +471,12 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         if (sh.action == 2) break;
         if (sh.action == 0) continue;
 
-        // ---- residual replacement: x += d (own rows), then r = b - A x in FP64
+        // ---- residual replacement: x += d (own rows, double-float), then
+        // r = b - A x in double-float
         for (int w = wg; w < we; w += G) {
             const int i = w * 256 + t;
             if (i < P.n) {
-                const float4 d = B.d4[i];
-                B.x[i] += (double)d.x;
-                B.x[np + i] += (double)d.y;
-                B.x[2 * np + i] += (double)d.z;
+                fold_correction(B, i, B.d4[i]);
                 B.d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -426,23 +486,11 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
             const int slot = w * 256 + chunk_lane(k, t);
             const int row = B.slot_row[slot];
             if (row >= 0) {
-                const int e0 = B.chunk_off[slot >> 5] + (slot & 31);
-                const int e1 = B.chunk_off[(slot >> 5) + 1];
-                double s[3];
-                p_row_sum64(B.col, B.val, B.x, np, e0, e1, s[0], s[1], s[2]);
-                const double d = B.diag[row];
-                const float di = B.dinv32[row];
-                double rk[3];
-                double rs = 0.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int k = c * np + row;
-                    rk[c] = B.b[k] - (d * B.x[k] - P.alpha * s[c]);
-                    rs += rk[c] * rk[c];
-                }
-                B.r4[row] = make_float4((float)rk[0], (float)rk[1], (float)rk[2], di);
-                trr += rs;
-                trz += (double)di * rs;
+                float rs;
+                const float4 rf = true_residual_row<2>(P, B, slot, row, rs);
+                B.r4[row] = rf;
+                trr += (double)rs;
+                trz += (double)(rf.w * rs);
             }
         }
         {
@@ -471,6 +519,11 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
         }
         __syncthreads();
         if (sh.action == 2) break;
+    }
+    // the solution in FP64 (own rows)
+    for (int w = wg; w < we; w += G) {
+        const int i = w * 256 + t;
+        if (i < P.n) store_x64(B, np, i);
     }
     // every block's thread 0 holds the same scalars; block 0 records them
     if (bid == 0 && threadIdx.x == 0) {
@@ -506,6 +559,8 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 constexpr int kResWindows = 8;                       // 2048 rows per block
 constexpr int kResChunks = kResWindows * 8;
 constexpr int kResHalo = 4;                          // halo gathers in flight per thread
+constexpr int kResSetupBatch = 8;                    // entries requested at a time in the set-up
+constexpr int kResCheckBatch = 8;                    // gathers in flight in the true residual
 
 struct RShared {
     int loff[kResChunks];    // shared-memory offset of the chunk's local entries
@@ -573,6 +628,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
     const float alpha_e = (float)P.alpha;
+    // requests in flight per thread in the set-up and the true residual (the
+    // 1024-thread form has half the registers)
+    constexpr int KS = BS >= 1024 ? 4 : kResSetupBatch, KC = BS >= 1024 ? 2 : kResCheckBatch;
 
     // ---- set-up 1: local and halo entry counts of every row of the block
     // (read in slot order, so that a warp's loads are coalesced), sort keys
@@ -592,10 +650,20 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         if (row < 0) continue;
         const int c = slot >> 5, e1 = B.chunk_off[c + 1];
         int nl = 0, nh = 0;
-        for (int e = B.chunk_off[c] + (slot & 31); e < e1; e += 32) {
-            if (B.val32[e] != 0.f) {
-                const int j = B.col[e];
-                if (j >= rb && j < re) ++nl; else ++nh;
+        for (int eb = B.chunk_off[c] + (slot & 31); eb < e1; eb += 32 * KS) {
+            int j[KS];
+            float v[KS];
+#pragma unroll
+            for (int u = 0; u < KS; ++u) {
+                const int e = eb + 32 * u;
+                j[u] = e < e1 ? ld_stream(B.col + e) : 0;
+                v[u] = e < e1 ? ld_stream(B.val32 + e) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < KS; ++u) {
+                if (v[u] != 0.f) {
+                    if (j[u] >= rb && j[u] < re) ++nl; else ++nh;
+                }
             }
         }
         const int i = row - rb;
@@ -681,17 +749,25 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const int hb = rs.hoff[c] + (owner & 31);
             const int e1 = B.chunk_off[(slot >> 5) + 1];
             int kl = 0, kh = 0;
-            for (int e = B.chunk_off[slot >> 5] + (slot & 31); e < e1; e += 32) {
-                const float v = B.val32[e];
-                if (v != 0.f) {
-                    const int j = B.col[e];
-                    if (j >= rb && j < re) {
-                        scol[lo + 32 * kl] = (unsigned short)(j - rb);
-                        sval[lo + 32 * kl] = v;
+            for (int eb = B.chunk_off[slot >> 5] + (slot & 31); eb < e1; eb += 32 * KS) {
+                int j[KS];
+                float v[KS];
+#pragma unroll
+                for (int u = 0; u < KS; ++u) {
+                    const int e = eb + 32 * u;
+                    j[u] = e < e1 ? ld_stream(B.col + e) : 0;
+                    v[u] = e < e1 ? ld_stream(B.val32 + e) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < KS; ++u) {
+                    if (v[u] == 0.f) continue;
+                    if (j[u] >= rb && j[u] < re) {
+                        scol[lo + 32 * kl] = (unsigned short)(j[u] - rb);
+                        sval[lo + 32 * kl] = v[u];
                         ++kl;
                     } else {
-                        B.hcol[hb + 32 * kh] = j;
-                        B.hval[hb + 32 * kh] = v;
+                        B.hcol[hb + 32 * kh] = j[u];
+                        B.hval[hb + 32 * kh] = v[u];
                         ++kh;
                     }
                 }
@@ -867,16 +943,15 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         if (sh.action == 2) break;
         if (sh.action == 0) continue;
 
-        // ---- residual replacement: x += d, then r = b - A x in FP64 (the
-        // FP64 matrix in its sliced layout, x of other blocks' rows gathered)
+        // ---- residual replacement: x += d (double-float), then r = b - A x in
+        // double-float (x of other blocks' rows gathered)
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
-            if (row[u] < 0) continue;
+            if (row[u] >= 0) fold_correction(B, row[u], make_float4(d[u][0], d[u][1], d[u][2], 0.f));
+            // d is folded; r, p and q are set anew after the check (beta = 0),
+            // so none of them holds a register through it
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                B.x[c * np + row[u]] += (double)d[u][c];
-                d[u][c] = 0.f;
-            }
+            for (int c = 0; c < 3; ++c) d[u][c] = r[u][c] = p[u][c] = q[u][c] = 0.f;
         }
         if (!grid_sync(st, gen, sh, nb)) break;
         // in slot order (coalesced); r goes to the owners through zbuf and is
@@ -886,21 +961,10 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const int slot = w * 256 + chunk_lane(k, t);
             const int rw = B.slot_row[slot];
             if (rw < 0) continue;
-            double sx[3];
-            p_row_sum64(B.col, B.val, B.x, np, B.chunk_off[slot >> 5] + (slot & 31), B.chunk_off[(slot >> 5) + 1],
-                        sx[0], sx[1], sx[2]);
-            const double dd = B.diag[rw];
-            const float di = B.dinv32[rw];
-            double rk[3], rsq = 0.0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int kk = a * np + rw;
-                rk[a] = B.b[kk] - (dd * B.x[kk] - P.alpha * sx[a]);
-                rsq += rk[a] * rk[a];
-            }
-            trr += rsq;
-            trz += (double)di * rsq;
-            const float4 rf = make_float4((float)rk[0], (float)rk[1], (float)rk[2], di);
+            float rs;
+            const float4 rf = true_residual_row<KC>(P, B, slot, rw, rs);
+            trr += (double)rs;
+            trz += (double)(rf.w * rs);
             B.r4[rw] = rf;
             zbuf[rw - rb] = rf;
         }
@@ -946,6 +1010,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+        if (row[u] >= 0) store_x64(B, np, row[u]);
     if (bid == 0 && threadIdx.x == 0) {
         st->iter = sh.iter;
         st->restarts = sh.restarts;

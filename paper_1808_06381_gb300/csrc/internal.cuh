@@ -41,6 +41,7 @@ struct KParams {
     double tol2;        // cg_tol^2
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
+    float alpha_hi, alpha_lo;   // alpha as a double-float (mixed solver's residuals)
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
 };
@@ -110,6 +111,7 @@ struct DevBuffers {
     unsigned char* img; // [nnz_cap] image of the partner: (a+2) | (m+1) << 3 | (c+1) << 5
     double* val;     // [nnz_cap] pair weights w_ij (A_ij = -alpha w_ij); padding 0
     float* val32;    // [nnz_cap] FP32 copy for the mixed solver
+    float* val32lo;  // [nnz_cap] mixed: val32 + val32lo is the weight as a double-float
     int* hcol;       // [nnz_cap] on-chip solve: each block's entries to other blocks' rows (mixed only)
     float* hval;     // [nnz_cap] their weights
     double* diag;    // [n] A_ii
@@ -126,6 +128,10 @@ struct DevBuffers {
     float4* p4;
     float4* q4;
     float4* d4;      // correction accumulated since the last fold into x
+    // mixed solver, double-float forms (hi + lo) for its true residuals b - A x
+    float* diag32lo; // [npad] A_ii = diag32 + diag32lo
+    float4* bdf;     // [2 npad] b of row i: hi at 2i, lo at 2i + 1, each (x, y, z, 0)
+    float4* xdf;     // [2 npad] x the same way (one 32-byte record per row, one sector per gather)
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
     float2* exp_tab_df; // [kExpTab] the same as double-floats
@@ -425,6 +431,71 @@ __device__ __forceinline__ dfloat df_neg(dfloat a) { return dfloat{-a.hi, -a.lo}
 
 __device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
 
+// The double-float nearest a double: hi = fp32(x), lo = fp32(x - hi).
+__device__ __forceinline__ dfloat df_split(double x)
+{
+    const float hi = __double2float_rn(x);
+    return dfloat{hi, __double2float_rn(x - (double)hi)};
+}
+
+// s_c = sum_j w_ij x_c[j] in double-float over the entries [e0, e1) (stride
+// 32) of one slot of the sliced layout: weights val32 + val32lo, x as the
+// double-float records of xdf.  KB entries are requested at a time.
+template <int KB>
+__device__ __forceinline__ void row_sum_df(const int* __restrict__ col, const float* __restrict__ wh,
+                                           const float* __restrict__ wl, const float4* xdf,
+                                           int e0, int e1, dfloat (&s)[3])
+{
+    s[0] = s[1] = s[2] = dfloat{0.f, 0.f};
+    for (int eb = e0; eb < e1; eb += 32 * KB) {
+        int j[KB];
+        float h[KB], l[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = eb + 32 * u;
+            j[u] = 0;
+            h[u] = l[u] = 0.f;
+            if (e < e1) {
+                j[u] = ld_stream(col + e);
+                h[u] = ld_stream(wh + e);
+                l[u] = ld_stream(wl + e);
+            }
+        }
+        float4 xh[KB], xl[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            xh[u] = xl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (h[u] != 0.f) {
+                xh[u] = xdf[2 * j[u]];
+                xl[u] = xdf[2 * j[u] + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const dfloat w{h[u], l[u]};
+            s[0] = df_add(s[0], df_mul(w, dfloat{xh[u].x, xl[u].x}));
+            s[1] = df_add(s[1], df_mul(w, dfloat{xh[u].y, xl[u].y}));
+            s[2] = df_add(s[2], df_mul(w, dfloat{xh[u].z, xl[u].z}));
+        }
+    }
+}
+
+// r = b - (A_ii x - alpha s) of one row in double-float, from the row's sum s
+// of row_sum_df (Eq. algebra: A = I + alpha L_w with L_w's off-diagonal -w_ij).
+__device__ __forceinline__ void residual_df(const KParams& P, const DevBuffers& B, int row, const dfloat (&s)[3],
+                                            dfloat (&r)[3])
+{
+    const dfloat d{B.diag32[row], B.diag32lo[row]}, al{P.alpha_hi, P.alpha_lo};
+    const float4 xh = B.xdf[2 * row], xl = B.xdf[2 * row + 1], bh = B.bdf[2 * row], bl = B.bdf[2 * row + 1];
+    const dfloat x[3] = {{xh.x, xl.x}, {xh.y, xl.y}, {xh.z, xl.z}};
+    const dfloat b[3] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const dfloat t = df_add(df_mul(d, x[c]), df_neg(df_mul(al, s[c])));
+        r[c] = df_add(b[c], df_neg(t));
+    }
+}
+
 __device__ __forceinline__ dfloat warp_sum_df(dfloat v)
 {
 #pragma unroll
@@ -532,7 +603,7 @@ struct CgLaunch {
 // One CG iteration is two kernels: spmv (q = A z + beta q, p = z + beta p, p.q)
 // and update (x or d += alpha p, r -= alpha q, r.r, r.z).  The true-residual
 // check is one kernel (FP64) or two (mixed: fold d into x, then FP64 residual).
-void launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L);
+int launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Launch L);
 // probe = 1: time the kernel on the current system without touching the solver state
 void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L, int probe = 0);
 void launch_cg_update(const KParams& P, DevBuffers& B, bool mixed, const CgLaunch& C, Launch L,

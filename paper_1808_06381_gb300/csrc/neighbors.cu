@@ -552,9 +552,16 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
     const double F1 = P.noise_amp * g1 + P.c_ev * fy;
     const double F2 = P.noise_amp * g2 + P.c_ev * fz;
     F0 += P.zeta * P.kappa * (yi - 0.5 * P.L[1]);
-    B.b[i] = F0 / P.zeta + P.alpha * P.kappa * P.L[1] * nw;
-    B.b[np + i] = F1 / P.zeta;
-    B.b[2 * np + i] = F2 / P.zeta;
+    const double b0 = F0 / P.zeta + P.alpha * P.kappa * P.L[1] * nw, b1 = F1 / P.zeta, b2 = F2 / P.zeta;
+    B.b[i] = b0;
+    B.b[np + i] = b1;
+    B.b[2 * np + i] = b2;
+    if (B.bdf) {   // mixed solver: A_ii and b as double-floats
+        B.diag32lo[i] = df_split(d).lo;
+        const dfloat c0 = df_split(b0), c1 = df_split(b1), c2 = df_split(b2);
+        B.bdf[2 * i] = make_float4(c0.hi, c1.hi, c2.hi, 0.f);
+        B.bdf[2 * i + 1] = make_float4(c0.lo, c1.lo, c2.lo, 0.f);
+    }
 }
 
 // The pair weight w = exp(-|R|^2 / 2 lambda^2) of §Method for a pair within
@@ -747,6 +754,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
             const dfloat w = pair_weight_df(P, B.exp_tab_df, r2);
             B.val[e] = df_to_double(w);
             B.val32[e] = w.hi;
+            if (B.val32lo) B.val32lo[e] = w.lo;
             s_w = df_add(s_w, w);
             s_x = df_add(s_x, df_mul(dx, w));
             s_y = df_add(s_y, df_mul(dy, w));
@@ -786,6 +794,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
             const double w = pair_weight(P, B.exp_tab, fma(dx, dx, fma(dy, dy, dz * dz)));
             B.val[e] = w;
             B.val32[e] = (float)w;
+            if (B.val32lo) B.val32lo[e] = df_split(w).lo;
             sw += w;
             fx = fma(dx, w, fx);
             fy = fma(dy, w, fy);
@@ -798,6 +807,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
         B.img[base + 32 * k] = (unsigned char)center;
         B.val[base + 32 * k] = 0.0;
         B.val32[base + 32 * k] = 0.f;
+        if (B.val32lo) B.val32lo[base + 32 * k] = 0.f;
     }
     finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, st->noise_step == st->step, sw, fx, fy, fz, nw);
 }

@@ -72,6 +72,8 @@ int alloc_pairs(sp_sim* s, long long cap)
     cudaFree(B.img);
     cudaFree(B.hcol);
     cudaFree(B.hval);
+    cudaFree(B.val32lo);
+    B.val32lo = nullptr;
     B.col = nullptr;
     B.val = nullptr;
     B.val32 = nullptr;
@@ -82,7 +84,8 @@ int alloc_pairs(sp_sim* s, long long cap)
     SS_TRY(dev_alloc(s, &B.val, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val32, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.img, (size_t)cap));
-    if (mixed(s)) {   // halo lists of the on-chip solve
+    if (mixed(s)) {   // low parts of the weights; halo lists of the on-chip solve
+        SS_TRY(dev_alloc(s, &B.val32lo, (size_t)cap));
         SS_TRY(dev_alloc(s, &B.hcol, (size_t)cap));
         SS_TRY(dev_alloc(s, &B.hval, (size_t)cap));
     }
@@ -125,6 +128,8 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
     k.res_smem = kResSmemBytes;
     k.alpha = p.alpha;
+    k.alpha_hi = (float)p.alpha;
+    k.alpha_lo = (float)(p.alpha - (double)k.alpha_hi);
     k.zeta = p.zeta;
     k.kappa = p.kappa;
     k.dt = p.dt;
@@ -291,8 +296,7 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
     KParams& P = s->kp;
     DevBuffers& B = s->B;
     Launch L = launch_of(s, cs);
-    launch_cg_init(P, B, from_x, mixed(s), L);
-    *launches += 1;
+    *launches += launch_cg_init(P, B, from_x, mixed(s), L);
     if (mixed(s) && s->persistent) {
         SS_CUDA(launch_cg32_persistent(P, B, L));
         *launches += 1;
@@ -483,7 +487,8 @@ int sp_sim_destroy(sp_sim* s)
     DevBuffers& B = s->B;
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
-                    B.chunk_off, B.col, B.img, B.val, B.val32, B.hcol, B.hval, B.diag, B.partials_df,
+                    B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
+                    B.diag32lo, B.bdf, B.xdf,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
                     B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
@@ -598,6 +603,11 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.q, v3));
     A(dev_alloc(s, &B.z, v3));
     A(dev_alloc(s, &B.r4, (size_t)npad));
+    if (mixed(s)) {   // double-float forms of the mixed solver's true residuals
+        A(dev_alloc(s, &B.diag32lo, (size_t)npad));
+        A(dev_alloc(s, &B.bdf, 2 * (size_t)npad));
+        A(dev_alloc(s, &B.xdf, 2 * (size_t)npad));
+    }
     A(dev_alloc(s, &B.p4, (size_t)npad));
     A(dev_alloc(s, &B.q4, (size_t)npad));
     A(dev_alloc(s, &B.d4, (size_t)npad));

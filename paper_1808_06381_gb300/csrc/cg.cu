@@ -403,7 +403,9 @@ __global__ void __launch_bounds__(kBlock) k32_split_x(KParams P, DevBuffers B)
 }
 
 // r = b - A x0 in double-float from the double-float matrix, b and x0 (or
-// r = b and x = 0); r4 = (fp32(r), D^-1); d = p = q = 0.  ||b||^2 in FP64.
+// r = b and x = 0); r4 = (fp32(r), D^-1); d = p = q = 0.  ||b||^2 from the
+// high parts of b (FP32 squares summed in FP64: the relative tolerance needs
+// a few digits of it).
 __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int from_x)
 {
     DevState* st = B.st;
@@ -426,12 +428,11 @@ __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int 
             B.xdf[2 * row + 1] = f4(0.f, 0.f, 0.f, 0.f);
         }
         const float di = B.dinv32[row];
+        const float4 bh = B.bdf[2 * row];
+        bb += (double)(bh.x * bh.x + bh.y * bh.y + bh.z * bh.z);
+        if (!from_x) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * np + row;
-            const double bk = B.b[k];
-            if (!from_x) B.x[k] = 0.0;
-            bb += bk * bk;
+            for (int c = 0; c < 3; ++c) B.x[c * np + row] = 0.0;
         }
         const float rs = r[0].hi * r[0].hi + r[1].hi * r[1].hi + r[2].hi * r[2].hi;
         B.r4[row] = f4(r[0].hi, r[1].hi, r[2].hi, di);
@@ -531,45 +532,42 @@ __global__ void __launch_bounds__(kBlock) k32_update(KParams P, DevBuffers B, Cg
     }
 }
 
-// x += d; d = 0 (FP64 accumulation of the FP32 correction).
+// x += d; d = 0: the FP32 correction folded into the double-float x, and x
+// also written in FP64 (the solution whenever the loop stops).
 __global__ void __launch_bounds__(kBlock) k32_fold(KParams P, DevBuffers B, int always)
 {
     const DevState* st = B.st;
     if (halted(st) || (!always && !st->check_true)) return;
     const int np = P.npad;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const float4 d = B.d4[i];
-        B.x[i] += (double)d.x;
-        B.x[np + i] += (double)d.y;
-        B.x[2 * np + i] += (double)d.z;
+        const float4 d = B.d4[i], xh = B.xdf[2 * i], xl = B.xdf[2 * i + 1];
+        const dfloat a = df_add(dfloat{xh.x, xl.x}, d.x), b = df_add(dfloat{xh.y, xl.y}, d.y),
+                     c = df_add(dfloat{xh.z, xl.z}, d.z);
+        B.xdf[2 * i] = f4(a.hi, b.hi, c.hi, 0.f);
+        B.xdf[2 * i + 1] = f4(a.lo, b.lo, c.lo, 0.f);
+        B.x[i] = df_to_double(a);
+        B.x[np + i] = df_to_double(b);
+        B.x[2 * np + i] = df_to_double(c);
         B.d4[i] = f4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-// r = b - A x with the FP64 matrix; r4 = (fp32(r), D^-1); r.r in FP64.
+// r = b - A x in double-float; r4 = (fp32(r), D^-1); r.r summed in FP64.
 __global__ void __launch_bounds__(kBlock) k32_true_residual(KParams P, DevBuffers B, int always, CgLaunch C)
 {
     DevState* st = B.st;
     if (halted(st) || (!always && !st->check_true)) return;
-    const int np = P.npad;
     double rr = 0.0, rz = 0.0;
     SS_SLOT_LOOP_BEGIN
     if (row >= 0) {
-        double s[3];
-        row_sum64(B.col, B.val, B.x, np, e0, e1, true, s[0], s[1], s[2]);
-        const double d = B.diag[row];
+        dfloat s[3], r[3];
+        row_sum_df<4>(B.col, B.val32, B.val32lo, B.xdf, e0, e1, s);
+        residual_df(P, B, row, s, r);
         const float di = B.dinv32[row];
-        double rk[3];
-        double rs = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int k = c * np + row;
-            rk[c] = B.b[k] - (d * B.x[k] - P.alpha * s[c]);
-            rs += rk[c] * rk[c];
-        }
-        B.r4[row] = f4((float)rk[0], (float)rk[1], (float)rk[2], di);
-        rr += rs;
-        rz += (double)di * rs;
+        const float rs = r[0].hi * r[0].hi + r[1].hi * r[1].hi + r[2].hi * r[2].hi;
+        B.r4[row] = f4(r[0].hi, r[1].hi, r[2].hi, di);
+        rr += (double)rs;
+        rz += (double)(di * rs);
     }
     SS_SLOT_LOOP_END
     const double v[2] = {rr, rz};

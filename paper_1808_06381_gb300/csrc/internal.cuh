@@ -42,6 +42,13 @@ struct KParams {
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
     float alpha_hi, alpha_lo;   // alpha as a double-float (mixed solver's residuals)
+    // the mixed assembly's row finish in double-float: b = amp_z g + cev_z f
+    // (+ kappa (y - L_y / 2) + akl sum n w for the x component)
+    float amp_z_hi, amp_z_lo;   // noise_amp / zeta
+    float cev_z_hi, cev_z_lo;   // c_ev / zeta
+    float kap_hi, kap_lo;       // kappa
+    float hly_hi, hly_lo;       // L_y / 2
+    float akl_hi, akl_lo;       // alpha kappa L_y
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
 };

@@ -431,13 +431,26 @@ namespace {
 
 // -------------------------------------------------------------- kernels
 
+// Component c of b at row i: the mixed path keeps b as double-floats only.
+__device__ __forceinline__ double b_at(const DevBuffers& B, int np, int c, int i)
+{
+    if (B.bdf) {
+        const float4 h = B.bdf[2 * i], l = B.bdf[2 * i + 1];
+        return c == 0 ? (double)h.x + (double)l.x : (c == 1 ? (double)h.y + (double)l.y : (double)h.z + (double)l.z);
+    }
+    return B.b[c * np + i];
+}
+
 // s = sqrt(sum b^2 / 3n) (1 if b = 0)
 __global__ void k_mp_scale(KParams P, DevBuffers B, MpBuffers M)
 {
     const int np = P.npad;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
-        for (int c = 0; c < 3; ++c) acc += B.b[c * np + i] * B.b[c * np + i];
+        for (int c = 0; c < 3; ++c) {
+            const double b = b_at(B, np, c, i);
+            acc += b * b;
+        }
     const double v[1] = {acc};
     if (publish_partials<1>(v, M.part, &M.ticket[0])) {
         double out[1];
@@ -456,10 +469,10 @@ __global__ void k_mp_input(KParams P, DevBuffers B, MpBuffers M)
     if (i >= P.n) return;
     const int np = P.npad;
     const float inv = (float)(1.0 / M.scal[0]);
-    const double di = B.dinv[i];
+    const double di = B.bdf ? (double)B.dinv32[i] : B.dinv[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double b = B.b[c * np + i];
+        const double b = b_at(B, np, c, i);
         M.x0[3 * i + c] = make_float4((float)(b * di) * inv, (float)B.x[c * np + i] * inv, (float)b * inv, 0.f);
     }
 }

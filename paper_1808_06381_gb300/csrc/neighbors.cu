@@ -556,12 +556,44 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
     B.b[i] = b0;
     B.b[np + i] = b1;
     B.b[2 * np + i] = b2;
-    if (B.bdf) {   // mixed solver: A_ii and b as double-floats
-        B.diag32lo[i] = df_split(d).lo;
-        const dfloat c0 = df_split(b0), c1 = df_split(b1), c2 = df_split(b2);
-        B.bdf[2 * i] = make_float4(c0.hi, c1.hi, c2.hi, 0.f);
-        B.bdf[2 * i + 1] = make_float4(c0.lo, c1.lo, c2.lo, 0.f);
+}
+
+// The same row of the mixed path, in double-float on the FP32 pipes from the
+// double-float pair sums: A_ii and b as double-floats (A_ii = diag32 +
+// diag32lo, b = bdf), D^-1 in FP32 for the Jacobi iterations.  Only the
+// split of the FP64 normals runs on the FP64 pipe.
+__device__ __forceinline__ void finish_row_df(const KParams& P, const DevBuffers& B, int i, dfloat yi,
+                                              unsigned long long step, int use_inj, bool drawn, dfloat sw,
+                                              dfloat fx, dfloat fy, dfloat fz, dfloat nw)
+{
+    const int np = P.npad;
+    const dfloat d = df_add(dfloat{1.f, 0.f}, df_mul(dfloat{P.alpha_hi, P.alpha_lo}, sw));
+    B.diag32[i] = d.hi;
+    B.diag32lo[i] = d.lo;
+    B.dinv32[i] = __frcp_rn(d.hi);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (P.noise_amp != 0.0) {
+        const int id = B.id_w[i];
+        if (use_inj) {
+            g0 = B.xi_inj[3 * (long long)id];
+            g1 = B.xi_inj[3 * (long long)id + 1];
+            g2 = B.xi_inj[3 * (long long)id + 2];
+        } else if (drawn) {   // drawn by the pair search of this step
+            g0 = B.noise3[i];
+            g1 = B.noise3[np + i];
+            g2 = B.noise3[2 * np + i];
+        } else {
+            normals3(P.seed, step, (unsigned long long)id, g0, g1, g2);
+        }
     }
+    const dfloat amp{P.amp_z_hi, P.amp_z_lo}, cev{P.cev_z_hi, P.cev_z_lo};
+    dfloat b0 = df_add(df_mul(amp, df_split(g0)), df_mul(cev, fx));
+    const dfloat b1 = df_add(df_mul(amp, df_split(g1)), df_mul(cev, fy));
+    const dfloat b2 = df_add(df_mul(amp, df_split(g2)), df_mul(cev, fz));
+    b0 = df_add(b0, df_mul(dfloat{P.kap_hi, P.kap_lo}, df_add(yi, df_neg(dfloat{P.hly_hi, P.hly_lo}))));
+    b0 = df_add(b0, df_mul(dfloat{P.akl_hi, P.akl_lo}, nw));
+    B.bdf[2 * i] = make_float4(b0.hi, b1.hi, b2.hi, 0.f);
+    B.bdf[2 * i + 1] = make_float4(b0.lo, b1.lo, b2.lo, 0.f);
 }
 
 // The pair weight w = exp(-|R|^2 / 2 lambda^2) of §Method for a pair within
@@ -681,11 +713,11 @@ __device__ __forceinline__ dfloat sep_df(float ih, float il, float jh, float jl,
 // a warp are neighbours in space) skips them.  Padding entries get weight 0.
 //
 // DF (the mixed-precision path): the per-entry arithmetic — separations,
-// |R|^2, weight, pair sums — runs in double-float on the FP32 pipes from the
-// double-float positions, leaving three FP64 operations per entry (the FP64
-// weight); the system then agrees with the FP64 assembly to ~1e-12 relative
-// (the 2^-48 representation of the positions), far inside the mixed solver's
-// tolerance.  The noise and the per-row finish stay FP64.
+// |R|^2, weight, pair sums — and the row finish run in double-float on the
+// FP32 pipes from the double-float positions, and the system is stored as
+// double-floats only (weights val32 + val32lo, A_ii, b); it agrees with the
+// FP64 assembly to ~1e-12 relative (the 2^-48 representation of the
+// positions), far inside the mixed solver's tolerance.
 template <bool DF>
 __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
 {
@@ -713,6 +745,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
         pstride = 32;
     }
     double sw = 0.0, fx = 0.0, fy = 0.0, fz = 0.0, nw = 0.0;
+    dfloat dsw{0.f, 0.f}, dsx{0.f, 0.f}, dsy{0.f, 0.f}, dsz{0.f, 0.f}, dsn{0.f, 0.f};
     if (DF) {
         const float* __restrict__ ph = B.pos32;
         const float* __restrict__ pl = B.pos32lo;
@@ -752,20 +785,19 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
             const dfloat dz = sep_df(zih, zil, ph[2 * np + j], pl[2 * np + j], shz);
             const dfloat r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
             const dfloat w = pair_weight_df(P, B.exp_tab_df, r2);
-            B.val[e] = df_to_double(w);
             B.val32[e] = w.hi;
-            if (B.val32lo) B.val32lo[e] = w.lo;
+            B.val32lo[e] = w.lo;
             s_w = df_add(s_w, w);
             s_x = df_add(s_x, df_mul(dx, w));
             s_y = df_add(s_y, df_mul(dy, w));
             s_z = df_add(s_z, df_mul(dz, w));
             if (shifted && m != 0) s_n = df_add(s_n, m > 0 ? w : df_neg(w));
         }
-        sw = df_to_double(s_w);
-        fx = df_to_double(s_x);
-        fy = df_to_double(s_y);
-        fz = df_to_double(s_z);
-        nw = df_to_double(s_n);
+        dsw = s_w;
+        dsx = s_x;
+        dsy = s_y;
+        dsz = s_z;
+        dsn = s_n;
     } else {
         const double Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
         const double* __restrict__ pos = B.pos_w;
@@ -805,11 +837,18 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
     for (int k = cnt; k < clen; ++k) {
         B.col[base + 32 * k] = i;
         B.img[base + 32 * k] = (unsigned char)center;
-        B.val[base + 32 * k] = 0.0;
         B.val32[base + 32 * k] = 0.f;
-        if (B.val32lo) B.val32lo[base + 32 * k] = 0.f;
+        if (DF)
+            B.val32lo[base + 32 * k] = 0.f;
+        else
+            B.val[base + 32 * k] = 0.0;
     }
-    finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, st->noise_step == st->step, sw, fx, fy, fz, nw);
+    if (DF)
+        finish_row_df(P, B, i, dfloat{B.pos32[np + i], B.pos32lo[np + i]}, (unsigned long long)st->step, use_inj,
+                      st->noise_step == st->step, dsw, dsx, dsy, dsz, dsn);
+    else
+        finish_row(P, B, i, yi, (unsigned long long)st->step, use_inj, st->noise_step == st->step, sw, fx, fy, fz,
+                   nw);
 }
 
 // Pair search writing the sliced columns and image codes (FP32 decisions).

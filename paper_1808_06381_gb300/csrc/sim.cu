@@ -135,6 +135,15 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.dt = p.dt;
     k.c_ev = p.eps * 0.1 * p.kT / l2;          // (v/lambda^3) kT / lambda^2 with v/lambda^3 = 0.1
     k.noise_amp = std::sqrt(2.0 * p.zeta * p.kT / p.dt);
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    split(k.noise_amp / p.zeta, k.amp_z_hi, k.amp_z_lo);
+    split(k.c_ev / p.zeta, k.cev_z_hi, k.cev_z_lo);
+    split(p.kappa, k.kap_hi, k.kap_lo);
+    split(0.5 * p.L[1], k.hly_hi, k.hly_lo);
+    split(p.alpha * p.kappa * p.L[1], k.akl_hi, k.akl_lo);
     k.seed = p.seed;
     // cells: edge >= r_c (1 + 1e-9) so that rounding never moves a partner
     // within r_c out of the 3 x 3 x 3 block; in a sparse box the cells are
@@ -1057,15 +1066,25 @@ int fetch_entries(sp_sim* s, std::vector<int>& rows, std::vector<int>& cols, std
     const long long slots = s->st_host->nnz_slots;
     std::vector<int> cnt(n), row_slot(n), chunk_off(s->kp.nchunks + 1), col(slots);
     std::vector<double> val(slots);
+    std::vector<float> vh, vl;   // the mixed path keeps its weights as double-floats only
     ids.resize(n);
     SS_CUDA(cudaMemcpyAsync(cnt.data(), s->B.row_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaMemcpyAsync(row_slot.data(), s->B.row_slot, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaMemcpyAsync(chunk_off.data(), s->B.chunk_off, sizeof(int) * (s->kp.nchunks + 1),
                             cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaMemcpyAsync(col.data(), s->B.col, sizeof(int) * slots, cudaMemcpyDeviceToHost, s->stream));
-    SS_CUDA(cudaMemcpyAsync(val.data(), s->B.val, sizeof(double) * slots, cudaMemcpyDeviceToHost, s->stream));
+    if (mixed(s)) {
+        vh.resize(slots);
+        vl.resize(slots);
+        SS_CUDA(cudaMemcpyAsync(vh.data(), s->B.val32, sizeof(float) * slots, cudaMemcpyDeviceToHost, s->stream));
+        SS_CUDA(cudaMemcpyAsync(vl.data(), s->B.val32lo, sizeof(float) * slots, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+        SS_CUDA(cudaMemcpyAsync(val.data(), s->B.val, sizeof(double) * slots, cudaMemcpyDeviceToHost, s->stream));
+    }
     SS_CUDA(cudaMemcpyAsync(ids.data(), s->B.id_w, sizeof(int) * n, cudaMemcpyDeviceToHost, s->stream));
     SS_CUDA(cudaStreamSynchronize(s->stream));
+    if (mixed(s))
+        for (long long e = 0; e < slots; ++e) val[e] = (double)vh[e] + (double)vl[e];
     rows.clear();
     cols.clear();
     vals.clear();
@@ -1119,12 +1138,26 @@ int sp_get_system(sp_sim* s, double* diag_host, double* b_host, double* w_host)
     SS_TRY(fetch_entries(s, rows, cols, vals, ids));
     if (diag_host) {
         std::vector<double> d(n);
-        SS_CUDA(cudaMemcpy(d.data(), s->B.diag, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (mixed(s)) {   // double-float A_ii
+            std::vector<float> h(n), l(n);
+            SS_CUDA(cudaMemcpy(h.data(), s->B.diag32, sizeof(float) * n, cudaMemcpyDeviceToHost));
+            SS_CUDA(cudaMemcpy(l.data(), s->B.diag32lo, sizeof(float) * n, cudaMemcpyDeviceToHost));
+            for (int r = 0; r < n; ++r) d[r] = (double)h[r] + (double)l[r];
+        } else {
+            SS_CUDA(cudaMemcpy(d.data(), s->B.diag, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        }
         for (int r = 0; r < n; ++r) diag_host[ids[r]] = d[r];
     }
     if (b_host) {
         std::vector<double> b(3 * np);
-        SS_CUDA(cudaMemcpy(b.data(), s->B.b, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost));
+        if (mixed(s)) {   // double-float rows (hi, lo)
+            std::vector<float> f(8 * np);
+            SS_CUDA(cudaMemcpy(f.data(), s->B.bdf, sizeof(float) * 8 * np, cudaMemcpyDeviceToHost));
+            for (size_t r = 0; r < np; ++r)
+                for (int a = 0; a < 3; ++a) b[a * np + r] = (double)f[8 * r + a] + (double)f[8 * r + 4 + a];
+        } else {
+            SS_CUDA(cudaMemcpy(b.data(), s->B.b, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost));
+        }
         for (int r = 0; r < n; ++r)
             for (int a = 0; a < 3; ++a) b_host[3 * (size_t)ids[r] + a] = b[a * np + r];
     }

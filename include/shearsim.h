@@ -58,7 +58,8 @@ typedef enum sp_status {
 
 enum sp_precision {
     SP_PREC_FP64 = 0,   /* matrix, vectors and dots in FP64 */
-    SP_PREC_MIXED = 1   /* FP32 SpMV, axpy and Jacobi; FP64 positions, dots, x, residual replacement */
+    SP_PREC_MIXED = 1   /* FP32 SpMV, axpy and Jacobi; double-float (FP32 pipes) assembly, normals, dots,
+                           x and residual replacement; FP64 positions */
 };
 
 enum sp_warm_start {
@@ -281,6 +282,14 @@ int sp_set_noise(sp_sim* sim, const double* xi_host);
  * checking: out_host[4 * k ...] = Philox(ctr = (ids[k], step, 0, 0), key = (seed, 0)). */
 int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count,
                      const int64_t* ids_host, uint64_t* out_host);
+/* The thermal normals of Eq. F (Box-Muller on the Philox block above: two
+ * 53-bit uniforms per pair) for particle ids at `step`, as a simulation of
+ * the given precision draws them: SP_PREC_FP64 in FP64, SP_PREC_MIXED in
+ * double-float arithmetic on the FP32 pipes (within ~1e-13 of the FP64
+ * ones).  out_host[3 * k + c], for checking.  Errors: SP_ERR_INVALID_ARG,
+ * SP_ERR_NO_DEVICE, SP_ERR_OOM, SP_ERR_CUDA. */
+int sp_normals(int32_t device, uint64_t seed, uint64_t step, int64_t count, const int64_t* ids_host,
+               int32_t precision, double* out_host);
 
 /* ---- learned warm start ----
  *

@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
+            ("sp_normals", [i32, u64, u64, i64, vp, i32, vp]),
             ("sp_profile_step", [vp, P(sp_kernel_profile)]), ("sp_autotune", [vp, i32, P(sp_tune_info)]),
             ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)]),
             ("sp_batch_create", [i32, vp, vp, P(vp)]), ("sp_batch_destroy", [vp]),
@@ -154,6 +155,15 @@ def philox_blocks(seed: int, step: int, ids, device: int = 0) -> np.ndarray:
     ids = np.ascontiguousarray(ids, dtype=np.int64)
     out = np.zeros((ids.shape[0], 4), dtype=np.uint64)
     _check(load().sp_philox_blocks(device, seed, step, ids.shape[0], _p(ids), _p(out)))
+    return out
+
+
+def normals(seed: int, step: int, ids, precision: str = "mixed", device: int = 0) -> np.ndarray:
+    """The thermal normals [n, 3] of particle ids at a step, as a simulation of that precision draws them."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    out = np.zeros((ids.shape[0], 3))
+    prec = {"fp64": 0, "mixed": 1}[precision]
+    _check(load().sp_normals(device, seed, step, ids.shape[0], _p(ids), prec, _p(out)))
     return out
 
 

@@ -41,6 +41,7 @@ struct KParams {
     double tol2;        // cg_tol^2
     double inner2;      // mixed solver: inner FP32 solve stops at ||r||^2 <= inner2 * ||r_restart||^2
     int max_iter;
+    int mixed;          // 1: the mixed path (double-float assembly and normals)
     float alpha_hi, alpha_lo;   // alpha as a double-float (mixed solver's residuals)
     // the mixed assembly's row finish in double-float: b = amp_z g + cev_z f
     // (+ kappa (y - L_y / 2) + akl sum n w for the x component)
@@ -142,6 +143,7 @@ struct DevBuffers {
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
     float2* exp_tab_df; // [kExpTab] the same as double-floats
+    float4* rng_tab;    // [kRngTab] double-float tables of the mixed path's normals (computed on the host)
     double* partials;// [kMaxPartials * 4]
     float2* partials_df; // [kMaxPartials * 4] double-float partial sums (mixed solver)
     int* scan_tmp;   // block sums of the scans
@@ -151,6 +153,16 @@ struct DevBuffers {
 
 constexpr int kMaxPartials = 4096;
 constexpr int kExpTab = 1024;
+// Double-float tables of the mixed path's Box-Muller normals: ln c and 1 / c
+// for c = j / 128, j = kLnTabBase + k; then (ln 2, 1 / 3); then cos and sin
+// of 2 pi j / 64; then (2 pi, -1 / 6).  Entries (hi, lo, hi, lo).
+constexpr int kLnTabBase = 90;
+constexpr int kLnTab = 96;
+constexpr int kTrigTab = 64;
+constexpr int kRngConstLn = kLnTab;                 // (ln 2, 1 / 3)
+constexpr int kRngTrig = kLnTab + 1;                // cos, sin of 2 pi j / 64
+constexpr int kRngConstTrig = kRngTrig + kTrigTab;  // (2 pi, -1 / 6)
+constexpr int kRngTab = kRngConstTrig + 1;
 constexpr int kCandCap = 32;    // partners kept per row by the search (rows with more are searched again)
 constexpr int kMaxSmIds = 1024;   // weight table: exp(-t) for t < 4 (pairs have t < ln 20)
 
@@ -445,6 +457,113 @@ __device__ __forceinline__ dfloat df_split(double x)
     return dfloat{hi, __double2float_rn(x - (double)hi)};
 }
 
+// ---- the same normals in double-float arithmetic on the FP32 pipes (the
+// mixed path): each step below is within a few units of 2^-47 of its FP64
+// counterpart, so the normals agree with the FP64 ones to ~1e-13.
+
+// u = m 2^-53 (m < 2^53 an integer) as a double-float.
+__device__ __forceinline__ dfloat df_u53(unsigned long long m)
+{
+    const float h = __ull2float_rn(m);
+    const long long rem = (long long)m - (long long)(unsigned long long)h;   // exact, |rem| < 2^29
+    const float s = 1.1102230246251565e-16f;                                  // 2^-53 (exact)
+    return dfloat{h * s, __ll2float_rn(rem) * s};
+}
+
+// ln u for u = k 2^-53 in (0, 1] (k the integer): u = 2^e m with m in
+// [sqrt(1/2), sqrt(2)), c = j / 128 the table point nearest m, t = (m - c) / c
+// (|t| < 0.0056), ln u = e ln 2 + ln c + ln(1 + t) with the series of
+// ln(1 + t): t, t^2 and t^3 terms in double-float, the rest (t^4 .. t^7) in
+// FP32.  Next to u = 1 (c = 1), where ln u is as small as 1 - u, t = -(2^53 -
+// k) 2^-53 is taken exactly from the integer, so ln u keeps its relative
+// accuracy.
+__device__ __forceinline__ dfloat df_log_unit(dfloat u, unsigned long long k53, const float4* __restrict__ tab)
+{
+    int e;
+    float mh = frexpf(u.hi, &e);
+    if (mh < 0.70710678f) {
+        mh *= 2.f;
+        e -= 1;
+    }
+    const float ml = ldexpf(u.lo, -e);   // exact
+    const int j = __float2int_rn(mh * 128.f);
+    const float4 lc = __ldg(tab + (j - kLnTabBase));
+    const float4 k = __ldg(tab + kRngConstLn);
+    dfloat t;
+    if (e == 0 && j == 128) {   // u in [1 - 1/256, 1]: 2^53 - k < 2^45, exact as a double-float
+        const long long v = (1ll << 53) - (long long)k53;
+        const float vh = __ll2float_rn(v);
+        const float s = 1.1102230246251565e-16f;   // 2^-53
+        t = dfloat{-vh * s, -__ll2float_rn(v - (long long)vh) * s};
+    } else {
+        const dfloat mc = two_sum(__fsub_rn(mh, (float)j * 0.0078125f), ml);   // m - c (the difference is exact)
+        t = df_mul(mc, dfloat{lc.z, lc.w});
+    }
+    const dfloat t2 = df_sqr(t);
+    const dfloat t3 = df_mul(t2, t);
+    const float th = t.hi;
+    const float tail = __fmul_rn(__fmul_rn(t2.hi, t2.hi),
+                                 fmaf(th, fmaf(th, fmaf(th, 1.f / 7.f, -1.f / 6.f), 0.2f), -0.25f));
+    dfloat s = df_add(t, dfloat{-0.5f * t2.hi, -0.5f * t2.lo});
+    s = df_add(s, df_mul(t3, dfloat{k.z, k.w}));
+    s = df_add(s, dfloat{tail, 0.f});
+    s = df_add(s, dfloat{lc.x, lc.y});
+    return df_add(s, df_mul(dfloat{(float)e, 0.f}, dfloat{k.x, k.y}));
+}
+
+// sqrt(x), x >= 0: one Newton step from the FP32 root (the square of the
+// FP32 root exact by one fused multiply-add).
+__device__ __forceinline__ dfloat df_sqrt(dfloat x)
+{
+    if (!(x.hi > 0.f)) return dfloat{0.f, 0.f};
+    const float y = sqrtf(x.hi);
+    const float p = __fmul_rn(y, y), pe = fmaf(y, y, -p);
+    const float r = __fadd_rn(__fsub_rn(x.hi, p), __fsub_rn(x.lo, pe));
+    return fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.f, y)));
+}
+
+// cos(2 pi u), sin(2 pi u) for u in [0, 1]: u = j / 64 + r (|r| <= 1/128),
+// theta = 2 pi r, the two series to theta^7 and theta^6 (leading terms in
+// double-float), combined with the table's cos and sin of 2 pi j / 64.
+__device__ __forceinline__ void df_sincos2pi(dfloat u, const float4* __restrict__ tab, dfloat& sn, dfloat& cs)
+{
+    const int j = __float2int_rn(u.hi * 64.f);
+    const dfloat r = two_sum(__fsub_rn(u.hi, (float)j * 0.015625f), u.lo);   // the difference is exact
+    const float4 k = __ldg(tab + kRngConstTrig);
+    const dfloat th = df_mul(r, dfloat{k.x, k.y});
+    const dfloat t2 = df_sqr(th);
+    dfloat s = df_add(th, df_mul(df_mul(t2, th), dfloat{k.z, k.w}));
+    s = df_add(s, dfloat{__fmul_rn(__fmul_rn(th.hi, __fmul_rn(t2.hi, t2.hi)), fmaf(t2.hi, -1.f / 5040.f, 1.f / 120.f)),
+                         0.f});
+    dfloat c = df_add(dfloat{1.f, 0.f}, dfloat{-0.5f * t2.hi, -0.5f * t2.lo});
+    c = df_add(c, dfloat{__fmul_rn(__fmul_rn(t2.hi, t2.hi), fmaf(t2.hi, -1.f / 720.f, 1.f / 24.f)), 0.f});
+    const float4 a = __ldg(tab + kRngTrig + (j & (kTrigTab - 1)));
+    const dfloat ca{a.x, a.y}, sa{a.z, a.w};
+    cs = df_add(df_mul(ca, c), df_neg(df_mul(sa, s)));
+    sn = df_add(df_mul(sa, c), df_mul(ca, s));
+}
+
+// normals3 in double-float: the same Philox block and Box-Muller formulas.
+__device__ __forceinline__ void normals3_df(const float4* __restrict__ tab, unsigned long long seed,
+                                            unsigned long long step, unsigned long long id, dfloat& g0, dfloat& g1,
+                                            dfloat& g2)
+{
+    unsigned long long c[4] = {id, step, 0ull, 0ull};
+    philox4x64_10(c, seed, 0ull);
+    const unsigned long long k1 = (c[0] >> 11) + 1ull, k3 = (c[2] >> 11) + 1ull;
+    const dfloat l1 = df_log_unit(df_u53(k1), k1, tab);
+    const dfloat l3 = df_log_unit(df_u53(k3), k3, tab);
+    const dfloat r1 = df_sqrt(dfloat{-2.f * l1.hi, -2.f * l1.lo});
+    const dfloat r2 = df_sqrt(dfloat{-2.f * l3.hi, -2.f * l3.lo});
+    dfloat s, co, s4, c4;
+    df_sincos2pi(df_u53(c[1] >> 11), tab, s, co);
+    df_sincos2pi(df_u53(c[3] >> 11), tab, s4, c4);
+    g0 = df_mul(r1, co);
+    g1 = df_mul(r1, s);
+    g2 = df_mul(r2, c4);
+}
+
+
 // s_c = sum_j w_ij x_c[j] in double-float over the entries [e0, e1) (stride
 // 32) of one slot of the sliced layout: weights val32 + val32lo, x as the
 // double-float records of xdf.  KB entries are requested at a time.
@@ -598,6 +717,9 @@ int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj
 void launch_assemble_only(const KParams& P, DevBuffers& B, bool use_inj, bool df, Launch L);
 // Fills the weight tables exp_tab and exp_tab_df (host computation, one copy each).
 cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t stream);
+cudaError_t upload_rng_table(float4* rng_tab, cudaStream_t stream);
+void launch_normals(const float4* tab, unsigned long long seed, unsigned long long step, long long count,
+                    const long long* ids, double* out, int df, cudaStream_t s);
 void launch_uniform_positions(const KParams& P, DevBuffers& B, Launch L);
 void launch_philox_blocks(unsigned long long seed, unsigned long long step, long long count,
                           const long long* ids, unsigned long long* out, cudaStream_t s);

@@ -459,11 +459,20 @@ __global__ void k_nbr_collect(KParams P, DevBuffers B, int draw_noise)
     }
     if (i >= P.n) return;
     if (draw_noise) {   // the step's normals of this row (the assembly uses them)
-        double g0, g1, g2;
-        normals3(P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
-        B.noise3[i] = g0;
-        B.noise3[P.npad + i] = g1;
-        B.noise3[2 * P.npad + i] = g2;
+        if (P.mixed) {   // double-float arithmetic; stored as (hi, lo) pairs in the same space
+            dfloat g0, g1, g2;
+            normals3_df(B.rng_tab, P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
+            float2* n2 = reinterpret_cast<float2*>(B.noise3);
+            n2[i] = make_float2(g0.hi, g0.lo);
+            n2[P.npad + i] = make_float2(g1.hi, g1.lo);
+            n2[2 * P.npad + i] = make_float2(g2.hi, g2.lo);
+        } else {
+            double g0, g1, g2;
+            normals3(P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
+            B.noise3[i] = g0;
+            B.noise3[P.npad + i] = g1;
+            B.noise3[2 * P.npad + i] = g2;
+        }
     }
     const double delta = st->delta;
     const int np = P.npad;
@@ -559,9 +568,8 @@ __device__ __forceinline__ void finish_row(const KParams& P, const DevBuffers& B
 }
 
 // The same row of the mixed path, in double-float on the FP32 pipes from the
-// double-float pair sums: A_ii and b as double-floats (A_ii = diag32 +
-// diag32lo, b = bdf), D^-1 in FP32 for the Jacobi iterations.  Only the
-// split of the FP64 normals runs on the FP64 pipe.
+// double-float pair sums and normals: A_ii and b as double-floats (A_ii =
+// diag32 + diag32lo, b = bdf), D^-1 in FP32 for the Jacobi iterations.
 __device__ __forceinline__ void finish_row_df(const KParams& P, const DevBuffers& B, int i, dfloat yi,
                                               unsigned long long step, int use_inj, bool drawn, dfloat sw,
                                               dfloat fx, dfloat fy, dfloat fz, dfloat nw)
@@ -571,25 +579,27 @@ __device__ __forceinline__ void finish_row_df(const KParams& P, const DevBuffers
     B.diag32[i] = d.hi;
     B.diag32lo[i] = d.lo;
     B.dinv32[i] = __frcp_rn(d.hi);
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    dfloat g0{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f};
     if (P.noise_amp != 0.0) {
         const int id = B.id_w[i];
         if (use_inj) {
-            g0 = B.xi_inj[3 * (long long)id];
-            g1 = B.xi_inj[3 * (long long)id + 1];
-            g2 = B.xi_inj[3 * (long long)id + 2];
-        } else if (drawn) {   // drawn by the pair search of this step
-            g0 = B.noise3[i];
-            g1 = B.noise3[np + i];
-            g2 = B.noise3[2 * np + i];
+            g0 = df_split(B.xi_inj[3 * (long long)id]);
+            g1 = df_split(B.xi_inj[3 * (long long)id + 1]);
+            g2 = df_split(B.xi_inj[3 * (long long)id + 2]);
+        } else if (drawn) {   // drawn by the pair search of this step, (hi, lo) pairs
+            const float2* n2 = reinterpret_cast<const float2*>(B.noise3);
+            const float2 a = n2[i], b = n2[np + i], c = n2[2 * np + i];
+            g0 = dfloat{a.x, a.y};
+            g1 = dfloat{b.x, b.y};
+            g2 = dfloat{c.x, c.y};
         } else {
-            normals3(P.seed, step, (unsigned long long)id, g0, g1, g2);
+            normals3_df(B.rng_tab, P.seed, step, (unsigned long long)id, g0, g1, g2);
         }
     }
     const dfloat amp{P.amp_z_hi, P.amp_z_lo}, cev{P.cev_z_hi, P.cev_z_lo};
-    dfloat b0 = df_add(df_mul(amp, df_split(g0)), df_mul(cev, fx));
-    const dfloat b1 = df_add(df_mul(amp, df_split(g1)), df_mul(cev, fy));
-    const dfloat b2 = df_add(df_mul(amp, df_split(g2)), df_mul(cev, fz));
+    dfloat b0 = df_add(df_mul(amp, g0), df_mul(cev, fx));
+    const dfloat b1 = df_add(df_mul(amp, g1), df_mul(cev, fy));
+    const dfloat b2 = df_add(df_mul(amp, g2), df_mul(cev, fz));
     b0 = df_add(b0, df_mul(dfloat{P.kap_hi, P.kap_lo}, df_add(yi, df_neg(dfloat{P.hly_hi, P.hly_lo}))));
     b0 = df_add(b0, df_mul(dfloat{P.akl_hi, P.akl_lo}, nw));
     B.bdf[2 * i] = make_float4(b0.hi, b1.hi, b2.hi, 0.f);
@@ -623,6 +633,38 @@ __device__ __forceinline__ double pair_weight(const KParams& P, const double* __
     q = fma(q, f, c1);
     q = fma(q, f, 1.0);
     return __ldg(etab + k) * q;
+}
+
+// The double-float tables of the mixed path's normals (layout at kRngTab),
+// from the host's FP64 log, cos and sin.
+cudaError_t upload_rng_table(float4* rng_tab, cudaStream_t stream)
+{
+    static const std::array<float4, kRngTab> host = [] {
+        auto df = [](double v, float& hi, float& lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        std::array<float4, kRngTab> t{};
+        for (int k = 0; k < kLnTab; ++k) {
+            const double c = (double)(kLnTabBase + k) / 128.0;
+            df(std::log(c), t[k].x, t[k].y);
+            df(1.0 / c, t[k].z, t[k].w);
+        }
+        df(std::log(2.0), t[kRngConstLn].x, t[kRngConstLn].y);
+        df(1.0 / 3.0, t[kRngConstLn].z, t[kRngConstLn].w);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int j = 0; j < kTrigTab; ++j) {
+            const double a = two_pi * (double)j / (double)kTrigTab;
+            df(std::cos(a), t[kRngTrig + j].x, t[kRngTrig + j].y);
+            df(std::sin(a), t[kRngTrig + j].z, t[kRngTrig + j].w);
+        }
+        df(two_pi, t[kRngConstTrig].x, t[kRngConstTrig].y);
+        df(-1.0 / 6.0, t[kRngConstTrig].z, t[kRngConstTrig].w);
+        return t;
+    }();
+    cudaError_t e = cudaMemcpyAsync(rng_tab, host.data(), sizeof(float4) * kRngTab, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
 }
 
 cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t stream)
@@ -936,6 +978,31 @@ __global__ void k_philox_blocks(unsigned long long seed, unsigned long long step
     philox4x64_10(c, seed, 0ull);
 #pragma unroll
     for (int a = 0; a < 4; ++a) out[4 * k + a] = c[a];
+}
+
+// Test hook: the normals of ids[k] at `step` as the FP64 path (df = 0) or the
+// mixed path (df = 1) draws them, out[3 k + c].
+__global__ void k_normals(const float4* __restrict__ tab, unsigned long long seed, unsigned long long step,
+                          long long count, const long long* __restrict__ ids, double* __restrict__ out, int df)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (df) {
+            dfloat g0, g1, g2;
+            normals3_df(tab, seed, step, (unsigned long long)ids[k], g0, g1, g2);
+            out[3 * k] = df_to_double(g0);
+            out[3 * k + 1] = df_to_double(g1);
+            out[3 * k + 2] = df_to_double(g2);
+        } else {
+            normals3(seed, step, (unsigned long long)ids[k], out[3 * k], out[3 * k + 1], out[3 * k + 2]);
+        }
+    }
+}
+
+void launch_normals(const float4* tab, unsigned long long seed, unsigned long long step, long long count,
+                    const long long* ids, double* out, int df, cudaStream_t s)
+{
+    k_normals<<<grid_for(count, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(tab, seed, step, count, ids, out, df);
 }
 
 void launch_philox_blocks(unsigned long long seed, unsigned long long step, long long count,

@@ -128,6 +128,7 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
     k.res_smem = kResSmemBytes;
     k.alpha = p.alpha;
+    k.mixed = p.precision == SP_PREC_MIXED ? 1 : 0;
     k.alpha_hi = (float)p.alpha;
     k.alpha_lo = (float)(p.alpha - (double)k.alpha_hi);
     k.zeta = p.zeta;
@@ -499,7 +500,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
                     B.diag32lo, B.bdf, B.xdf,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -624,6 +625,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.partials_df, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.exp_tab, (size_t)kExpTab));
     A(dev_alloc(s, &B.exp_tab_df, (size_t)kExpTab));
+    A(dev_alloc(s, &B.rng_tab, (size_t)kRngTab));
     A(dev_alloc(s, &B.scan_tmp, (size_t)(std::max(std::max(n, s->kp.ncell), s->kp.nchunks) / 4096 + 2)));
     A(dev_alloc(s, &B.stage, 3 * (size_t)n));
     A(dev_alloc(s, &B.st, 1));
@@ -639,7 +641,8 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.pos_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.pos_w, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
-        upload_exp_table(B.exp_tab, B.exp_tab_df, s->stream) != cudaSuccess) {
+        upload_exp_table(B.exp_tab, B.exp_tab_df, s->stream) != cudaSuccess ||
+        upload_rng_table(B.rng_tab, s->stream) != cudaSuccess) {
         s->err = "initialising device state failed";
         return fail(SP_ERR_CUDA);
     }
@@ -1207,6 +1210,34 @@ int sp_philox_blocks(int32_t device, uint64_t seed, uint64_t step, int64_t count
     }
     cudaFree(ids);
     cudaFree(out);
+    return rc;
+}
+
+int sp_normals(int32_t device, uint64_t seed, uint64_t step, int64_t count, const int64_t* ids_host,
+               int32_t precision, double* out_host)
+{
+    if (count < 0 || (count > 0 && (!ids_host || !out_host))) return SP_ERR_INVALID_ARG;
+    if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED) return SP_ERR_INVALID_ARG;
+    if (count == 0) return SP_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return SP_ERR_NO_DEVICE;
+    long long* ids = nullptr;
+    double* out = nullptr;
+    float4* tab = nullptr;
+    int rc = SP_OK;
+    if (cudaMalloc(&ids, sizeof(long long) * count) != cudaSuccess || cudaMalloc(&out, sizeof(double) * 3 * count) != cudaSuccess ||
+        cudaMalloc(&tab, sizeof(float4) * kRngTab) != cudaSuccess)
+        rc = SP_ERR_OOM;
+    if (rc == SP_OK && (cudaMemcpy(ids, ids_host, sizeof(long long) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+                        upload_rng_table(tab, 0) != cudaSuccess))
+        rc = SP_ERR_CUDA;
+    if (rc == SP_OK) {
+        launch_normals(tab, seed, step, count, ids, out, precision == SP_PREC_MIXED ? 1 : 0, 0);
+        if (cudaMemcpy(out_host, out, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SP_ERR_CUDA;
+    }
+    cudaGetLastError();
+    cudaFree(ids);
+    cudaFree(out);
+    cudaFree(tab);
     return rc;
 }
 

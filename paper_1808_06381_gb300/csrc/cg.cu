@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int 
         dfloat r[3];
         if (from_x) {
             dfloat s[3];
-            row_sum_df<4>(B.col, B.val32, B.val32lo, B.xdf, e0, e1, s);
+            row_sum_df<8>(B.col, B.val32, B.val32lo, B.xdf, e0, e1, s);
             residual_df(P, B, row, s, r);
         } else {
             const float4 bh = B.bdf[2 * row], bl = B.bdf[2 * row + 1];
@@ -587,6 +587,8 @@ __global__ void k_cg_finish(KParams P, DevBuffers B)
     if (st->error | st->overflow) return;
     if (st->zero_b) {
         for (int k = threadIdx.x; k < 3 * P.npad; k += blockDim.x) B.x[k] = 0.0;
+        if (B.xdf)
+            for (int k = threadIdx.x; k < 2 * P.npad; k += blockDim.x) B.xdf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (threadIdx.x == 0) {
         st->iter_sum += st->iter;

@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
 // each component is within about 5 L 2^-24 of the exact one, below 1e-5
 // relative for the boxes used here), weights from the FP32 matrix, FP32
 // velocities, and a double-float accumulation.
+constexpr int kStressBatch = 4;   // entries requested at a time
+
 __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
 {
     DevState* st = B.st;
@@ -109,25 +111,36 @@ __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
     const int np = P.npad;
     const float deltaf = (float)st->delta;
     const float c_ev = (float)P.c_ev, za = (float)(P.zeta * P.alpha), kl = (float)(P.kappa * P.L[1]);
+    // shifts of the image codes by selection (GB300 converts integers to
+    // floats at the FP64 rate); velocities from the solver's double-float x
+    auto sel = [](int k, float v) { return k == 0 ? 0.f : (k > 0 ? v : -v); };
     dfloat acc{0.f, 0.f};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const float xi = B.pos32[i], yi = B.pos32[np + i];
-        const float vxi = (float)B.x[i];
+        const float vxi = B.xdf[2 * i].x;
         const int slot = B.row_slot[i];
         const int base = B.chunk_off[slot >> 5] + (slot & 31);
         const int cnt = B.row_cnt[i];
         float row = 0.f;
-        for (int k = 0; k < cnt; ++k) {
-            const int e = base + 32 * k;
-            const int j = B.col[e];
-            const unsigned char code = B.img[e];
-            const float a = (float)((int)(code & 7) - 2);
-            const float m = (float)((int)((code >> 3) & 3) - 1);
-            const float dx = (xi - B.pos32[j]) - (m * deltaf + a * P.Lf[0]);
-            const float dy = (yi - B.pos32[np + j]) - m * P.Lf[1];
-            const float w = B.val32[e];
-            const float fx = c_ev * dx * w + za * w * ((float)B.x[j] - vxi + kl * m);
-            row = fmaf(dy, fx, row);
+        for (int kb = 0; kb < cnt; kb += kStressBatch) {
+            int j[kStressBatch], code[kStressBatch];
+            float w[kStressBatch];
+#pragma unroll
+            for (int u = 0; u < kStressBatch; ++u) {
+                const int e = base + 32 * (kb + u);
+                j[u] = kb + u < cnt ? B.col[e] : i;
+                code[u] = kb + u < cnt ? (int)B.img[e] : image_code(0, 0, 0);
+                w[u] = kb + u < cnt ? B.val32[e] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kStressBatch; ++u) {
+                const int a = (code[u] & 7) - 2, m = ((code[u] >> 3) & 3) - 1;
+                const float ax = a == 0 ? 0.f : (a == 1 ? P.Lf[0] : (a == -1 ? -P.Lf[0] : (a == 2 ? 2.f * P.Lf[0] : -2.f * P.Lf[0])));
+                const float dx = (xi - B.pos32[j[u]]) - (sel(m, deltaf) + ax);
+                const float dy = (yi - B.pos32[np + j[u]]) - sel(m, P.Lf[1]);
+                const float fx = c_ev * dx * w[u] + za * w[u] * (B.xdf[2 * j[u]].x - vxi + sel(m, kl));
+                row = fmaf(dy, fx, row);
+            }
         }
         acc = df_add(acc, row);
     }

@@ -388,8 +388,9 @@ def main():
                                "one launch per solve; CUDA events on the simulation's stream; the "
                                "solver's working set (~60 MB) is L2-resident during the solve")}
 
-    # end to end through the public API: host positions in, step, host positions out
-    # (two pinned host buffers used in turn: each step's output is the next step's input)
+    # end to end through the public API: host positions in, step, host positions out in
+    # one call (sp_step_host; two pinned host buffers used in turn: each step's output is
+    # the next step's input)
     import ctypes  # noqa: F401
     bufs = [torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     sim.get_positions(bufs[0])
@@ -397,9 +398,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.e2e_steps):
-        sim.set_positions(bufs[k & 1], delta)
-        delta = sim.step(1)["delta"]
-        sim.get_positions(bufs[(k + 1) & 1])
+        delta = sim.step_host(bufs[k & 1], delta, 1, bufs[(k + 1) & 1])["delta"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_value(n, world, args.e2e_steps, max_over_ranks(1e3 * e2e_s, dist, "cuda"))
@@ -442,7 +441,8 @@ def main():
             "matrix": {"nnz": prof["nnz"], "stored_with_padding": prof["nnz_slots"]},
             "fp64_comparison": fp64,
             "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": n * 24 + 8,
-                    "d2h_bytes_per_step": n * 24 + 16, "steps": args.e2e_steps},
+                    "d2h_bytes_per_step": n * 24 + int(ss.load().sp_state_record_bytes()),
+                    "steps": args.e2e_steps},
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -149,6 +149,17 @@ int sp_solve_velocities(sp_sim* sim, const double* v0_dev, sp_solve_info* info);
  * counter, which advances by one per step.  info may be NULL.  Stops early on
  * the first failing step (info->steps_done tells how many finished). */
 int sp_step(sp_sim* sim, int32_t nsteps, sp_step_info* info);
+/* The same steps from and to host memory in one call: pos_in [n][3] by
+ * particle id (each in [0, L)) and the Lees-Edwards offset delta in [0, L_x)
+ * replace the state, nsteps steps run, and the positions after them are
+ * written to pos_out [n][3] by particle id (may alias pos_in).  One
+ * synchronisation in the common case (the host arrays are read and written
+ * before the call returns).  Errors: those of sp_set_positions and sp_step. */
+int sp_step_host(sp_sim* sim, const double* pos_in, double delta, int32_t nsteps, double* pos_out,
+                 sp_step_info* info);
+/* Bytes of the state record (step statistics, CG scalars, flags) that
+ * sp_step and sp_step_host copy to the host once per call. */
+int64_t sp_state_record_bytes(void);
 
 /* Eq. Sfactor at q_z = 0 on the sheared reciprocal lattice of the current
  * positions: q_x = 2 pi kx / L_x, q_y = 2 pi ky / L_y - (delta / L_y) q_x for

@@ -86,7 +86,7 @@ class sp_tune_info(ctypes.Structure):
 def declared_symbols() -> list:
     """Entry points declared in include/shearsim.h."""
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^(?:int|double|const char\*)\s+(sp_[a-z0-9_]+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^(?:int|int64_t|double|const char\*)\s+(sp_[a-z0-9_]+)\s*\(", text, re.M)))
 
 
 _lib = None
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     sims = [("sp_sim_create", [P(sp_params), vp, P(vp)]), ("sp_sim_destroy", [vp]),
             ("sp_build_neighbors", [vp]), ("sp_assemble", [vp]),
             ("sp_solve_velocities", [vp, vp, P(sp_solve_info)]), ("sp_step", [vp, i32, P(sp_step_info)]),
+            ("sp_step_host", [vp, vp, ctypes.c_double, i32, vp, P(sp_step_info)]),
             ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH):
     lib.sp_mpnn_num_params.restype = ctypes.c_int
     lib.sp_kappa_from_kappa_tau.argtypes = [d, d, d, d]
     lib.sp_kappa_from_kappa_tau.restype = d
+    lib.sp_state_record_bytes.argtypes = []
+    lib.sp_state_record_bytes.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -291,6 +294,19 @@ class Simulation:
     def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
         info = sp_step_info()
         rc = load().sp_step(self._h, int(nsteps), ctypes.byref(info))
+        if raise_on_error:
+            self._c(rc)
+        return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,
+                "max_iterations": info.max_iterations, "last_residual": info.last_residual,
+                "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches, "delta": info.delta,
+                "step": info.step}
+
+    def step_host(self, pos_in, delta: float, nsteps: int, pos_out, raise_on_error: bool = True) -> dict:
+        """sp_step_host: host positions [n][3] (by id) and offset in, nsteps steps, positions out."""
+        assert pos_in.dtype == np.float64 and pos_in.flags["C_CONTIGUOUS"] and pos_in.shape == (self.n, 3)
+        assert pos_out.dtype == np.float64 and pos_out.flags["C_CONTIGUOUS"] and pos_out.shape == (self.n, 3)
+        info = sp_step_info()
+        rc = load().sp_step_host(self._h, _p(pos_in), float(delta), int(nsteps), _p(pos_out), ctypes.byref(info))
         if raise_on_error:
             self._c(rc)
         return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,

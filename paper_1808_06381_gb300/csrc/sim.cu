@@ -752,10 +752,12 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
     return status;
 }
 
-int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
+namespace {
+// nsteps steps; with pos_out, the positions after them are copied out (by
+// particle id) in the same stream before the one synchronisation that reads
+// the step statistics (again after a pair-storage regrowth).
+int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
 {
-    if (!s || nsteps < 0) return SP_ERR_INVALID_ARG;
-    SS_TRY(set_device(s));
     SS_TRY(ensure_step_graph(s));
     launch_reset_step_stats(s->B.st, s->stream);
     long long launches = 1;
@@ -779,6 +781,11 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
             }
         } else {
             for (long long k = 0; k < todo; ++k) SS_CUDA(cudaGraphLaunch(s->step_exec, s->stream));
+        }
+        if (pos_out) {
+            launch_scatter_by_id(s->B.pos_s, s->kp.npad, s->B.id_s, s->kp.n, s->B.stage, s->stream);
+            SS_CUDA(cudaMemcpyAsync(pos_out, s->B.stage, sizeof(double) * 3 * s->kp.n, cudaMemcpyDeviceToHost,
+                                    s->stream));
         }
         SS_TRY(read_state(s));
         done = s->st_host->steps_in_call;
@@ -818,6 +825,37 @@ int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
         return SP_ERR_CUDA;
     }
     return status;
+}
+}  // namespace
+
+int64_t sp_state_record_bytes(void) { return (int64_t)sizeof(DevState); }
+
+int sp_step(sp_sim* s, int32_t nsteps, sp_step_info* info)
+{
+    if (!s || nsteps < 0) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    return run_steps(s, nsteps, nullptr, info);
+}
+
+int sp_step_host(sp_sim* s, const double* pos_in, double delta, int32_t nsteps, double* pos_out,
+                 sp_step_info* info)
+{
+    if (!s || !pos_in || !pos_out || nsteps < 0) return SP_ERR_INVALID_ARG;
+    if (!(delta >= 0.0) || !(delta < s->p.L[0])) {
+        s->err = "delta must lie in [0, L_x)";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    // positions by particle id into the state order; the offset through the
+    // pinned state mirror (an asynchronous copy, read before the mirror is
+    // next written by the statistics read-back in the same stream)
+    SS_CUDA(cudaMemcpyAsync(s->B.stage, pos_in, sizeof(double) * 3 * s->kp.n, cudaMemcpyHostToDevice, s->stream));
+    launch_gather_by_id(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->stream);
+    s->st_host->delta = delta;
+    SS_CUDA(cudaMemcpyAsync(&s->B.st->delta, &s->st_host->delta, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    s->built = false;
+    s->assembled = false;
+    return run_steps(s, nsteps, pos_out, info);
 }
 
 int sp_profile_step(sp_sim* s, sp_kernel_profile* out)

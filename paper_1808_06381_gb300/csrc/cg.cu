@@ -436,6 +436,8 @@ __global__ void __launch_bounds__(kBlock) k32_init(KParams P, DevBuffers B, int 
         }
         const float rs = r[0].hi * r[0].hi + r[1].hi * r[1].hi + r[2].hi * r[2].hi;
         B.r4[row] = f4(r[0].hi, r[1].hi, r[2].hi, di);
+        B.rdf[2 * row] = f4(r[0].hi, r[1].hi, r[2].hi, 0.f);
+        B.rdf[2 * row + 1] = f4(r[0].lo, r[1].lo, r[2].lo, 0.f);
         B.p4[row] = f4(0.f, 0.f, 0.f, 0.f);
         B.q4[row] = f4(0.f, 0.f, 0.f, 0.f);
         B.d4[row] = f4(0.f, 0.f, 0.f, 0.f);

@@ -560,7 +560,8 @@ constexpr int kResWindows = 8;                       // 2048 rows per block
 constexpr int kResChunks = kResWindows * 8;
 constexpr int kResHalo = 4;                          // halo gathers in flight per thread
 constexpr int kResSetupBatch = 8;                    // entries requested at a time in the set-up
-constexpr int kResCheckBatch = 8;                    // gathers in flight in the true residual
+constexpr int kResCheckBatch = 4;                    // gathers in flight in the off-chip blocks' true residual
+constexpr int kResCheckLocal = 8;                    // low parts requested at a time in the on-chip check
 
 struct RShared {
     int loff[kResChunks];    // shared-memory offset of the chunk's local entries
@@ -625,11 +626,12 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 6;
     float* sval = reinterpret_cast<float*>(dyn + nwmax * 256);
     unsigned short* scol = reinterpret_cast<unsigned short*>(sval + cap);
+    float* __restrict__ rlo = B.rlo + (size_t)bid * kResLoStride;   // low parts of the local weights
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
     const float alpha_e = (float)P.alpha;
-    // requests in flight per thread in the set-up and the true residual (the
-    // 1024-thread form has half the registers)
+    // requests in flight per thread in the set-up and in the true residual of
+    // blocks whose entries are off chip (the 1024-thread form has half the registers)
     constexpr int KS = BS >= 1024 ? 4 : kResSetupBatch, KC = BS >= 1024 ? 2 : kResCheckBatch;
 
     // ---- set-up 1: local and halo entry counts of every row of the block
@@ -751,12 +753,13 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             int kl = 0, kh = 0;
             for (int eb = B.chunk_off[slot >> 5] + (slot & 31); eb < e1; eb += 32 * KS) {
                 int j[KS];
-                float v[KS];
+                float v[KS], vl[KS];
 #pragma unroll
                 for (int u = 0; u < KS; ++u) {
                     const int e = eb + 32 * u;
                     j[u] = e < e1 ? ld_stream(B.col + e) : 0;
                     v[u] = e < e1 ? ld_stream(B.val32 + e) : 0.f;
+                    vl[u] = e < e1 ? ld_stream(B.val32lo + e) : 0.f;
                 }
 #pragma unroll
                 for (int u = 0; u < KS; ++u) {
@@ -764,10 +767,12 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     if (j[u] >= rb && j[u] < re) {
                         scol[lo + 32 * kl] = (unsigned short)(j[u] - rb);
                         sval[lo + 32 * kl] = v[u];
+                        rlo[lo + 32 * kl] = vl[u];
                         ++kl;
                     } else {
                         B.hcol[hb + 32 * kh] = j[u];
                         B.hval[hb + 32 * kh] = v[u];
+                        B.hlo[hb + 32 * kh] = vl[u];
                         ++kh;
                     }
                 }
@@ -775,10 +780,12 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             for (; kl < nl; ++kl) {
                 scol[lo + 32 * kl] = 0;
                 sval[lo + 32 * kl] = 0.f;
+                rlo[lo + 32 * kl] = 0.f;
             }
             for (; kh < nh; ++kh) {
                 B.hcol[hb + 32 * kh] = row;
                 B.hval[hb + 32 * kh] = 0.f;
+                B.hlo[hb + 32 * kh] = 0.f;
             }
         }
     }
@@ -943,30 +950,142 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         if (sh.action == 2) break;
         if (sh.action == 0) continue;
 
-        // ---- residual replacement: x += d (double-float), then r = b - A x in
-        // double-float (x of other blocks' rows gathered)
+        // ---- residual replacement: x += d (double-float) and the true residual
+        // r = b - A x.  On chip it follows from the last one, b - A (x + d) =
+        // (b - A x) - A d, with A d in double-float (weights hi + lo, d exact
+        // as FP32): the local half from shared memory (d of the block's rows in
+        // zbuf), the halo half from d published in global memory; the residual
+        // itself kept as a double-float record per row (rdf).  A block whose
+        // entries are off chip recomputes b - A x from x in slot order.
+        {
+            // every row's x record is requested before the first is updated
+            float4 xh[RPT], xl[RPT];
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            if (row[u] >= 0) fold_correction(B, row[u], make_float4(d[u][0], d[u][1], d[u][2], 0.f));
-            // d is folded; r, p and q are set anew after the check (beta = 0),
-            // so none of them holds a register through it
+            for (int u = 0; u < RPT; ++u) {
+                xh[u] = xl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row[u] >= 0) {
+                    xh[u] = B.xdf[2 * row[u]];
+                    xl[u] = B.xdf[2 * row[u] + 1];
+                }
+            }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) d[u][c] = r[u][c] = p[u][c] = q[u][c] = 0.f;
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                const float4 df = make_float4(d[u][0], d[u][1], d[u][2], 0.f);
+                const dfloat a = df_add(dfloat{xh[u].x, xl[u].x}, df.x), b = df_add(dfloat{xh[u].y, xl[u].y}, df.y),
+                             c = df_add(dfloat{xh[u].z, xl[u].z}, df.z);
+                B.xdf[2 * row[u]] = make_float4(a.hi, b.hi, c.hi, 0.f);
+                B.xdf[2 * row[u] + 1] = make_float4(a.lo, b.lo, c.lo, 0.f);
+                B.d4[row[u]] = df;
+                zbuf[row[u] - rb] = df;
+                // r, p and q are set anew after the check (beta = 0), so none of
+                // them holds a register through it
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r[u][c] = p[u][c] = q[u][c] = 0.f;
+            }
         }
         if (!grid_sync(st, gen, sh, nb)) break;
-        // in slot order (coalesced); r goes to the owners through zbuf and is
-        // published for the other blocks' halo gathers before the barrier
         double trr = 0.0, trz = 0.0;
-        for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
-            const int slot = w * 256 + chunk_lane(k, t);
-            const int rw = B.slot_row[slot];
-            if (rw < 0) continue;
-            float rs;
-            const float4 rf = true_residual_row<KC>(P, B, slot, rw, rs);
-            trr += (double)rs;
-            trz += (double)(rf.w * rs);
-            B.r4[rw] = rf;
-            zbuf[rw - rb] = rf;
+        if (onchip) {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                const int c = u * (BS / 32) + warp;
+                const int lo = rs.loff[c] + lane, nl = rs.nloc[c], nh = rs.nhalo[c];
+                const int hb = rs.hoff[c] + lane;
+                // the row's residual record and A_ii are requested first (they
+                // arrive under the sums)
+                const float4 rh = B.rdf[2 * row[u]], rl = B.rdf[2 * row[u] + 1];
+                const dfloat dg{B.diag32[row[u]], B.diag32lo[row[u]]};
+                dfloat s[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                auto add = [&](float wh, float wl, float4 dj) {
+                    const float dd[3] = {dj.x, dj.y, dj.z};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float pr = __fmul_rn(wh, dd[a]);
+                        s[a] = df_add(s[a], dfloat{pr, fmaf(wl, dd[a], fmaf(wh, dd[a], -pr))});
+                    }
+                };
+                // loads in batches (one latency per batch): the low parts of the
+                // local weights, then the halo entries and their gathers of d
+                for (int kb = 0; kb < nl; kb += kResCheckLocal) {
+                    float wl[kResCheckLocal];
+#pragma unroll
+                    for (int k = 0; k < kResCheckLocal; ++k)
+                        wl[k] = kb + k < nl ? ld_stream(rlo + lo + 32 * (kb + k)) : 0.f;
+#pragma unroll
+                    for (int k = 0; k < kResCheckLocal; ++k) {
+                        if (kb + k < nl) {
+                            const int e = lo + 32 * (kb + k);
+                            add(sval[e], wl[k], zbuf[scol[e]]);
+                        }
+                    }
+                }
+                for (int kb = 0; kb < nh; kb += kResHalo) {
+                    int j[kResHalo];
+                    float wh[kResHalo], wl[kResHalo];
+#pragma unroll
+                    for (int k = 0; k < kResHalo; ++k) {
+                        j[k] = 0;
+                        wh[k] = wl[k] = 0.f;
+                        if (kb + k < nh) {
+                            const int e = hb + 32 * (kb + k);
+                            j[k] = ld_stream(B.hcol + e);
+                            wh[k] = ld_stream(B.hval + e);
+                            wl[k] = ld_stream(B.hlo + e);
+                        }
+                    }
+                    float4 dj[kResHalo];
+#pragma unroll
+                    for (int k = 0; k < kResHalo; ++k) {
+                        dj[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (wh[k] != 0.f) dj[k] = B.d4[j[k]];
+                    }
+#pragma unroll
+                    for (int k = 0; k < kResHalo; ++k) add(wh[k], wl[k], dj[k]);
+                }
+                const dfloat al{P.alpha_hi, P.alpha_lo};
+                const dfloat ro[3] = {{rh.x, rl.x}, {rh.y, rl.y}, {rh.z, rl.z}};
+                dfloat rn[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const dfloat ad = df_add(df_mul(dg, dfloat{d[u][a], 0.f}), df_neg(df_mul(al, s[a])));
+                    rn[a] = df_add(ro[a], df_neg(ad));
+                    r[u][a] = rn[a].hi;
+                    d[u][a] = 0.f;
+                }
+                B.rdf[2 * row[u]] = make_float4(rn[0].hi, rn[1].hi, rn[2].hi, 0.f);
+                B.rdf[2 * row[u] + 1] = make_float4(rn[0].lo, rn[1].lo, rn[2].lo, 0.f);
+                const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
+                trr += (double)rsq;
+                trz += (double)(dv[u] * rsq);
+            }
+            __syncthreads();   // zbuf (d) read by every row before it changes
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
+                zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[u][c] = 0.f;
+            __syncthreads();   // zbuf (d) is not read off chip, but it is rewritten below
+            // in slot order (coalesced); r goes to the owners through zbuf and is
+            // published for the other blocks' halo gathers before the barrier
+            for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
+                const int slot = w * 256 + chunk_lane(k, t);
+                const int rw = B.slot_row[slot];
+                if (rw < 0) continue;
+                float rs;
+                const float4 rf = true_residual_row<KC>(P, B, slot, rw, rs);
+                trr += (double)rs;
+                trz += (double)(rf.w * rs);
+                B.r4[rw] = rf;
+                zbuf[rw - rb] = rf;
+            }
         }
         {
             const double v[2] = {trr, trz};
@@ -994,21 +1113,23 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         __syncthreads();
         if (sh.action == 2) break;
+        if (!onchip) {
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            if (row[u] < 0) continue;
-            const float4 rf = zbuf[row[u] - rb];
-            r[u][0] = rf.x;
-            r[u][1] = rf.y;
-            r[u][2] = rf.z;
-        }
-        __syncthreads();
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                const float4 rf = zbuf[row[u] - rb];
+                r[u][0] = rf.x;
+                r[u][1] = rf.y;
+                r[u][2] = rf.z;
+            }
+            __syncthreads();
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-            if (row[u] < 0) continue;
-            zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int u = 0; u < RPT; ++u)
@@ -1127,9 +1248,9 @@ long long grid_of(const PCfg& c, const KParams& P, Launch L)
 // The on-chip solve needs its halo lists and at most kResWindows windows per block.
 bool resident_fits(const PCfg& c, const KParams& P, const DevBuffers& B, Launch L)
 {
-    if (!B.hcol || !B.hval) return false;
-    const long long g = grid_of(c, P, L);
-    return g >= 1 && (P.nslots / 256 + g - 1) / g <= kResWindows;
+    if (!B.hcol || !B.hval || !B.hlo || !B.rlo || !B.rdf) return false;
+    const long long g = grid_of(c, P, L);   // at most one block per SM: rlo holds num_sms blocks
+    return g >= 1 && g <= L.num_sms && (P.nslots / 256 + g - 1) / g <= kResWindows;
 }
 
 // The configuration a launch uses: the chosen one, or entry 0 where the

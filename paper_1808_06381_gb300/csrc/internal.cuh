@@ -56,6 +56,7 @@ struct KParams {
 
 constexpr int kPersistentConfigs = 10;
 constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
+constexpr int kResLoStride = 32768;          // >= kResSmemBytes / 6: local entries of one block
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {
@@ -122,6 +123,9 @@ struct DevBuffers {
     float* val32lo;  // [nnz_cap] mixed: val32 + val32lo is the weight as a double-float
     int* hcol;       // [nnz_cap] on-chip solve: each block's entries to other blocks' rows (mixed only)
     float* hval;     // [nnz_cap] their weights
+    float* hlo;      // [nnz_cap] the low parts of those weights (double-float)
+    float* rlo;      // [SMs][kResLoStride] on-chip solve: the local entries' weight low parts, per block
+                     // in its shared-memory layout
     double* diag;    // [n] A_ii
     double* dinv;    // [n] 1 / A_ii
     float* diag32;   // [n]
@@ -140,6 +144,7 @@ struct DevBuffers {
     float* diag32lo; // [npad] A_ii = diag32 + diag32lo
     float4* bdf;     // [2 npad] b of row i: hi at 2i, lo at 2i + 1, each (x, y, z, 0)
     float4* xdf;     // [2 npad] x the same way (one 32-byte record per row, one sector per gather)
+    float4* rdf;     // [2 npad] the true residual b - A x the same way (initial residual; on-chip checks)
     double* xi_inj;  // [n][3] injected normals by id (or null)
     double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
     float2* exp_tab_df; // [kExpTab] the same as double-floats

@@ -72,6 +72,8 @@ int alloc_pairs(sp_sim* s, long long cap)
     cudaFree(B.img);
     cudaFree(B.hcol);
     cudaFree(B.hval);
+    cudaFree(B.hlo);
+    B.hlo = nullptr;
     cudaFree(B.val32lo);
     B.val32lo = nullptr;
     B.col = nullptr;
@@ -88,6 +90,7 @@ int alloc_pairs(sp_sim* s, long long cap)
         SS_TRY(dev_alloc(s, &B.val32lo, (size_t)cap));
         SS_TRY(dev_alloc(s, &B.hcol, (size_t)cap));
         SS_TRY(dev_alloc(s, &B.hval, (size_t)cap));
+        SS_TRY(dev_alloc(s, &B.hlo, (size_t)cap));
     }
     s->nnz_cap = cap;
     s->st_host->nnz_cap = cap;
@@ -498,7 +501,7 @@ int sp_sim_destroy(sp_sim* s)
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
-                    B.diag32lo, B.bdf, B.xdf,
+                    B.diag32lo, B.bdf, B.xdf, B.rdf, B.rlo, B.hlo,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
                     B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
@@ -617,6 +620,8 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         A(dev_alloc(s, &B.diag32lo, (size_t)npad));
         A(dev_alloc(s, &B.bdf, 2 * (size_t)npad));
         A(dev_alloc(s, &B.xdf, 2 * (size_t)npad));
+        A(dev_alloc(s, &B.rdf, 2 * (size_t)npad));
+        A(dev_alloc(s, &B.rlo, (size_t)s->num_sms * kResLoStride));
     }
     A(dev_alloc(s, &B.p4, (size_t)npad));
     A(dev_alloc(s, &B.q4, (size_t)npad));

@@ -81,6 +81,7 @@ def _load():
         lib.or_stress_xy.restype = d
         lib.or_stress_xy.argtypes = [P(_Params), vp, d, i64, vp, vp]
         lib.or_min_image.argtypes = [P(_Params), d, vp, vp, vp, vp]
+        lib.or_velocity_correlation.argtypes = [P(_Params), vp, d, vp, i64, d, vp, vp, P(d)]
         lib.or_row_neighbors.restype = i64
         lib.or_row_neighbors.argtypes = [P(_Params), vp, d, i64, i64, vp]
         _lib = lib
@@ -160,6 +161,19 @@ def neighbors(p: Params, pos, delta: float = 0.0, method: str = "auto") -> np.nd
         if rc != OR_ERR_CAPACITY:
             raise RuntimeError(f"oracle neighbour search failed: {rc}")
         cap = m.value
+
+
+def velocity_correlation(p: Params, pos, delta: float, v, nbins: int, rmax: float):
+    """Fig. vv: per-bin sums of u_c . u_c' and pair counts over all pairs c < c'
+    with minimum-image distance below rmax (bins of width rmax / nbins), and
+    <|u|^2>; u = v minus the imposed flow kappa (y - L_y/2) x.  The correlation
+    of bin k is sums[k] / (counts[k] * vsq)."""
+    sums = np.zeros(nbins)
+    counts = np.zeros(nbins, dtype=np.int64)
+    vsq = ctypes.c_double()
+    _load().or_velocity_correlation(ctypes.byref(p.c()), _ptr(_f64(pos)), float(delta), _ptr(_f64(v)),
+                                    int(nbins), float(rmax), _ptr(sums), _ptr(counts), ctypes.byref(vsq))
+    return sums, counts, vsq.value
 
 
 def row_neighbors(p: Params, pos, delta: float, i: int) -> np.ndarray:

@@ -31,6 +31,7 @@
  *   or_integrate         §Method: first order in time, v = dR/dt, Lees-Edwards wrap
  *   or_structure_factor  Eq. Sfactor at q_z = 0 on the sheared reciprocal lattice
  *   or_stress_xy         pair virial of the ev and friction forces (the paper defines no stress)
+ *   or_velocity_correlation  §Results, Fig. vv: <v_c . v_c'> / <v_c^2> binned by |R_cc'|
  */
 #include <math.h>
 #include <stdint.h>
@@ -604,4 +605,52 @@ int64_t or_row_neighbors(const or_params* p, const double* pos, double delta, in
         }
     }
     return m;
+}
+
+/* Velocity cross-correlation versus distance (§Results, Fig. vv): the average
+ * inter-chain velocity product <v_c . v_c'> / <v_c^2> as a function of the
+ * inter-chain distance |R_cc'|.
+ *   u_c = v_c - kappa (y_c - L_y/2) x   (velocity relative to the imposed flow;
+ *         the Lees-Edwards image of c' moves with v_c' + kappa L_y n x, so it
+ *         carries the same u; at kappa = 0, u = v)
+ *   for every pair c < c' with R = the minimum-image separation and
+ *   |R|^2 < rmax^2:  r = sqrt(|R|^2), k = floor(r * (nbins / rmax)) (nbins - 1
+ *   where that rounds up to nbins), sum[k] += u_c . u_c', count[k] += 1
+ *   vsq = (1/n) sum_c |u_c|^2;  the correlation of bin k is sum[k] / (count[k] vsq).
+ * Every pair is checked (cost n^2 / 2). */
+static void peculiar(const or_params* p, const double* pos, const double* v, int64_t c, double* u)
+{
+    u[0] = v[3 * c] - p->kappa * (pos[3 * c + 1] - 0.5 * p->L[1]);
+    u[1] = v[3 * c + 1];
+    u[2] = v[3 * c + 2];
+}
+
+void or_velocity_correlation(const or_params* p, const double* pos, double delta, const double* v,
+                             int64_t nbins, double rmax, double* sum, int64_t* count, double* vsq)
+{
+    const double rmax2 = rmax * rmax;
+    const double inv = (double)nbins / rmax;
+    for (int64_t k = 0; k < nbins; ++k) {
+        sum[k] = 0.0;
+        count[k] = 0;
+    }
+    double s2 = 0.0;
+    for (int64_t c = 0; c < p->n; ++c) {
+        double uc[3];
+        peculiar(p, pos, v, c, uc);
+        s2 += uc[0] * uc[0] + uc[1] * uc[1] + uc[2] * uc[2];
+        for (int64_t c2 = c + 1; c2 < p->n; ++c2) {
+            double d[3], nimg;
+            or_min_image(p, delta, pos + 3 * c, pos + 3 * c2, d, &nimg);
+            double r2 = sq_dist(d);
+            if (!(r2 < rmax2)) continue;
+            int64_t k = (int64_t)floor(sqrt(r2) * inv);
+            if (k > nbins - 1) k = nbins - 1;
+            double u2[3];
+            peculiar(p, pos, v, c2, u2);
+            sum[k] += uc[0] * u2[0] + uc[1] * u2[1] + uc[2] * u2[2];
+            count[k] += 1;
+        }
+    }
+    *vsq = p->n > 0 ? s2 / (double)p->n : 0.0;
 }

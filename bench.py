@@ -283,14 +283,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "learned", "batch", "large"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "learned", "batch", "large", "vcorr"],
                     help="mixed: N=262,144 precision workload (the default line); learned: the same with the "
-                         "learned warm start; batch: 64 replicas; large: N=4,194,304")
+                         "learned warm start; batch: 64 replicas; large: N=4,194,304; vcorr: the velocity "
+                         "cross-correlation of Fig. vv on the paper's box")
     ap.add_argument("--train-steps", type=int, default=60)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "ours" and args.workload != "mixed":
-        return {"learned": run_learned, "batch": run_batch, "large": run_large}[args.workload](args)
+        return {"learned": run_learned, "batch": run_batch, "large": run_large,
+                "vcorr": run_vcorr}[args.workload](args)
 
     workload = synth.PRECISION
     if args.n:
@@ -614,6 +616,88 @@ def run_large(args):
                                                                       "assemble_ms", "count_ms", "sort_ms",
                                                                       "other_ms")},
                          "autotune": tune, "structure_factor_ms": 1e3 * t_sq, "clocks": clk})
+    print(json.dumps(line), flush=True)
+
+
+# FP32 operations per pair of the all-pairs velocity correlation, counted from
+# its definition: the separation (3), the y image with the sheared x shift (4),
+# the x and z images (3 each) and |R|^2 (3); for a pair inside the cut-off also
+# the square root, the bin scaling and floor, and the product u . u' (6).
+VCORR_OPS_ALL, VCORR_OPS_IN = 16, 6
+FP32_LANES_PER_SM = 128
+
+
+def run_vcorr(args):
+    """Fig. vv on the paper's box (87.6 x 43.6 x 22 lambda^3, N = 17,191, kappa tau = 0):
+    every pair, 120 bins of 0.25 lambda up to 30 lambda.  Value: pairs per second of the
+    whole call through the C ABI with the simulation's state resident (CUDA events on its
+    stream); e2e: the host-array entry (positions and velocities copied in every call)."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    w = synth.PAPER_BOX_VV
+    nbins, rmax = 120, 12.25
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    sim = _sim(ss, w, "mixed", "prev")
+    sim.step(20)
+    for _ in range(args.warmup):
+        sim.velocity_correlation(nbins, rmax)
+    clocks = ClockSampler(None)
+    clocks.start()
+    total, kern = 0.0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sim.velocity_correlation(nbins, rmax)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+        kern += r["pairs_ms"]
+    clk = clocks.stop()
+    pos, v = sim.get_positions(), sim.get_velocities()
+    delta = sim.state()[0]
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    sim.close()
+    pairs = r["pairs"]
+    t_e2e = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        ss.velocity_correlation(pos, v, w.L, delta, kappa, nbins, rmax)
+    t_e2e = (time.perf_counter() - t_e2e) / max(1, args.e2e_steps)
+    ms = total / args.steps
+    kms = kern / args.steps
+    in_range = float(r["counts"].sum()) / pairs
+    ops = pairs * (VCORR_OPS_ALL + VCORR_OPS_IN * in_range)
+    sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = 152 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops / (kms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        p = oracle.Params(n=w.n, L=w.L, kappa=kappa)
+        t0 = time.perf_counter()
+        oracle.velocity_correlation(p, pos, delta, v, nbins, rmax)
+        dt = time.perf_counter() - t0
+        cpu = {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole workload once (N={w.n}, {pairs} pairs), single thread, {dt:.2f} s"}
+    line = {"metric": "velocity cross-correlation pairs/s (Fig. vv, all pairs, exact counts)",
+            "value": pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (simulated state after 20 steps)",
+            "config": {"workload": w.name, "n": w.n, "box": list(w.L), "kappa_tau": w.kappa_tau,
+                       "nbins": nbins, "rmax": rmax, "l2": "flushed between calls (512 MB write)"},
+            "gpu_launches": 6 * args.steps,
+            "roofline": {"kernel": "k_vc_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"152 SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
+                                        "(one FP32 operation per lane per clock)",
+                         "ops_per_pair": VCORR_OPS_ALL + VCORR_OPS_IN * in_range, "avg_launch_ms": kms},
+            "boundary_pairs": r["boundary_pairs"], "pairs_in_range": int(r["counts"].sum()),
+            "e2e": {"value": pairs / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": 2 * w.n * 24,
+                    "d2h_bytes_per_step": nbins * 16 + 16},
+            "clocks": clk, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 

@@ -180,6 +180,40 @@ int sp_structure_factor(sp_sim* sim, int32_t nkx, int32_t nky, int32_t grid, dou
  * The paper defines no stress; this is the pair virial of its pair forces. */
 int sp_stress_xy(sp_sim* sim, double* sigma_xy);
 
+/* Velocity cross-correlation versus distance (§Results, Fig. vv): the average
+ * inter-chain velocity product <v_c . v_c'> / <v_c^2> against |R_cc'|.
+ * u_c = v_c - kappa (y_c - L_y/2) x is the velocity relative to the imposed
+ * flow (the lab velocity at kappa = 0; a Lees-Edwards image carries the same
+ * u).  Every pair c < c' whose minimum-image distance r is below rmax adds
+ * u_c . u_c' to bin k = floor(r nbins / rmax) (nbins - 1 where that rounds up
+ * to nbins) and counts there; the correlation of bin k is
+ * sum_host[k] / (count_host[k] vsq_host) with vsq_host = <|u|^2> over all
+ * particles.  All n^2 / 2 pairs are visited.  The counts are exact (a pair
+ * whose FP32 distance lies near a bin edge, the cut-off or an image boundary
+ * is decided with the FP64 operations of the definition); each product enters
+ * its sum rounded to a fixed point of 2^-20 of the largest |u|^2 (absolute
+ * error per pair below 2^-19 max |u|^2, independent of the order of the sums).
+ * Uses the simulation's current positions and the velocities of its last
+ * solve.  Outputs (host): sum_host[nbins], count_host[nbins], vsq_host; info
+ * may be NULL.  Errors: SP_ERR_INVALID_ARG (NULL pointer, nbins outside
+ * [1, 1024], rmax <= 0), SP_ERR_OOM, SP_ERR_CUDA. */
+typedef struct sp_vcorr_info {
+    double pairs_ms;          /* the all-pairs kernel, CUDA events on the simulation's stream */
+    int64_t boundary_pairs;   /* pairs decided in FP64 */
+    int64_t pairs;            /* pairs visited, n (n - 1) / 2 */
+} sp_vcorr_info;
+int sp_velocity_correlation(sp_sim* sim, int32_t nbins, double rmax, double* sum_host, int64_t* count_host,
+                            double* vsq_host, sp_vcorr_info* info);
+
+/* The same for given positions and velocities (host arrays pos_host[n][3] with
+ * every coordinate in [0, L_a), v_host[n][3]) in the box L3[3] with shift delta
+ * (0 <= delta < L_x) and shear rate kappa, on device `device`.  Allocates and
+ * frees its own device memory.  Errors as above, SP_ERR_INVALID_ARG also for a
+ * position outside the box, SP_ERR_NO_DEVICE. */
+int sp_velocity_correlation_host(int32_t device, int64_t n, const double* L3, double delta, double kappa,
+                                 const double* pos_host, const double* v_host, int32_t nbins, double rmax,
+                                 double* sum_host, int64_t* count_host, double* vsq_host, sp_vcorr_info* info);
+
 /* Per-kernel timing of one time step (a diagnostic for roofline reports).
  * Runs one full step (it advances the simulation exactly like sp_step(sim, 1))
  * with the CG loop driven from the host and a CUDA event pair on the

@@ -77,6 +77,10 @@ class sp_kernel_profile(ctypes.Structure):
                 ("assemble_ms", ctypes.c_double)]
 
 
+class sp_vcorr_info(ctypes.Structure):
+    _fields_ = [("pairs_ms", ctypes.c_double), ("boundary_pairs", ctypes.c_int64), ("pairs", ctypes.c_int64)]
+
+
 class sp_tune_info(ctypes.Structure):
     _fields_ = [("config", ctypes.c_int32), ("gathers_in_flight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 12),
@@ -108,6 +112,8 @@ def load(path: str = LIB_PATH):
             ("sp_solve_velocities", [vp, vp, P(sp_solve_info)]), ("sp_step", [vp, i32, P(sp_step_info)]),
             ("sp_step_host", [vp, vp, ctypes.c_double, i32, vp, P(sp_step_info)]),
             ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
+            ("sp_velocity_correlation", [vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
+            ("sp_velocity_correlation_host", [i32, i64, vp, d, d, vp, vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
@@ -168,6 +174,28 @@ def normals(seed: int, step: int, ids, precision: str = "mixed", device: int = 0
     prec = {"fp64": 0, "mixed": 1}[precision]
     _check(load().sp_normals(device, seed, step, ids.shape[0], _p(ids), prec, _p(out)))
     return out
+
+
+def _vcorr_out(sums, counts, vsq, info) -> dict:
+    with np.errstate(invalid="ignore", divide="ignore"):
+        corr = sums / (counts * vsq)
+    return {"sums": sums, "counts": counts, "vsq": vsq, "correlation": corr, "pairs_ms": info.pairs_ms,
+            "boundary_pairs": info.boundary_pairs, "pairs": info.pairs}
+
+
+def velocity_correlation(pos, v, L, delta: float, kappa: float, nbins: int, rmax: float, device: int = 0) -> dict:
+    """Fig. vv for given positions [n, 3] (each coordinate in [0, L_a)) and velocities [n, 3]:
+    per-bin sums of u_c . u_c', pair counts, <|u|^2> and their ratio (sp_velocity_correlation_host)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    sums, counts = np.zeros(nbins), np.zeros(nbins, dtype=np.int64)
+    vsq = ctypes.c_double()
+    info = sp_vcorr_info()
+    _check(load().sp_velocity_correlation_host(device, pos.shape[0], _p(Lc), float(delta), float(kappa), _p(pos),
+                                               _p(v), int(nbins), float(rmax), _p(sums), _p(counts),
+                                               ctypes.byref(vsq), ctypes.byref(info)))
+    return _vcorr_out(sums, counts, vsq.value, info)
 
 
 NOALLOC_MAX_ROWS = 32768
@@ -376,6 +404,15 @@ class Simulation:
         self._c(load().sp_mpnn_train_step(self._h, float(lr), ctypes.byref(loss),
                                           _p(grad) if grad is not None else None))
         return (loss.value, grad) if want_grad else loss.value
+
+    def velocity_correlation(self, nbins: int, rmax: float) -> dict:
+        """Fig. vv on the current positions and the last solve's velocities (sp_velocity_correlation)."""
+        sums, counts = np.zeros(nbins), np.zeros(nbins, dtype=np.int64)
+        vsq = ctypes.c_double()
+        info = sp_vcorr_info()
+        self._c(load().sp_velocity_correlation(self._h, int(nbins), float(rmax), _p(sums), _p(counts),
+                                               ctypes.byref(vsq), ctypes.byref(info)))
+        return _vcorr_out(sums, counts, vsq.value, info)
 
     def stress_xy(self) -> float:
         v = ctypes.c_double()

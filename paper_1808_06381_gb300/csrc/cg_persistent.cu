@@ -997,13 +997,19 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 // arrive under the sums)
                 const float4 rh = B.rdf[2 * row[u]], rl = B.rdf[2 * row[u] + 1];
                 const dfloat dg{B.diag32[row[u]], B.diag32lo[row[u]]};
-                dfloat s[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                // A d in double-float: each product of a high weight part splits
+                // exactly (pr + e); the pr are summed by TwoSum, every low-order
+                // term (e, the low part's product, the TwoSum errors) goes into
+                // one FP32 compensation
+                float sh[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f};
                 auto add = [&](float wh, float wl, float4 dj) {
                     const float dd[3] = {dj.x, dj.y, dj.z};
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const float pr = __fmul_rn(wh, dd[a]);
-                        s[a] = df_add(s[a], dfloat{pr, fmaf(wl, dd[a], fmaf(wh, dd[a], -pr))});
+                        const dfloat t = two_sum(sh[a], pr);
+                        sh[a] = t.hi;
+                        sc[a] = __fadd_rn(sc[a], __fadd_rn(t.lo, fmaf(wl, dd[a], fmaf(wh, dd[a], -pr))));
                     }
                 };
                 // loads in batches (one latency per batch): the low parts of the
@@ -1044,6 +1050,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
                     for (int k = 0; k < kResHalo; ++k) add(wh[k], wl[k], dj[k]);
                 }
+                dfloat s[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) s[a] = two_sum(sh[a], sc[a]);
                 const dfloat al{P.alpha_hi, P.alpha_lo};
                 const dfloat ro[3] = {{rh.x, rl.x}, {rh.y, rl.y}, {rh.z, rl.z}};
                 dfloat rn[3];

@@ -786,4 +786,33 @@ cudaError_t run_structure_factor(const KParams& P, const DevBuffers& B, double d
                                  const double* twiddle_dev, unsigned long long* grid_dev, double2* A_dev,
                                  double* S_dev, double* qx_dev, double* qy_dev, cudaStream_t s);
 
+// vcorr.cu: velocity cross-correlation versus distance (Fig. vv)
+constexpr int kVcMaxBins = 1024;
+struct VcBuffers {
+    double* pos_n3 = nullptr;   // [n][3] positions (particle order of the caller)
+    double* v_n3 = nullptr;     // [n][3] velocities
+    float4* p4 = nullptr;       // [n] FP32 positions
+    float4* u4 = nullptr;       // [n] FP32 velocities relative to the imposed flow
+    unsigned long long* sum = nullptr;   // [kVcMaxBins] fixed-point sums of the products
+    unsigned long long* cnt = nullptr;   // [kVcMaxBins] pair counts
+    int2* band = nullptr;       // [band_cap] pairs decided in FP64
+    unsigned int* misc = nullptr;        // [4] listed pairs, bits of max |u|^2, position flag
+    double* part = nullptr;     // per-block sums of |u|^2
+    double* scal = nullptr;     // [2] <|u|^2>, fixed-point scale
+    int2* tiles = nullptr;      // (I, first J) of every block
+    long long n_cap = 0, band_cap = 0, tiles_cap = 0, tiles_n = 0, tiles_for = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+struct VcStats {
+    double pairs_ms;            // the all-pairs kernel (CUDA events on the caller's stream)
+    long long band_pairs;       // pairs decided in FP64
+    long long blocks;           // blocks of the all-pairs kernel
+};
+void vc_free(VcBuffers& V);
+cudaError_t vc_reserve(VcBuffers& V, long long n);
+// Inputs in V.pos_n3 / V.v_n3 (n rows, positions in [0, L)); results to the host.
+int run_velocity_correlation(VcBuffers& V, long long n, const double L[3], double delta, double kappa, int nbins,
+                             double rmax, cudaStream_t s, double* sum_host, long long* cnt_host, double* vsq_host,
+                             VcStats* stats, const char** err);
+
 }  // namespace ss

@@ -498,6 +498,7 @@ int sp_sim_destroy(sp_sim* s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     free_graphs(s);
     DevBuffers& B = s->B;
+    vc_free(s->vc);
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
@@ -1281,6 +1282,69 @@ int sp_normals(int32_t device, uint64_t seed, uint64_t step, int64_t count, cons
     cudaFree(ids);
     cudaFree(out);
     cudaFree(tab);
+    return rc;
+}
+
+static void vc_info(const VcStats& st, long long n, sp_vcorr_info* info)
+{
+    if (!info) return;
+    info->pairs_ms = st.pairs_ms;
+    info->boundary_pairs = st.band_pairs;
+    info->pairs = n * (n - 1) / 2;
+}
+
+int sp_velocity_correlation(sp_sim* s, int32_t nbins, double rmax, double* sum_host, int64_t* count_host,
+                            double* vsq_host, sp_vcorr_info* info)
+{
+    if (!s || !sum_host || !count_host || !vsq_host) return SP_ERR_INVALID_ARG;
+    if (nbins < 1 || nbins > kVcMaxBins || !(rmax > 0.0) || !std::isfinite(rmax)) {
+        s->err = "velocity correlation: needs 1 <= nbins <= 1024 and rmax > 0";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    SS_TRY(read_state(s));
+    const long long n = s->kp.n;
+    if (vc_reserve(s->vc, n) != cudaSuccess) {
+        cudaGetLastError();
+        s->err = "velocity correlation: device allocation failed";
+        return SP_ERR_OOM;
+    }
+    // positions and the last solve's velocities, both in particle-id order
+    launch_scatter_by_id(s->B.pos_s, s->kp.npad, s->B.id_s, s->kp.n, s->vc.pos_n3, s->stream);
+    launch_scatter_by_id(s->B.x, s->kp.npad, s->B.id_w, s->kp.n, s->vc.v_n3, s->stream);
+    VcStats st{};
+    const char* e = nullptr;
+    const int rc = run_velocity_correlation(s->vc, n, s->p.L, s->st_host->delta, s->kp.kappa, nbins, rmax, s->stream,
+                                            sum_host, reinterpret_cast<long long*>(count_host), vsq_host, &st, &e);
+    if (e) s->err = e;
+    if (rc == SP_OK) vc_info(st, n, info);
+    return rc;
+}
+
+int sp_velocity_correlation_host(int32_t device, int64_t n, const double* L3, double delta, double kappa,
+                                 const double* pos_host, const double* v_host, int32_t nbins, double rmax,
+                                 double* sum_host, int64_t* count_host, double* vsq_host, sp_vcorr_info* info)
+{
+    if (n < 1 || !L3 || !pos_host || !v_host || !sum_host || !count_host || !vsq_host) return SP_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ERR_NO_DEVICE;
+    }
+    VcBuffers V{};
+    int rc = SP_OK;
+    if (vc_reserve(V, n) != cudaSuccess) rc = SP_ERR_OOM;
+    if (rc == SP_OK && (cudaMemcpy(V.pos_n3, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+                        cudaMemcpy(V.v_n3, v_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = SP_ERR_CUDA;
+    VcStats st{};
+    const char* e = nullptr;
+    if (rc == SP_OK)
+        rc = run_velocity_correlation(V, n, L3, delta, kappa, nbins, rmax, 0, sum_host,
+                                      reinterpret_cast<long long*>(count_host), vsq_host, &st, &e);
+    if (e) sp_global_error() = e;
+    if (rc == SP_OK) vc_info(st, n, info);
+    cudaGetLastError();
+    vc_free(V);
     return rc;
 }
 

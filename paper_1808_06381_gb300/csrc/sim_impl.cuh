@@ -34,6 +34,7 @@ struct sp_sim {
     bool mp_alloc = false;
     bool learned = false;         // run the network before every solve of a step
     int mp_t = 0;                 // Adam step counter
+    ss::VcBuffers vc{};           // velocity correlation (allocated by its first call)
     std::string err;
 };
 

@@ -93,6 +93,14 @@ LEARNED = cubic("learned-n262144", 262144, 0.5, 2000, 1e-8, SEED_BASE + 4)
 LARGE = cubic("large-n4194304", 4194304, 0.5, 10000, 1e-8, SEED_BASE + 5)
 
 
+# The paper's box for its result figures, 87.6 x 43.6 x 22 lambda^3 (§Results),
+# in units of r_c (lambda = 0.408539 r_c from the 5 % truncation at r_c), at
+# density 3 per r_c^3: 17,191 particles; kappa tau = 0 as for Fig. vv.
+PAPER_BOX_L = (35.79, 17.81, 8.99)
+PAPER_BOX_VV = Workload(name="paper-box-n17191", n=17191, L=PAPER_BOX_L, kappa_tau=0.0, steps=200, tol=1e-8,
+                        seed=SEED_BASE + 6)
+
+
 def batch_replicas(count: int = 64, seed: int = SEED_BASE + 3):
     """Ensemble of replicas: N log-uniform in [8192, 131072], kappa*tau log-uniform in [0.01, 1]."""
     rng = np.random.Generator(np.random.PCG64(seed))

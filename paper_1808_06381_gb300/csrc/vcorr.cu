@@ -7,8 +7,9 @@
 // carries the same u).  Every pair c < c' whose minimum-image distance r is
 // below rmax adds u_c . u_c' to bin floor(r nbins / rmax) and counts there.
 //
-// All pairs are visited (n^2 / 2): one block per 256 particles c and a run of
-// 256-particle tiles of c' staged in shared memory, every pair in FP32.  The
+// All pairs are visited (n^2 / 2): one block per 512 particles c (two per
+// thread) and a run of 256-particle tiles of c' staged in shared memory, every
+// pair in FP32.  The
 // decisions that make the result exact are taken in FP64 where FP32 could get
 // them wrong: a pair whose FP32 image index, bin or cut-off test lies within
 // the FP32 error bound of a boundary is appended to a list, and a second
@@ -32,7 +33,13 @@ namespace {
 constexpr int kVcTile = 256;               // particles per tile; threads per block
 constexpr int kVcWarps = kVcTile / 32;
 constexpr int kVcPrepBlocks = 1024;        // vsq partial sums
-constexpr float kU = 5.9604644775390625e-8f;   // 2^-24, the FP32 unit roundoff
+
+// rint(x) for |x| < 2^22 by the 1.5 2^23 shift (two FP32 additions instead of
+// a rounding instruction); ties go to even like rintf
+__device__ __forceinline__ float rint_shift(float x)
+{
+    return __fsub_rn(__fadd_rn(x, 12582912.f), 12582912.f);
+}
 
 struct VcConst {
     int n, nbins, ntile, chunk;
@@ -41,8 +48,9 @@ struct VcConst {
     float r_band;              // FP32 |R| > r_band: decided in FP64
     float inv_f;               // nbins / rmax
     float eb;                  // FP32 bin position within eb of an edge: decided in FP64
-    float tie;                 // |ratio - rint(ratio)| > tie: image index decided in FP64
+    float half[3];             // |component| > half[a] (L_a/2 less the FP32 error): image decided in FP64
     double delta, kappa, rmax2, inv;
+    double invL[3];            // 1 / L_a (FP64)
 };
 
 // FP32 copies of the positions and of u; FP64 sums of |u|^2 per block and the
@@ -104,6 +112,50 @@ __global__ void k_vc_scale(int n, int nparts, const double* __restrict__ part, c
     }
 }
 
+// One pair (i, j), i < j: the FP32 minimum image and distance; the pair goes
+// to the per-warp histogram, or to the FP64 list when one of its decisions
+// lies within the FP32 error bound of a boundary.
+__device__ __forceinline__ void vc_pair(const VcConst& C, float4 pi, float4 ui, int i, float4 pj,
+                                        const float4* su, int jj, int j, float S, unsigned long long* hsw,
+                                        int2* band, unsigned int* band_n, unsigned int band_cap)
+{
+    float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+    const float ny = rint_shift(dy * C.iLf[1]);
+    dy = fmaf(-ny, C.Lf[1], dy);
+    dx = fmaf(-ny, C.df, dx);
+    dx = fmaf(-rint_shift(dx * C.iLf[0]), C.Lf[0], dx);
+    dz = fmaf(-rint_shift(dz * C.iLf[2]), C.Lf[2], dz);
+    // an image index taken within the FP32 error of a tie leaves that
+    // component within the same error of half the box edge
+    const bool tie = fabsf(dx) > C.half[0] || fabsf(dy) > C.half[1] || fabsf(dz) > C.half[2];
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (!(j > i)) return;
+    bool push = tie;
+    if (!tie && r2 < C.r2_hi) {
+        // |R| from the reciprocal square root (within 3 ulp; the bands allow for it)
+        const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+        const float t = r * C.inv_f;
+        const float tk = __fadd_rd(t, 8388608.f);   // 2^23 + floor(t) (0 <= t < 2^23)
+        const float fr = t - (tk - 8388608.f);      // exact
+        if (r > C.r_band || fr < C.eb || fr > 1.f - C.eb) {
+            push = true;
+        } else {
+            const int k = __float_as_int(tk) - 0x4B000000;
+            const float4 uj = su[jj];
+            const float dot = fmaf(ui.x, uj.x, fmaf(ui.y, uj.y, ui.z * uj.z));
+            // round(dot S) by the 1.5 2^23 shift (|dot S| < 2^21)
+            const int q = __float_as_int(fmaf(dot, S, 12582912.f)) - 0x4B400000;
+            atomicAdd(hsw + k, (1ull << 40) + (unsigned long long)(long long)q);
+        }
+    }
+    if (push) {   // rare (a few per thousand pairs)
+        const unsigned int idx = atomicAdd(band_n, 1u);
+        if (idx < band_cap) band[idx] = make_int2(i, j);
+    }
+}
+
+// Block (I, J0): particles i = 512 I + tid and 512 I + 256 + tid against the
+// c' tiles J0 .. J0 + chunk - 1 (256 particles each).
 __global__ void __launch_bounds__(kVcTile) k_vc_pairs(VcConst C, const float4* __restrict__ p4,
                                                         const float4* __restrict__ u4, const int2* __restrict__ tiles,
                                                         const double* __restrict__ scal,
@@ -116,18 +168,20 @@ __global__ void __launch_bounds__(kVcTile) k_vc_pairs(VcConst C, const float4* _
     float4* sp = vc_smem;                  // [kVcTile] positions of the c' tile
     float4* su = sp + kVcTile;             // [kVcTile] their u
     // per-warp histograms, one 64-bit word per bin: count 2^40 + fixed-point sum
-    // (a warp adds at most 32 x 16 x 256 = 2^17 pairs to a bin, so the count
-    // fits the top 24 bits and the sum, below 2^17 2^21 in magnitude, the low
-    // 40 bits in two's complement)
+    // (a warp adds at most 32 x 2 x 16 x 256 = 2^18 pairs to a bin, so the count
+    // fits the top 24 bits and the sum, below 2^18 (2^20 + 1) in magnitude, the
+    // low 40 bits in two's complement)
     unsigned long long* hs = reinterpret_cast<unsigned long long*>(su + kVcTile);   // [warps][nbins]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     for (int k = tid; k < kVcWarps * C.nbins; k += kVcTile) hs[k] = 0ull;
     const int2 tb = tiles[blockIdx.x];
     const int I = tb.x, J0 = tb.y, J1 = min(C.ntile - 1, J0 + C.chunk - 1);
-    const int i = I * kVcTile + tid;
-    const bool has_i = i < C.n;
-    const float4 pi = has_i ? p4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 ui = has_i ? u4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int i0 = I * 2 * kVcTile + tid, i1 = i0 + kVcTile;
+    // a particle past n pairs with no j (index n + 2^30 is above every j)
+    const int e0 = i0 < C.n ? i0 : (1 << 30), e1 = i1 < C.n ? i1 : (1 << 30);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pi0 = i0 < C.n ? p4[i0] : z4, ui0 = i0 < C.n ? u4[i0] : z4;
+    const float4 pi1 = i1 < C.n ? p4[i1] : z4, ui1 = i1 < C.n ? u4[i1] : z4;
     const float S = (float)scal[1];
     unsigned long long* hsw = hs + warp * C.nbins;
     for (int J = J0; J <= J1; ++J) {
@@ -139,57 +193,12 @@ __global__ void __launch_bounds__(kVcTile) k_vc_pairs(VcConst C, const float4* _
         }
         __syncthreads();
         const int jn = min(kVcTile, C.n - J * kVcTile);
-#pragma unroll 4
-        for (int jj = 0; jj < jn; ++jj) {   // uniform over the block: every lane reaches the ballot
+#pragma unroll 2
+        for (int jj = 0; jj < jn; ++jj) {
             const int j = J * kVcTile + jj;
             const float4 pj = sp[jj];
-            float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float ry = dy * C.iLf[1];
-            const float ny = rintf(ry);
-            bool tie = fabsf(ry - ny) > C.tie;
-            dy = fmaf(-ny, C.Lf[1], dy);
-            dx = fmaf(-ny, C.df, dx);
-            const float rx = dx * C.iLf[0];
-            const float mx = rintf(rx);
-            tie |= fabsf(rx - mx) > C.tie;
-            dx = fmaf(-mx, C.Lf[0], dx);
-            const float rz = dz * C.iLf[2];
-            const float mz = rintf(rz);
-            tie |= fabsf(rz - mz) > C.tie;
-            dz = fmaf(-mz, C.Lf[2], dz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool push = false;
-            if (has_i && j > i) {
-                if (tie) {
-                    push = true;
-                } else if (r2 < C.r2_hi) {
-                    const float r = sqrtf(r2);
-                    const float t = r * C.inv_f;
-                    const float tk = __fadd_rd(t, 8388608.f);   // 2^23 + floor(t) (0 <= t < 2^23)
-                    const float fr = t - (tk - 8388608.f);      // exact
-                    if (r > C.r_band || fr < C.eb || fr > 1.f - C.eb) {
-                        push = true;
-                    } else {
-                        const int k = __float_as_int(tk) - 0x4B000000;
-                        const float4 uj = su[jj];
-                        const float dot = fmaf(ui.x, uj.x, fmaf(ui.y, uj.y, ui.z * uj.z));
-                        // round(dot S) by the 1.5 2^23 shift (|dot S| < 2^21)
-                        const int q = __float_as_int(fmaf(dot, S, 12582912.f)) - 0x4B400000;
-                        atomicAdd(hsw + k, (1ull << 40) + (unsigned long long)(long long)q);
-                    }
-                }
-            }
-            const unsigned int m = __ballot_sync(0xffffffffu, push);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned int base = 0u;
-                if (lane == leader) base = atomicAdd(band_n, (unsigned int)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (push) {
-                    const unsigned int idx = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
-                    if (idx < band_cap) band[idx] = make_int2(i, j);
-                }
-            }
+            vc_pair(C, pi0, ui0, e0, pj, su, jj, j, S, hsw, band, band_n, band_cap);
+            vc_pair(C, pi1, ui1, e1, pj, su, jj, j, S, hsw, band, band_n, band_cap);
         }
     }
     __syncthreads();
@@ -209,6 +218,32 @@ __global__ void __launch_bounds__(kVcTile) k_vc_pairs(VcConst C, const float4* _
     }
 }
 
+// round(a / L) as the definition computes it (quotient rounded to FP64, then
+// rounded half away from zero), with the division taken only where the
+// product by 1/L (within 2^-50 of the quotient for |a / L| < 2) lies near a
+// half-integer.
+__device__ __forceinline__ double round_quotient(double a, double L, double invL)
+{
+    const double q = __dmul_rn(a, invL);
+    const double f = fabs(q - trunc(q));
+    return fabs(f - 0.5) < 0x1p-46 ? round(__ddiv_rn(a, L)) : round(q);
+}
+
+// The Lees-Edwards minimum image with every operation of the definition
+// (the same results as min_image()).
+__device__ __forceinline__ void vc_min_image(const KParams& P, const VcConst& C, double xi, double yi, double zi,
+                                             double xj, double yj, double zj, double& dx, double& dy, double& dz)
+{
+    dx = __dsub_rn(xi, xj);
+    dy = __dsub_rn(yi, yj);
+    dz = __dsub_rn(zi, zj);
+    const double n = round_quotient(dy, P.L[1], C.invL[1]);
+    dy = __dsub_rn(dy, __dmul_rn(n, P.L[1]));
+    dx = __dsub_rn(dx, __dmul_rn(n, C.delta));
+    dx = __dsub_rn(dx, __dmul_rn(P.L[0], round_quotient(dx, P.L[0], C.invL[0])));
+    dz = __dsub_rn(dz, __dmul_rn(P.L[2], round_quotient(dz, P.L[2], C.invL[2])));
+}
+
 // The listed pairs with the FP64 operations of the definition (the minimum
 // image rounded exactly as written, |R|^2 < rmax^2, floor(sqrt(|R|^2) nbins /
 // rmax)); products in FP64, rounded to the same fixed point.
@@ -223,8 +258,8 @@ __global__ void k_vc_band(VcConst C, KParams P, const double* __restrict__ pos, 
         const int2 pr = band[t];
         const int i = pr.x, j = pr.y;
         double dx, dy, dz;
-        min_image(P, C.delta, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pos[3 * j],
-                  pos[3 * j + 1], pos[3 * j + 2], dx, dy, dz);
+        vc_min_image(P, C, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], pos[3 * j], pos[3 * j + 1], pos[3 * j + 2],
+                     dx, dy, dz);
         const double r2 = sq_norm_exact(dx, dy, dz);
         if (!(r2 < C.rmax2)) continue;
         long long k = (long long)floor(__dmul_rn(__dsqrt_rn(r2), C.inv));
@@ -327,7 +362,7 @@ int run_velocity_correlation(VcBuffers& V, long long n, const double L[3], doubl
     C.n = (int)n;
     C.nbins = nbins;
     C.ntile = (int)((n + kVcTile - 1) / kVcTile);
-    C.chunk = C.ntile <= 256 ? 4 : 16;   // at most 16 (the packed histogram words)
+    C.chunk = C.ntile <= 128 ? 1 : (C.ntile <= 256 ? 4 : 16);   // at most 16 (the packed histogram words)
     for (int a = 0; a < 3; ++a) {
         C.Lf[a] = (float)L[a];
         C.iLf[a] = (float)(1.0 / L[a]);
@@ -335,15 +370,19 @@ int run_velocity_correlation(VcBuffers& V, long long n, const double L[3], doubl
     C.df = (float)delta;
     // E bounds |r_FP32 - r| for positions in [0, L): each FP32 operation rounds
     // by at most 2^-24 of a result no larger than 2 L_x (x), L_y, L_z, plus the
-    // relative roundings of the squares, the square root and the scaling.
+    // relative roundings of the squares, the approximate square root (3 ulp)
+    // and the scaling.
     const double u = 5.9604644775390625e-8;
-    const double E = u * (20.0 * (L[0] + L[1] + L[2]) + 8.0 * rmax);
+    const double E = u * (20.0 * (L[0] + L[1] + L[2]) + 16.0 * rmax);
     C.r2_hi = nextafterf((float)((rmax + 2.0 * E) * (rmax + 2.0 * E)), INFINITY);
     C.r_band = nextafterf((float)(rmax - 2.0 * E), -INFINITY);
     C.inv = (double)nbins / rmax;
     C.inv_f = (float)C.inv;
     C.eb = (float)std::min(0.5, 2.0 * E * C.inv + 8.0 * u * nbins + 4.0 * u);
-    C.tie = 0.5f - 64.f * kU;
+    for (int a = 0; a < 3; ++a) {
+        C.half[a] = (float)(L[a] * (0.5 - 64.0 * u));
+        C.invL[a] = 1.0 / L[a];
+    }
     C.delta = delta;
     C.kappa = kappa;
     C.rmax2 = rmax * rmax;
@@ -353,10 +392,12 @@ int run_velocity_correlation(VcBuffers& V, long long n, const double L[3], doubl
     P.L[1] = L[1];
     P.L[2] = L[2];
 
-    // tile pairs (I, first J of a run of `chunk` tiles), J >= I
+    // blocks (I, first J of a run of `chunk` c' tiles): I covers particles
+    // [512 I, 512 I + 512), so the tiles below 2 I hold no partner j > i
     std::vector<int2> tl;
-    for (int I = 0; I < C.ntile; ++I)
-        for (int J = I; J < C.ntile; J += C.chunk) tl.push_back(make_int2(I, J));
+    const int ni = (int)((n + 2 * kVcTile - 1) / (2 * kVcTile));
+    for (int I = 0; I < ni; ++I)
+        for (int J = 2 * I; J < C.ntile; J += C.chunk) tl.push_back(make_int2(I, J));
     if ((long long)tl.size() > V.tiles_cap) {
         V.tiles_cap = 0;
         V.tiles_n = 0;

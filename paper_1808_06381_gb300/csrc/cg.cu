@@ -655,6 +655,11 @@ int launch_cg_init(const KParams& P, DevBuffers& B, bool from_x, bool mixed, Lau
     return 1;
 }
 
+void launch_cg_split_x(const KParams& P, DevBuffers& B, Launch L)
+{
+    k32_split_x<<<wave_grid(P.n, 8, L), kBlock, 0, L.stream>>>(P, B);
+}
+
 void launch_cg_spmv(const KParams& P, DevBuffers& B, bool mixed, Launch L, int probe)
 {
     if (mixed)

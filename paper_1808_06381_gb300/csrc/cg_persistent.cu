@@ -35,7 +35,7 @@ struct PShared {
     float2 df[32];
     double d[32];
     float2 dfk[2][32];   // per-warp sums of the grid reductions
-    double dk[2][32];
+    double dk[4][32];
     double bcast[4];
     int flag;
     // decided by thread 0 (FP64 scalars once per block, not once per thread)
@@ -179,7 +179,7 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
                                                const double (&v)[K], double* partials, double (&out)[K],
                                                int bid, int nb)
 {
-    static_assert(K <= 2, "two values at most");
+    static_assert(K <= 4, "four values at most");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double w[K];
 #pragma unroll
@@ -610,9 +610,10 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                                                RShared& rs, float4* dyn, int smem_bytes)
 {
     DevState* st = B.st;
+    const bool fused = P.fused_init != 0;   // the initial residual is formed here
     if (threadIdx.x == 0) sh.flag = 0;
     __syncthreads();
-    if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
+    if (st->error | st->overflow | (fused ? 0 : st->done)) return;   // uniform: set before the launch
     unsigned int gen = 0u;
     if (threadIdx.x == 0) gen = *(volatile unsigned int*)&st->bar_gen;
 
@@ -724,7 +725,10 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             ho += 32 * rs.nhalo[c];
         }
         rs.mode = (lo <= cap && ho <= hcap) ? 0 : 1;
-        if (rs.mode) atomicAdd(&st->res_offchip, 1);
+        if (fused)   // summed by block 0 at the end (the counter is not reset before this launch)
+            B.partials[3 * kMaxPartials + bid] = (double)rs.mode;
+        else if (rs.mode)
+            atomicAdd(&st->res_offchip, 1);
     }
     __syncthreads();
     const bool onchip = rs.mode == 0;
@@ -736,8 +740,39 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
     }
 
+    // the initial residual of the fused form, row by row: r = b - (A_ii x0 -
+    // alpha s) from the row's double-float sum s (x0 from xdf), or r = b with
+    // x = 0; r4, rdf and the sums ||b||^2, r.r, r.D^-1 r
+    double bb = 0.0, rr0 = 0.0, rz0 = 0.0;
+    auto init_row = [&](int rw, const dfloat (&sd)[3]) {
+        dfloat rd[3];
+        if (P.fused_init == 2) {
+            residual_df(P, B, rw, sd, rd);
+        } else {
+            const float4 bh = B.bdf[2 * rw], bl = B.bdf[2 * rw + 1];
+            rd[0] = dfloat{bh.x, bl.x};
+            rd[1] = dfloat{bh.y, bl.y};
+            rd[2] = dfloat{bh.z, bl.z};
+            B.xdf[2 * rw] = make_float4(0.f, 0.f, 0.f, 0.f);
+            B.xdf[2 * rw + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) B.x[c * np + rw] = 0.0;
+        }
+        const float di = B.dinv32[rw];
+        const float4 bh = B.bdf[2 * rw];
+        bb += (double)(bh.x * bh.x + bh.y * bh.y + bh.z * bh.z);
+        const float rsq = rd[0].hi * rd[0].hi + rd[1].hi * rd[1].hi + rd[2].hi * rd[2].hi;
+        B.r4[rw] = make_float4(rd[0].hi, rd[1].hi, rd[2].hi, di);
+        B.rdf[2 * rw] = make_float4(rd[0].hi, rd[1].hi, rd[2].hi, 0.f);
+        B.rdf[2 * rw + 1] = make_float4(rd[0].lo, rd[1].lo, rd[2].lo, 0.f);
+        rr0 += (double)rsq;
+        rz0 += (double)(di * rsq);
+    };
+    const bool from_x = P.fused_init == 2;
+
     // ---- set-up 3: place the entries (read in slot order; each row's lists
-    // go to the chunk and lane of the thread that owns the row)
+    // go to the chunk and lane of the thread that owns the row); in the fused
+    // form the same pass sums A x0 for the initial residual
     if (onchip) {
         for (int w = wb + g; w < we; w += BS / 256) {
             const int slot = w * 256 + t;
@@ -751,6 +786,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const int hb = rs.hoff[c] + (owner & 31);
             const int e1 = B.chunk_off[(slot >> 5) + 1];
             int kl = 0, kh = 0;
+            dfloat sd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int eb = B.chunk_off[slot >> 5] + (slot & 31); eb < e1; eb += 32 * KS) {
                 int j[KS];
                 float v[KS], vl[KS];
@@ -760,6 +796,24 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     j[u] = e < e1 ? ld_stream(B.col + e) : 0;
                     v[u] = e < e1 ? ld_stream(B.val32 + e) : 0.f;
                     vl[u] = e < e1 ? ld_stream(B.val32lo + e) : 0.f;
+                }
+                if (from_x) {   // the row's sum of w_ij x0_j (as row_sum_df)
+                    float4 xh[KS], xl[KS];
+#pragma unroll
+                    for (int u = 0; u < KS; ++u) {
+                        xh[u] = xl[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (v[u] != 0.f) {
+                            xh[u] = B.xdf[2 * j[u]];
+                            xl[u] = B.xdf[2 * j[u] + 1];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < KS; ++u) {
+                        const dfloat wd{v[u], vl[u]};
+                        sd[0] = df_add(sd[0], df_mul(wd, dfloat{xh[u].x, xl[u].x}));
+                        sd[1] = df_add(sd[1], df_mul(wd, dfloat{xh[u].y, xl[u].y}));
+                        sd[2] = df_add(sd[2], df_mul(wd, dfloat{xh[u].z, xl[u].z}));
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < KS; ++u) {
@@ -787,9 +841,67 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 B.hval[hb + 32 * kh] = 0.f;
                 B.hlo[hb + 32 * kh] = 0.f;
             }
+            if (fused) init_row(row, sd);
         }
     }
     __syncthreads();   // sinv (in zbuf) is read until here
+
+    // ---- the initial residual (fused form): r = b - A x0 in double-float, or
+    // r = b with x = 0, for the block's rows in slot order, with ||b||^2,
+    // r.r and r.D^-1 r summed over the grid (as the initial-residual kernel)
+    bool start_done = false;
+    double init_tot[3] = {0.0, 0.0, 0.0};
+    if (fused) {
+        if (threadIdx.x == 0) {
+            sh.status = SP_OK;
+            sh.last_res = 0.0;
+        }
+        if (!onchip) {   // the placement pass did not run: the rows' sums here
+            for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
+                const int slot = w * 256 + chunk_lane(k, t);
+                const int rw = B.slot_row[slot];
+                if (rw < 0) continue;
+                dfloat sd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                if (from_x)
+                    row_sum_df<KC>(B.col, B.val32, B.val32lo, B.xdf, B.chunk_off[slot >> 5] + (slot & 31),
+                                   B.chunk_off[(slot >> 5) + 1], sd);
+                init_row(rw, sd);
+            }
+        }
+        const double v[3] = {bb, rr0, rz0};
+        if (!grid_allreduce<3>(st, gen, sh, v, B.partials, init_tot, bid, nb)) start_done = true;
+        if (threadIdx.x == 0 && !start_done) {
+            sh.status = SP_OK;
+            sh.action = 0;
+            sh.last_res = 1.0;
+            const double bb2 = init_tot[0], rr2 = init_tot[1];
+            if (!isfinite(bb2) || !isfinite(rr2)) {
+                sh.status = SP_ERR_NONFINITE;
+                sh.action = 2;
+            } else if (bb2 == 0.0) {
+                sh.action = 2;   // b = 0: the solution is v = 0 (written by the finishing kernel)
+                sh.last_res = 0.0;
+            } else if (rr2 <= P.tol2 * bb2) {
+                sh.action = 2;   // x0 already meets the tolerance (exact r)
+                sh.last_res = sqrt(rr2 / bb2);
+            }
+            if (bid == 0) {
+                st->bnorm2 = bb2;
+                st->rr = rr2;
+                st->rr_restart = rr2;
+                st->rho = init_tot[2];
+                st->beta = 0.0;
+                st->iter = 0;
+                st->restarts = 0;
+                st->check_true = 0;
+                st->status = 0;
+                st->zero_b = (isfinite(bb2) && bb2 == 0.0) ? 1 : 0;
+                st->done = 0;
+            }
+        }
+        __syncthreads();
+        if (start_done || sh.action == 2) start_done = true;
+    }
 
     // ---- load r and D^-1 of the own rows
     float r[RPT][3], dv[RPT], p[RPT][3], q[RPT][3], d[RPT][3];
@@ -810,18 +922,24 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         zbuf[row[u] - rb] = make_float4(r4.w * r4.x, r4.w * r4.y, r4.w * r4.z, 0.f);
     }
     if (threadIdx.x == 0) {
-        sh.rho = st->rho;
-        sh.rr_restart = st->rr_restart;
-        sh.bnorm2 = st->bnorm2;
-        sh.last_res = st->last_res;
+        if (fused) {
+            sh.rho = init_tot[2];
+            sh.rr_restart = init_tot[1];
+            sh.bnorm2 = init_tot[0];
+        } else {
+            sh.rho = st->rho;
+            sh.rr_restart = st->rr_restart;
+            sh.bnorm2 = st->bnorm2;
+            sh.last_res = st->last_res;
+            sh.status = SP_OK;
+        }
         sh.iter = 0;
         sh.restarts = 0;
-        sh.status = SP_OK;
         sh.beta_f = 0.f;
     }
     __syncthreads();
 
-    for (;;) {
+    while (!start_done) {
         // ---- SpMV with the fused direction update; p.q
         dfloat pq{0.f, 0.f};
         const float betaf = sh.beta_f;
@@ -1140,10 +1258,17 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             __syncthreads();
         }
     }
+    if (!(fused && sh.iter == 0)) {   // a solve that met the tolerance at x0 keeps x0 as it was
 #pragma unroll
-    for (int u = 0; u < RPT; ++u)
-        if (row[u] >= 0) store_x64(B, np, row[u]);
+        for (int u = 0; u < RPT; ++u)
+            if (row[u] >= 0) store_x64(B, np, row[u]);
+    }
     if (bid == 0 && threadIdx.x == 0) {
+        if (fused) {   // every block wrote its mode before the first grid reduction
+            int off = 0;
+            for (int b = 0; b < nb; ++b) off += B.partials[3 * kMaxPartials + b] != 0.0 ? 1 : 0;
+            st->res_offchip = off;
+        }
         st->iter = sh.iter;
         st->restarts = sh.restarts;
         st->last_res = sh.last_res;
@@ -1312,6 +1437,11 @@ bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L
     pocc_init();
     if (k < 0 || k >= kPersistentConfigs || g_pcfg[k].occ < 1) return false;
     return !g_pcfg[k].resident || resident_fits(g_pcfg[k], P, B, L);
+}
+
+bool cg_persistent_on_chip(const KParams& P, const DevBuffers& B, Launch L)
+{
+    return cfg_of(P, B, L).resident != 0;
 }
 
 int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L)

@@ -52,6 +52,7 @@ struct KParams {
     float akl_hi, akl_lo;       // alpha kappa L_y
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
+    int fused_init;     // on-chip solve: 0 after the initial-residual kernel; 1 forms r = b itself (x0 = 0), 2 r = b - A x0
 };
 
 constexpr int kPersistentConfigs = 10;
@@ -749,6 +750,11 @@ int cg_kernels_per_iteration(bool mixed);
 void cg_prepare();   // resident-block counts of the solver kernels (once per process)
 // cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
+// Whether the persistent solve of this system runs on chip (and so can form
+// its initial residual itself: launch it with fused_init set and without
+// launch_cg_init, after launch_cg_split_x where it starts from x).
+bool cg_persistent_on_chip(const KParams& P, const DevBuffers& B, Launch L);
+void launch_cg_split_x(const KParams& P, DevBuffers& B, Launch L);
 int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L);
 // Tile configuration k of the persistent solver: gathers in flight, blocks per
 // SM, next batch requested during the current gathers (1) or not (0), threads

@@ -309,6 +309,22 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
     KParams& P = s->kp;
     DevBuffers& B = s->B;
     Launch L = launch_of(s, cs);
+    if (mixed(s) && s->persistent && cg_persistent_on_chip(P, B, L)) {
+        // the on-chip solve forms its initial residual itself (one pass over
+        // its rows' entries, beside placing them in shared memory)
+        KParams Pf = P;
+        Pf.fused_init = from_x ? 2 : 1;
+        if (from_x) {
+            launch_cg_split_x(P, B, L);
+            *launches += 1;
+        }
+        SS_CUDA(launch_cg32_persistent(Pf, B, L));
+        *launches += 1;
+        launch_cg_finish(P, B, true, L);
+        launch_stress(P, B, true, L);
+        *launches += 2;
+        return SP_OK;
+    }
     *launches += launch_cg_init(P, B, from_x, mixed(s), L);
     if (mixed(s) && s->persistent) {
         SS_CUDA(launch_cg32_persistent(P, B, L));

@@ -146,3 +146,34 @@ def test_resident_steps_are_deterministic_and_follow_config_zero():
     d -= np.round(d / L) * L
     # each step's velocities agree within cond * tol: |dx| <= 3 dt |dv| ~ 1e-6
     assert np.abs(d).max() < 1e-5
+
+
+def test_resident_zero_rhs_gives_zero_velocities():
+    """No noise, no shear, no excluded volume: b = 0 and v = 0 (the on-chip
+    solve forms the initial residual itself and stops before iterating)."""
+    n = 4096
+    L = synth.box_length(n)
+    pos = synth.uniform_positions(n, (L, L, L), 5)
+    sim = ss.Simulation(n, (L, L, L), 0.0, kT=0.0, eps=0.0, seed=5, cg_tol=1e-8, positions=pos,
+                        warm_start="prev", precision="mixed")
+    sim.set_solver_config(_resident_configs(sim)[1])
+    info = sim.step(2)
+    assert info["status"] == 0 and info["cg_iterations"] == 0
+    assert np.all(sim.get_velocities() == 0.0)
+    sim.close()
+
+
+def test_resident_start_that_meets_the_tolerance_keeps_x0():
+    """A second solve of the same system from its own solution stops at once
+    and returns that solution unchanged."""
+    sim, p, pos, delta = _make(30000, 17, 1e-8, warm_start="prev")
+    sim.set_solver_config(_resident_configs(sim)[1])
+    sim.build_neighbors()
+    sim.assemble()
+    first = sim.solve_velocities()
+    assert first["status"] == 0 and first["iterations"] > 0
+    v1 = sim.get_velocities()
+    again = sim.solve_velocities()
+    assert again["status"] == 0 and again["iterations"] == 0 and again["residual"] <= 1e-8
+    assert np.array_equal(sim.get_velocities(), v1)
+    sim.close()

@@ -37,12 +37,14 @@ struct PShared {
     float2 dfk[2][32];   // per-warp sums of the grid reductions
     double dk[4][32];
     double bcast[4];
+    float bcastf[2];     // the same totals rounded to FP32 (the on-chip iteration's scalars)
     int flag;
     // decided by thread 0 (FP64 scalars once per block, not once per thread)
     float alpha_f, beta_f;
     int action;   // 0 continue, 1 replace the residual, 2 stop
     // thread 0's CG state, kept here rather than in every thread's registers
     double rho, rr_restart, bnorm2, last_res;
+    float rho_f, target_f;   // on-chip iteration: rho and its stopping target in FP32
     int iter, restarts, status;
 };
 
@@ -116,10 +118,10 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShar
 // reading one set when a faster block writes the next.
 constexpr int kPartialsPerLane = 8;   // covers grids of up to 256 blocks in one round of loads
 
-template <int K>
-__device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
-                                               const dfloat (&v)[K], float2* partials, double (&out)[K],
-                                               int bid, int nb)
+template <int K, class OutT>
+__device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& gen, PShared& sh,
+                                                  const dfloat (&v)[K], float2* partials, OutT (&out)[K],
+                                                  int bid, int nb)
 {
     static_assert(K <= 2, "two values at most");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -163,14 +165,32 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
                 a = df_add(a, dfloat{p.x, p.y});
             }
             a = warp_sum_df(a);
-            if (lane == 0) sh.bcast[k] = (double)a.hi + (double)a.lo;
+            if (lane == 0) {
+                if constexpr (sizeof(OutT) == sizeof(float))
+                    sh.bcastf[k] = __fadd_rn(a.hi, a.lo);   // no FP64 operation on the iteration's path
+                else
+                    sh.bcast[k] = (double)a.hi + (double)a.lo;
+            }
         }
     }
     __syncthreads();
     gen += 1u;
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
+    for (int k = 0; k < K; ++k) {
+        if constexpr (sizeof(OutT) == sizeof(float))
+            out[k] = sh.bcastf[k];
+        else
+            out[k] = sh.bcast[k];
+    }
     return sh.flag == 0;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, PShared& sh,
+                                               const dfloat (&v)[K], float2* partials, double (&out)[K],
+                                               int bid, int nb)
+{
+    return grid_allreduce_df<K, double>(st, gen, sh, v, partials, out, bid, nb);
 }
 
 // The same for FP64 values (the rare FP64 residual replacement).
@@ -936,6 +956,10 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         sh.iter = 0;
         sh.restarts = 0;
         sh.beta_f = 0.f;
+        // the iteration's scalars in FP32 (its vectors are FP32; the FP64
+        // divisions cost ~0.5 us per iteration on GB300's FP64 pipe)
+        sh.rho_f = (float)sh.rho;
+        sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
     }
     __syncthreads();
 
@@ -1014,15 +1038,15 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         {
             const dfloat v[1] = {pq};
-            double tot[1];
-            if (!grid_allreduce<1>(st, gen, sh, v, B.partials_df, tot, bid, nb)) break;
+            float tot[1];
+            if (!grid_allreduce_df<1, float>(st, gen, sh, v, B.partials_df, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 sh.action = 0;
-                if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+                if (!(tot[0] > 0.f) || !isfinite(tot[0])) {
                     sh.status = SP_ERR_NONFINITE;
                     sh.action = 2;
                 } else {
-                    sh.alpha_f = (float)(sh.rho / tot[0]);
+                    sh.alpha_f = sh.rho_f / tot[0];
                 }
             }
         }
@@ -1048,8 +1072,8 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         {
             const dfloat v[2] = {rr, rz};
-            double tot[2];
-            if (!grid_allreduce<2>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb)) break;
+            float tot[2];
+            if (!grid_allreduce_df<2, float>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb)) break;
             if (threadIdx.x == 0) {
                 ++sh.iter;
                 sh.action = 0;
@@ -1057,10 +1081,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     sh.status = SP_ERR_NONFINITE;
                     sh.action = 2;
                 } else {
-                    sh.beta_f = (float)(tot[1] / sh.rho);
-                    sh.rho = tot[1];
-                    const double target = fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
-                    if (tot[0] <= target || sh.iter >= P.max_iter) sh.action = 1;
+                    sh.beta_f = tot[1] / sh.rho_f;
+                    sh.rho_f = tot[1];
+                    if (tot[0] <= sh.target_f || sh.iter >= P.max_iter) sh.action = 1;
                 }
             }
         }
@@ -1235,6 +1258,8 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     sh.rho = tot[1];
                     sh.beta_f = 0.f;
                     sh.rr_restart = tot[0];
+                    sh.rho_f = (float)tot[1];
+                    sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
                 }
             }
         }

@@ -118,10 +118,17 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShar
 // reading one set when a faster block writes the next.
 constexpr int kPartialsPerLane = 8;   // covers grids of up to 256 blocks in one round of loads
 
-template <int K, class OutT>
+struct NoPost {
+    template <class T>
+    __device__ void operator()(const T&) const {}
+};
+
+// post(totals) runs on thread 0 before the closing block barrier, so the
+// scalars it derives are visible to every thread when the call returns.
+template <int K, class OutT, class Post = NoPost>
 __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& gen, PShared& sh,
                                                   const dfloat (&v)[K], float2* partials, OutT (&out)[K],
-                                                  int bid, int nb)
+                                                  int bid, int nb, Post post = Post())
 {
     static_assert(K <= 2, "two values at most");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -171,6 +178,17 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
                 else
                     sh.bcast[k] = (double)a.hi + (double)a.lo;
             }
+        }
+        if (lane == 0) {
+            OutT t[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if constexpr (sizeof(OutT) == sizeof(float))
+                    t[k] = sh.bcastf[k];
+                else
+                    t[k] = sh.bcast[k];
+            }
+            post(t);
         }
     }
     __syncthreads();
@@ -1039,18 +1057,18 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         {
             const dfloat v[1] = {pq};
             float tot[1];
-            if (!grid_allreduce_df<1, float>(st, gen, sh, v, B.partials_df, tot, bid, nb)) break;
-            if (threadIdx.x == 0) {
-                sh.action = 0;
-                if (!(tot[0] > 0.f) || !isfinite(tot[0])) {
-                    sh.status = SP_ERR_NONFINITE;
-                    sh.action = 2;
-                } else {
-                    sh.alpha_f = sh.rho_f / tot[0];
-                }
-            }
+            if (!grid_allreduce_df<1, float>(st, gen, sh, v, B.partials_df, tot, bid, nb,
+                                              [&](const float (&t)[1]) {
+                                                  sh.action = 0;
+                                                  if (!(t[0] > 0.f) || !isfinite(t[0])) {
+                                                      sh.status = SP_ERR_NONFINITE;
+                                                      sh.action = 2;
+                                                  } else {
+                                                      sh.alpha_f = sh.rho_f / t[0];
+                                                  }
+                                              }))
+                break;
         }
-        __syncthreads();
         if (sh.action == 2) break;
 
         // ---- update of d and r; r.r and r.D^-1 r; z of the own rows published
@@ -1073,21 +1091,22 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         {
             const dfloat v[2] = {rr, rz};
             float tot[2];
-            if (!grid_allreduce_df<2, float>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb)) break;
-            if (threadIdx.x == 0) {
-                ++sh.iter;
-                sh.action = 0;
-                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-                    sh.status = SP_ERR_NONFINITE;
-                    sh.action = 2;
-                } else {
-                    sh.beta_f = tot[1] / sh.rho_f;
-                    sh.rho_f = tot[1];
-                    if (tot[0] <= sh.target_f || sh.iter >= P.max_iter) sh.action = 1;
-                }
-            }
+            if (!grid_allreduce_df<2, float>(st, gen, sh, v, B.partials_df + kMaxPartials, tot, bid, nb,
+                                              [&](const float (&t)[2]) {
+                                                  ++sh.iter;
+                                                  sh.action = 0;
+                                                  if (!isfinite(t[0]) || !isfinite(t[1])) {
+                                                      sh.status = SP_ERR_NONFINITE;
+                                                      sh.action = 2;
+                                                  } else {
+                                                      sh.beta_f = t[1] / sh.rho_f;
+                                                      sh.rho_f = t[1];
+                                                      if (t[0] <= sh.target_f || sh.iter >= P.max_iter)
+                                                          sh.action = 1;
+                                                  }
+                                              }))
+                break;
         }
-        __syncthreads();
         if (sh.action == 2) break;
         if (sh.action == 0) continue;
 

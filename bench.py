@@ -143,7 +143,7 @@ class ClockSampler:
 # and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
 # block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 74.1e6,
+PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 97.0e6,
                     ("mixed-n262144", 6, 1, False, 1024, False): 122.0e6}
 
 
@@ -183,14 +183,18 @@ def update_algorithmic_bytes(n: int, precision: str) -> float:
     return n * (4 * 24.0 + 8.0 + 3 * 24.0)
 
 
-def persistent_algorithmic_bytes(n: int, nnz: int, iters: int, checks: int) -> float:
+def persistent_algorithmic_bytes(n: int, nnz: int, iters: int, checks: int, init: bool = False) -> float:
     """Bytes one persistent mixed solve must move: per iteration one SpMV and one
     update; per FP64 residual replacement the fold of d into x (x read and
     written, d read and cleared) and the FP64 SpMV r = b - A x (columns and FP64
-    weights, one read of x, b and the diagonals, r written)."""
+    weights, one read of x, b and the diagonals, r written).  init: the launch
+    also forms r = b - A x0 in double-float (per entry the column, both weight
+    parts and a 32-byte x0 record; per row b and x0 records, A_ii in two parts,
+    D^-1, and r written as a float4 and a 32-byte record)."""
     per_check = n * (48.0 + 32.0) + n * (4.0 + 24.0 + 24.0 + 24.0 + 8.0 + 4.0 + 16.0) + 12.0 * nnz
+    per_init = n * (32.0 + 32.0 + 8.0 + 4.0 + 16.0 + 32.0) + 44.0 * nnz if init else 0.0
     return iters * (spmv_algorithmic_bytes(n, nnz, "mixed") + update_algorithmic_bytes(n, "mixed")) \
-        + checks * per_check
+        + checks * per_check + per_init
 
 
 def run_steps(sim, steps, stream, flush):
@@ -374,7 +378,8 @@ def main():
     upd_achieved = upd_algo / (prof["update_probe_ms"] * 1e-3) / 1e9
     persistent = None
     if prof["persistent_ms"] > 0:
-        pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
+        pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"],
+                                              bool(prof.get("persistent_init")))
         pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
         kname = solver_kernel_name(tune)
         persistent = {"kernel": kname, "bound": "hbm", "achieved": pach, "peak": peak,
@@ -592,7 +597,8 @@ def run_large(args):
     clk = clocks.stop()
     prof = sim.profile_step()
     peak, peak_kind = measured_peaks()
-    pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"])
+    pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"],
+                                              bool(prof.get("persistent_init")))
     pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
     spmv = spmv_algorithmic_bytes(prof["n"], prof["nnz"], "mixed") / (prof["spmv_probe_ms"] * 1e-3) / 1e9
     t_sq = time.perf_counter()
@@ -624,6 +630,9 @@ def run_large(args):
 # the x and z images (3 each) and |R|^2 (3); for a pair inside the cut-off also
 # the square root, the bin scaling and floor, and the product u . u' (6).
 VCORR_OPS_ALL, VCORR_OPS_IN = 16, 6
+# DRAM bytes per launch of k_vc_pairs on this workload (one ncu capture); the
+# particles stay in L2 and shared memory
+VCORR_PROFILED_TRAFFIC = 578304.0
 FP32_LANES_PER_SM = 128
 
 
@@ -690,7 +699,7 @@ def run_vcorr(args):
                        "nbins": nbins, "rmax": rmax, "l2": "flushed between calls (512 MB write)"},
             "gpu_launches": 6 * args.steps,
             "roofline": {"kernel": "k_vc_pairs", "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": VCORR_PROFILED_TRAFFIC,
                          "peak_source": f"152 SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                         "(one FP32 operation per lane per clock)",
                          "ops_per_pair": VCORR_OPS_ALL + VCORR_OPS_IN * in_range, "avg_launch_ms": kms},

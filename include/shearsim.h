@@ -240,11 +240,13 @@ typedef struct sp_kernel_profile {
     double persistent_ms;            /* the persistent mixed solver kernel (0 when not used) */
     int32_t true_checks;             /* FP64 true-residual computations of the solve */
     int32_t persistent_blocks;       /* its grid (cooperative launch), 0 when not used */
-    double init_ms;                  /* part of other_ms: solver set-up (r = b - A x0) */
+    double init_ms;                  /* part of other_ms: solver set-up (r = b - A x0, or the split of x0) */
     double stress_ms;                /* part of other_ms: the stress kernel */
     double integrate_ms;             /* part of other_ms: the position update */
     double mpnn_ms;                  /* the learned warm start's inference (0 when not used) */
     double assemble_ms;              /* part of build_ms: FP64 assembly of the matrix and right-hand side */
+    int32_t persistent_init;         /* 1: the persistent (on-chip) solve formed r = b - A x0 itself, as in
+                                        sp_step; init_ms then holds only the split of x0 */
 } sp_kernel_profile;
 int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
 

@@ -74,7 +74,7 @@ class sp_kernel_profile(ctypes.Structure):
                 ("persistent_ms", ctypes.c_double), ("true_checks", ctypes.c_int32),
                 ("persistent_blocks", ctypes.c_int32), ("init_ms", ctypes.c_double), ("stress_ms", ctypes.c_double),
                 ("integrate_ms", ctypes.c_double), ("mpnn_ms", ctypes.c_double),
-                ("assemble_ms", ctypes.c_double)]
+                ("assemble_ms", ctypes.c_double), ("persistent_init", ctypes.c_int32)]
 
 
 class sp_vcorr_info(ctypes.Structure):

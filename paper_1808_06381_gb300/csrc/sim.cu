@@ -925,15 +925,24 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
             rc = mark(MPNN);
         }
     }
+    const bool pers = mx && s->persistent;
+    // as a step runs it: the on-chip solve forms its initial residual itself
+    // (init_ms then holds only the split of x0 into double-floats)
+    const bool fused = pers && cg_persistent_on_chip(P, B, L);
     if (rc == SP_OK) {
-        launch_cg_init(P, B, warm_from_prev(s), mx, L);
+        if (!fused)
+            launch_cg_init(P, B, warm_from_prev(s), mx, L);
+        else if (warm_from_prev(s))
+            launch_cg_split_x(P, B, L);
         rc = mark(INIT);
     }
-    const bool pers = mx && s->persistent;
     if (rc == SP_OK && pers) {
-        if (launch_cg32_persistent(P, B, L) != cudaSuccess) rc = SP_ERR_CUDA;
+        KParams Pf = P;
+        Pf.fused_init = fused ? (warm_from_prev(s) ? 2 : 1) : 0;
+        if (launch_cg32_persistent(Pf, B, L) != cudaSuccess) rc = SP_ERR_CUDA;
         if (rc == SP_OK) rc = mark(PERSIST);
         out->persistent_blocks = cg_persistent_grid(P, B, L);
+        out->persistent_init = fused ? 1 : 0;
     }
     for (int it = 0; rc == SP_OK && !pers && it < P.max_iter + kMaxCgRestarts + 8; ++it) {
         launch_cg_spmv(P, B, mx, L);

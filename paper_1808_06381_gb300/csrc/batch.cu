@@ -143,7 +143,7 @@ int capture(sp_batch* b)
         launch_cg_finish(s->kp, s->B, true, launch_of(s, st));
         launch_stress(s->kp, s->B, true, launch_of(s, st));
         launch_integrate(s->kp, s->B, launch_of(s, st));
-        launches += 3;
+        launches += 4;   // finish, stress, update, commit of the new offset
     }
     join();
     cudaGraph_t g = nullptr;

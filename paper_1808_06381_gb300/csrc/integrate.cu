@@ -49,15 +49,28 @@ __global__ void __launch_bounds__(kVecBlock) k_integrate(KParams P, DevBuffers B
     __syncthreads();
     if (last && threadIdx.x == 0) {
         st->ticket[1] = 0u;
-        st->delta = dnew;
+        st->delta_next = dnew;
         st->step += 1;
         st->steps_in_call += 1;
     }
 }
 
-void launch_integrate(const KParams& P, DevBuffers& B, Launch L)
+__global__ void k_commit_step(DevBuffers B)
+{
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    st->delta = st->delta_next;
+}
+
+void launch_commit_step(DevBuffers& B, Launch L)
+{
+    k_commit_step<<<1, 1, 0, L.stream>>>(B);
+}
+
+void launch_integrate(const KParams& P, DevBuffers& B, Launch L, bool commit)
 {
     k_integrate<<<grid_for(P.n, kVecBlock, L.num_sms * 8), kVecBlock, 0, L.stream>>>(P, B);
+    if (commit) launch_commit_step(B, L);
 }
 
 // sigma_xy = -(1/V) sum_{i<j} y_ij f_ij,x with the pair forces of Eq. F and

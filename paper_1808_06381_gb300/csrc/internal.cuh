@@ -88,6 +88,7 @@ struct DevState {
     int bar_err;
     long long noise_step;     // step whose normals noise3 holds (-1: none)
     int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
+    double delta_next;        // the offset the position update advanced to (committed after the stress)
 };
 
 // Device buffers of one simulation (all in the current cell order unless noted).
@@ -779,7 +780,10 @@ int mp_weights_bf16_count();
 void launch_mp_convert(MpBuffers& M, cudaStream_t s);
 
 // integrate.cu
-void launch_integrate(const KParams& P, DevBuffers& B, Launch L);
+// commit = false: the new offset stays in delta_next until launch_commit_step
+// (so that a stress kernel running beside the update still reads the step's offset)
+void launch_integrate(const KParams& P, DevBuffers& B, Launch L, bool commit = true);
+void launch_commit_step(DevBuffers& B, Launch L);
 void launch_stress(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 void launch_scatter_by_id(const double* planes, int npad, const int* ids, int n, double* out_n3,
                           cudaStream_t s);

@@ -304,7 +304,7 @@ int host_cg_loop(sp_sim* s, long long* launches)
 }
 
 // Everything of a solve after assembly: init, loop, finish, stress.
-int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches)
+int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches, bool with_stress)
 {
     KParams& P = s->kp;
     DevBuffers& B = s->B;
@@ -321,8 +321,11 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
         SS_CUDA(launch_cg32_persistent(Pf, B, L));
         *launches += 1;
         launch_cg_finish(P, B, true, L);
-        launch_stress(P, B, true, L);
-        *launches += 2;
+        *launches += 1;
+        if (with_stress) {
+            launch_stress(P, B, true, L);
+            *launches += 1;
+        }
         return SP_OK;
     }
     *launches += launch_cg_init(P, B, from_x, mixed(s), L);
@@ -335,8 +338,11 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
         SS_TRY(host_cg_loop(s, launches));
     }
     launch_cg_finish(P, B, mixed(s), L);
-    launch_stress(P, B, mixed(s), L);
-    *launches += 2;
+    *launches += 1;
+    if (with_stress) {
+        launch_stress(P, B, mixed(s), L);
+        *launches += 1;
+    }
     return SP_OK;
 }
 
@@ -352,11 +358,29 @@ int capture_step_graph(sp_sim* s)
         launches += mp_infer_launches();
     }
     const bool warm = warm_from_prev(s);
-    int rc = enqueue_solve(s, cs, warm, true, &launches);
-    launch_integrate(s->kp, s->B, launch_of(s, cs));
-    launches += 1;
+    int rc = enqueue_solve(s, cs, warm, true, &launches, false);
+    // the stress and the position update read the step's state and write
+    // different arrays: the stress runs on a second captured stream beside the
+    // update, and the new image offset is committed after both
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess)
+        rc = SP_ERR_CUDA;
+    if (rc == SP_OK) {
+        cudaStream_t side = s->cap_stream[1];
+        cudaEventRecord(ev[0], cs);
+        cudaStreamWaitEvent(side, ev[0], 0);
+        launch_stress(s->kp, s->B, mixed(s), launch_of(s, side));
+        cudaEventRecord(ev[1], side);
+        launch_integrate(s->kp, s->B, launch_of(s, cs), false);
+        cudaStreamWaitEvent(cs, ev[1], 0);
+        launch_commit_step(s->B, launch_of(s, cs));
+        launches += 3;
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (rc != SP_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -797,7 +821,7 @@ int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
                 }
                 SS_TRY(enqueue_solve(s, s->stream, warm_from_prev(s), false, &launches));
                 launch_integrate(s->kp, s->B, launch_of(s, s->stream));
-                launches += 1;
+                launches += 2;   // the update and the commit of the new offset
                 SS_TRY(read_state(s));
                 if (s->st_host->error || s->st_host->overflow) break;
             }

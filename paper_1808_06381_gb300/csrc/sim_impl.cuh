@@ -66,7 +66,9 @@ void free_graphs(sp_sim* s);
 bool warm_from_prev(const sp_sim* s);   // the solve starts from x (previous velocities or the network's guess)
 int do_build(sp_sim* s);                // pair list for the current positions (grows storage if needed)
 // init, loop, finish and stress of one solve, enqueued on cs
-int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches);
+// with_stress = false: the caller launches the stress kernel itself
+int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches,
+                  bool with_stress = true);
 }  // namespace ss_host
 
 std::string& sp_global_error();

@@ -208,7 +208,7 @@ void derive(const sp_params& p, KParams& k, int npad)
 
 // --------------------------------------------------------------- enqueueing
 
-long long enqueue_build(sp_sim* s, cudaStream_t cs)
+long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent_t* ev)
 {
     KParams& P = s->kp;
     DevBuffers& B = s->B;
@@ -223,6 +223,13 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs)
         launch_scan(B.cell_count, B.cell_start, P.ncell, B.scan_tmp, 0, B.st, 0, L);
         launch_scatter_sort_gather(P, B, warm, L);
         launches += 6;
+    }
+    if (side && ev) {   // x0 (just gathered) split into double-floats beside the search and assembly
+        cudaEventRecord(ev[0], cs);
+        cudaStreamWaitEvent(side, ev[0], 0);
+        launch_cg_split_x(P, B, launch_of(s, side));
+        cudaEventRecord(ev[1], side);
+        launches += 1;
     }
     launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L);
     launch_sell_plan(P, B, L);
@@ -304,7 +311,8 @@ int host_cg_loop(sp_sim* s, long long* launches)
 }
 
 // Everything of a solve after assembly: init, loop, finish, stress.
-int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches, bool with_stress)
+int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches, bool with_stress,
+                  bool x_split)
 {
     KParams& P = s->kp;
     DevBuffers& B = s->B;
@@ -314,7 +322,7 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
         // its rows' entries, beside placing them in shared memory)
         KParams Pf = P;
         Pf.fused_init = from_x ? 2 : 1;
-        if (from_x) {
+        if (from_x && !x_split) {
             launch_cg_split_x(P, B, L);
             *launches += 1;
         }
@@ -350,24 +358,33 @@ int capture_step_graph(sp_sim* s)
 {
     free_graphs(s);
     cudaStream_t cs = s->cap_stream[0];
+    cudaStream_t side = s->cap_stream[1];
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (cudaEvent_t& x : ev)
+        if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) {
+            for (cudaEvent_t y : ev)
+                if (y) cudaEventDestroy(y);
+            s->err = "cudaEventCreateWithFlags failed";
+            return SP_ERR_CUDA;
+        }
+    const bool warm = warm_from_prev(s);
+    // the on-chip solve from the previous velocities: their split into
+    // double-floats runs beside the pair search and the assembly
+    const bool side_split = mixed(s) && s->persistent && warm && !s->learned &&
+                            cg_persistent_on_chip(s->kp, s->B, launch_of(s, cs));
     SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    long long launches = enqueue_build(s, cs);
+    long long launches = enqueue_build(s, cs, side_split ? side : nullptr, side_split ? ev + 2 : nullptr);
     launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
     if (s->learned) {
         launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
         launches += mp_infer_launches();
     }
-    const bool warm = warm_from_prev(s);
-    int rc = enqueue_solve(s, cs, warm, true, &launches, false);
+    if (side_split) cudaStreamWaitEvent(cs, ev[3], 0);
+    int rc = enqueue_solve(s, cs, warm, true, &launches, false, side_split);
     // the stress and the position update read the step's state and write
     // different arrays: the stress runs on a second captured stream beside the
     // update, and the new image offset is committed after both
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess)
-        rc = SP_ERR_CUDA;
     if (rc == SP_OK) {
-        cudaStream_t side = s->cap_stream[1];
         cudaEventRecord(ev[0], cs);
         cudaStreamWaitEvent(side, ev[0], 0);
         launch_stress(s->kp, s->B, mixed(s), launch_of(s, side));

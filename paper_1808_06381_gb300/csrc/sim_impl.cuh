@@ -57,7 +57,9 @@ struct sp_sim {
 namespace ss_host {
 ss::Launch launch_of(const sp_sim* s, cudaStream_t st);
 bool mixed(const sp_sim* s);
-long long enqueue_build(sp_sim* s, cudaStream_t cs);
+// side/ev (optional, mixed path): right after the gather, the split of x0 into
+// double-floats is launched on side between ev[0] and ev[1]
+long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side = nullptr, cudaEvent_t* ev = nullptr);
 int read_state(sp_sim* s);
 int grow_pairs(sp_sim* s);
 int clear_flags(sp_sim* s);
@@ -67,8 +69,9 @@ bool warm_from_prev(const sp_sim* s);   // the solve starts from x (previous vel
 int do_build(sp_sim* s);                // pair list for the current positions (grows storage if needed)
 // init, loop, finish and stress of one solve, enqueued on cs
 // with_stress = false: the caller launches the stress kernel itself
+// x_split: xdf already holds x0 (split beside the build)
 int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long long* launches,
-                  bool with_stress = true);
+                  bool with_stress = true, bool x_split = false);
 }  // namespace ss_host
 
 std::string& sp_global_error();

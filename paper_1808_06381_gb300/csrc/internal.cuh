@@ -717,7 +717,10 @@ void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Laun
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 // The step's pair search; with draw_noise it also draws the thermal normals
 // of every row (FP64 Box-Muller, overlapping the search's memory latency).
-void launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L);
+// side/ev (optional): the normals run on side between ev[0] and ev[1], beside
+// the search, and L.stream waits for them; returns the kernels launched
+int launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L, cudaStream_t side = nullptr,
+                     cudaEvent_t* ev = nullptr);
 // Pair fill (columns and image codes), followed, with assemble, by the FP64
 // assembly of the matrix and right-hand side; returns the kernels launched.
 int launch_nbr_fill(const KParams& P, DevBuffers& B, bool assemble, bool use_inj, bool df, Launch L);

@@ -455,10 +455,10 @@ __global__ void k_nbr_collect(KParams P, DevBuffers B, int draw_noise)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         st->nnz = 0;
-        st->noise_step = draw_noise ? st->step : -1;
+        if (draw_noise != 2) st->noise_step = draw_noise ? st->step : -1;   // 2: drawn by k_row_normals
     }
     if (i >= P.n) return;
-    if (draw_noise) {   // the step's normals of this row (the assembly uses them)
+    if (draw_noise == 1) {   // the step's normals of this row (the assembly uses them)
         if (P.mixed) {   // double-float arithmetic; stored as (hi, lo) pairs in the same space
             dfloat g0, g1, g2;
             normals3_df(B.rng_tab, P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
@@ -490,9 +490,44 @@ __global__ void k_nbr_collect(KParams P, DevBuffers B, int draw_noise)
     B.row_cnt[i] = cnt;
 }
 
-void launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L)
+// The step's normals of every row as the pair search draws them, in a kernel
+// of their own (so that they can run beside the search).
+__global__ void k_row_normals(KParams P, DevBuffers B)
 {
+    DevState* st = B.st;
+    if (st->error | st->overflow) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) st->noise_step = st->step;
+    if (i >= P.n) return;
+    if (P.mixed) {
+        dfloat g0, g1, g2;
+        normals3_df(B.rng_tab, P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
+        float2* n2 = reinterpret_cast<float2*>(B.noise3);
+        n2[i] = make_float2(g0.hi, g0.lo);
+        n2[P.npad + i] = make_float2(g1.hi, g1.lo);
+        n2[2 * P.npad + i] = make_float2(g2.hi, g2.lo);
+    } else {
+        double g0, g1, g2;
+        normals3(P.seed, (unsigned long long)st->step, (unsigned long long)B.id_w[i], g0, g1, g2);
+        B.noise3[i] = g0;
+        B.noise3[P.npad + i] = g1;
+        B.noise3[2 * P.npad + i] = g2;
+    }
+}
+
+int launch_nbr_count(const KParams& P, DevBuffers& B, bool draw_noise, Launch L, cudaStream_t side, cudaEvent_t* ev)
+{
+    if (draw_noise && side && ev) {   // the normals beside the search, joined before anything after it
+        cudaEventRecord(ev[0], L.stream);
+        cudaStreamWaitEvent(side, ev[0], 0);
+        k_row_normals<<<grid_for(P.n, 256, 1 << 30), 256, 0, side>>>(P, B);
+        cudaEventRecord(ev[1], side);
+        k_nbr_collect<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, 2);
+        cudaStreamWaitEvent(L.stream, ev[1], 0);
+        return 2;
+    }
     k_nbr_collect<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, draw_noise ? 1 : 0);
+    return 1;
 }
 
 // Slices of the matrix: inside each window of 256 rows, rank the rows by

@@ -208,7 +208,7 @@ void derive(const sp_params& p, KParams& k, int npad)
 
 // --------------------------------------------------------------- enqueueing
 
-long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent_t* ev)
+long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent_t* ev, bool split_x)
 {
     KParams& P = s->kp;
     DevBuffers& B = s->B;
@@ -224,17 +224,17 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent
         launch_scatter_sort_gather(P, B, warm, L);
         launches += 6;
     }
-    if (side && ev) {   // x0 (just gathered) split into double-floats beside the search and assembly
+    if (side && ev && split_x) {   // x0 (just gathered) split into double-floats beside the search and assembly
         cudaEventRecord(ev[0], cs);
         cudaStreamWaitEvent(side, ev[0], 0);
         launch_cg_split_x(P, B, launch_of(s, side));
         cudaEventRecord(ev[1], side);
         launches += 1;
     }
-    launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L);
+    launches += launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L, side, (side && ev) ? ev + 2 : nullptr);
     launch_sell_plan(P, B, L);
     launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
-    return launches + 5;
+    return launches + 4;
 }
 
 // Conditional WHILE node holding one CG iteration, with an IF node for the
@@ -359,7 +359,7 @@ int capture_step_graph(sp_sim* s)
     free_graphs(s);
     cudaStream_t cs = s->cap_stream[0];
     cudaStream_t side = s->cap_stream[1];
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     for (cudaEvent_t& x : ev)
         if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) {
             for (cudaEvent_t y : ev)
@@ -373,24 +373,24 @@ int capture_step_graph(sp_sim* s)
     const bool side_split = mixed(s) && s->persistent && warm && !s->learned &&
                             cg_persistent_on_chip(s->kp, s->B, launch_of(s, cs));
     SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    long long launches = enqueue_build(s, cs, side_split ? side : nullptr, side_split ? ev + 2 : nullptr);
+    long long launches = enqueue_build(s, cs, side, ev, side_split);
     launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
     if (s->learned) {
         launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
         launches += mp_infer_launches();
     }
-    if (side_split) cudaStreamWaitEvent(cs, ev[3], 0);
+    if (side_split) cudaStreamWaitEvent(cs, ev[1], 0);
     int rc = enqueue_solve(s, cs, warm, true, &launches, false, side_split);
     // the stress and the position update read the step's state and write
     // different arrays: the stress runs on a second captured stream beside the
     // update, and the new image offset is committed after both
     if (rc == SP_OK) {
-        cudaEventRecord(ev[0], cs);
-        cudaStreamWaitEvent(side, ev[0], 0);
+        cudaEventRecord(ev[4], cs);
+        cudaStreamWaitEvent(side, ev[4], 0);
         launch_stress(s->kp, s->B, mixed(s), launch_of(s, side));
-        cudaEventRecord(ev[1], side);
+        cudaEventRecord(ev[5], side);
         launch_integrate(s->kp, s->B, launch_of(s, cs), false);
-        cudaStreamWaitEvent(cs, ev[1], 0);
+        cudaStreamWaitEvent(cs, ev[5], 0);
         launch_commit_step(s->B, launch_of(s, cs));
         launches += 3;
     }

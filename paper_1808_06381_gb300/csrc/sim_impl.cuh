@@ -57,9 +57,11 @@ struct sp_sim {
 namespace ss_host {
 ss::Launch launch_of(const sp_sim* s, cudaStream_t st);
 bool mixed(const sp_sim* s);
-// side/ev (optional, mixed path): right after the gather, the split of x0 into
-// double-floats is launched on side between ev[0] and ev[1]
-long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side = nullptr, cudaEvent_t* ev = nullptr);
+// side/ev (optional): the step's normals run on side beside the pair search
+// (ev[2], ev[3]); with split_x also the split of x0 into double-floats right
+// after the gather (ev[0], ev[1]; the caller waits for ev[1])
+long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side = nullptr, cudaEvent_t* ev = nullptr,
+                        bool split_x = false);
 int read_state(sp_sim* s);
 int grow_pairs(sp_sim* s);
 int clear_flags(sp_sim* s);

@@ -795,8 +795,10 @@ __device__ __forceinline__ dfloat sep_df(float ih, float il, float jh, float jl,
 // double-floats only (weights val32 + val32lo, A_ii, b); it agrees with the
 // FP64 assembly to ~1e-12 relative (the 2^-48 representation of the
 // positions), far inside the mixed solver's tolerance.
+constexpr int kAsmBatch = 4;   // partners requested at a time by the double-float assembly
+
 template <bool DF>
-__global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
+__global__ void __launch_bounds__(256, 3) k_assemble_slots(KParams P, DevBuffers B, int use_inj)
 {
     const DevState* st = B.st;
     if (st->error | st->overflow) return;
@@ -833,10 +835,34 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
         const dfloat Lx{P.Lf[0], P.Llo[0]}, Ly{P.Lf[1], P.Llo[1]}, Lz{P.Lf[2], P.Llo[2]};
         const dfloat zero{0.f, 0.f};
         dfloat s_w = zero, s_x = zero, s_y = zero, s_z = zero, s_n = zero;
-        for (int k = 0; k < cnt; ++k) {
+        // partners in batches of kAsmBatch: their indices, then their positions,
+        // are requested together (one latency per batch, not per partner)
+        for (int k0 = 0; k0 < cnt; k0 += kAsmBatch) {
+        int jb[kAsmBatch], cb[kAsmBatch];
+#pragma unroll
+        for (int u = 0; u < kAsmBatch; ++u) {
+            const bool in = k0 + u < cnt;
+            jb[u] = in ? pj[(k0 + u) * pstride] : i;
+            cb[u] = in ? pimg[(k0 + u) * pstride] : center;
+        }
+        float pxh[kAsmBatch], pxl[kAsmBatch], pyh[kAsmBatch], pyl[kAsmBatch], pzh[kAsmBatch], pzl[kAsmBatch];
+#pragma unroll
+        for (int u = 0; u < kAsmBatch; ++u) {
+            const int j = jb[u];
+            pxh[u] = ph[j];
+            pxl[u] = pl[j];
+            pyh[u] = ph[np + j];
+            pyl[u] = pl[np + j];
+            pzh[u] = ph[2 * np + j];
+            pzl[u] = pl[2 * np + j];
+        }
+#pragma unroll
+        for (int u = 0; u < kAsmBatch; ++u) {
+            const int k = k0 + u;
+            if (k >= cnt) break;
             const int e = base + 32 * k;
-            const int j = pj[k * pstride];
-            const int code = pimg[k * pstride];
+            const int j = jb[u];
+            const int code = cb[u];
             B.col[e] = j;
             B.img[e] = (unsigned char)code;
             const bool shifted = !__all_sync(__activemask(), code == center);   // warp-uniform
@@ -857,9 +883,9 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
                 shy = m == 0 ? zero : (m > 0 ? Ly : df_neg(Ly));
                 shz = c == 0 ? zero : (c > 0 ? Lz : df_neg(Lz));
             }
-            const dfloat dx = sep_df(xih, xil, ph[j], pl[j], shx);
-            const dfloat dy = sep_df(yih, yil, ph[np + j], pl[np + j], shy);
-            const dfloat dz = sep_df(zih, zil, ph[2 * np + j], pl[2 * np + j], shz);
+            const dfloat dx = sep_df(xih, xil, pxh[u], pxl[u], shx);
+            const dfloat dy = sep_df(yih, yil, pyh[u], pyl[u], shy);
+            const dfloat dz = sep_df(zih, zil, pzh[u], pzl[u], shz);
             const dfloat r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
             const dfloat w = pair_weight_df(P, B.exp_tab_df, r2);
             B.val32[e] = w.hi;
@@ -869,6 +895,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_slots(KParams P, DevBuffers
             s_y = df_add(s_y, df_mul(dy, w));
             s_z = df_add(s_z, df_mul(dz, w));
             if (shifted && m != 0) s_n = df_add(s_n, m > 0 ? w : df_neg(w));
+        }
         }
         dsw = s_w;
         dsx = s_x;

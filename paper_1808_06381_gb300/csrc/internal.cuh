@@ -102,7 +102,8 @@ struct DevBuffers {
     float* pos32;    // [3][npad] FP32 copy of pos_w for the pair pre-filter
     float* pos32lo;  // [3][npad] pos_w - pos32: positions as double-floats (pos32, pos32lo)
     int* id_w;       // [n]
-    int* cell_of;    // [n]
+    int* cell_of;    // [n] cell of each row: in the state order while binning, then (written by the
+                     // gather) in the cell order of the current rows, where the pair search reads it
     int* slot;       // [n]
     int* perm;       // [n] new row -> state row
     int* cell_count; // [ncell]

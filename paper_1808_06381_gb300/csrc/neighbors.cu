@@ -177,7 +177,7 @@ __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int
                               const int* __restrict__ id_s, const double* __restrict__ pos_s,
                               const double* __restrict__ v_s, double* __restrict__ pos_w,
                               float* __restrict__ pos32, float* __restrict__ pos32lo, int* __restrict__ id_w,
-                              double* __restrict__ x, int warm, const DevState* st)
+                              double* __restrict__ x, int* __restrict__ cell_w, int warm, const DevState* st)
 {
     if (st->error | st->overflow) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,6 +205,7 @@ __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int
             pos32lo[a * np + k] = (float)(v - (double)vh);
         }
         id_w[k] = id_s[s];
+        cell_w[k] = c;   // the cell of row k (the pair search reads it instead of recomputing it)
         x[k] = warm ? v_s[s] : 0.0;
         x[np + k] = warm ? v_s[np + s] : 0.0;
         x[2 * np + k] = warm ? v_s[2 * np + s] : 0.0;
@@ -216,8 +217,8 @@ void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Laun
     k_scatter<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P.n, B.cell_of, B.slot,
                                                                                 B.cell_start, B.perm, B.st);
     k_sort_gather<<<grid_for(P.ncell, 128, 1 << 30), 128, 0, L.stream>>>(
-        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, warm ? 1 : 0,
-        B.st);
+        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, B.cell_of,
+        warm ? 1 : 0, B.st);
 }
 
 // Single-cell boxes (every edge below 3 r_c): keep the state order.
@@ -360,20 +361,29 @@ template <class F>
 __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double delta,
                                                        const double* __restrict__ pos,
                                                        const float* __restrict__ pos32,
-                                                       const int* __restrict__ cell_start, int i,
+                                                       const int* __restrict__ cell_start,
+                                                       const int* __restrict__ cell_w, int i,
                                                        double xi, double yi, double zi, F&& visit)
 {
     const int np = P.npad;
     const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
     const float xf = pos32[i], yf = pos32[np + i], zf = pos32[2 * np + i];
     const float deltaf = (float)delta;
-    const int cx = cell_coord(xi, P.inv_cw[0], nc0);
-    const int cy = cell_coord(yi, P.inv_cw[1], nc1);
-    const int cz = cell_coord(zi, P.inv_cw[2], nc2);
-    // x cell of x_i - m delta for the rows of cells that wrap through y (m = -1, +1),
-    // computed once per particle (FP64 work is scarce on GB300)
-    const int cx_m1 = (int)floor((xi + delta) * P.inv_cw[0]);
-    const int cx_p1 = (int)floor((xi - delta) * P.inv_cw[0]);
+    // the row's cell coordinates from its cell index (integer work; the
+    // binning computed the index from the same FP64 position)
+    const int ci = cell_w[i];
+    const int tl = ci >> 9, lc = ci & 511;
+    const int tx = tl % P.ntile[0], ty = (tl / P.ntile[0]) % P.ntile[1], tz = tl / (P.ntile[0] * P.ntile[1]);
+    const int cx = 8 * tx + ((lc & 1) | ((lc >> 2) & 2) | ((lc >> 4) & 4));
+    const int cy = 8 * ty + (((lc >> 1) & 1) | ((lc >> 3) & 2) | ((lc >> 5) & 4));
+    const int cz = 8 * tz + (((lc >> 2) & 1) | ((lc >> 4) & 2) | ((lc >> 6) & 4));
+    // x cell of x_i - m delta for the rows of cells that wrap through y (m = -1, +1):
+    // FP64, so only for rows whose cell touches a y face
+    int cx_m1 = cx, cx_p1 = cx;
+    if (cy == 0 || cy == nc1 - 1) {
+        cx_m1 = (int)floor((xi + delta) * P.inv_cw[0]);
+        cx_p1 = (int)floor((xi - delta) * P.inv_cw[0]);
+    }
     // image shifts by selection (no int-to-float conversions: GB300 runs them
     // at the FP64 rate); every product below is exact, as before
     auto times = [](int k, float v) { return k == 0 ? 0.f : (k > 0 ? v : -v); };
@@ -435,11 +445,12 @@ template <class F>
 __device__ __forceinline__ void for_each_neighbor(const KParams& P, double delta,
                                                   const double* __restrict__ pos,
                                                   const float* __restrict__ pos32,
-                                                  const int* __restrict__ cell_start, int i,
+                                                  const int* __restrict__ cell_start,
+                                                  const int* __restrict__ cell_w, int i,
                                                   double xi, double yi, double zi, F&& visit)
 {
     if (P.fast_cells)
-        for_each_neighbor_fast(P, delta, pos, pos32, cell_start, i, xi, yi, zi, visit);
+        for_each_neighbor_fast(P, delta, pos, pos32, cell_start, cell_w, i, xi, yi, zi, visit);
     else
         for_each_neighbor_generic(P, delta, pos, cell_start, i, xi, yi, zi, visit);
 }
@@ -479,7 +490,7 @@ __global__ void k_nbr_collect(KParams P, DevBuffers B, int draw_noise)
     int cnt = 0;
     int* __restrict__ cj = B.cand_j;
     unsigned char* __restrict__ ci = B.cand_img;
-    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, B.pos_w[i], B.pos_w[np + i],
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, B.cell_of, i, B.pos_w[i], B.pos_w[np + i],
                       B.pos_w[2 * np + i], [&](int j, unsigned char code) {
                           if (cnt < kCandCap) {
                               cj[(size_t)cnt * np + i] = j;
@@ -732,7 +743,8 @@ __device__ __noinline__ void search_row_into_slots(const KParams& P, const DevBu
 {
     const int np = P.npad;
     int k = 0;
-    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, B.pos_w[i], B.pos_w[np + i], B.pos_w[2 * np + i],
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, B.cell_of, i, B.pos_w[i], B.pos_w[np + i],
+                      B.pos_w[2 * np + i],
                       [&](int j, unsigned char code) {
                           if (k < cnt) {
                               B.col[base + 32 * k] = j;
@@ -972,7 +984,7 @@ __global__ void k_nbr_fill(KParams P, DevBuffers B)
     int k = 0;
     int* __restrict__ col = B.col;
     unsigned char* __restrict__ img = B.img;
-    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, i, xi, yi, zi, [&](int j, unsigned char code) {
+    for_each_neighbor(P, delta, B.pos_w, B.pos32, B.cell_start, B.cell_of, i, xi, yi, zi, [&](int j, unsigned char code) {
         if (k < cnt) {
             col[base + 32 * k] = j;
             img[base + 32 * k] = code;

@@ -244,6 +244,52 @@ def assemble(p: Params, pos, pairs, xi=None, delta: float = 0.0) -> System:
     return System(p.n, p.alpha, pairs, w, diag, b)
 
 
+def gershgorin_max(sys: System) -> float:
+    """Upper bound of A's spectrum by Gershgorin's theorem: max_i (A_ii + alpha sum_j w_ij).
+    (The lower bound is 1: A = I + alpha L_w with L_w positive semidefinite.)"""
+    rowsum = np.zeros(sys.n)
+    np.add.at(rowsum, sys.pairs[:, 0], sys.w)
+    np.add.at(rowsum, sys.pairs[:, 1], sys.w)
+    return float(np.max(sys.diag + sys.alpha * rowsum))
+
+
+def chebyshev_sqrt_coeffs(a: float, b: float, degree: int) -> np.ndarray:
+    """Coefficients c_0..c_K of the Chebyshev interpolant of sqrt on [a, b] at the
+    K + 1 Chebyshev points of the first kind: p(x) = c_0 / 2 + sum_{k >= 1} c_k T_k(u),
+    u = (2 x - b - a) / (b - a)."""
+    N = degree + 1
+    theta = np.pi * (np.arange(N) + 0.5) / N
+    f = np.sqrt(0.5 * (b - a) * np.cos(theta) + 0.5 * (b + a))
+    return np.array([2.0 / N * np.sum(f * np.cos(k * theta)) for k in range(N)])
+
+
+def sqrt_apply(sys: System, g, degree: int):
+    """xi = p(A) g with p the degree-K Chebyshev interpolant of sqrt on [1, Gershgorin
+    max], by the three-term recurrence T_{k+1} = 2 u T_k - T_{k-1} applied to g (FDT-
+    consistent noise: xi has covariance A if g has covariance I).  A = I returns g.
+    Returns (xi [n, 3], the interval's upper end)."""
+    g = _f64(g)
+    lmax = gershgorin_max(sys)
+    if not (lmax - 1.0 > 1e-12):
+        return g.copy(), lmax
+    c = chebyshev_sqrt_coeffs(1.0, lmax, degree)
+
+    def u(v):   # the map of [1, lmax] onto [-1, 1], applied to A
+        return (2.0 * sys.matvec(v) - (lmax + 1.0) * v) / (lmax - 1.0)
+
+    t0 = g.copy()
+    y = 0.5 * c[0] * t0
+    if degree == 0:
+        return y, lmax
+    t1 = u(t0)
+    y = y + c[1] * t1
+    for k in range(2, degree + 1):
+        t2 = 2.0 * u(t1) - t0
+        y = y + c[k] * t2
+        t0, t1 = t1, t2
+    return y, lmax
+
+
 def pcg(sys: System, tol: float = 1e-13, max_iter: int = 100000, x0=None):
     """Jacobi-PCG; returns (v [n,3], iterations, true relative residual)."""
     x = np.zeros((sys.n, 3)) if x0 is None else _f64(x0).copy()

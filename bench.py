@@ -287,16 +287,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "learned", "batch", "large", "vcorr"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "learned", "batch", "large", "vcorr", "fdt"],
                     help="mixed: N=262,144 precision workload (the default line); learned: the same with the "
                          "learned warm start; batch: 64 replicas; large: N=4,194,304; vcorr: the velocity "
-                         "cross-correlation of Fig. vv on the paper's box")
+                         "cross-correlation of Fig. vv on the paper's box; fdt: A^(1/2) g (FDT-consistent "
+                         "noise) on the N=262,144 system")
     ap.add_argument("--train-steps", type=int, default=60)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "ours" and args.workload != "mixed":
         return {"learned": run_learned, "batch": run_batch, "large": run_large,
-                "vcorr": run_vcorr}[args.workload](args)
+                "vcorr": run_vcorr, "fdt": run_fdt}[args.workload](args)
 
     workload = synth.PRECISION
     if args.n:
@@ -707,6 +708,67 @@ def run_vcorr(args):
             "e2e": {"value": pairs / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": 2 * w.n * 24,
                     "d2h_bytes_per_step": nbins * 16 + 16},
             "clocks": clk, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
+def fdt_algorithmic_bytes(n: int, nnz: int) -> float:
+    """One Chebyshev degree step (mixed path, double-float records): per entry the
+    column, the weight's two FP32 parts and the gathered 32-byte record of T_k; per row
+    the slot map, A_ii's two parts, T_k and T_(k-1) read, T_(k+1) written, xi read and
+    written (32 bytes each)."""
+    return nnz * (4.0 + 8.0 + 32.0) + n * (4.0 + 8.0 + 5 * 32.0)
+
+
+def run_fdt(args):
+    """xi = p(A) g ~ A^(1/2) g on the N=262,144 mixed system after the warm-up steps
+    (degree 32 on [1, Gershgorin max]); value: particles per second of the whole call
+    (host arrays in and out, so it is also the end-to-end figure); roofline: the
+    degree steps, CUDA events on the simulation's stream."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    w = synth.PRECISION
+    degree = 32
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    sim = _sim(ss, w, "mixed", "prev")
+    sim.step(args.warmup)
+    sim.build_neighbors()
+    sim.assemble()
+    g = np.random.default_rng(w.seed).standard_normal((w.n, 3))
+    for _ in range(2):
+        sim.sqrt_apply(g, degree)
+    clocks = ClockSampler(None)
+    clocks.start()
+    total, kern = 0.0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, lmax, ms = sim.sqrt_apply(g, degree, timing=True)
+        total += time.perf_counter() - t0
+        kern += ms
+    clk = clocks.stop()
+    prof = sim.profile_step()
+    sim.close()
+    ms_call = 1e3 * total / args.steps
+    step_ms = kern / args.steps / degree
+    nbytes = fdt_algorithmic_bytes(prof["n"], prof["nnz"])
+    peak, peak_kind = measured_peaks()
+    ach = nbytes / (step_ms * 1e-3) / 1e9
+    line = {"metric": "A^(1/2) g (FDT-consistent noise) particles/s, Chebyshev degree 32",
+            "value": w.n / (ms_call * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_call, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32x2 (double-float)",
+            "data": "synthetic (the simulated system after the warm-up steps)",
+            "config": {"workload": w.name, "n": w.n, "degree": degree, "lambda_max": lmax,
+                       "l2": "flushed between calls (512 MB write)"},
+            "gpu_launches": args.steps * (degree + 4),
+            "roofline": {"kernel": "k_cheb_step", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": None, "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                         "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": step_ms},
+            "e2e": {"value": w.n / (ms_call * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": w.n * 24,
+                    "d2h_bytes_per_step": w.n * 24 + 8},
+            "clocks": clk, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
 

@@ -180,6 +180,24 @@ int sp_structure_factor(sp_sim* sim, int32_t nkx, int32_t nky, int32_t grid, dou
  * The paper defines no stress; this is the pair virial of its pair forces. */
 int sp_stress_xy(sp_sim* sim, double* sigma_xy);
 
+/* FDT-consistent thermal noise (not in the paper, which draws the noise of
+ * Eq. F independently per particle): xi = p(A) g ~ A^(1/2) g for the current
+ * assembled matrix A of Eq. algebra, p the degree-`degree` Chebyshev
+ * interpolant of sqrt on [1, lambda_max] (Chebyshev points of the first kind;
+ * lambda_max = max_i (A_ii + alpha sum_j w_ij), Gershgorin's bound; the
+ * spectrum starts at 1 because A = I + alpha L_w with L_w positive
+ * semidefinite).  If g has covariance I, xi has covariance p(A)^2 ~ A; passing
+ * xi to sp_set_noise and assembling again gives a step whose noise is
+ * correlated like the friction.  g_host, xi_host: [n][3] in particle order
+ * (host).  lambda_max (may be NULL) receives the interval's upper end; when it
+ * is 1 (no coupling) xi = g.  One sliced-layout SpMV per degree (FP64 for the
+ * FP64 path, double-float on the FP32 pipes for the mixed path); steps_ms (may be NULL)
+ * receives their time (CUDA events on the simulation's stream).  Errors:
+ * SP_ERR_INVALID_ARG (NULL pointer, degree outside [1, 4096], no assembled
+ * system), SP_ERR_OOM, SP_ERR_CUDA. */
+int sp_sqrt_apply(sp_sim* sim, int32_t degree, const double* g_host, double* xi_host, double* lambda_max,
+                  double* steps_ms);
+
 /* Velocity cross-correlation versus distance (§Results, Fig. vv): the average
  * inter-chain velocity product <v_c . v_c'> / <v_c^2> against |R_cc'|.
  * u_c = v_c - kappa (y_c - L_y/2) x is the velocity relative to the imposed

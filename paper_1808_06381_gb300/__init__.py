@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
             ("sp_step_host", [vp, vp, ctypes.c_double, i32, vp, P(sp_step_info)]),
             ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
             ("sp_velocity_correlation", [vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
+            ("sp_sqrt_apply", [vp, i32, vp, vp, P(d), P(d)]),
             ("sp_velocity_correlation_host", [i32, i64, vp, d, d, vp, vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
@@ -404,6 +405,16 @@ class Simulation:
         self._c(load().sp_mpnn_train_step(self._h, float(lr), ctypes.byref(loss),
                                           _p(grad) if grad is not None else None))
         return (loss.value, grad) if want_grad else loss.value
+
+    def sqrt_apply(self, g, degree: int = 32, timing: bool = False):
+        """xi = p(A) g ~ A^(1/2) g for the assembled system (Chebyshev degree `degree` on
+        [1, Gershgorin max]; sp_sqrt_apply).  g: [n, 3] in particle order.  Returns
+        (xi, lambda_max), and the degree steps' device time in ms when timing is set."""
+        g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.n, 3)
+        xi = np.zeros_like(g)
+        lmax, ms = ctypes.c_double(), ctypes.c_double()
+        self._c(load().sp_sqrt_apply(self._h, int(degree), _p(g), _p(xi), ctypes.byref(lmax), ctypes.byref(ms)))
+        return (xi, lmax.value, ms.value) if timing else (xi, lmax.value)
 
     def velocity_correlation(self, nbins: int, rmax: float) -> dict:
         """Fig. vv on the current positions and the last solve's velocities (sp_velocity_correlation)."""

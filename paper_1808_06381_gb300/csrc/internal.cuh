@@ -800,6 +800,15 @@ cudaError_t run_structure_factor(const KParams& P, const DevBuffers& B, double d
                                  const double* twiddle_dev, unsigned long long* grid_dev, double2* A_dev,
                                  double* S_dev, double* qx_dev, double* qy_dev, cudaStream_t s);
 
+// fdt.cu: xi = p(A) g ~ A^(1/2) g (Chebyshev interpolant of sqrt on [1, lambda_max])
+cudaError_t cheb_bound(const KParams& P, DevBuffers& B, unsigned long long* out_dev, cudaStream_t s);
+cudaError_t cheb_step(const KParams& P, DevBuffers& B, const double* tc, const double* tp, double* tn, double* y,
+                      double s1, double s0, double ck, double c0h, bool first, cudaStream_t s);
+cudaError_t cheb_step_df(const KParams& P, DevBuffers& B, const float4* tc, const float4* tp, float4* tn, float4* y,
+                         double s1, double s0, double ck, double c0h, bool first, cudaStream_t s);
+cudaError_t cheb_split(const KParams& P, const double* g, float4* t, cudaStream_t s);
+cudaError_t cheb_join(const KParams& P, const float4* y, double* out, cudaStream_t s);
+
 // vcorr.cu: velocity cross-correlation versus distance (Fig. vv)
 constexpr int kVcMaxBins = 1024;
 struct VcBuffers {

@@ -1351,6 +1351,120 @@ int sp_normals(int32_t device, uint64_t seed, uint64_t step, int64_t count, cons
     return rc;
 }
 
+int sp_sqrt_apply(sp_sim* s, int32_t degree, const double* g_host, double* xi_host, double* lambda_max,
+                  double* steps_ms)
+{
+    if (!s || !g_host || !xi_host) return SP_ERR_INVALID_ARG;
+    if (degree < 1 || degree > 4096) {
+        s->err = "sqrt_apply: degree must be in [1, 4096]";
+        return SP_ERR_INVALID_ARG;
+    }
+    if (!s->assembled) {
+        s->err = "sqrt_apply: assemble the system first";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    const KParams& P = s->kp;
+    DevBuffers& B = s->B;
+    const int n = P.n, np = P.npad;
+    const size_t v3 = 3 * (size_t)np;
+    double* t[3] = {nullptr, nullptr, nullptr};
+    double* y = nullptr;
+    float4* td[4] = {nullptr, nullptr, nullptr, nullptr};   // mixed path: T_k records x 3 and xi
+    unsigned long long* bound = nullptr;
+    int rc = SP_OK;
+    auto A_ = [&](int r) { if (rc == SP_OK) rc = r; };
+    const bool df = P.mixed != 0;
+    A_(dev_alloc(s, &t[0], v3));   // g in the rows' order (both paths)
+    A_(dev_alloc(s, &y, v3));
+    if (df) {
+        for (auto& p : td) A_(dev_alloc(s, &p, 2 * (size_t)np));
+    } else {
+        A_(dev_alloc(s, &t[1], v3));
+        A_(dev_alloc(s, &t[2], v3));
+    }
+    A_(dev_alloc(s, &bound, 1));
+    unsigned long long bbits = 0;
+    if (rc == SP_OK) {
+        // g (particle order) into the rows' order
+        if (cudaMemcpyAsync(B.stage, g_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+            rc = SP_ERR_CUDA;
+        if (rc == SP_OK) {
+            launch_gather_by_id(B.stage, B.id_w, n, np, t[0], s->stream);
+            if (cheb_bound(P, B, bound, s->stream) != cudaSuccess ||
+                cudaMemcpyAsync(&bbits, bound, sizeof(bbits), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+                cudaStreamSynchronize(s->stream) != cudaSuccess)
+                rc = SP_ERR_CUDA;
+        }
+    }
+    double lmax = 1.0;
+    std::memcpy(&lmax, &bbits, sizeof(lmax));
+    if (rc == SP_OK && lambda_max) *lambda_max = lmax;
+    if (rc == SP_OK && !(lmax - 1.0 > 1e-12)) {   // A = I: xi = g
+        std::memcpy(xi_host, g_host, sizeof(double) * 3 * n);
+    } else if (rc == SP_OK) {
+        // Chebyshev interpolant of sqrt on [1, lmax] at degree + 1 points of the first kind
+        const int N = degree + 1;
+        const double pi = 3.141592653589793238462643383279502884;
+        std::vector<double> c(N);
+        for (int k = 0; k < N; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < N; ++j) {
+                const double th = pi * (j + 0.5) / N;
+                acc += std::sqrt(0.5 * (lmax - 1.0) * std::cos(th) + 0.5 * (lmax + 1.0)) * std::cos(k * th);
+            }
+            c[k] = 2.0 / N * acc;
+        }
+        const double s1 = 2.0 / (lmax - 1.0), s0 = (lmax + 1.0) / (lmax - 1.0);
+        // T_0 = g in t[0]; T_1 in t[1]; then T_{k+1} = 2 u T_k - T_{k-1}
+        int i0 = 0, i1 = 1, i2 = 2;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (df && cheb_split(P, t[0], td[0], s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+        if (steps_ms) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, s->stream);
+        }
+        auto step = [&](int tc, int tp, int tn, double ck, double c0h, bool first) {
+            return df ? cheb_step_df(P, B, td[tc], first ? nullptr : td[tp], td[tn], td[3], s1, s0, ck, c0h, first,
+                                     s->stream)
+                      : cheb_step(P, B, t[tc], first ? nullptr : t[tp], t[tn], y, s1, s0, ck, c0h, first, s->stream);
+        };
+        if (rc == SP_OK && step(i0, 0, i1, c[1], 0.5 * c[0], true) != cudaSuccess) rc = SP_ERR_CUDA;
+        for (int k = 2; rc == SP_OK && k <= degree; ++k) {
+            if (step(i1, i0, i2, c[k], 0.0, false) != cudaSuccess) rc = SP_ERR_CUDA;
+            const int tmp = i0;
+            i0 = i1;
+            i1 = i2;
+            i2 = tmp;
+        }
+        if (steps_ms) cudaEventRecord(e1, s->stream);
+        if (rc == SP_OK && df && cheb_join(P, td[3], y, s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+        if (rc == SP_OK) {
+            launch_scatter_by_id(y, np, B.id_w, n, B.stage, s->stream);
+            if (cudaMemcpyAsync(xi_host, B.stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s->stream) != cudaSuccess)
+                rc = SP_ERR_CUDA;
+        }
+        if (steps_ms) {
+            float ms = 0.f;
+            if (rc == SP_OK) cudaEventElapsedTime(&ms, e0, e1);
+            *steps_ms = ms;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+    } else if (steps_ms) {
+        *steps_ms = 0.0;
+    }
+    if (rc == SP_ERR_CUDA) s->err = std::string("sqrt_apply: ") + cudaGetErrorString(cudaGetLastError());
+    for (auto p : t) cudaFree(p);
+    for (auto p : td) cudaFree(p);
+    cudaFree(y);
+    cudaFree(bound);
+    return rc;
+}
+
 static void vc_info(const VcStats& st, long long n, sp_vcorr_info* info)
 {
     if (!info) return;

@@ -198,6 +198,15 @@ int sp_stress_xy(sp_sim* sim, double* sigma_xy);
 int sp_sqrt_apply(sp_sim* sim, int32_t degree, const double* g_host, double* xi_host, double* lambda_max,
                   double* steps_ms);
 
+/* Steps with A^(1/2)-correlated noise: with degree > 0 every step of sp_step /
+ * sp_step_host replaces the independent normals g in its right-hand side by
+ * xi = p(A) g as sp_sqrt_apply forms it (on the device, inside the step's
+ * graph): b += (noise amplitude / zeta) (xi - g) after the assembly.  degree =
+ * 0 restores the paper's independent noise (the default).  Costs one SpMV
+ * per degree per step.  Errors: SP_ERR_INVALID_ARG (degree outside [0, 4096]),
+ * SP_ERR_OOM. */
+int sp_set_fdt_noise(sp_sim* sim, int32_t degree);
+
 /* Velocity cross-correlation versus distance (§Results, Fig. vv): the average
  * inter-chain velocity product <v_c . v_c'> / <v_c^2> against |R_cc'|.
  * u_c = v_c - kappa (y_c - L_y/2) x is the velocity relative to the imposed

@@ -113,7 +113,7 @@ def load(path: str = LIB_PATH):
             ("sp_step_host", [vp, vp, ctypes.c_double, i32, vp, P(sp_step_info)]),
             ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
             ("sp_velocity_correlation", [vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
-            ("sp_sqrt_apply", [vp, i32, vp, vp, P(d), P(d)]),
+            ("sp_sqrt_apply", [vp, i32, vp, vp, P(d), P(d)]), ("sp_set_fdt_noise", [vp, i32]),
             ("sp_velocity_correlation_host", [i32, i64, vp, d, d, vp, vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
@@ -415,6 +415,10 @@ class Simulation:
         lmax, ms = ctypes.c_double(), ctypes.c_double()
         self._c(load().sp_sqrt_apply(self._h, int(degree), _p(g), _p(xi), ctypes.byref(lmax), ctypes.byref(ms)))
         return (xi, lmax.value, ms.value) if timing else (xi, lmax.value)
+
+    def set_fdt_noise(self, degree: int):
+        """Steps with A^(1/2)-correlated noise (Chebyshev degree `degree`; 0: independent noise)."""
+        self._c(load().sp_set_fdt_noise(self._h, int(degree)))
 
     def velocity_correlation(self, nbins: int, rmax: float) -> dict:
         """Fig. vv on the current positions and the last solve's velocities (sp_velocity_correlation)."""

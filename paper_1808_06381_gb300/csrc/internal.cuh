@@ -802,10 +802,26 @@ cudaError_t run_structure_factor(const KParams& P, const DevBuffers& B, double d
 
 // fdt.cu: xi = p(A) g ~ A^(1/2) g (Chebyshev interpolant of sqrt on [1, lambda_max])
 cudaError_t cheb_bound(const KParams& P, DevBuffers& B, unsigned long long* out_dev, cudaStream_t s);
+// Work arrays of xi = p(A) g: v[0] holds g, v[1..3] the rotating T_k, v[4] xi;
+// each 3 npad doubles (FP64 path) or 2 npad float4 records (mixed path).
+struct FdtBuffers {
+    void* v[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* cs = nullptr;            // [2 + 4097] interval map and coefficients
+    float2* csf = nullptr;           // the same as double-floats
+    unsigned long long* bound = nullptr;
+};
+constexpr int kFdtMaxDegree = 4096;
+// xi = p(A) g with g already in V.v[0]; returns the kernels launched
+int enqueue_cheb(const KParams& P, DevBuffers& B, FdtBuffers& V, int degree, cudaStream_t s);
+// the step's right-hand side with A^(1/2)-correlated noise: g from the assembly's
+// normals into V.v[0], xi = p(A) g, b += (amp / zeta) (xi - g); returns the kernels launched
+int enqueue_fdt_noise(const KParams& P, DevBuffers& B, FdtBuffers& V, int degree, bool use_inj, cudaStream_t s);
+// cs: [0] 2 / (b - a), [1] (b + a) / (b - a), [2 + k] c_k (k <= degree); csf: the same as double-floats
+cudaError_t cheb_coeffs(const unsigned long long* bound, int degree, double* cs, float2* csf, cudaStream_t s);
 cudaError_t cheb_step(const KParams& P, DevBuffers& B, const double* tc, const double* tp, double* tn, double* y,
-                      double s1, double s0, double ck, double c0h, bool first, cudaStream_t s);
+                      const double* cs, int k, cudaStream_t s);
 cudaError_t cheb_step_df(const KParams& P, DevBuffers& B, const float4* tc, const float4* tp, float4* tn, float4* y,
-                         double s1, double s0, double ck, double c0h, bool first, cudaStream_t s);
+                         const float2* csf, int k, cudaStream_t s);
 cudaError_t cheb_split(const KParams& P, const double* g, float4* t, cudaStream_t s);
 cudaError_t cheb_join(const KParams& P, const float4* y, double* out, cudaStream_t s);
 

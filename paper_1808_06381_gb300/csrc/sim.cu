@@ -23,6 +23,7 @@
 
 using namespace ss;
 
+
 #include "sim_impl.cuh"
 
 namespace ss_host {
@@ -48,6 +49,38 @@ int dev_alloc(sp_sim* s, T** ptr, size_t count)
     *ptr = static_cast<T*>(q);
     return SP_OK;
 }
+
+namespace {
+// Work arrays of xi = p(A) g for this simulation's sizes (the form of its solver).
+int fdt_alloc(sp_sim* s, FdtBuffers& V)
+{
+    const size_t bytes = s->kp.mixed ? sizeof(float4) * 2 * (size_t)s->kp.npad : sizeof(double) * 3 * (size_t)s->kp.npad;
+    int rc = SP_OK;
+    auto A_ = [&](int r) { if (rc == SP_OK) rc = r; };
+    for (auto& p : V.v) {
+        char* q = nullptr;
+        A_(dev_alloc(s, &q, bytes));
+        p = q;
+    }
+    A_(dev_alloc(s, &V.cs, 2 + kFdtMaxDegree + 1));
+    A_(dev_alloc(s, &V.csf, 2 + kFdtMaxDegree + 1));
+    A_(dev_alloc(s, &V.bound, 1));
+    return rc;
+}
+
+void fdt_free(FdtBuffers& V)
+{
+    for (auto& p : V.v) {
+        cudaFree(p);
+        p = nullptr;
+    }
+    cudaFree(V.cs);
+    cudaFree(V.csf);
+    cudaFree(V.bound);
+    V = FdtBuffers{};
+}
+}  // namespace
+
 
 void free_graphs(sp_sim* s)
 {
@@ -375,6 +408,8 @@ int capture_step_graph(sp_sim* s)
     SS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     long long launches = enqueue_build(s, cs, side, ev, side_split);
     launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, cs));
+    if (s->fdt_degree > 0)   // the right-hand side with A^(1/2)-correlated noise
+        launches += enqueue_fdt_noise(s->kp, s->B, s->fdt, s->fdt_degree, s->use_inj, cs);
     if (s->learned) {
         launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, cs));
         launches += mp_infer_launches();
@@ -556,6 +591,7 @@ int sp_sim_destroy(sp_sim* s)
     free_graphs(s);
     DevBuffers& B = s->B;
     vc_free(s->vc);
+    fdt_free(s->fdt);
     void* ptrs[] = {B.pos_s, B.id_s, B.v_s, B.pos_w, B.pos32, B.id_w, B.cell_of, B.slot, B.perm,
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
@@ -832,6 +868,8 @@ int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
             for (long long k = 0; k < todo; ++k) {
                 launches += enqueue_build(s, s->stream);
                 launches += launch_nbr_fill(s->kp, s->B, true, s->use_inj, mixed(s), launch_of(s, s->stream));
+                if (s->fdt_degree > 0)
+                    launches += enqueue_fdt_noise(s->kp, s->B, s->fdt, s->fdt_degree, s->use_inj, s->stream);
                 if (s->learned) {
                     launch_mp_infer(s->kp, s->B, s->mp, launch_of(s, s->stream));
                     launches += mp_infer_launches();
@@ -1355,7 +1393,7 @@ int sp_sqrt_apply(sp_sim* s, int32_t degree, const double* g_host, double* xi_ho
                   double* steps_ms)
 {
     if (!s || !g_host || !xi_host) return SP_ERR_INVALID_ARG;
-    if (degree < 1 || degree > 4096) {
+    if (degree < 1 || degree > kFdtMaxDegree) {
         s->err = "sqrt_apply: degree must be in [1, 4096]";
         return SP_ERR_INVALID_ARG;
     }
@@ -1367,102 +1405,71 @@ int sp_sqrt_apply(sp_sim* s, int32_t degree, const double* g_host, double* xi_ho
     const KParams& P = s->kp;
     DevBuffers& B = s->B;
     const int n = P.n, np = P.npad;
-    const size_t v3 = 3 * (size_t)np;
-    double* t[3] = {nullptr, nullptr, nullptr};
-    double* y = nullptr;
-    float4* td[4] = {nullptr, nullptr, nullptr, nullptr};   // mixed path: T_k records x 3 and xi
-    unsigned long long* bound = nullptr;
-    int rc = SP_OK;
-    auto A_ = [&](int r) { if (rc == SP_OK) rc = r; };
-    const bool df = P.mixed != 0;
-    A_(dev_alloc(s, &t[0], v3));   // g in the rows' order (both paths)
-    A_(dev_alloc(s, &y, v3));
-    if (df) {
-        for (auto& p : td) A_(dev_alloc(s, &p, 2 * (size_t)np));
-    } else {
-        A_(dev_alloc(s, &t[1], v3));
-        A_(dev_alloc(s, &t[2], v3));
-    }
-    A_(dev_alloc(s, &bound, 1));
+    FdtBuffers V;
+    double* planes = nullptr;   // g, then xi, as FP64 planes in the rows' order
+    int rc = fdt_alloc(s, V);
+    if (rc == SP_OK) rc = dev_alloc(s, &planes, 3 * (size_t)np);
     unsigned long long bbits = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == SP_OK) {
-        // g (particle order) into the rows' order
         if (cudaMemcpyAsync(B.stage, g_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
             rc = SP_ERR_CUDA;
-        if (rc == SP_OK) {
-            launch_gather_by_id(B.stage, B.id_w, n, np, t[0], s->stream);
-            if (cheb_bound(P, B, bound, s->stream) != cudaSuccess ||
-                cudaMemcpyAsync(&bbits, bound, sizeof(bbits), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
-                cudaStreamSynchronize(s->stream) != cudaSuccess)
-                rc = SP_ERR_CUDA;
-        }
     }
-    double lmax = 1.0;
-    std::memcpy(&lmax, &bbits, sizeof(lmax));
-    if (rc == SP_OK && lambda_max) *lambda_max = lmax;
-    if (rc == SP_OK && !(lmax - 1.0 > 1e-12)) {   // A = I: xi = g
-        std::memcpy(xi_host, g_host, sizeof(double) * 3 * n);
-    } else if (rc == SP_OK) {
-        // Chebyshev interpolant of sqrt on [1, lmax] at degree + 1 points of the first kind
-        const int N = degree + 1;
-        const double pi = 3.141592653589793238462643383279502884;
-        std::vector<double> c(N);
-        for (int k = 0; k < N; ++k) {
-            double acc = 0.0;
-            for (int j = 0; j < N; ++j) {
-                const double th = pi * (j + 0.5) / N;
-                acc += std::sqrt(0.5 * (lmax - 1.0) * std::cos(th) + 0.5 * (lmax + 1.0)) * std::cos(k * th);
-            }
-            c[k] = 2.0 / N * acc;
-        }
-        const double s1 = 2.0 / (lmax - 1.0), s0 = (lmax + 1.0) / (lmax - 1.0);
-        // T_0 = g in t[0]; T_1 in t[1]; then T_{k+1} = 2 u T_k - T_{k-1}
-        int i0 = 0, i1 = 1, i2 = 2;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (df && cheb_split(P, t[0], td[0], s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
+    if (rc == SP_OK) {
+        launch_gather_by_id(B.stage, B.id_w, n, np, planes, s->stream);
+        if (P.mixed)
+            cheb_split(P, planes, static_cast<float4*>(V.v[0]), s->stream);
+        else
+            cudaMemcpyAsync(V.v[0], planes, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream);
         if (steps_ms) {
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             cudaEventRecord(e0, s->stream);
         }
-        auto step = [&](int tc, int tp, int tn, double ck, double c0h, bool first) {
-            return df ? cheb_step_df(P, B, td[tc], first ? nullptr : td[tp], td[tn], td[3], s1, s0, ck, c0h, first,
-                                     s->stream)
-                      : cheb_step(P, B, t[tc], first ? nullptr : t[tp], t[tn], y, s1, s0, ck, c0h, first, s->stream);
-        };
-        if (rc == SP_OK && step(i0, 0, i1, c[1], 0.5 * c[0], true) != cudaSuccess) rc = SP_ERR_CUDA;
-        for (int k = 2; rc == SP_OK && k <= degree; ++k) {
-            if (step(i1, i0, i2, c[k], 0.0, false) != cudaSuccess) rc = SP_ERR_CUDA;
-            const int tmp = i0;
-            i0 = i1;
-            i1 = i2;
-            i2 = tmp;
-        }
+        enqueue_cheb(P, B, V, degree, s->stream);
         if (steps_ms) cudaEventRecord(e1, s->stream);
-        if (rc == SP_OK && df && cheb_join(P, td[3], y, s->stream) != cudaSuccess) rc = SP_ERR_CUDA;
-        if (rc == SP_OK) {
-            launch_scatter_by_id(y, np, B.id_w, n, B.stage, s->stream);
-            if (cudaMemcpyAsync(xi_host, B.stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(s->stream) != cudaSuccess)
-                rc = SP_ERR_CUDA;
-        }
+        if (P.mixed)
+            cheb_join(P, static_cast<float4*>(V.v[4]), planes, s->stream);
+        else
+            cudaMemcpyAsync(planes, V.v[4], sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream);
+        launch_scatter_by_id(planes, np, B.id_w, n, B.stage, s->stream);
+        if (cudaMemcpyAsync(xi_host, B.stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&bbits, V.bound, sizeof(bbits), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            rc = SP_ERR_CUDA;
+    }
+    if (rc == SP_OK) {
+        double lmax = 1.0;
+        std::memcpy(&lmax, &bbits, sizeof(lmax));
+        if (lambda_max) *lambda_max = lmax;
         if (steps_ms) {
             float ms = 0.f;
-            if (rc == SP_OK) cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&ms, e0, e1);
             *steps_ms = ms;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
         }
-    } else if (steps_ms) {
-        *steps_ms = 0.0;
     }
     if (rc == SP_ERR_CUDA) s->err = std::string("sqrt_apply: ") + cudaGetErrorString(cudaGetLastError());
-    for (auto p : t) cudaFree(p);
-    for (auto p : td) cudaFree(p);
-    cudaFree(y);
-    cudaFree(bound);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    fdt_free(V);
+    cudaFree(planes);
     return rc;
+}
+
+int sp_set_fdt_noise(sp_sim* s, int32_t degree)
+{
+    if (!s) return SP_ERR_INVALID_ARG;
+    if (degree < 0 || degree > kFdtMaxDegree) {
+        s->err = "fdt noise: degree must be in [0, 4096]";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    if (degree > 0 && !s->fdt.v[0]) SS_TRY(fdt_alloc(s, s->fdt));
+    s->fdt_degree = degree;
+    free_graphs(s);   // the step graph is captured again with (or without) the noise pass
+    return SP_OK;
 }
 
 static void vc_info(const VcStats& st, long long n, sp_vcorr_info* info)

@@ -35,6 +35,8 @@ struct sp_sim {
     bool learned = false;         // run the network before every solve of a step
     int mp_t = 0;                 // Adam step counter
     ss::VcBuffers vc{};           // velocity correlation (allocated by its first call)
+    ss::FdtBuffers fdt{};         // A^(1/2)-correlated noise in the steps (sp_set_fdt_noise)
+    int fdt_degree = 0;           // 0: independent noise per particle (the paper's)
     std::string err;
 };
 

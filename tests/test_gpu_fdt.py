@@ -73,3 +73,48 @@ def test_fdt_step_through_the_api_matches_the_oracle():
     xi_ref, _ = oracle.sqrt_apply(sysr, g, 32)
     ref, _, _ = oracle.pcg(oracle.assemble(p, pos, pairs, xi_ref, delta), 1e-13)
     assert np.abs(v - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision,tol,pos_tol", [("fp64", 1e-13, 1e-10), ("mixed", 1e-11, 1e-9)])
+def test_fdt_steps_follow_the_oracle(precision, tol, pos_tol):
+    """sp_step with A^(1/2)-correlated noise against the oracle's step whose
+    normals are the oracle's p(A) g for the same step (two steps: the second
+    uses the first's positions, offset and step counter)."""
+    n, steps, degree = 1500, 2, 24
+    L = synth.box_length(n)
+    seed = 31
+    pos = synth.uniform_positions(n, (L, L, L), seed)
+    kappa = ss.kappa_from_kappa_tau(0.5)
+    sim = ss.Simulation(n, (L, L, L), kappa, seed=seed, positions=pos, precision=precision, warm_start="prev",
+                        cg_tol=tol, cg_max_iter=5000)
+    sim.set_fdt_noise(degree)
+    info = sim.step(steps)
+    assert info["status"] == 0
+    gpos = sim.get_positions()
+    sim.close()
+    p = oracle.Params(n=n, L=(L, L, L), kappa=kappa, seed=seed)
+    opos, od = pos, 0.0
+    for s in range(steps):
+        sysr = oracle.assemble(p, opos, oracle.neighbors(p, opos, od), np.zeros((n, 3)), od)
+        xi, _ = oracle.sqrt_apply(sysr, oracle.noise(seed, s, np.arange(n)), degree)
+        r = oracle.step(p, opos, od, s, xi=xi, tol=1e-13)
+        opos, od = r.pos, r.delta
+    d = gpos - opos
+    d -= np.round(d / L) * L
+    assert np.abs(d).max() < pos_tol * steps
+
+
+def test_fdt_off_again_is_the_paper_noise():
+    n = 1200
+    L = synth.box_length(n)
+    outs = []
+    for toggle in (False, True):
+        pos = synth.uniform_positions(n, (L, L, L), 5)
+        sim = ss.Simulation(n, (L, L, L), ss.kappa_from_kappa_tau(0.5), seed=5, positions=pos, warm_start="prev")
+        if toggle:
+            sim.set_fdt_noise(16)
+            sim.set_fdt_noise(0)
+        sim.step(2)
+        outs.append(sim.get_positions())
+        sim.close()
+    assert np.array_equal(outs[0], outs[1])

@@ -711,6 +711,10 @@ def run_vcorr(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per launch of k_cheb_step_df on this workload (one ncu capture)
+FDT_PROFILED_TRAFFIC = 55.94e6
+
+
 def fdt_algorithmic_bytes(n: int, nnz: int) -> float:
     """One Chebyshev degree step (mixed path, double-float records): per entry the
     column, the weight's two FP32 parts and the gathered 32-byte record of T_k; per row
@@ -764,7 +768,8 @@ def run_fdt(args):
                        "l2": "flushed between calls (512 MB write)"},
             "gpu_launches": args.steps * (degree + 4),
             "roofline": {"kernel": "k_cheb_step", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "traffic": None, "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                         "frac": ach / peak, "traffic": FDT_PROFILED_TRAFFIC,
+                         "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
                          "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": step_ms},
             "e2e": {"value": w.n / (ms_call * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": w.n * 24,
                     "d2h_bytes_per_step": w.n * 24 + 8},

@@ -767,7 +767,7 @@ def run_fdt(args):
             "config": {"workload": w.name, "n": w.n, "degree": degree, "lambda_max": lmax,
                        "l2": "flushed between calls (512 MB write)"},
             "gpu_launches": args.steps * (degree + 4),
-            "roofline": {"kernel": "k_cheb_step", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "roofline": {"kernel": "k_cheb_step_df", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "traffic": FDT_PROFILED_TRAFFIC,
                          "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
                          "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": step_ms},

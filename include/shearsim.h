@@ -203,7 +203,8 @@ int sp_sqrt_apply(sp_sim* sim, int32_t degree, const double* g_host, double* xi_
  * xi = p(A) g as sp_sqrt_apply forms it (on the device, inside the step's
  * graph): b += (noise amplitude / zeta) (xi - g) after the assembly.  degree =
  * 0 restores the paper's independent noise (the default).  Costs one SpMV
- * per degree per step.  Errors: SP_ERR_INVALID_ARG (degree outside [0, 4096]),
+ * per degree per step.  Batched steps (sp_batch_step) keep the independent
+ * noise.  Errors: SP_ERR_INVALID_ARG (degree outside [0, 4096]),
  * SP_ERR_OOM. */
 int sp_set_fdt_noise(sp_sim* sim, int32_t degree);
 

@@ -133,8 +133,20 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
     static_assert(K <= 2, "two values at most");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     dfloat w[K];
+    constexpr bool f32 = sizeof(OutT) == sizeof(float);
+    // FP32 totals (the iteration's scalars): the block's sums in FP32 (a tree
+    // of ~10 levels, ~6e-7 of the summed magnitudes), the grid's in double-float
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = warp_sum_df(v[k]);
+    for (int k = 0; k < K; ++k) {
+        if constexpr (f32) {
+            float f = __fadd_rn(v[k].hi, v[k].lo);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+            w[k] = dfloat{f, 0.f};
+        } else {
+            w[k] = warp_sum_df(v[k]);
+        }
+    }
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) sh.dfk[k][warp] = make_float2(w[k].hi, w[k].lo);
@@ -145,7 +157,14 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float2 a = lane < nw ? sh.dfk[k][lane] : make_float2(0.f, 0.f);
-            w[k] = warp_sum_df(dfloat{a.x, a.y});
+            if constexpr (f32) {
+                float f = a.x;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+                w[k] = dfloat{f, 0.f};
+            } else {
+                w[k] = warp_sum_df(dfloat{a.x, a.y});
+            }
         }
         if (lane == 0) {
 #pragma unroll

@@ -1071,7 +1071,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             q[u][0] = q0;
             q[u][1] = q1;
             q[u][2] = q2;
-            pq = df_add(pq, p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2]);
+            pq.hi += p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2];   // FP32, as the block sums
         }
         {
             const dfloat v[1] = {pq};
@@ -1102,8 +1102,8 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 r[u][c] = fmaf(-af, q[u][c], r[u][c]);
             }
             const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
-            rr = df_add(rr, rsq);
-            rz = df_add(rz, dv[u] * rsq);
+            rr.hi += rsq;   // FP32, as the block sums
+            rz.hi += dv[u] * rsq;
             B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
             zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
         }

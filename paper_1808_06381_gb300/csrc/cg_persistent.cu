@@ -134,8 +134,9 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     dfloat w[K];
     constexpr bool f32 = sizeof(OutT) == sizeof(float);
-    // FP32 totals (the iteration's scalars): the block's sums in FP32 (a tree
-    // of ~10 levels, ~6e-7 of the summed magnitudes), the grid's in double-float
+    // FP32 totals (the iteration's scalars): every level of the sums in FP32
+    // (trees and short runs, ~1e-6 of the summed magnitudes; the scalars are
+    // FP32 anyway), in one fixed order, so every block holds the same totals
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if constexpr (f32) {
@@ -183,19 +184,24 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
             }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            dfloat a{0.f, 0.f};
+            if constexpr (f32) {   // the blocks' FP32 sums, summed in FP32 in a fixed order
+                float a = 0.f;
 #pragma unroll
-            for (int u = 0; u < kPartialsPerLane; ++u) a = df_add(a, dfloat{pv[k][u].x, pv[k][u].y});
-            for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) {
-                const float2 p = __ldcg(partials + k * kMaxPartials + b);
-                a = df_add(a, dfloat{p.x, p.y});
-            }
-            a = warp_sum_df(a);
-            if (lane == 0) {
-                if constexpr (sizeof(OutT) == sizeof(float))
-                    sh.bcastf[k] = __fadd_rn(a.hi, a.lo);   // no FP64 operation on the iteration's path
-                else
-                    sh.bcast[k] = (double)a.hi + (double)a.lo;
+                for (int u = 0; u < kPartialsPerLane; ++u) a += pv[k][u].x;
+                for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) a += __ldcg(partials + k * kMaxPartials + b).x;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) sh.bcastf[k] = a;   // no FP64 operation on the iteration's path
+            } else {
+                dfloat a{0.f, 0.f};
+#pragma unroll
+                for (int u = 0; u < kPartialsPerLane; ++u) a = df_add(a, dfloat{pv[k][u].x, pv[k][u].y});
+                for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) {
+                    const float2 p = __ldcg(partials + k * kMaxPartials + b);
+                    a = df_add(a, dfloat{p.x, p.y});
+                }
+                a = warp_sum_df(a);
+                if (lane == 0) sh.bcast[k] = (double)a.hi + (double)a.lo;
             }
         }
         if (lane == 0) {

@@ -716,18 +716,18 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         if (row < 0) continue;
         const int c = slot >> 5, e1 = B.chunk_off[c + 1];
         int nl = 0, nh = 0;
-        for (int eb = B.chunk_off[c] + (slot & 31); eb < e1; eb += 32 * KS) {
-            int j[KS];
-            float v[KS];
+        // the columns alone: a padding entry of the sliced layout points at its
+        // own row (and has weight 0), a real partner never does
+        for (int eb = B.chunk_off[c] + (slot & 31); eb < e1; eb += 32 * 2 * KS) {
+            int j[2 * KS];
 #pragma unroll
-            for (int u = 0; u < KS; ++u) {
+            for (int u = 0; u < 2 * KS; ++u) {
                 const int e = eb + 32 * u;
-                j[u] = e < e1 ? ld_stream(B.col + e) : 0;
-                v[u] = e < e1 ? ld_stream(B.val32 + e) : 0.f;
+                j[u] = e < e1 ? ld_stream(B.col + e) : row;
             }
 #pragma unroll
-            for (int u = 0; u < KS; ++u) {
-                if (v[u] != 0.f) {
+            for (int u = 0; u < 2 * KS; ++u) {
+                if (j[u] != row) {
                     if (j[u] >= rb && j[u] < re) ++nl; else ++nh;
                 }
             }

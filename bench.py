@@ -143,7 +143,7 @@ class ClockSampler:
 # and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
 # block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 96.4e6,
+PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 95.5e6,
                     ("mixed-n262144", 6, 1, False, 1024, False): 122.0e6}
 
 

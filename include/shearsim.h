@@ -53,7 +53,8 @@ typedef enum sp_status {
     SP_ERR_OOM = -5,            /* device allocation failed */
     SP_ERR_BOX_TOO_SMALL = -6,  /* some box edge is below 2 r_c: the minimum image is ambiguous */
     SP_ERR_NO_DEVICE = -7,      /* no CUDA device, or the requested ordinal does not exist */
-    SP_ERR_TIMEOUT = -8         /* a device-side wait of the persistent solver ran past its limit */
+    SP_ERR_TIMEOUT = -8         /* a device-side wait of the persistent solver ran past its limit
+                                   (sp_set_wait_limit) */
 } sp_status;
 
 enum sp_precision {
@@ -95,6 +96,8 @@ typedef struct sp_solve_info {
     double bnorm;         /* ||b||_2 */
     int32_t offchip_blocks; /* on-chip solver configuration: blocks whose rows and entries did not
                                fit on their SM and were solved with global gathers (0 otherwise) */
+    int32_t host_driven;    /* 1: the solve's CG loop was driven from the host (graph capture
+                               unavailable, or SHEARSIM_HOST_LOOP=1); 0: it ran as one CUDA graph */
 } sp_solve_info;
 
 typedef struct sp_step_info {
@@ -107,6 +110,9 @@ typedef struct sp_step_info {
     int64_t kernel_launches; /* kernels this call ran on the GPU */
     double delta;            /* Lees-Edwards offset after the steps (as sp_get_state) */
     int64_t step;            /* step counter after the steps (as sp_get_state) */
+    int32_t host_driven;     /* 1: the steps' kernels were launched from a host loop (graph capture
+                                unavailable, or SHEARSIM_HOST_LOOP=1); 0: each step ran as one CUDA
+                                graph with the CG loop inside it */
 } sp_step_info;
 
 typedef struct sp_sim sp_sim;
@@ -154,7 +160,10 @@ int sp_step(sp_sim* sim, int32_t nsteps, sp_step_info* info);
  * replace the state, nsteps steps run, and the positions after them are
  * written to pos_out [n][3] by particle id (may alias pos_in).  One
  * synchronisation in the common case (the host arrays are read and written
- * before the call returns).  Errors: those of sp_set_positions and sp_step. */
+ * before the call returns).  The positions are checked on the device as in
+ * sp_set_positions, inside the same synchronisation: invalid ones return
+ * SP_ERR_INVALID_ARG with no step taken.  Errors: those of sp_set_positions
+ * and sp_step. */
 int sp_step_host(sp_sim* sim, const double* pos_in, double delta, int32_t nsteps, double* pos_out,
                  sp_step_info* info);
 /* Bytes of the state record (step statistics, CG scalars, flags) that
@@ -331,7 +340,10 @@ int sp_set_solver_config(sp_sim* sim, int32_t config, sp_tune_info* info);
 /* Positions [n][3] by particle id. */
 int sp_get_positions(sp_sim* sim, double* pos_host);
 /* Replace positions ([n][3] by particle id, each in [0, L)) and the
- * Lees-Edwards offset delta in [0, L_x). */
+ * Lees-Edwards offset delta in [0, L_x).  Every coordinate is checked on the
+ * device as it is gathered: a NaN, an infinity or a value outside [0, L_a)
+ * returns SP_ERR_INVALID_ARG, after which the simulation's positions are
+ * undefined until valid ones are set (the simulation itself stays usable). */
 int sp_set_positions(sp_sim* sim, const double* pos_host, double delta);
 /* Velocities of the last solve [n][3] by particle id. */
 int sp_get_velocities(sp_sim* sim, double* v_host);
@@ -339,6 +351,12 @@ int sp_get_velocities(sp_sim* sim, double* v_host);
 int sp_get_state(sp_sim* sim, double* delta, int64_t* step);
 /* Set the step counter, e.g. to resume a checkpoint (positions via sp_set_positions). */
 int sp_set_step(sp_sim* sim, int64_t step);
+/* Limit of one device-side wait of the persistent solvers (a block waiting at
+ * a grid barrier for the other blocks), in seconds, (0, 60]; 2 s by default.
+ * A wait that runs past it makes the solve return SP_ERR_TIMEOUT instead of
+ * waiting on; the simulation stays usable.  Not in the paper (a safety bound
+ * of the implementation).  Errors: SP_ERR_INVALID_ARG. */
+int sp_set_wait_limit(sp_sim* sim, double seconds);
 /* Particle id of each internal row, [n] (rows are kept in cell order). */
 int sp_get_order(sp_sim* sim, int64_t* ids_host);
 /* Number of pairs i < j found by the last sp_build_neighbors / sp_step. */
@@ -436,6 +454,10 @@ const char* sp_batch_last_error(const sp_batch* b);
  *   row_ptr_dev [n+1], col_dev [nnz] (int32), w_dev [nnz], diag_dev [n] (A_ii),
  *   b_dev [3][n] and x_dev [3][n] (x, y, z planes) — all caller-owned device
  *   memory on `device`; x_dev is overwritten.  stream: a cudaStream_t or NULL.
+ *   row_ptr must start at 0 and never decrease, and every col entry must lie
+ *   in [0, n); a call that breaks either returns SP_ERR_INVALID_ARG before
+ *   any gather through the CSR (row_ptr[n] itself is the caller's to bound by
+ *   the real length of col_dev and w_dev).
  *
  * It allocates nothing: its working vectors live in one fixed device array
  * (about 3.2 MB) that every device context loading this library holds until
@@ -444,10 +466,17 @@ const char* sp_batch_last_error(const sp_batch* b);
  *   - every call on a device shares that array, so calls that may overlap on
  *     the GPU (several streams or host threads) race; serialise them;
  *   - the first call on a device looks up the array's address with that device
- *     current (the caller's current device is restored); make that first call
- *     before any stream capture.
- * Returns SP_OK, SP_ERR_NOT_CONVERGED (max_iter reached), SP_ERR_NONFINITE or
- * SP_ERR_CUDA; info (may be NULL) receives iterations and the true residual. */
+ *     current (the caller's current device is restored);
+ *   - every call reads the solver state back and synchronises `stream`, so it
+ *     can never be made while that stream is being captured into a CUDA graph
+ *     (such a call returns SP_ERR_INVALID_ARG and leaves the capture intact);
+ *   - device must be in [0, 63].
+ * Returns SP_OK; SP_ERR_INVALID_ARG (n, a pointer, tol, max_iter, alpha or
+ * device out of range, a malformed CSR, a capturing stream); SP_ERR_NOT_CONVERGED
+ * when max_iter iterations are reached, or when the exactly recomputed residual
+ * is still above tol after the restart limit (info->iterations is then below
+ * max_iter); SP_ERR_NONFINITE; SP_ERR_NO_DEVICE; SP_ERR_CUDA.  info (may be
+ * NULL) receives iterations and the true residual. */
 int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, const int32_t* row_ptr_dev,
                          const int32_t* col_dev, const double* w_dev, const double* diag_dev, double alpha,
                          const double* b_dev, double* x_dev, double tol, int32_t max_iter,

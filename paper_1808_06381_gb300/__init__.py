@@ -52,14 +52,14 @@ class sp_params(ctypes.Structure):
 
 class sp_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("residual", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32)]
+                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32), ("host_driven", ctypes.c_int32)]
 
 
 class sp_step_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("steps_done", ctypes.c_int64),
                 ("cg_iterations", ctypes.c_int64), ("last_residual", ctypes.c_double),
                 ("stress_xy", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("delta", ctypes.c_double),
-                ("step", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("host_driven", ctypes.c_int32)]
 
 
 class sp_kernel_profile(ctypes.Structure):
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
             ("sp_velocity_correlation_host", [i32, i64, vp, d, d, vp, vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
+            ("sp_set_wait_limit", [vp, d]),
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
@@ -318,7 +319,7 @@ class Simulation:
         if raise_on_error:
             self._c(rc)
         return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
-                "offchip_blocks": info.offchip_blocks}
+                "offchip_blocks": info.offchip_blocks, "host_driven": info.host_driven}
 
     def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
         info = sp_step_info()
@@ -328,7 +329,7 @@ class Simulation:
         return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,
                 "max_iterations": info.max_iterations, "last_residual": info.last_residual,
                 "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches, "delta": info.delta,
-                "step": info.step}
+                "step": info.step, "host_driven": info.host_driven}
 
     def step_host(self, pos_in, delta: float, nsteps: int, pos_out, raise_on_error: bool = True) -> dict:
         """sp_step_host: host positions [n][3] (by id) and offset in, nsteps steps, positions out."""
@@ -341,7 +342,7 @@ class Simulation:
         return {"status": rc, "steps_done": info.steps_done, "cg_iterations": info.cg_iterations,
                 "max_iterations": info.max_iterations, "last_residual": info.last_residual,
                 "stress_xy": info.stress_xy, "kernel_launches": info.kernel_launches, "delta": info.delta,
-                "step": info.step}
+                "step": info.step, "host_driven": info.host_driven}
 
     def structure_factor(self, nkx: int, nky: int, grid: int = 256):
         m = (2 * nkx + 1) * (2 * nky + 1)
@@ -456,6 +457,10 @@ class Simulation:
 
     def set_step(self, step: int):
         self._c(load().sp_set_step(self._h, int(step)))
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of one device-side grid-barrier wait of the persistent solvers (default 2 s)."""
+        self._c(load().sp_set_wait_limit(self._h, float(seconds)))
 
     def order(self) -> np.ndarray:
         out = np.zeros(self.n, dtype=np.int64)

@@ -297,6 +297,7 @@ int sp_batch_step(sp_batch* b, int32_t nsteps, sp_step_info* info)
             info[k].delta = s->st_host->delta;
             info[k].step = s->st_host->step;
             info[k].kernel_launches = (k == 0 ? (long long)nsteps * b->fixed_launches : 0) + 0 * checks;
+            info[k].host_driven = 0;   // the batch always steps by its captured graph
         }
         s->built = false;
         s->assembled = false;

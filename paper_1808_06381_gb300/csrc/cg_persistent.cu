@@ -16,7 +16,8 @@
 // flag copied next to it by that block.  After the barrier every block sums
 // all blocks' partial sums itself, in one fixed order.  The launch is
 // cooperative (all blocks resident), and every wait is bounded by the global
-// timer: a block that waits longer than kBarrierTimeoutNs sets
+// timer: a block that waits longer than the simulation's wait limit
+// (DevState::bar_timeout_ns, 2 s unless sp_set_wait_limit changed it) sets
 // SP_ERR_TIMEOUT and leaves the solve, so no GPU can hang on it.
 #include <math.h>
 
@@ -29,7 +30,6 @@ namespace ss {
 namespace {
 
 constexpr int kPBlock = 256;
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
 
 struct PShared {
     float2 df[32];
@@ -88,9 +88,10 @@ __device__ __forceinline__ int barrier_thread0(DevState* st, unsigned int target
         return e;
     }
     const unsigned long long t0 = global_ns();
-    for (unsigned int polls = 1;; ++polls) {
+    const unsigned long long limit = st->bar_timeout_ns;   // set by the host between launches
+    for (;;) {
         if (ld_acquire_gpu(&st->bar_gen) == target) return *(volatile int*)&st->bar_err;
-        if ((polls & 255u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
+        if (global_ns() - t0 > limit) {   // a timer read per poll: polls are L2 round trips anyway
             atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
             return (int)SP_ERR_TIMEOUT;
         }

@@ -203,6 +203,28 @@ void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, d
     k_gather_by_id<<<grid_for(n, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(in_n3, ids, n, npad, planes);
 }
 
+__global__ void k_gather_positions(const double* __restrict__ in, const int* __restrict__ ids, int n, int npad,
+                                   double* __restrict__ planes, double L0, double L1, double L2, DevState* st)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long id = ids[k];
+    const double x = in[3 * id], y = in[3 * id + 1], z = in[3 * id + 2];
+    // the comparisons are false for NaN, so a NaN fails them too
+    const bool ok = x >= 0.0 && x < L0 && y >= 0.0 && y < L1 && z >= 0.0 && z < L2;
+    if (!ok) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
+    planes[k] = x;
+    planes[npad + k] = y;
+    planes[2 * npad + k] = z;
+}
+
+void launch_gather_positions(const double* in_n3, const int* ids, int n, int npad, double* planes,
+                             const KParams& P, DevState* st, cudaStream_t s)
+{
+    k_gather_positions<<<grid_for(n, kVecBlock, 1 << 30), kVecBlock, 0, s>>>(in_n3, ids, n, npad, planes, P.L[0],
+                                                                             P.L[1], P.L[2], st);
+}
+
 __global__ void k_reset_step_stats(DevState* st)
 {
     st->iter_sum = 0;

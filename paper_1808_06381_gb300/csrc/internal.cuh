@@ -89,7 +89,10 @@ struct DevState {
     long long noise_step;     // step whose normals noise3 holds (-1: none)
     int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
     double delta_next;        // the offset the position update advanced to (committed after the stress)
+    unsigned long long bar_timeout_ns;   // limit of one grid-barrier wait of the persistent solvers
 };
+
+constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;   // 2 s
 
 // Device buffers of one simulation (all in the current cell order unless noted).
 struct DevBuffers {
@@ -793,6 +796,11 @@ void launch_scatter_by_id(const double* planes, int npad, const int* ids, int n,
                           cudaStream_t s);
 void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, double* planes,
                          cudaStream_t s);
+// The same for positions given by a caller: a coordinate that is not finite or
+// lies outside [0, L_a) sets st->error to SP_ERR_INVALID_ARG (the steps that
+// follow then do nothing and report it).
+void launch_gather_positions(const double* in_n3, const int* ids, int n, int npad, double* planes,
+                             const KParams& P, DevState* st, cudaStream_t s);
 void launch_reset_step_stats(DevState* st, cudaStream_t s);
 // sfactor.cu: S(q) at q_z = 0 for kx in [-nkx, nkx], ky in [-nky, nky] (kx slowest);
 // G = 0: direct sum over particles; G > 0: CIC grid of G x G in the sheared frame.

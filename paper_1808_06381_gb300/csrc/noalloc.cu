@@ -17,7 +17,10 @@
 //     the GPU (other streams, other host threads) race and must be serialised
 //     by the caller;
 //   - the first call on a device looks up the array's device address with that
-//     device current; make that first call before any stream capture.
+//     device current; every call reads the solver state back and synchronises
+//     its stream, so no call may be made on a stream that is being captured
+//     (such a call is rejected);
+//   - device ordinals 0 .. 63 (one looked-up address per device).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -124,9 +127,30 @@ __device__ __forceinline__ void na_row_apply(const NaSystem& S, const double* u,
     out3[2] = d * u[2 * kPlane + i] - S.alpha * s2;
 }
 
+// Rejects a malformed CSR before anything gathers through it: row_ptr must
+// start at 0 and never decrease, and every column must lie in [0, n) (a
+// column in [n, kPlane) would read another call's stale entries of the shared
+// array, one beyond it memory outside the array).
+__global__ void k_na_validate(NaSystem S, NaPtrs W)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+        const int b = S.row_ptr[i], e = S.row_ptr[i + 1];
+        bool bad = (i == 0 && b != 0) || e < b;
+        for (int k = b; k < e && !bad; ++k) {
+            const int j = S.col[k];
+            bad = j < 0 || (long long)j >= S.n;
+        }
+        if (bad) {
+            W.st->status = SP_ERR_INVALID_ARG;
+            W.st->done = 1;
+        }
+    }
+}
+
 // x = 0, r = b, z = D^-1 r, p = z; b.b and r.z.
 __global__ void k_na_init(NaSystem S, NaPtrs W)
 {
+    if (W.st->done) return;   // rejected by k_na_validate (uniform over the grid)
     double v[2] = {0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
         const double di = 1.0 / S.diag[i];
@@ -306,6 +330,16 @@ extern "C" int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, con
         cudaSetDevice(prev);
         return rc;
     };
+    // every call reads the solver state back and synchronises, which a stream
+    // under capture does not allow (checked before anything else touches the device)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess)
+        return finish(SP_ERR_CUDA, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone) {
+        err = "sp_solve_csr_noalloc: the stream is being captured; this call synchronises and cannot be captured";
+        cudaSetDevice(prev);
+        return SP_ERR_INVALID_ARG;
+    }
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);
@@ -323,6 +357,7 @@ extern "C" int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, con
     // the state (and the reduction ticket) must start at zero on every call
     if (cudaMemsetAsync(Wp.st, 0, sizeof(NaState), s) != cudaSuccess) return finish(SP_ERR_CUDA, "cudaMemsetAsync");
     const int grid = (int)std::min<long long>(kNaBlocks, (n + kNaThreads - 1) / kNaThreads);
+    k_na_validate<<<grid, kNaThreads, 0, s>>>(S, Wp);
     k_na_init<<<grid, kNaThreads, 0, s>>>(S, Wp);
     NaState h;
     std::memset(&h, 0, sizeof(h));
@@ -346,6 +381,12 @@ extern "C" int sp_solve_csr_noalloc(int32_t device, void* stream, int64_t n, con
         info->bnorm = std::sqrt(h.bnorm2);
         info->offchip_blocks = 0;
     }
-    if (status != SP_OK) err = "sp_solve_csr_noalloc: solve failed";
+    if (status == SP_ERR_INVALID_ARG)
+        err = "sp_solve_csr_noalloc: row_ptr must start at 0 and not decrease, and every col must lie in [0, n)";
+    else if (status == SP_ERR_NOT_CONVERGED)
+        err = "sp_solve_csr_noalloc: not converged (max_iter reached, or the true residual stayed above tol "
+              "after the restart limit)";
+    else if (status != SP_OK)
+        err = "sp_solve_csr_noalloc: solve failed";
     return finish(status, nullptr);
 }

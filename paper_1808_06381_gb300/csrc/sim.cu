@@ -293,7 +293,7 @@ int capture_cg_loop(sp_sim* s, cudaStream_t cs)
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     SS_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
 
-    cudaStream_t bs = s->cap_stream[1];
+    cudaStream_t bs = s->cap_stream[2];
     SS_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     cudaGraphConditionalHandle h_check;
     SS_CUDA(cudaGraphConditionalHandleCreate(&h_check, body, 0u, cudaGraphCondAssignDefault));
@@ -310,7 +310,7 @@ int capture_cg_loop(sp_sim* s, cudaStream_t cs)
     SS_CUDA(cudaGraphAddNode(&inode, bg, deps, nullptr, nd, &ip));
     cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
     SS_CUDA(cudaStreamUpdateCaptureDependencies(bs, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaStream_t is = s->cap_stream[2];
+    cudaStream_t is = s->cap_stream[3];
     SS_CUDA(cudaStreamBeginCaptureToGraph(is, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     launch_cg_true_residual(P, B, mx, true, C, launch_of(s, is));
     SS_CUDA(cudaStreamEndCapture(is, &ifbody));
@@ -491,6 +491,20 @@ int set_device(sp_sim* s)
 {
     SS_CUDA(cudaSetDevice(s->p.device));
     return SP_OK;
+}
+
+// The message of a failure raised on the device (DevState::error).
+const char* status_text(int status)
+{
+    switch (status) {
+    case SP_ERR_NOT_CONVERGED: return "CG did not converge";
+    case SP_ERR_NONFINITE: return "non-finite value in CG";
+    case SP_ERR_TIMEOUT: return "a grid-barrier wait of the persistent solver ran past the wait limit";
+    case SP_ERR_INVALID_ARG:
+        return "positions must be finite and lie in [0, L) (the simulation's positions are undefined until "
+               "valid ones are set)";
+    default: return "device-side failure";
+    }
 }
 
 // After a failed step or solve, clear the sticky flags so the simulation stays usable.
@@ -735,6 +749,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     }
     std::memset(s->st_host, 0, sizeof(DevState));
     s->st_host->noise_step = -1;   // no normals drawn yet
+    s->st_host->bar_timeout_ns = kDefaultWaitLimitNs;
     if (cudaMemcpyAsync(B.st, s->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.v_s, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
         cudaMemsetAsync(B.x, 0, sizeof(double) * v3, s->stream) != cudaSuccess ||
@@ -841,11 +856,12 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
         info->residual = h.last_res;
         info->bnorm = std::sqrt(h.bnorm2);
         info->offchip_blocks = h.res_offchip;
+        info->host_driven = s->host_loop ? 1 : 0;
     }
     SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
     if (h.error) {
         SS_TRY(clear_flags(s));
-        s->err = status == SP_ERR_NOT_CONVERGED ? "CG did not converge" : "non-finite value in CG";
+        s->err = status_text(status);
     }
     SS_CUDA(cudaStreamSynchronize(s->stream));
     return status;
@@ -897,7 +913,7 @@ int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
         }
         if (s->st_host->error) {
             status = s->st_host->error;
-            s->err = status == SP_ERR_NOT_CONVERGED ? "CG did not converge" : "non-finite value in CG";
+            s->err = status_text(status);
             SS_TRY(clear_flags(s));
             break;
         }
@@ -918,6 +934,7 @@ int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
         info->kernel_launches = launches;
         info->delta = h.delta;
         info->step = h.step;
+        info->host_driven = s->host_loop ? 1 : 0;
     }
     s->built = false;
     s->assembled = false;
@@ -951,7 +968,7 @@ int sp_step_host(sp_sim* s, const double* pos_in, double delta, int32_t nsteps, 
     // pinned state mirror (an asynchronous copy, read before the mirror is
     // next written by the statistics read-back in the same stream)
     SS_CUDA(cudaMemcpyAsync(s->B.stage, pos_in, sizeof(double) * 3 * s->kp.n, cudaMemcpyHostToDevice, s->stream));
-    launch_gather_by_id(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->stream);
+    launch_gather_positions(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->kp, s->B.st, s->stream);
     s->st_host->delta = delta;
     SS_CUDA(cudaMemcpyAsync(&s->B.st->delta, &s->st_host->delta, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     s->built = false;
@@ -1149,11 +1166,17 @@ int sp_set_positions(sp_sim* s, const double* pos_host, double delta)
     }
     SS_TRY(set_device(s));
     SS_CUDA(cudaMemcpyAsync(s->B.stage, pos_host, sizeof(double) * 3 * s->kp.n, cudaMemcpyHostToDevice, s->stream));
-    launch_gather_by_id(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->stream);
+    launch_gather_positions(s->B.stage, s->B.id_s, s->kp.n, s->kp.npad, s->B.pos_s, s->kp, s->B.st, s->stream);
     SS_CUDA(cudaMemcpyAsync(&s->B.st->delta, &delta, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     SS_CUDA(cudaStreamSynchronize(s->stream));
     s->built = false;
     s->assembled = false;
+    SS_TRY(read_state(s));
+    if (s->st_host->error == SP_ERR_INVALID_ARG) {
+        SS_TRY(clear_flags(s));
+        s->err = status_text(SP_ERR_INVALID_ARG);
+        return SP_ERR_INVALID_ARG;
+    }
     return SP_OK;
 }
 
@@ -1183,6 +1206,19 @@ int sp_set_step(sp_sim* s, int64_t step)
     SS_TRY(set_device(s));
     long long v = step;
     SS_TRY(write_field(s, &s->B.st->step, v));
+    return SP_OK;
+}
+
+int sp_set_wait_limit(sp_sim* s, double seconds)
+{
+    if (!s || !(seconds > 0.0) || !(seconds <= 60.0)) {
+        if (s) s->err = "the wait limit must lie in (0, 60] seconds";
+        return SP_ERR_INVALID_ARG;
+    }
+    SS_TRY(set_device(s));
+    const unsigned long long ns = std::max(1ull, (unsigned long long)std::llround(seconds * 1e9));
+    SS_TRY(write_field(s, &s->B.st->bar_timeout_ns, ns));
+    s->st_host->bar_timeout_ns = ns;
     return SP_OK;
 }
 

@@ -16,7 +16,11 @@ struct sp_sim {
     ss::DevState* st_host = nullptr;  // pinned mirror of the device state
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
+    // capture streams: [0] the graph's main stream, [1] its side branch (normals,
+    // split of x0, stress), [2] the body of the CG loop's WHILE node, [3] the
+    // body of its IF node; a stream still joined to one capture cannot begin
+    // another, so the side branch and the node bodies never share one
+    cudaStream_t cap_stream[4] = {nullptr, nullptr, nullptr, nullptr};
     int num_sms = 0;
     long long nnz_cap = 0;
     bool use_inj = false;

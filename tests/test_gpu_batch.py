@@ -59,3 +59,56 @@ def test_batch_is_deterministic():
         batch.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def test_batch_follows_the_oracle():
+    """Each replica of a batch, stepped by the FP64 CPU oracle from the same positions with its own
+    seed, shear rate and box: the positions after the steps agree to the solve tolerance."""
+    import oracle
+    reps = _replicas(1e-10)
+    pos = _positions()
+    steps = 3
+    batch = ss.Batch(reps, positions=pos)
+    infos = batch.step(steps)
+    for k, kw in enumerate(reps):
+        assert infos[k]["status"] == 0 and infos[k]["steps_done"] == steps
+        p = oracle.Params(n=kw["n"], L=kw["L"], kappa=kw["kappa"], seed=kw["seed"])
+        opos, od = pos[k], 0.0
+        for s in range(steps):
+            r = oracle.step(p, opos, od, s, tol=1e-13)
+            opos, od = r.pos, r.delta
+        got = batch.sim(k).get_positions()
+        delta, _ = batch.sim(k).state()
+        L = kw["L"][0]
+        d = got - opos
+        d -= np.round(d / L) * L
+        # per step |v_gpu - v| <= ~cond * 1e-10 * max|v| (cond ~ 22, max|v| ~ 60), times dt = 0.01
+        assert np.abs(d).max() < 1e-9 * steps, (k, np.abs(d).max())
+        assert abs(delta - od) < 1e-12
+    batch.close()
+
+
+def test_batch_with_a_replica_at_the_largest_ensemble_size():
+    """A replica of 131,072 particles (the ensemble's upper end) beside a small one, against the
+    single-system path."""
+    sizes = [(131072, 0.3), (8192, 0.01)]
+    reps, pos = [], []
+    for k, (n, kt) in enumerate(sizes):
+        L = synth.box_length(n)
+        reps.append(dict(n=n, L=(L, L, L), kappa=ss.kappa_from_kappa_tau(kt), seed=950 + k, cg_tol=1e-10,
+                         cg_max_iter=2000, precision="mixed", warm_start="prev"))
+        pos.append(synth.uniform_positions(n, (L, L, L), 500 + k))
+    steps = 2
+    batch = ss.Batch(reps, positions=pos)
+    infos = batch.step(steps)
+    for k, kw in enumerate(reps):
+        assert infos[k]["status"] == 0 and infos[k]["steps_done"] == steps
+        got = batch.sim(k).get_positions()
+        with ss.Simulation(positions=pos[k], **kw) as sim:
+            sim.step(steps)
+            ref = sim.get_positions()
+        L = kw["L"][0]
+        d = got - ref
+        d -= np.round(d / L) * L
+        assert np.abs(d).max() < 1e-9 * steps, (k, np.abs(d).max())
+    batch.close()

@@ -169,7 +169,41 @@ def test_steps_follow_the_oracle():
     sim.close()
 
 
+def test_plain_fp64_workload_follows_the_oracle_for_200_steps():
+    """The plain FP64 workload in full: N = 4,096, kappa tau = 0.5, Jacobi-PCG to 1e-10 warm-started
+    from the previous velocities, 200 steps in graph mode, against the oracle stepping the same
+    trajectory (its solves to 1e-13).  Per step |v_gpu - v| <= ~cond * 1e-10 * max|v| (cond ~ 22 after
+    Jacobi scaling), i.e. ~1e-9 in position per step of dt = 0.01."""
+    w = synth.PLAIN_FP64
+    pos = synth.uniform_positions(w.n, w.L, w.seed)
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    sim = ss.Simulation(w.n, w.L, kappa, seed=w.seed, precision="fp64", warm_start="prev", cg_tol=w.tol,
+                        cg_max_iter=2000, positions=pos)
+    p = oracle.Params.from_workload(w)
+    opos, od = pos, 0.0
+    L = w.L[0]
+    done = 0
+    for chunk in (50, 50, 50, 50):
+        info = sim.step(chunk)
+        assert info["status"] == 0 and info["steps_done"] == chunk and info["host_driven"] == 0
+        assert info["last_residual"] <= w.tol
+        for s in range(done, done + chunk):
+            r = oracle.step(p, opos, od, s, tol=1e-13, neighbor_method="cells")
+            opos, od = r.pos, r.delta
+        done += chunk
+        delta, step = sim.state()
+        assert step == done and abs(delta - od) < 1e-11
+        d = sim.get_positions() - opos
+        d -= np.round(d / L) * L
+        assert np.abs(d).max() < 2e-9 * done, (done, np.abs(d).max())
+    assert np.abs(sim.get_velocities() - r.v).max() <= 1e-7 * np.abs(r.v).max()
+    sim.close()
+
+
 def test_graph_and_host_loop_modes_agree(monkeypatch):
+    """The FP64 step as one CUDA graph (CG loop in a conditional WHILE node, thermal
+    normals on the graph's side branch) and the host-driven loop give identical steps;
+    the graph mode must really have captured (host_driven == 0)."""
     n = 2000
     L = synth.box_length(n)
     outs = []
@@ -177,11 +211,33 @@ def test_graph_and_host_loop_modes_agree(monkeypatch):
         monkeypatch.setenv("SHEARSIM_HOST_LOOP", mode)
         sim, p, pos = make(n, L, seed=4, tol=1e-10, warm_start="prev")
         info = sim.step(3)
+        assert info["host_driven"] == int(mode), (mode, info)
         outs.append((sim.get_positions(), sim.get_velocities(), info["cg_iterations"]))
         sim.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+@pytest.mark.parametrize("precision,persistent,warm", [
+    ("fp64", "1", "prev"), ("fp64", "1", "none"), ("mixed", "0", "prev"), ("mixed", "1", "prev"),
+    ("mixed", "1", "none")])
+def test_steps_and_solves_never_fall_back_to_the_host_loop(monkeypatch, capfd, precision, persistent, warm):
+    """Every form of the step and of the stand-alone solve captures its CUDA graph."""
+    monkeypatch.delenv("SHEARSIM_HOST_LOOP", raising=False)
+    monkeypatch.setenv("SHEARSIM_PERSISTENT", persistent)
+    n = 3000
+    L = synth.box_length(n)
+    sim, p, pos = make(n, L, seed=9, tol=1e-8, warm_start=warm, precision=precision)
+    info = sim.step(2)
+    assert info["host_driven"] == 0, info
+    sim.build_neighbors()
+    sim.assemble()
+    sinfo = sim.solve_velocities()
+    assert sinfo["host_driven"] == 0, sinfo
+    sim.close()
+    err = capfd.readouterr().err
+    assert "capture failed" not in err, err
 
 
 def test_runs_are_deterministic():

@@ -73,3 +73,48 @@ def test_noalloc_rejects_oversized_systems():
     info = ss.solve_csr_noalloc(n, 1, 1, 1, 1, 4.0, 1, 1)
     assert info["status"] == ss.SP_ERR_INVALID_ARG
     assert "32768" in info["error"]
+
+
+def test_noalloc_rejects_a_column_outside_the_system():
+    """A column index >= n is refused before any gather through it (no stale or outside read)."""
+    ss.load()
+    dev = torch.device("cuda", 0)
+    n = 64
+    row_ptr = torch.tensor([0, 1] + [1] * (n - 1), dtype=torch.int32, device=dev)
+    col = torch.tensor([n], dtype=torch.int32, device=dev)
+    w = torch.tensor([0.5], dtype=torch.float64, device=dev)
+    diag = torch.ones(n, dtype=torch.float64, device=dev)
+    b = torch.ones(3, n, dtype=torch.float64, device=dev)
+    x = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    info = ss.solve_csr_noalloc(n, row_ptr.data_ptr(), col.data_ptr(), w.data_ptr(), diag.data_ptr(), 1.0,
+                                b.data_ptr(), x.data_ptr(), tol=1e-12, max_iter=100,
+                                stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert info["status"] == ss.SP_ERR_INVALID_ARG, info
+    assert "col" in info["error"]
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream, so under stream capture it must refuse and leave the capture intact."""
+    ss.load()
+    dev = torch.device("cuda", 0)
+    n = 16
+    row_ptr = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    col = torch.zeros(1, dtype=torch.int32, device=dev)
+    w = torch.zeros(1, dtype=torch.float64, device=dev)
+    diag = torch.ones(n, dtype=torch.float64, device=dev)
+    b = torch.ones(3, n, dtype=torch.float64, device=dev)
+    x = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    y = torch.zeros(8, device=dev)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        info = ss.solve_csr_noalloc(n, row_ptr.data_ptr(), col.data_ptr(), w.data_ptr(), diag.data_ptr(), 1.0,
+                                    b.data_ptr(), x.data_ptr(), tol=1e-12, max_iter=10,
+                                    stream=torch.cuda.current_stream().cuda_stream)
+        y.add_(1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert info["status"] == ss.SP_ERR_INVALID_ARG, info
+    assert "captured" in info["error"]
+    assert float(y[0]) == 1.0   # the capture stayed valid: its one op ran once, by the replay

@@ -349,6 +349,14 @@ int sp_set_positions(sp_sim* sim, const double* pos_host, double delta);
 int sp_get_velocities(sp_sim* sim, double* v_host);
 /* Lees-Edwards offset and step counter (the noise key). */
 int sp_get_state(sp_sim* sim, double* delta, int64_t* step);
+/* Architecture of the device code that `device` runs for this library
+ * (cudaFuncGetAttributes of one of its kernels): *binary_version = 10 x major +
+ * minor of the machine code (103 for a build for sm_103a on a GB300),
+ * *ptx_version likewise for the virtual architecture it was compiled from.
+ * Not in the paper (a build check).  Errors: SP_ERR_INVALID_ARG (NULL
+ * output), SP_ERR_NO_DEVICE, SP_ERR_CUDA (no code for this device). */
+int sp_device_code_version(int32_t device, int32_t* binary_version, int32_t* ptx_version);
+
 /* Set the step counter, e.g. to resume a checkpoint (positions via sp_set_positions). */
 int sp_set_step(sp_sim* sim, int64_t step);
 /* Limit of one device-side wait of the persistent solvers (a block waiting at

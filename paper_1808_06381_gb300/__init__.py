@@ -117,7 +117,7 @@ def load(path: str = LIB_PATH):
             ("sp_velocity_correlation_host", [i32, i64, vp, d, d, vp, vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
             ("sp_get_positions", [vp, vp]), ("sp_set_positions", [vp, vp, d]), ("sp_get_velocities", [vp, vp]),
             ("sp_get_state", [vp, P(d), P(i64)]), ("sp_set_step", [vp, i64]), ("sp_get_order", [vp, vp]),
-            ("sp_set_wait_limit", [vp, d]),
+            ("sp_set_wait_limit", [vp, d]), ("sp_device_code_version", [i32, P(i32), P(i32)]),
             ("sp_get_num_pairs", [vp, P(i64)]), ("sp_get_neighbors", [vp, i64, vp, P(i64)]),
             ("sp_get_system", [vp, vp, vp, vp]), ("sp_set_noise", [vp, vp]),
             ("sp_philox_blocks", [i32, u64, u64, i64, vp, vp]),
@@ -156,6 +156,13 @@ def _check(rc: int, handle=None):
 
 def _p(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def device_code_version(device: int = 0) -> tuple:
+    """(binary, ptx) architecture versions of the device code this library runs on `device`."""
+    b, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().sp_device_code_version(int(device), ctypes.byref(b), ctypes.byref(p)))
+    return b.value, p.value
 
 
 def kappa_from_kappa_tau(kappa_tau: float, rc: float = 1.0, zeta: float = 1.0, kT: float = 1.0) -> float:

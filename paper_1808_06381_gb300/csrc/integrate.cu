@@ -225,6 +225,19 @@ void launch_gather_positions(const double* in_n3, const int* ids, int n, int npa
                                                                              P.L[1], P.L[2], st);
 }
 
+__global__ void k_reset_step_stats(DevState* st);
+
+cudaError_t device_code_version(int* binary_version, int* ptx_version)
+{
+    cudaFuncAttributes a{};
+    const cudaError_t e = cudaFuncGetAttributes(&a, k_reset_step_stats);
+    if (e == cudaSuccess) {
+        *binary_version = a.binaryVersion;
+        *ptx_version = a.ptxVersion;
+    }
+    return e;
+}
+
 __global__ void k_reset_step_stats(DevState* st)
 {
     st->iter_sum = 0;

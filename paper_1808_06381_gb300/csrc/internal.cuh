@@ -802,6 +802,9 @@ void launch_gather_by_id(const double* in_n3, const int* ids, int n, int npad, d
 void launch_gather_positions(const double* in_n3, const int* ids, int n, int npad, double* planes,
                              const KParams& P, DevState* st, cudaStream_t s);
 void launch_reset_step_stats(DevState* st, cudaStream_t s);
+// Architecture of the device code the current device runs (cudaFuncGetAttributes
+// of one of this library's kernels): 10 major + minor, e.g. 103 for sm_103.
+cudaError_t device_code_version(int* binary_version, int* ptx_version);
 // sfactor.cu: S(q) at q_z = 0 for kx in [-nkx, nkx], ky in [-nky, nky] (kx slowest);
 // G = 0: direct sum over particles; G > 0: CIC grid of G x G in the sheared frame.
 cudaError_t run_structure_factor(const KParams& P, const DevBuffers& B, double delta, int G, int nkx, int nky,

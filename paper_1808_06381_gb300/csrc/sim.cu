@@ -1209,6 +1209,31 @@ int sp_set_step(sp_sim* s, int64_t step)
     return SP_OK;
 }
 
+int sp_device_code_version(int32_t device, int32_t* binary_version, int32_t* ptx_version)
+{
+    if (!binary_version || !ptx_version) return SP_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device with the requested ordinal";
+        return SP_ERR_NO_DEVICE;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    int bin = 0, ptx = 0;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = device_code_version(&bin, &ptx);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaFuncGetAttributes: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return SP_ERR_CUDA;
+    }
+    *binary_version = bin;
+    *ptx_version = ptx;
+    return SP_OK;
+}
+
 int sp_set_wait_limit(sp_sim* s, double seconds)
 {
     if (!s || !(seconds > 0.0) || !(seconds <= 60.0)) {

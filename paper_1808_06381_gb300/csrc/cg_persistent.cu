@@ -11,10 +11,11 @@
 // rows only; its gathers of r (and of x in the FP64 residual) read rows that
 // other blocks wrote before the last barrier.
 //
-// Grid barrier: one arrival counter (acquire-release atomic), a generation
-// word on its own line that the last arriving block releases, and the error
-// flag copied next to it by that block.  After the barrier every block sums
-// all blocks' partial sums itself, in one fixed order.  The launch is
+// Grid barrier: one arrival counter that only grows during a launch (barrier
+// k is passed once k x blocks have arrived; one release-add per block, polled
+// with acquire loads), reset by the last block to leave the launch.  After
+// the barrier every block sums all blocks' partial sums itself, in one fixed
+// order.  The launch is
 // cooperative (all blocks resident), and every wait is bounded by the global
 // timer: a block that waits longer than the simulation's wait limit
 // (DevState::bar_timeout_ns, 2 s unless sp_set_wait_limit changed it) sets
@@ -55,16 +56,9 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v)
+__device__ __forceinline__ void red_add_release_gpu(unsigned int* p, unsigned int v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v)
-{
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -74,27 +68,40 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Arrival and release by thread 0; returns the error flag (0 = continue).
-// The writes of every thread of every block before the barrier are visible
-// to every thread after it (release by each arrival, acquire by the waiters,
-// and the block barriers on both sides).
-__device__ __forceinline__ int barrier_thread0(DevState* st, unsigned int target, int nb)
+// Arrival at barrier k of the launch by thread 0 (target = k x blocks): one
+// release-add on a counter that only grows during the launch, then polls
+// until it reaches the target.  No block releases the others, so the wait
+// after the last arrival is one poll.  The writes of every thread of every
+// block before the barrier are visible to every thread after it (release by
+// each arrival, acquire by the polls, block barriers on both sides).  Returns
+// 0, or SP_ERR_TIMEOUT (also raised in st->error) when the wait ran past the
+// simulation's limit.  The solvers take every other stopping decision
+// identically in every block from identical totals, so nothing else has to
+// travel with the barrier; a block that timed out leaves, and the others time
+// out at the next barrier it misses.
+__device__ __forceinline__ int barrier_thread0(DevState* st, unsigned int target)
 {
-    if (atom_add_acq_rel_gpu(&st->bar_count, 1u) == (unsigned)nb - 1) {
-        const int e = *(volatile int*)&st->error;
-        st->bar_err = e;
-        st->bar_count = 0u;
-        st_release_gpu(&st->bar_gen, target);
-        return e;
-    }
+    red_add_release_gpu(&st->bar_count, 1u);
     const unsigned long long t0 = global_ns();
     const unsigned long long limit = st->bar_timeout_ns;   // set by the host between launches
     for (;;) {
-        if (ld_acquire_gpu(&st->bar_gen) == target) return *(volatile int*)&st->bar_err;
+        if (ld_acquire_gpu(&st->bar_count) >= target) return 0;
         if (global_ns() - t0 > limit) {   // a timer read per poll: polls are L2 round trips anyway
             atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
             return (int)SP_ERR_TIMEOUT;
         }
+    }
+}
+
+// Every block of a launch leaves through here (with its system's state and
+// block count): the last one to leave, when no block polls the counter any
+// more, resets the barrier for the next launch.
+__device__ __forceinline__ void barrier_leave(DevState* st, int nb)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&st->bar_exit, 1u) == (unsigned)nb - 1) {
+        st->bar_count = 0u;
+        st->bar_exit = 0u;
     }
 }
 
@@ -103,7 +110,7 @@ __device__ __forceinline__ int barrier_thread0(DevState* st, unsigned int target
 __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int& gen, PShared& sh, int nb)
 {
     __syncthreads();
-    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, gen + 1u, nb);
+    if (threadIdx.x == 0) sh.flag = barrier_thread0(st, (gen + 1u) * (unsigned int)nb);
     __syncthreads();
     gen += 1u;
     return sh.flag == 0;
@@ -171,7 +178,7 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) partials[k * kMaxPartials + bid] = make_float2(w[k].hi, w[k].lo);
-            sh.flag = barrier_thread0(st, gen + 1u, nb);
+            sh.flag = barrier_thread0(st, (gen + 1u) * (unsigned int)nb);
         }
         __syncwarp();   // orders thread 0's acquire before the other lanes' loads
         // all of a lane's loads are issued before the first sum (one latency)
@@ -260,7 +267,7 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k) partials[k * kMaxPartials + bid] = w[k];
-            sh.flag = barrier_thread0(st, gen + 1u, nb);
+            sh.flag = barrier_thread0(st, (gen + 1u) * (unsigned int)nb);
         }
         __syncwarp();
         double pv[K][kPartialsPerLane];
@@ -397,8 +404,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     if (threadIdx.x == 0) sh.flag = 0;
     __syncthreads();
     if (st->error | st->overflow | st->done) return;   // uniform: set before the launch
-    unsigned int gen = 0u;   // used by thread 0 only
-    if (threadIdx.x == 0) gen = *(volatile unsigned int*)&st->bar_gen;
+    unsigned int gen = 0u;   // barriers passed in this launch (the counter starts at 0)
 
     const int nwin = P.nslots / 256;
     const int wb = (int)((long long)bid * nwin / nb);
@@ -644,9 +650,9 @@ __device__ __forceinline__ void res_halo_batch(const DevBuffers& B, int hb, int 
     for (int u = 0; u < kResHalo; ++u) {
         j[u] = 0;
         w[u] = 0.f;
-        if (kb + u < nh) {
-            j[u] = ld_stream(B.hcol + hb + 32 * (kb + u));
-            w[u] = ld_stream(B.hval + hb + 32 * (kb + u));
+        if (kb + u < nh) {   // L1-cached: every iteration reads the same lists
+            j[u] = B.hcol[hb + 32 * (kb + u)];
+            w[u] = B.hval[hb + 32 * (kb + u)];
         }
     }
     float4 g[kResHalo];
@@ -678,8 +684,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     if (threadIdx.x == 0) sh.flag = 0;
     __syncthreads();
     if (st->error | st->overflow | (fused ? 0 : st->done)) return;   // uniform: set before the launch
-    unsigned int gen = 0u;
-    if (threadIdx.x == 0) gen = *(volatile unsigned int*)&st->bar_gen;
+    unsigned int gen = 0u;   // barriers passed in this launch (the counter starts at 0)
 
     const int nwin = P.nslots / 256;
     const int wb = (int)((long long)bid * nwin / nb);
@@ -1028,9 +1033,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 for (int k = 0; k < kResHalo; ++k) {
                     j[k] = 0;
                     w[k] = 0.f;
-                    if (k < nh) {
-                        j[k] = ld_stream(B.hcol + hb + 32 * k);
-                        w[k] = ld_stream(B.hval + hb + 32 * k);
+                    if (k < nh) {   // L1-cached: every iteration reads the same lists
+                        j[k] = B.hcol[hb + 32 * k];
+                        w[k] = B.hval[hb + 32 * k];
                     }
                 }
                 float4 gh[kResHalo];
@@ -1361,6 +1366,7 @@ __global__ void __launch_bounds__(BS, 1) k32_cg_resident(KParams P, DevBuffers B
     __shared__ PShared sh;
     __shared__ RShared rs;
     resident_solve<BS, RPT>(P, B, blockIdx.x, gridDim.x, sh, rs, res_dyn, smem_bytes);
+    barrier_leave(B.st, gridDim.x);
 }
 
 // Tile configurations of the single-system kernel: gathers in flight per
@@ -1373,6 +1379,7 @@ __global__ void __launch_bounds__(BS, MINB) k32_cg_persistent(KParams P, DevBuff
 {
     __shared__ PShared sh;
     persistent_solve<KB, PIPE>(P, B, blockIdx.x, gridDim.x, sh);
+    barrier_leave(B.st, gridDim.x);
 }
 
 // Batch: block b serves replica k with blk_off[k] <= b < blk_off[k + 1]; each
@@ -1395,6 +1402,7 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
     __syncthreads();
     const int k = rep;
     persistent_solve<kBatchP, false>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
+    barrier_leave(Bs[k].st, blk_off[k + 1] - blk_off[k]);
 }
 
 namespace {

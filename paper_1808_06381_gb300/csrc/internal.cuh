@@ -81,11 +81,12 @@ struct DevState {
     double last_res;
     double stress_xy;
     unsigned int ticket[4];
-    // grid barrier of the persistent solver: arrivals, and (on its own line)
-    // the release generation with the error flag seen by the releasing block
+    // grid barriers of the persistent solvers: arrivals counted up through a
+    // launch (barrier k of a launch is passed once k x blocks have arrived),
+    // and on its own line the blocks that have left the launch (the last one
+    // resets both, so every launch starts from 0)
     alignas(128) unsigned int bar_count;
-    alignas(128) unsigned int bar_gen;
-    int bar_err;
+    alignas(128) unsigned int bar_exit;
     long long noise_step;     // step whose normals noise3 holds (-1: none)
     int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
     double delta_next;        // the offset the position update advanced to (committed after the stress)

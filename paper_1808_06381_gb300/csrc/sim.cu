@@ -515,6 +515,7 @@ int clear_flags(sp_sim* s)
     SS_TRY(write_field(s, &d->overflow, 0));
     // a persistent solve that stopped on an error may have left arrivals behind
     SS_TRY(write_field(s, &d->bar_count, 0u));
+    SS_TRY(write_field(s, &d->bar_exit, 0u));
     return SP_OK;
 }
 
@@ -1765,8 +1766,8 @@ int sp_mpnn_train_step(sp_sim* s, float lr, double* loss, float* grad_host)
 {
     if (!s || !s->mp_alloc || !(lr >= 0.f)) return SP_ERR_INVALID_ARG;
     SS_TRY(set_device(s));
-    s->mp_t += 1;
-    launch_mp_train(s->kp, s->B, s->mp, lr, s->mp_t, launch_of(s, s->stream));
+    if (lr > 0.f) s->mp_t += 1;   // a gradient-only call (lr = 0) is no Adam step
+    launch_mp_train(s->kp, s->B, s->mp, lr, std::max(s->mp_t, 1), launch_of(s, s->stream));
     SS_CUDA(cudaGetLastError());
     if (loss) SS_CUDA(cudaMemcpyAsync(loss, s->mp.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     if (grad_host)

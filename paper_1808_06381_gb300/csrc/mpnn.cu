@@ -11,14 +11,12 @@
 // The message passes run on the narrow features (like an SpMV of the solver);
 // the MLP of inference is one kernel on the tcgen05 tensor cores (BF16
 // operands in shared memory, FP32 accumulators in tensor memory, 128-row
-// tiles; k_mp_mlp_fwd_tc).  The training pass recomputes the forward with
-// mma.sync m16n8k16 fragments (a warp takes 16 rows, the FP32 accumulators of
-// a layer pass through tanh — the hardware approximation — and are repacked
-// in registers as the A operand of the next layer).  Training (MSE to the converged
-// velocities) runs the backward pass in one fused kernel that stages a tile of
-// 128 rows in shared memory and forms the weight gradients with tensor-core
-// products of transposed tiles (ldmatrix.trans), then a deterministic
-// reduction over blocks and Adam on FP32 master weights.
+// tiles; k_mp_mlp_fwd_tc).  Training (MSE to the converged velocities)
+// recomputes the forward and runs the backward on the same tensor cores
+// (k_mp_mlp_bwd_tc: activation gradients and the weight gradients as
+// products over each tile's rows, accumulated in tensor memory across a
+// block's tiles), then a deterministic reduction over blocks and Adam on FP32
+// master weights.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -32,56 +30,18 @@ namespace ss {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kTileRows = 128;
 constexpr int kMaxGradBlocks = 1024;
-constexpr int kSW = 24;   // padded smem row stride for 16-wide tiles (48 B)
-constexpr int kSH = 72;   // padded smem row stride for 64-wide tiles (144 B)
 
 __device__ __forceinline__ unsigned smem_addr(const void* p)
 {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n"
-                 : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void ldsm_x2_t(unsigned& r0, unsigned& r1, const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n"
-                 : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_addr(p)));
-}
-
-// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators.
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<unsigned*>(&v);
-}
-
-// B fragment (k16 x n8) from a shared [n][k] array (k contiguous), stride ld.
-__device__ __forceinline__ void load_b(const __nv_bfloat16* Bt, int ld, int n0, int k0, unsigned& b0, unsigned& b1)
-{
-    const int lane = threadIdx.x & 31;
-    ldsm_x2(b0, b1, Bt + (n0 + (lane & 7)) * ld + k0 + ((lane >> 3) & 1) * 8);
 }
 
 // Weight layouts in the packed BF16 array (element offsets).
@@ -92,17 +52,6 @@ constexpr int kW2N = kW3T + 8 * 64;     // [64][64]: W2 as is (backward)
 constexpr int kW3P = kW2N + 64 * 64;    // [64][16]: W3 as is, k padded 4 -> 16 (backward)
 constexpr int kWB = kW3P + 64 * 16;
 
-// Forward of the MLP for one warp's 16 rows, from the A fragment of the
-// inputs; returns the FP32 activations (for the backward pass) and the output
-// accumulator of layer 3.
-struct FwdRegs {
-    float h1[8][4];
-    float h2[8][4];
-    unsigned a1[4][4];
-    unsigned a2[4][4];
-    float y[4];
-};
-
 // tanh by the hardware approximation (one MUFU operation, relative error
 // below 2^-10): finer than the BF16 rounding the activations get next.
 __device__ __forceinline__ float tanh_fast(float x)
@@ -110,88 +59,6 @@ __device__ __forceinline__ float tanh_fast(float x)
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-__device__ __forceinline__ void mlp_forward(const unsigned (&a0)[4], const __nv_bfloat16* sW1T,
-                                            const __nv_bfloat16* sW2T, const __nv_bfloat16* sW3T, FwdRegs& R)
-{
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-        R.h1[nb][0] = R.h1[nb][1] = R.h1[nb][2] = R.h1[nb][3] = 0.f;
-        unsigned b0, b1;
-        load_b(sW1T, kSW, nb * 8, 0, b0, b1);
-        mma16816(R.h1[nb], a0, b0, b1);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) R.h1[nb][q] = tanh_fast(R.h1[nb][q]);
-    }
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        R.a1[kb][0] = pack_bf16(R.h1[2 * kb][0], R.h1[2 * kb][1]);
-        R.a1[kb][1] = pack_bf16(R.h1[2 * kb][2], R.h1[2 * kb][3]);
-        R.a1[kb][2] = pack_bf16(R.h1[2 * kb + 1][0], R.h1[2 * kb + 1][1]);
-        R.a1[kb][3] = pack_bf16(R.h1[2 * kb + 1][2], R.h1[2 * kb + 1][3]);
-    }
-#pragma unroll
-    for (int nb = 0; nb < 8; ++nb) {
-        R.h2[nb][0] = R.h2[nb][1] = R.h2[nb][2] = R.h2[nb][3] = 0.f;
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            unsigned b0, b1;
-            load_b(sW2T, kSH, nb * 8, kb * 16, b0, b1);
-            mma16816(R.h2[nb], R.a1[kb], b0, b1);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) R.h2[nb][q] = tanh_fast(R.h2[nb][q]);
-    }
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        R.a2[kb][0] = pack_bf16(R.h2[2 * kb][0], R.h2[2 * kb][1]);
-        R.a2[kb][1] = pack_bf16(R.h2[2 * kb][2], R.h2[2 * kb][3]);
-        R.a2[kb][2] = pack_bf16(R.h2[2 * kb + 1][0], R.h2[2 * kb + 1][1]);
-        R.a2[kb][3] = pack_bf16(R.h2[2 * kb + 1][2], R.h2[2 * kb + 1][3]);
-    }
-    R.y[0] = R.y[1] = R.y[2] = R.y[3] = 0.f;
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        unsigned b0, b1;
-        load_b(sW3T, kSH, 0, kb * 16, b0, b1);
-        mma16816(R.y, R.a2[kb], b0, b1);
-    }
-}
-
-__device__ __forceinline__ float feat6(const float4& x, const float4& a, int k)
-{
-    switch (k) {
-        case 0: return x.x;
-        case 1: return x.y;
-        case 2: return x.z;
-        case 3: return a.x;
-        case 4: return a.y;
-        case 5: return a.z;
-        default: return 0.f;
-    }
-}
-
-// A fragment of the inputs [x0, a0] (6 features, k padded to 16) for rows r0, r1.
-__device__ __forceinline__ void input_frag(const float4* x0, const float4* a0, int rows, int r0, int r1,
-                                           unsigned (&a)[4])
-{
-    const int t = threadIdx.x & 3;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 x_0 = r0 < rows ? x0[r0] : z, a_0 = r0 < rows ? a0[r0] : z;
-    const float4 x_1 = r1 < rows ? x0[r1] : z, a_1 = r1 < rows ? a0[r1] : z;
-    a[0] = pack_bf16(feat6(x_0, a_0, 2 * t), feat6(x_0, a_0, 2 * t + 1));
-    a[1] = pack_bf16(feat6(x_1, a_1, 2 * t), feat6(x_1, a_1, 2 * t + 1));
-    a[2] = 0u;
-    a[3] = 0u;
-}
-
-__device__ __forceinline__ void load_weights_fwd(const __nv_bfloat16* wb, __nv_bfloat16* sW1T, __nv_bfloat16* sW2T,
-                                                 __nv_bfloat16* sW3T)
-{
-    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) sW1T[(e / 16) * kSW + e % 16] = wb[kW1T + e];
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) sW2T[(e / 64) * kSH + e % 64] = wb[kW2T + e];
-    for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) sW3T[(e / 64) * kSH + e % 64] = wb[kW3T + e];
 }
 
 // ------------------------------------------- forward MLP on tcgen05 tensor cores
@@ -426,6 +293,248 @@ __global__ void __launch_bounds__(128) k_mp_mlp_fwd_tc(int rows, MpBuffers M, De
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ------------------------------------------ training backward on tcgen05
+//
+// One tile of 128 rows at a time, one thread per row, 128 threads; every
+// product is a tcgen05.mma with M = 128 (BF16 operands in the no-swizzle
+// K-major core-matrix layout above, FP32 accumulators in tensor memory):
+//   h1 = tanh(X W1), h2 = tanh(h1 W2)             (forward recomputed; K 16, 64)
+//   dp2 = (dY W3^T) (1 - h2^2)                     (A = dY [128][16], B = W3 [64][16])
+//   dp1 = (dp2 W2^T) (1 - h1^2)                    (A = dp2 [128][64], B = W2 [64][64])
+// and the weight gradients as products over the tile's rows (K = 128), with
+// the tile's activations written transposed into the A and B operands:
+//   [h1^T; h2^T] (128 x 128) x dp2^T (64 x 128)^T -> rows 0-63: dW2 = h1^T dp2
+//   [h1^T; h2^T]             x dY^T  (16 x 128)^T -> rows 64-127: dW3 = h2^T dY
+//   [dp1^T; 0]               x X^T   (16 x 128)^T -> rows 0-63: dW1^T = dp1^T X
+// The three gradient accumulators stay in tensor memory across all the
+// block's tiles and are read back once: one partial gradient per block,
+// summed over blocks in a fixed order (k_mp_grad_reduce).  Tensor memory:
+// columns 0-63 for the activations' products (reused), 64-127 dW2, 128-143
+// dW3, 144-159 dW1^T.  The derivative of tanh uses the BF16 activations the
+// products use.  Every wait is bounded.
+namespace tcb {
+constexpr int kBRows = 128;
+constexpr int kBTmemCols = 256;
+constexpr int kColW2 = 64, kColW3 = 128, kColW1 = 144;
+// dynamic shared memory layout (byte offsets, 128-byte aligned)
+constexpr int oW1T = 0;                      // [64][16]  W1^T          (B, layer 1)
+constexpr int oW2T = oW1T + 64 * 16 * 2;     // [64][64]  W2^T          (B, layer 2)
+constexpr int oW3P = oW2T + 64 * 64 * 2;     // [64][16]  W3 (k 4 -> 16) (B, dh2)
+constexpr int oW2N = oW3P + 64 * 16 * 2;     // [64][64]  W2            (B, dh1)
+constexpr int oX = oW2N + 64 * 64 * 2;       // [128][16] [x0, a0]      (A, layer 1)
+constexpr int oH1 = oX + kBRows * 16 * 2;     // [128][64] h1            (A, layer 2)
+constexpr int oDY = oH1 + kBRows * 64 * 2;    // [128][16] dY            (A, dh2)
+constexpr int oP2 = oDY + kBRows * 16 * 2;    // [128][64] dp2           (A, dh1)
+constexpr int oAT1 = oP2 + kBRows * 64 * 2;   // [128][128] [h1^T; h2^T] (A, dW2 and dW3)
+constexpr int oAT2 = oAT1 + 128 * 128 * 2;   // [128][128] [dp1^T; 0]   (A, dW1^T)
+constexpr int oBP2 = oAT2 + 128 * 128 * 2;   // [64][128] dp2^T         (B, dW2)
+constexpr int oBDY = oBP2 + 64 * 128 * 2;    // [16][128] dY^T          (B, dW3)
+constexpr int oBX = oBDY + 16 * 128 * 2;     // [16][128] X^T           (B, dW1^T)
+constexpr int kSmem = oBX + 16 * 128 * 2;
+}  // namespace tcb
+
+int mp_bwd_tc_smem_bytes() { return tcb::kSmem + 128; }
+
+__global__ void __launch_bounds__(128, 1) k_mp_mlp_bwd_tc(int rows, MpBuffers M, DevState* st)
+{
+    using namespace tc;
+    using namespace tcb;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    // the operand tiles start on a 128-byte boundary (the launch adds 128 bytes)
+    unsigned char* sm = sm_raw + ((128u - (smem_addr(sm_raw) & 127u)) & 127u);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    auto put = [&](int off, int r, int k, int K, float v) {
+        *reinterpret_cast<__nv_bfloat16*>(sm + off + core_off(r, k, K)) = __float2bfloat16_rn(v);
+    };
+    auto get = [&](int off, int r, int k, int K) {
+        return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sm + off + core_off(r, k, K)));
+    };
+    // weights (BF16 layouts of k_mp_adam) into core-matrix tiles
+    for (int e = tid; e < 64 * 16; e += blockDim.x) {
+        *reinterpret_cast<__nv_bfloat16*>(sm + oW1T + core_off(e / 16, e % 16, 16)) = M.wb[kW1T + e];
+        *reinterpret_cast<__nv_bfloat16*>(sm + oW3P + core_off(e / 16, e % 16, 16)) = M.wb[kW3P + e];
+    }
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        *reinterpret_cast<__nv_bfloat16*>(sm + oW2T + core_off(e / 64, e % 64, 64)) = M.wb[kW2T + e];
+        *reinterpret_cast<__nv_bfloat16*>(sm + oW2N + core_off(e / 64, e % 64, 64)) = M.wb[kW2N + e];
+    }
+    // rows 64-127 of [dp1^T; 0], rows 4-15 of dY^T and 6-15 of X^T stay zero
+    for (int e = tid; e < 64 * 128; e += blockDim.x) put(oAT2, 64 + e / 128, e % 128, 128, 0.f);
+    for (int e = tid; e < 12 * 128; e += blockDim.x) put(oBDY, 4 + e / 128, e % 128, 128, 0.f);
+    for (int e = tid; e < 10 * 128; e += blockDim.x) put(oBX, 6 + e / 128, e % 128, 128, 0.f);
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kBTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_base;
+    const unsigned tlane = tmem + ((unsigned)(warp * 32) << 16);   // this warp's lane quarter
+    const unsigned id64 = idesc_bf16(kBRows, 64), id16 = idesc_bf16(kBRows, 16);
+    unsigned phase = 0;
+    int acc = 0;   // the gradient products accumulate after the block's first tile
+    auto sync_mma = [&]() {   // operands written by all threads -> visible to the MMA issuer
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+    };
+    auto wait_mma = [&]() {
+        if (!wait_phase(&mbar, phase)) atomicExch(&failed, 1);
+        phase ^= 1u;
+        fence_after();
+    };
+
+    for (int base = blockIdx.x * kBRows; base < rows && !failed; base += gridDim.x * kBRows) {
+        const int r = base + tid;   // this thread's row (tile row tid)
+        {   // X = [x0, a0] (k 6..15 zero) and dY (k 4..15 zero): rows, and transposed
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x = r < rows ? M.x0[r] : z, a = r < rows ? M.a0[r] : z, d = r < rows ? M.dy[r] : z;
+            const float xs[6] = {x.x, x.y, x.z, a.x, a.y, a.z}, ds[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                put(oX, tid, k, 16, k < 6 ? xs[k] : 0.f);
+                put(oDY, tid, k, 16, k < 4 ? ds[k] : 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) put(oBX, k, tid, 128, xs[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) put(oBDY, k, tid, 128, ds[k]);
+        }
+        sync_mma();
+        if (tid == 0) {
+            mma(tmem, smem_desc(sm + oX, 16), smem_desc(sm + oW1T, 16), id64, 0);
+            commit(&mbar);
+        }
+        wait_mma();
+        // h1 = tanh(D): row operand and rows 0-63 of [h1^T; h2^T]
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h = tanh_fast(v[q]);
+                put(oH1, tid, c + q, 64, h);
+                put(oAT1, c + q, tid, 128, h);
+            }
+        }
+        sync_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma(tmem, smem_desc(sm + oH1 + ks * 256, 64), smem_desc(sm + oW2T + ks * 256, 64), id64, ks > 0);
+            commit(&mbar);
+        }
+        wait_mma();
+        // h2 = tanh(D): rows 64-127 of [h1^T; h2^T]
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) put(oAT1, 64 + c + q, tid, 128, tanh_fast(v[q]));
+        }
+        sync_mma();
+        if (tid == 0) {   // dh2 = dY W3^T
+            mma(tmem, smem_desc(sm + oDY, 16), smem_desc(sm + oW3P, 16), id64, 0);
+            commit(&mbar);
+        }
+        wait_mma();
+        // dp2 = dh2 (1 - h2^2): row operand and transposed
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h = get(oAT1, 64 + c + q, tid, 128);
+                const float g = v[q] * (1.f - h * h);
+                put(oP2, tid, c + q, 64, g);
+                put(oBP2, c + q, tid, 128, g);
+            }
+        }
+        sync_mma();
+        if (tid == 0) {   // dh1 = dp2 W2^T
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma(tmem, smem_desc(sm + oP2 + ks * 256, 64), smem_desc(sm + oW2N + ks * 256, 64), id64, ks > 0);
+            commit(&mbar);
+        }
+        wait_mma();
+        // dp1 = dh1 (1 - h1^2), transposed into rows 0-63 of [dp1^T; 0]
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            ld16(tlane + c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float h = get(oH1, tid, c + q, 64);
+                put(oAT2, c + q, tid, 128, v[q] * (1.f - h * h));
+            }
+        }
+        sync_mma();
+        if (tid == 0) {   // the weight gradients, summed over the tile's rows (K = 128)
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                const int a = acc | (ks > 0);
+                mma(tmem + kColW2, smem_desc(sm + oAT1 + ks * 256, 128), smem_desc(sm + oBP2 + ks * 256, 128), id64, a);
+                mma(tmem + kColW3, smem_desc(sm + oAT1 + ks * 256, 128), smem_desc(sm + oBDY + ks * 256, 128), id16, a);
+                mma(tmem + kColW1, smem_desc(sm + oAT2 + ks * 256, 128), smem_desc(sm + oBX + ks * 256, 128), id16, a);
+            }
+            commit(&mbar);
+        }
+        wait_mma();   // the next tile overwrites the operands
+        acc = 1;
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
+    // this block's partial gradient (zero if it had no tile)
+    float* gp = M.gpart + (size_t)blockIdx.x * kMpParams;
+    if (acc && !failed) {
+        if (warp < 2) {   // rows 0-63: dW2[i][h] (i = row) and dW1^T[i][f]
+            const int i = tid;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float v[16];
+                ld16(tlane + kColW2 + c, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) gp[kMpOffW2 + i * 64 + c + q] = v[q];
+            }
+            float v[16];
+            ld16(tlane + kColW1, v);
+#pragma unroll
+            for (int f = 0; f < 6; ++f) gp[kMpOffW1 + f * 64 + i] = v[f];
+        } else {          // rows 64-127: dW3[h][m] (h = row - 64)
+            const int h = tid - 64;
+            float v[16];
+            ld16(tlane + kColW3, v);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) gp[kMpOffW3 + h * 4 + m] = v[m];
+        }
+    } else {
+        for (int e = tid; e < kMpOffO; e += blockDim.x) gp[e] = 0.f;
+    }
+    if (failed && tid == 0) atomicCAS(&st->error, 0, (int)SP_ERR_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBTmemCols) : "memory");
+}
+
 namespace {
 }  // namespace
 
@@ -590,173 +699,6 @@ __global__ void k_mp_loss(KParams P, DevBuffers B, MpBuffers M)
     }
 }
 
-// Backward of the MLP: per warp 16 rows (forward recomputed), activation
-// gradients on tensor cores; the block's 128 rows are staged in shared memory
-// and the weight gradients accumulated with transposed-tile products; one
-// partial gradient per block.
-__global__ void __launch_bounds__(kThreads, 1) k_mp_mlp_bwd(int rows, MpBuffers M)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16* sW1T = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-    __nv_bfloat16* sW2T = sW1T + 64 * kSW;
-    __nv_bfloat16* sW3T = sW2T + 64 * kSH;
-    __nv_bfloat16* sW2N = sW3T + 8 * kSH;
-    __nv_bfloat16* sW3P = sW2N + 64 * kSH;
-    __nv_bfloat16* tIn = sW3P + 64 * kSW;
-    __nv_bfloat16* tDY = tIn + kTileRows * kSW;
-    __nv_bfloat16* tH1 = tDY + kTileRows * kSW;
-    __nv_bfloat16* tH2 = tH1 + kTileRows * kSH;
-    __nv_bfloat16* tP1 = tH2 + kTileRows * kSH;
-    __nv_bfloat16* tP2 = tP1 + kTileRows * kSH;
-    load_weights_fwd(M.wb, sW1T, sW2T, sW3T);
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) sW2N[(e / 64) * kSH + e % 64] = M.wb[kW2N + e];
-    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) sW3P[(e / 16) * kSW + e % 16] = M.wb[kW3P + e];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float gW2[4][4], gW1[4], gW3[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        gW1[q] = gW3[q] = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) gW2[q][u] = 0.f;
-    }
-    const int lr0 = warp * 16 + g, lr1 = lr0 + 8;   // rows of this warp inside the tile
-    for (int tile = blockIdx.x * kTileRows; tile < rows; tile += gridDim.x * kTileRows) {
-        const int r0 = tile + lr0, r1 = tile + lr1;
-        unsigned ain[4];
-        input_frag(M.x0, M.a0, rows, r0, r1, ain);
-        FwdRegs R;
-        mlp_forward(ain, sW1T, sW2T, sW3T, R);
-        // dY fragment (k = the 4 message features, padded to 16)
-        unsigned ady[4] = {0u, 0u, 0u, 0u};
-        if (t < 2) {
-            const float* dy = reinterpret_cast<const float*>(M.dy);
-            const float2 u0 = r0 < rows ? *reinterpret_cast<const float2*>(dy + 4 * (size_t)r0 + 2 * t) : make_float2(0.f, 0.f);
-            const float2 u1 = r1 < rows ? *reinterpret_cast<const float2*>(dy + 4 * (size_t)r1 + 2 * t) : make_float2(0.f, 0.f);
-            ady[0] = pack_bf16(u0.x, u0.y);
-            ady[1] = pack_bf16(u1.x, u1.y);
-        }
-        // dh2 = dY W3^T, dp2 = dh2 (1 - h2^2)
-        float p2[8][4];
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            p2[nb][0] = p2[nb][1] = p2[nb][2] = p2[nb][3] = 0.f;
-            unsigned b0, b1;
-            load_b(sW3P, kSW, nb * 8, 0, b0, b1);
-            mma16816(p2[nb], ady, b0, b1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) p2[nb][q] *= 1.f - R.h2[nb][q] * R.h2[nb][q];
-        }
-        unsigned ap2[4][4];
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            ap2[kb][0] = pack_bf16(p2[2 * kb][0], p2[2 * kb][1]);
-            ap2[kb][1] = pack_bf16(p2[2 * kb][2], p2[2 * kb][3]);
-            ap2[kb][2] = pack_bf16(p2[2 * kb + 1][0], p2[2 * kb + 1][1]);
-            ap2[kb][3] = pack_bf16(p2[2 * kb + 1][2], p2[2 * kb + 1][3]);
-        }
-        // dh1 = dp2 W2^T, dp1 = dh1 (1 - h1^2)
-        float p1[8][4];
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            p1[nb][0] = p1[nb][1] = p1[nb][2] = p1[nb][3] = 0.f;
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb) {
-                unsigned b0, b1;
-                load_b(sW2N, kSH, nb * 8, kb * 16, b0, b1);
-                mma16816(p1[nb], ap2[kb], b0, b1);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) p1[nb][q] *= 1.f - R.h1[nb][q] * R.h1[nb][q];
-        }
-        // stage the tile (BF16): inputs, dY, h1, h2, dp1, dp2
-        unsigned* u;
-        u = reinterpret_cast<unsigned*>(tIn);
-        u[(lr0 * kSW + 2 * t) / 2] = ain[0];
-        u[(lr1 * kSW + 2 * t) / 2] = ain[1];
-        u[(lr0 * kSW + 8 + 2 * t) / 2] = ain[2];
-        u[(lr1 * kSW + 8 + 2 * t) / 2] = ain[3];
-        u = reinterpret_cast<unsigned*>(tDY);
-        u[(lr0 * kSW + 2 * t) / 2] = ady[0];
-        u[(lr1 * kSW + 2 * t) / 2] = ady[1];
-        u[(lr0 * kSW + 8 + 2 * t) / 2] = 0u;
-        u[(lr1 * kSW + 8 + 2 * t) / 2] = 0u;
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-            const int c0 = nb * 8 + 2 * t;
-            reinterpret_cast<unsigned*>(tH1)[(lr0 * kSH + c0) / 2] = pack_bf16(R.h1[nb][0], R.h1[nb][1]);
-            reinterpret_cast<unsigned*>(tH1)[(lr1 * kSH + c0) / 2] = pack_bf16(R.h1[nb][2], R.h1[nb][3]);
-            reinterpret_cast<unsigned*>(tH2)[(lr0 * kSH + c0) / 2] = pack_bf16(R.h2[nb][0], R.h2[nb][1]);
-            reinterpret_cast<unsigned*>(tH2)[(lr1 * kSH + c0) / 2] = pack_bf16(R.h2[nb][2], R.h2[nb][3]);
-            reinterpret_cast<unsigned*>(tP1)[(lr0 * kSH + c0) / 2] = pack_bf16(p1[nb][0], p1[nb][1]);
-            reinterpret_cast<unsigned*>(tP1)[(lr1 * kSH + c0) / 2] = pack_bf16(p1[nb][2], p1[nb][3]);
-            reinterpret_cast<unsigned*>(tP2)[(lr0 * kSH + c0) / 2] = pack_bf16(p2[nb][0], p2[nb][1]);
-            reinterpret_cast<unsigned*>(tP2)[(lr1 * kSH + c0) / 2] = pack_bf16(p2[nb][2], p2[nb][3]);
-        }
-        __syncthreads();
-        // weight gradients: sum over the tile's rows (k = row)
-        // A operand rows (m) come from a tile's columns: x4.trans over (rows kr.., cols m0..)
-        const int ar = (lane & 7) + ((lane >> 4) & 1) * 8;   // stored row offset for A (x4.trans)
-        const int ac = ((lane >> 3) & 1) * 8;                // stored col offset for A
-        const int br = (lane & 7) + ((lane >> 3) & 1) * 8;   // stored row offset for B (x2.trans)
-#pragma unroll
-        for (int kb = 0; kb < kTileRows / 16; ++kb) {
-            const int kr = kb * 16;
-            {   // dW2[i][h] += h1^T dp2: warp -> i block (warp % 4) x h half (warp / 4)
-                const int m0 = (warp & 3) * 16, h0 = (warp >> 2) * 32;
-                unsigned a[4];
-                ldsm_x4_t(a[0], a[1], a[2], a[3], tH1 + (kr + ar) * kSH + m0 + ac);
-#pragma unroll
-                for (int nb = 0; nb < 4; ++nb) {
-                    unsigned b0, b1;
-                    ldsm_x2_t(b0, b1, tP2 + (kr + br) * kSH + h0 + nb * 8);
-                    mma16816(gW2[nb], a, b0, b1);
-                }
-            }
-            {   // dW1[f][i] += in^T dp1: warp -> i block of 8
-                unsigned a[4];
-                ldsm_x4_t(a[0], a[1], a[2], a[3], tIn + (kr + ar) * kSW + ac);
-                unsigned b0, b1;
-                ldsm_x2_t(b0, b1, tP1 + (kr + br) * kSH + warp * 8);
-                mma16816(gW1, a, b0, b1);
-            }
-            if (warp < 4) {   // dW3[h][m] += h2^T dY: warp -> h block
-                unsigned a[4];
-                ldsm_x4_t(a[0], a[1], a[2], a[3], tH2 + (kr + ar) * kSH + warp * 16 + ac);
-                unsigned b0, b1;
-                ldsm_x2_t(b0, b1, tDY + (kr + br) * kSW);
-                mma16816(gW3, a, b0, b1);
-            }
-        }
-        __syncthreads();
-    }
-    // this block's partial gradient
-    float* gp = M.gpart + (size_t)blockIdx.x * kMpParams;
-    {
-        const int m0 = (warp & 3) * 16, h0 = (warp >> 2) * 32;
-#pragma unroll
-        for (int nb = 0; nb < 4; ++nb) {
-            const int h = h0 + nb * 8 + 2 * t;
-            gp[kMpOffW2 + (m0 + g) * 64 + h] = gW2[nb][0];
-            gp[kMpOffW2 + (m0 + g) * 64 + h + 1] = gW2[nb][1];
-            gp[kMpOffW2 + (m0 + g + 8) * 64 + h] = gW2[nb][2];
-            gp[kMpOffW2 + (m0 + g + 8) * 64 + h + 1] = gW2[nb][3];
-        }
-    }
-    if (g < 6) {
-        const int i = warp * 8 + 2 * t;
-        gp[kMpOffW1 + g * 64 + i] = gW1[0];
-        gp[kMpOffW1 + g * 64 + i + 1] = gW1[1];
-    }
-    if (warp < 4 && t < 2) {
-        const int h = warp * 16 + g;
-        gp[kMpOffW3 + h * 4 + 2 * t] = gW3[0];
-        gp[kMpOffW3 + h * 4 + 2 * t + 1] = gW3[1];
-        gp[kMpOffW3 + (h + 8) * 4 + 2 * t] = gW3[2];
-        gp[kMpOffW3 + (h + 8) * 4 + 2 * t + 1] = gW3[3];
-    }
-}
-
 // grad = sum over blocks (fixed order); the readout's gradient and the loss from the loss blocks.
 __global__ void k_mp_grad_reduce(MpBuffers M, int nblocks_mlp, int nblocks_loss, int rows)
 {
@@ -809,12 +751,6 @@ __global__ void k_mp_adam(MpBuffers M, float lr, int t)
 
 // ------------------------------------------------------------------ launchers
 
-int mp_bwd_smem_bytes()
-{
-    return (int)sizeof(__nv_bfloat16) *
-           (64 * kSW + 64 * kSH + 8 * kSH + 64 * kSH + 64 * kSW + 2 * kTileRows * kSW + 4 * kTileRows * kSH);
-}
-
 void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L)
 {
     const int rows = 3 * P.n;
@@ -834,14 +770,15 @@ void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, in
     k_mp_loss<<<nloss, kVecBlock, 0, L.stream>>>(P, B, M);
     k_mp_aggregate<<<grid_for(P.n, 128, 1 << 30), 128, 0, L.stream>>>(P, B, M.g1, M.dy, 2);
     const int nmlp = grid_for(rows, kTileRows, std::min(kMaxGradBlocks, L.num_sms));
-    k_mp_mlp_bwd<<<nmlp, kThreads, mp_bwd_smem_bytes(), L.stream>>>(rows, M);
+    k_mp_mlp_bwd_tc<<<nmlp, 128, mp_bwd_tc_smem_bytes(), L.stream>>>(rows, M, B.st);
     k_mp_grad_reduce<<<grid_for(kMpParams + 1, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(M, nmlp, nloss, rows);
     k_mp_adam<<<grid_for(kMpParams, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(M, lr, t);
 }
 
 int mp_prepare()
 {
-    return (int)cudaFuncSetAttribute(k_mp_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mp_bwd_smem_bytes());
+    return (int)cudaFuncSetAttribute(k_mp_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     mp_bwd_tc_smem_bytes());
 }
 
 int mp_weights_bf16_count() { return kWB; }

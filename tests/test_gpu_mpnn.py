@@ -95,3 +95,79 @@ def test_online_training_lowers_the_loss_and_keeps_cg_exact():
         losses.append(sim.mpnn_train_step(lr=2e-3))
     assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:5]), (losses[:5], losses[-10:])
     sim.close()
+
+
+def test_adam_steps_match_the_oracle_element_by_element():
+    """Two GPU Adam steps on the FP32 masters against oracle/mpnn.py's adam_step, fed the
+    same gradients (the GPU's), after a gradient-only call that must not count as a step."""
+    n, lr = 3000, 2e-3
+    sim = _solved_sim(n, 17, precision="mixed")
+    W = _weights(21)
+    w = W.flat().astype(np.float32)
+    sim.mpnn_enable(weights=w)
+    sim.step(1)
+    sim.mpnn_train_step(lr=0.0)   # gradient only
+    assert np.array_equal(sim.mpnn_weights(), w)
+    m = np.zeros(w.shape)
+    v = np.zeros(w.shape)
+    for t in (1, 2):
+        sim.step(1)
+        _, g = sim.mpnn_train_step(lr=lr, want_grad=True)
+        got = sim.mpnn_weights()
+        ref, m, v = mpnn.adam_step(mpnn.Weights.unflat(w.astype(np.float64)),
+                                   mpnn.Weights.unflat(g.astype(np.float64)), m, v, t, lr)
+        ref = ref.flat()
+        # FP32 masters and moments: the update lr m^/(sqrt(v^) + eps) to ~1e-6 relative, the
+        # stored weight to its FP32 rounding
+        err = np.abs(got - ref)
+        assert np.all(err <= 2e-7 * np.maximum(np.abs(ref), 1.0) + 1e-5 * lr), (t, err.max())
+        w = got
+    sim.close()
+
+
+def _train_on_streamed_solves(seeds, steps_per_seed, lr=2e-3):
+    """Online training on the precision workload's dynamics (N = 262,144, kappa tau 0.5): one Adam
+    step per time step, the weights carried from one seed's trajectory to the next."""
+    w = synth.PRECISION
+    weights = None
+    for sd in seeds:
+        pos = synth.uniform_positions(w.n, w.L, sd)
+        sim = ss.Simulation(w.n, w.L, ss.kappa_from_kappa_tau(w.kappa_tau), seed=sd, cg_tol=w.tol, positions=pos,
+                            precision="mixed", warm_start="prev")
+        sim.step(3)
+        sim.mpnn_enable(seed=1, weights=weights)
+        for _ in range(steps_per_seed):
+            info = sim.step(1)
+            assert info["status"] == 0 and info["last_residual"] <= w.tol
+            sim.mpnn_train_step(lr=lr)
+        weights = sim.mpnn_weights()
+        sim.close()
+    return weights
+
+
+def test_trained_network_cuts_cg_iterations():
+    """The network trained on streamed solves of three seeds, then run on a held-out seed: CG
+    iterations per step to the same 1e-8 with its guess, with a cold start (v0 = 0) and with the
+    previous velocities, from the same state after a common burn-in."""
+    w = synth.PRECISION
+    weights = _train_on_streamed_solves([101, 102, 103], 40)
+    held_out = 104
+    pos = synth.uniform_positions(w.n, w.L, held_out)
+    kappa = ss.kappa_from_kappa_tau(w.kappa_tau)
+    iters = {}
+    for mode in ("learned", "prev", "none"):
+        sim = ss.Simulation(w.n, w.L, kappa, seed=held_out, cg_tol=w.tol, positions=pos, precision="mixed",
+                            warm_start="none" if mode == "none" else "prev")
+        sim.step(5)
+        if mode == "learned":
+            sim.mpnn_enable(weights=weights)
+        its = []
+        for _ in range(20):
+            info = sim.step(1)
+            assert info["status"] == 0 and info["last_residual"] <= w.tol
+            its.append(info["cg_iterations"])
+        iters[mode] = float(np.mean(its))
+        sim.close()
+    print("CG iterations per step:", iters)
+    assert iters["learned"] < iters["none"] - 1.0, iters
+    assert iters["learned"] < iters["prev"], iters

@@ -143,8 +143,9 @@ class ClockSampler:
 # and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
 # block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 95.5e6,
-                    ("mixed-n262144", 6, 1, False, 1024, False): 122.0e6}
+PROFILED_TRAFFIC = {}
+# the same for the large workload (N = 4,194,304), by solver kernel
+LARGE_PROFILED_TRAFFIC = {}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
@@ -303,13 +304,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
     ap.add_argument("--workload", default="mixed",
-                    choices=["mixed", "lowshear", "plain", "learned", "batch", "large", "vcorr", "fdt"],
+                    choices=["mixed", "lowshear", "plain", "learned", "batch", "large", "config5", "vcorr", "fdt"],
                     help="mixed: N=262,144 precision workload at kappa tau 0.5 (the default line); lowshear: "
                          "the same at kappa tau 0.05; plain: the FP64 workload (N=4,096, 1e-10); learned: "
                          "N=262,144 with the learned warm start; batch: 64 replicas; large: N=4,194,304; "
                          "vcorr: the velocity cross-correlation of Fig. vv on the paper's box; fdt: "
                          "A^(1/2) g (FDT-consistent noise) on the N=262,144 system")
-    ap.add_argument("--train-steps", type=int, default=60)
+    ap.add_argument("--train-steps", type=int, default=520,
+                    help="learned workload: solves streamed into the online training (13 trajectories)")
     ap.add_argument("--solver-config", type=int, default=None,
                     help="tile configuration of the persistent mixed solver (sp_set_solver_config) instead of "
                          "autotuning; 9 is the on-chip k32_cg_resident<512,4>, 0 the streaming "
@@ -317,7 +319,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "ours" and args.workload not in ("mixed", "lowshear", "plain"):
-        return {"learned": run_learned, "batch": run_batch, "large": run_large,
+        return {"learned": run_learned, "batch": run_batch, "large": run_large, "config5": run_large,
                 "vcorr": run_vcorr, "fdt": run_fdt}[args.workload](args)
 
     workload = {"mixed": synth.PRECISION, "lowshear": synth.PRECISION_LOW_SHEAR,
@@ -520,42 +522,46 @@ def _sim(ss, w, precision, warm, pos=None, seed=None):
                          positions=synth.uniform_positions(w.n, w.L, w.seed) if pos is None else pos)
 
 
+TRAIN_SEEDS = 13   # trajectories of the precision workload the training streams its solves from
+
+
 def run_learned(args):
-    """Learned warm start at N=262,144, kappa*tau=0.5: the network is trained online for
-    --train-steps steps (untimed), then K steps are timed with it and, from the same state,
-    with a cold start (v0 = 0) and with the previous-velocity start."""
+    """Learned warm start at N=262,144, kappa*tau=0.5: the network is trained online on solves
+    streamed from TRAIN_SEEDS trajectories of the precision workload (--train-steps solves in all,
+    one Adam step per solve, untimed), then K steps of a held-out trajectory are timed with it
+    and, from the same state, with a cold start (v0 = 0) and with the previous-velocity start."""
     import torch
     import paper_1808_06381_gb300 as ss
     ss.load()
     w = synth.LEARNED
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sim = _sim(ss, w, "mixed", "prev")
-    sim.step(args.warmup)
-    sim.mpnn_enable(seed=1)
-    losses = []
-    for _ in range(args.train_steps):
-        sim.step(1)
-        losses.append(sim.mpnn_train_step(lr=2e-3))
-    pos = sim.get_positions()
-    delta, step = sim.state()
-    results = {}
-    clocks = ClockSampler(None)
-    clocks.start()
-    t, launches, iters, res = run_steps(sim, args.steps, stream, flush)
-    clk = clocks.stop()
-    prof = sim.profile_step()
-    results["learned"] = (t, iters, res)
-    for warm in ("none", "prev"):
-        other = _sim(ss, w, "mixed", warm, pos=pos)
-        other.set_positions(pos, delta)
-        other.set_step(step)
-        if warm == "prev":
-            other.step(1)   # one step so that the previous velocities exist
-        t2, _, it2, r2 = run_steps(other, args.steps, stream, flush)
-        results[warm] = (t2, it2, r2)
-        other.close()
-    sim.close()
+    weights, losses, t_train = train_network(ss, args.train_steps)
+    # the held-out trajectory three times from the same start and burn-in: with the trained
+    # network, with a cold start (v0 = 0) and with the previous velocities; the solver
+    # configuration the autotuner picks for the first
+    results, tune, clk, launches, prof = {}, None, None, 0, None
+    for mode in ("learned", "none", "prev"):
+        sim = _sim(ss, w, "mixed", "none" if mode == "none" else "prev")
+        if tune is None:
+            tune = sim.autotune(trials=1)
+        else:
+            sim.set_solver_config(tune["config"])
+        sim.step(args.warmup)
+        if mode == "learned":
+            sim.mpnn_enable(weights=weights)
+        sim.step(1)   # (the learned form's graph is captured here)
+        if mode == "learned":
+            clocks = ClockSampler(None)
+            clocks.start()
+        torch.cuda.synchronize()
+        t, nl, iters, res = run_steps(sim, args.steps, stream, flush)
+        if mode == "learned":
+            clk = clocks.stop()
+            launches = nl
+            prof = sim.profile_step()
+        results[mode] = (t, iters, res)
+        sim.close()
     n = w.n
     val = n * args.steps / (results["learned"][0] / 1e3)
     line = _common_line(val, n, args.steps, args.warmup, results["learned"][0] / args.steps, "bf16+f32+f64",
@@ -569,7 +575,9 @@ def run_learned(args):
                                             "max_true_residual": v[2]}
                                         for k, v in results.items()},
                          "training_loss_first_last": [losses[0], losses[-1]] if losses else None,
-                         "mpnn_ms_per_step": prof["mpnn_ms"], "gpu_launches": launches, "clocks": clk})
+                         "training": {"solves": len(losses), "trajectories": TRAIN_SEEDS, "seconds": t_train},
+                         "mpnn_ms_per_step": prof["mpnn_ms"], "gpu_launches": launches, "clocks": clk,
+                         "autotune": tune})
     print(json.dumps(line), flush=True)
 
 
@@ -587,6 +595,13 @@ def run_batch(args):
     ntot = sum(r.n for r in reps)
     batch = ss.Batch(kws, positions=pos)
     batch.step(args.warmup)
+    torch.cuda.synchronize()
+    # the untuned configuration (0) first, then the autotuner's choice
+    t0 = time.perf_counter()
+    batch.step(args.steps)
+    t_untuned = time.perf_counter() - t0
+    tune = batch.autotune(trials=2)
+    batch.step(1)   # the re-captured graph
     torch.cuda.synchronize()
     clocks = ClockSampler(None)
     clocks.start()
@@ -620,54 +635,126 @@ def run_batch(args):
                          "max_true_residual": worst, "gpu_launches": launches,
                          "sequential": {"value": ntot * args.steps / t_seq, "ms_per_step": 1e3 * t_seq / args.steps},
                          "speedup_vs_sequential": t_seq / t_batch, "blocks_per_replica": blocks,
+                         "untuned": {"config": 0, "value": ntot * args.steps / t_untuned,
+                                     "ms_per_step": 1e3 * t_untuned / args.steps},
+                         "autotune": tune,
                          "timing": "host wall clock around the synchronising batch call", "clocks": clk})
     print(json.dumps(line), flush=True)
 
 
+def train_network(ss, steps: int):
+    """Online training on solves streamed from TRAIN_SEEDS trajectories of the precision workload
+    (N = 262,144); returns (weights, losses, seconds)."""
+    w = synth.LEARNED
+    losses, weights = [], None
+    per_seed = max(1, steps // TRAIN_SEEDS)
+    t0 = time.perf_counter()
+    for k in range(TRAIN_SEEDS):
+        seed = synth.PRECISION.seed + 100 + k
+        tr = _sim(ss, w, "mixed", "prev", pos=synth.uniform_positions(w.n, w.L, seed), seed=seed)
+        tr.step(3)
+        tr.mpnn_enable(seed=1, weights=weights)
+        for _ in range(per_seed):
+            tr.step(1)
+            losses.append(tr.mpnn_train_step(lr=2e-3))
+        weights = tr.mpnn_weights()
+        tr.close()
+    return weights, losses, time.perf_counter() - t0
+
+
+SQ_EVERY = 100   # steps between two S(qx, qy) of the large-scale workload
+
+
 def run_large(args):
     """N = 4,194,304 (box 111.8), mixed solver: the solver's working set (~2 GB) is far larger
-    than L2, so this is the HBM-bound regime of the same kernels."""
+    than L2, so this is the HBM-bound regime of the same kernels.  --workload config5 adds the
+    large-scale workload's learned warm start (the network trained on solves streamed from
+    trajectories of the N = 262,144 workload; its weights do not depend on N) and S(qx, qy) on
+    a 256^3 grid every SQ_EVERY steps, inside the timed region (K >= SQ_EVERY) and amortised."""
     import torch
     import paper_1808_06381_gb300 as ss
     ss.load()
     w = synth.LARGE
+    learned = args.workload == "config5"
     stream = torch.cuda.current_stream()
     flush = torch.empty(4, dtype=torch.float32, device="cuda")   # inputs are larger than L2
+    training = None
+    if learned:
+        weights, losses, t_train = train_network(ss, args.train_steps)
+        training = {"solves": len(losses), "trajectories": TRAIN_SEEDS, "seconds": t_train, "n": synth.LEARNED.n,
+                    "loss_first_last": [losses[0], losses[-1]] if losses else None}
     sim = _sim(ss, w, "mixed", "prev")
     tune = (sim.set_solver_config(args.solver_config) if args.solver_config is not None
             else sim.autotune(trials=1))
     sim.step(args.warmup)
+    if learned:
+        sim.mpnn_enable(weights=weights)
+        sim.step(1)
+    t_sq = time.perf_counter()
+    sim.structure_factor(48, 48, grid=256)
+    torch.cuda.synchronize()
+    t_sq = time.perf_counter() - t_sq
     clocks = ClockSampler(None)
     clocks.start()
-    t, launches, iters, res = run_steps(sim, args.steps, stream, flush)
+    t, launches, iters, res = 0.0, 0, 0, 0.0
+    n_sq, t_sq_in = 0, 0.0
+    done = 0
+    while done < args.steps:
+        chunk = min(SQ_EVERY, args.steps - done)
+        tc, lc, ic, rc = run_steps(sim, chunk, stream, flush)
+        t += tc
+        launches += lc
+        iters += ic
+        res = max(res, rc)
+        done += chunk
+        if chunk == SQ_EVERY:   # S(qx, qy) every SQ_EVERY steps, timed with the steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.structure_factor(48, 48, grid=256)
+            e1.record(stream)
+            e1.synchronize()
+            t_sq_in += e0.elapsed_time(e1)
+            n_sq += 1
     clk = clocks.stop()
     prof = sim.profile_step()
     peak, peak_kind = measured_peaks()
+    plan = plan_algorithmic_bytes(prof["n"], prof["cg_iterations"], "mixed")
+    pach = plan / (prof["persistent_ms"] * 1e-3) / 1e9
     pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"],
-                                              bool(prof.get("persistent_init")))
-    pach = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9
+                                          bool(prof.get("persistent_init")))
     spmv = spmv_algorithmic_bytes(prof["n"], prof["nnz"], "mixed") / (prof["spmv_probe_ms"] * 1e-3) / 1e9
-    t_sq = time.perf_counter()
-    S, qx, qy = sim.structure_factor(48, 48, grid=256)
-    t_sq = time.perf_counter() - t_sq
+    traffic = LARGE_PROFILED_TRAFFIC.get(solver_kernel_name(tune))
     sim.close()
     n = w.n
-    line = _common_line(n * args.steps / (t / 1e3), n, args.steps, args.warmup, t / args.steps, "f32+f64",
-                        {"workload": w.name, "n": n, "box": w.L[0], "kappa_tau": w.kappa_tau, "cg_tol": w.tol,
-                         "precision": "mixed", "warm_start": "prev", "l2": "working set > L2"},
+    total = t + t_sq_in
+    line = _common_line(n * args.steps / (total / 1e3), n, args.steps, args.warmup, total / args.steps, "f32+f64",
+                        {"workload": ("config5-" if learned else "") + w.name, "n": n, "box": w.L[0],
+                         "kappa_tau": w.kappa_tau, "cg_tol": w.tol, "precision": "mixed",
+                         "warm_start": "learned" if learned else "prev", "l2": "working set > L2",
+                         "structure_factor": f"256^3 CIC grid every {SQ_EVERY} steps (timed)"},
                         {"cg_iterations_per_step": iters / args.steps, "max_true_residual": res,
                          "gpu_launches": launches,
-                         "roofline": {"kernel": "k32_cg_persistent", "bound": "hbm", "achieved": pach, "peak": peak,
-                                      "unit": "GB/s", "frac": pach / peak, "traffic": None,
+                         "roofline": {"kernel": solver_kernel_name(tune), "bound": "hbm", "achieved": pach,
+                                      "peak": peak, "unit": "GB/s", "frac": pach / peak, "traffic": traffic,
                                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
-                                      "algorithmic_bytes_per_launch": pbytes,
-                                      "avg_launch_ms": prof["persistent_ms"]},
+                                      "algorithmic_bytes_per_launch": plan,
+                                      "algorithmic_bytes_rule": f"{MIXED_BYTES_PER_PARTICLE_ITERATION:g} B per "
+                                                                "particle per CG iteration x n x iterations",
+                                      "avg_launch_ms": prof["persistent_ms"],
+                                      "detailed_bytes_per_launch": pbytes,
+                                      "dram_gbs": traffic / (prof["persistent_ms"] * 1e-3) / 1e9 if traffic else None,
+                                      "dram_frac": (traffic / (prof["persistent_ms"] * 1e-3) / 1e9 / peak
+                                                    if traffic else None)},
                          "roofline_spmv_kernel": {"achieved": spmv, "frac": spmv / peak,
                                                   "avg_launch_ms": prof["spmv_probe_ms"]},
                          "kernel_ms_per_step": {k: prof[k] for k in ("persistent_ms", "build_ms", "fill_ms",
                                                                       "assemble_ms", "count_ms", "sort_ms",
-                                                                      "other_ms")},
-                         "autotune": tune, "structure_factor_ms": 1e3 * t_sq, "clocks": clk})
+                                                                      "other_ms", "mpnn_ms")},
+                         "autotune": tune, "structure_factor_ms": 1e3 * t_sq,
+                         "structure_factor_in_region": {"calls": n_sq, "ms": t_sq_in},
+                         "steps_only_value": n * args.steps / (t / 1e3),
+                         "training": training, "clocks": clk})
     print(json.dumps(line), flush=True)
 
 

@@ -98,6 +98,8 @@ typedef struct sp_solve_info {
                                fit on their SM and were solved with global gathers (0 otherwise) */
     int32_t host_driven;    /* 1: the solve's CG loop was driven from the host (graph capture
                                unavailable, or SHEARSIM_HOST_LOOP=1); 0: it ran as one CUDA graph */
+    int32_t staged_blocks;  /* on-chip solver configuration: blocks that copied the rows of other
+                               blocks their entries reach into shared memory every iteration */
 } sp_solve_info;
 
 typedef struct sp_step_info {
@@ -446,6 +448,26 @@ int sp_batch_step(sp_batch* b, int32_t nsteps, sp_step_info* info);
 int sp_batch_get_sim(sp_batch* b, int32_t k, sp_sim** sim);
 /* Blocks of the cooperative launch given to each replica, [R]. */
 int sp_batch_blocks(sp_batch* b, int32_t* blocks);
+/* Tile configuration of the batched solver, chosen by timing (not in the
+ * paper; an implementation parameter): the batched solve runs in several
+ * compiled configurations (gathers in flight per thread, resident blocks per
+ * SM, threads per block: 256, 512 or 1024; fewer, larger blocks give each
+ * replica fewer blocks to synchronise), and the blocks of the cooperative
+ * launch are shared out in proportion to the replicas' rows within that
+ * configuration's co-resident capacity.  sp_batch_autotune builds every
+ * replica's pair list and system for its current positions, times `trials`
+ * batched solves from a zero start per configuration (CUDA events on the
+ * batch's stream), keeps the fastest and re-shares the blocks; positions,
+ * offsets, step counters and the previous velocities are unchanged.
+ * info (may be NULL): chosen config, its gathers_in_flight, blocks_per_sm and
+ * block_threads, num_configs, and ms[k] the best solve time of configuration
+ * k (0: not timed, e.g. fewer resident blocks than replicas).  trials < 1
+ * keeps the current configuration.  The configurations round the dot
+ * products differently (results agree to ~1e-13 relative); each is
+ * deterministic.  sp_batch_set_config selects configuration `config` without
+ * timing.  Errors: SP_ERR_INVALID_ARG, SP_ERR_CUDA, and those of a build. */
+int sp_batch_autotune(sp_batch* b, int32_t trials, sp_tune_info* info);
+int sp_batch_set_config(sp_batch* b, int32_t config);
 const char* sp_batch_last_error(const sp_batch* b);
 
 /* ---- allocation-free solve ----

@@ -52,7 +52,8 @@ class sp_params(ctypes.Structure):
 
 class sp_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("residual", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32), ("host_driven", ctypes.c_int32)]
+                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32), ("host_driven", ctypes.c_int32),
+                ("staged_blocks", ctypes.c_int32)]
 
 
 class sp_step_info(ctypes.Structure):
@@ -126,7 +127,8 @@ def load(path: str = LIB_PATH):
             ("sp_solve_csr_noalloc", [i32, vp, i64, vp, vp, vp, vp, d, vp, vp, d, i32, P(sp_solve_info)]),
             ("sp_batch_create", [i32, vp, vp, P(vp)]), ("sp_batch_destroy", [vp]),
             ("sp_batch_step", [vp, i32, vp]), ("sp_batch_get_sim", [vp, i32, P(vp)]),
-            ("sp_batch_blocks", [vp, vp]),
+            ("sp_batch_blocks", [vp, vp]), ("sp_batch_autotune", [vp, i32, P(sp_tune_info)]),
+            ("sp_batch_set_config", [vp, i32]),
             ("sp_mpnn_enable", [vp, u64, vp]), ("sp_mpnn_disable", [vp]), ("sp_mpnn_get_weights", [vp, vp]),
             ("sp_mpnn_set_weights", [vp, vp]), ("sp_mpnn_forward", [vp, vp]),
             ("sp_mpnn_train_step", [vp, ctypes.c_float, P(d), vp])]
@@ -326,7 +328,8 @@ class Simulation:
         if raise_on_error:
             self._c(rc)
         return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
-                "offchip_blocks": info.offchip_blocks, "host_driven": info.host_driven}
+                "offchip_blocks": info.offchip_blocks, "host_driven": info.host_driven,
+                "staged_blocks": info.staged_blocks}
 
     def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
         info = sp_step_info()
@@ -562,6 +565,21 @@ class Batch:
         out = np.zeros(self.R, dtype=np.int32)
         _check(load().sp_batch_blocks(self._h, _p(out)))
         return out
+
+    def autotune(self, trials: int = 2) -> dict:
+        """Time the batched solver's tile configurations on the current systems; keep the fastest."""
+        info = sp_tune_info()
+        rc = load().sp_batch_autotune(self._h, int(trials), ctypes.byref(info))
+        if rc != SP_OK:
+            raise ShearsimError(rc, (load().sp_batch_last_error(self._h) or b"").decode())
+        return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
+                "blocks_per_sm": info.blocks_per_sm, "block_threads": info.block_threads,
+                "num_configs": info.num_configs, "ms": list(info.ms)[: info.num_configs]}
+
+    def set_config(self, config: int):
+        rc = load().sp_batch_set_config(self._h, int(config))
+        if rc != SP_OK:
+            raise ShearsimError(rc, (load().sp_batch_last_error(self._h) or b"").decode())
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -35,6 +35,7 @@ struct sp_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long fixed_launches = 0;
+    int cfg = 0;   // tile configuration of the batched solver (sp_batch_autotune)
     std::string err;
 };
 
@@ -73,7 +74,7 @@ int upload(sp_batch* b)
         win[k] = P[k].nslots / 256;
         total_win += win[k];
     }
-    const int cap = cg_persistent_batch_capacity(Launch{b->stream, b->sims[0]->num_sms});
+    const int cap = cg_persistent_batch_capacity(Launch{b->stream, b->sims[0]->num_sms}, b->cfg);
     if (cap < b->R) {
         b->err = "more replicas than resident blocks of the batched solver";
         return SP_ERR_INVALID_ARG;
@@ -132,7 +133,7 @@ int capture(sp_batch* b)
         launches += launch_cg_init(s->kp, s->B, s->p.warm_start == SP_WARM_PREV, true, launch_of(s, st));
     }
     join();
-    if (launch_cg32_persistent_batch(b->d_P, b->d_B, b->d_blk_off, b->R, b->total_blocks,
+    if (launch_cg32_persistent_batch(b->d_P, b->d_B, b->d_blk_off, b->R, b->total_blocks, b->cfg,
                                      Launch{cs, b->sims[0]->num_sms}) != cudaSuccess)
         rc = SP_ERR_CUDA;
     launches += 1;
@@ -309,6 +310,103 @@ int sp_batch_step(sp_batch* b, int32_t nsteps, sp_step_info* info)
     }
     if (status != SP_OK) b->err = "a replica failed (see its step info)";
     return status;
+}
+
+int sp_batch_autotune(sp_batch* b, int32_t trials, sp_tune_info* info)
+{
+    if (!b) return SP_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return SP_ERR_NO_DEVICE;
+    sp_tune_info out{};
+    out.num_configs = std::min(kBatchConfigs, SP_TUNE_MAX_CONFIGS);
+    const int prev = b->cfg;
+    int best = prev;
+    if (trials >= 1) {
+        // every replica's pair list and system for its current positions (the
+        // state is kept: a build only reorders it; the solves below overwrite
+        // only the solution vectors, which the next step's build refills)
+        for (sp_sim* s : b->sims) {
+            int rc = do_build(s);
+            if (rc == SP_OK) rc = sp_assemble(s);
+            if (rc != SP_OK) {
+                b->err = "autotune: building a replica's system failed";
+                return rc;
+            }
+        }
+        cudaEvent_t e0, e1;
+        SB_CUDA(cudaEventCreate(&e0));
+        SB_CUDA(cudaEventCreate(&e1));
+        double best_ms = 1e30;
+        for (int k = 0; k < out.num_configs; ++k) {
+            b->cfg = k;
+            if (upload(b) != SP_OK) {   // fewer resident blocks than replicas
+                cudaGetLastError();
+                continue;
+            }
+            double t = 1e30;
+            for (int r = 0; r < trials; ++r) {
+                for (sp_sim* s : b->sims) launch_cg_init(s->kp, s->B, false, true, launch_of(s, b->stream));
+                cudaEventRecord(e0, b->stream);
+                const cudaError_t le = launch_cg32_persistent_batch(b->d_P, b->d_B, b->d_blk_off, b->R,
+                                                                    b->total_blocks, k,
+                                                                    Launch{b->stream, b->sims[0]->num_sms});
+                cudaEventRecord(e1, b->stream);
+                if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    b->cfg = prev;
+                    upload(b);
+                    b->err = std::string("autotune: batched solve failed: ") + cudaGetErrorString(le);
+                    return SP_ERR_CUDA;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t = std::min(t, (double)ms);
+            }
+            for (sp_sim* s : b->sims) {   // a failed trial (e.g. a timeout) is not a candidate
+                if (read_state(s) != SP_OK) break;
+                if (s->st_host->error) {
+                    clear_flags(s);
+                    t = 1e30;
+                }
+            }
+            if (k < SP_TUNE_MAX_CONFIGS) out.ms[k] = t < 1e30 ? t : 0.0;
+            if (t < best_ms) {
+                best_ms = t;
+                best = k;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    b->cfg = best;
+    free_graph(b);
+    const int rc = upload(b);
+    if (rc != SP_OK) return rc;
+    for (sp_sim* s : b->sims) {
+        s->built = false;
+        s->assembled = false;
+    }
+    if (info) {
+        out.config = best;
+        cg_batch_config(best, &out.gathers_in_flight, &out.blocks_per_sm, &out.block_threads);
+        *info = out;
+    }
+    return SP_OK;
+}
+
+int sp_batch_set_config(sp_batch* b, int32_t config)
+{
+    if (!b || config < 0 || config >= kBatchConfigs) return SP_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return SP_ERR_NO_DEVICE;
+    const int prev = b->cfg;
+    b->cfg = config;
+    free_graph(b);
+    const int rc = upload(b);
+    if (rc != SP_OK) {
+        b->cfg = prev;
+        upload(b);
+    }
+    return rc;
 }
 
 const char* sp_batch_last_error(const sp_batch* b)

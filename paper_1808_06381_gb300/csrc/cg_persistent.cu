@@ -30,7 +30,6 @@ namespace ss {
 
 namespace {
 
-constexpr int kPBlock = 256;
 
 struct PShared {
     float2 df[32];
@@ -294,8 +293,6 @@ __device__ __forceinline__ bool grid_allreduce(DevState* st, unsigned int& gen, 
     for (int k = 0; k < K; ++k) out[k] = sh.bcast[k];
     return sh.flag == 0;
 }
-
-constexpr int kBatchP = 6;    // FP32 gathers in flight per thread (batch kernel; see kPersistentCfg)
 
 // s = sum_j w_ij D^-1_j r_j (FP32).  Rows of r written by other blocks before
 // the last barrier are visible to plain loads (the barrier's acquire orders
@@ -639,7 +636,54 @@ struct RShared {
     int nhalo[kResChunks];   // halo entries per row of the chunk
     int hoff[kResChunks];    // global offset of the chunk's halo list
     int mode;                // 0: on chip; 1: the block's entries did not fit, all gathers global
+    int lo_total, ho_total;  // local and halo list lengths of the block (padding included)
+    int nstage;              // distinct rows of other blocks that the halo entries reach
+    int staged;              // 1: those rows' r are staged in shared memory every iteration
+    int hash_fail;
 };
+
+// cp.async of 16 bytes from global to shared memory (L2 only, bypassing L1)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<unsigned>(__cvta_generic_to_shared(smem_dst))),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned halo_hash(int j) { return (unsigned)j * 2654435761u; }
+
+// Exclusive prefix sum over the block of one value per thread (all threads
+// call it); returns this thread's offset and the block total in *total.
+template <int BS>
+__device__ __forceinline__ int block_excl_scan(int v, int* tmp, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < BS / 32 ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < BS / 32) tmp[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = (warp > 0 ? tmp[warp - 1] : 0) + x - v;
+    *total = tmp[BS / 32 - 1];
+    __syncthreads();   // tmp may be reused by the caller
+    return before;
+}
 
 __device__ __forceinline__ void res_halo_batch(const DevBuffers& B, int hb, int kb, int nh, float& s0, float& s1,
                                                float& s2)
@@ -695,7 +739,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows
     const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 6;
     float* sval = reinterpret_cast<float*>(dyn + nwmax * 256);
-    unsigned short* scol = reinterpret_cast<unsigned short*>(sval + cap);
+    unsigned short* scol = nullptr;   // after the block's local entries are counted (set-up 2)
     float* __restrict__ rlo = B.rlo + (size_t)bid * kResLoStride;   // low parts of the local weights
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
@@ -794,13 +838,16 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             ho += 32 * rs.nhalo[c];
         }
         rs.mode = (lo <= cap && ho <= hcap) ? 0 : 1;
-        if (fused)   // summed by block 0 at the end (the counter is not reset before this launch)
-            B.partials[3 * kMaxPartials + bid] = (double)rs.mode;
-        else if (rs.mode)
-            atomicAdd(&st->res_offchip, 1);
+        rs.lo_total = lo;
+        rs.ho_total = ho;
+        rs.staged = 0;
+        rs.nstage = 0;
+        rs.hash_fail = 0;
+        if (!fused && rs.mode) atomicAdd(&st->res_offchip, 1);   // (fused: recorded after set-up 4)
     }
     __syncthreads();
     const bool onchip = rs.mode == 0;
+    scol = reinterpret_cast<unsigned short*>(sval + rs.lo_total);   // 6 lo_total <= 6 cap bytes in mode 0
     if (!onchip) {   // the sliced layout's own assignment, every gather global
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
@@ -915,6 +962,105 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     }
     __syncthreads();   // sinv (in zbuf) is read until here
 
+    // ---- set-up 4 (on chip): the distinct rows of other blocks that the halo
+    // entries reach, numbered 0 .. nstage-1 by a hash table in zbuf (free
+    // until the iteration starts); each halo entry's column and weight are
+    // copied into shared memory with the row's number, and every SpMV phase
+    // stages those rows' r (and D^-1) into shared memory with asynchronous
+    // copies while the local half of the products runs.  Shared memory after
+    // the local entries: halo weights [ho], their numbers [ho], the staged
+    // rows [nstage] (float4) and their global rows [nstage].
+    const int hbase = B.chunk_off[wb * 8];
+    const int zbytes = nwmax * 256 * (int)sizeof(float4);
+    unsigned char* dynb = reinterpret_cast<unsigned char*>(dyn);
+    const int hoff_b = (zbytes + 6 * rs.lo_total + 15) & ~15;
+    float* shw = reinterpret_cast<float*>(dynb + hoff_b);
+    unsigned short* shidx = reinterpret_cast<unsigned short*>(shw + rs.ho_total);
+    const int stage_b = (hoff_b + 6 * rs.ho_total + 15) & ~15;
+    float4* stage = reinterpret_cast<float4*>(dynb + stage_b);
+    int nstage = 0;
+    int* hrow = nullptr;
+    if (onchip && P.res_stage && rs.ho_total > 0) {
+        int hsize = 4096;
+        while (hsize > 32 && 6 * hsize > zbytes) hsize >>= 1;
+        if (6 * hsize <= zbytes && hsize >= rs.ho_total / 2 + 32) {
+            int* keys = reinterpret_cast<int*>(zbuf);
+            unsigned short* tidx = reinterpret_cast<unsigned short*>(keys + hsize);
+            const unsigned mask = (unsigned)hsize - 1u;
+            for (int h = threadIdx.x; h < hsize; h += BS) keys[h] = -1;
+            __syncthreads();
+            bool fail = false;
+            for (int e = threadIdx.x; e < rs.ho_total; e += BS) {
+                if (B.hval[hbase + e] == 0.f) continue;   // padding of a chunk's list
+                const int j = B.hcol[hbase + e];
+                unsigned h = halo_hash(j) & mask;
+                int probe = 0;
+                for (; probe < hsize; ++probe) {
+                    const int old = atomicCAS(&keys[h], -1, j);
+                    if (old == -1 || old == j) break;
+                    h = (h + 1u) & mask;
+                }
+                if (probe == hsize) fail = true;
+            }
+            if (fail) rs.hash_fail = 1;
+            __syncthreads();
+            // number the occupied slots in slot order (each thread a run of slots)
+            const int per = (hsize + BS - 1) / BS, s0 = threadIdx.x * per, s1 = min(s0 + per, hsize);
+            int cnt = 0;
+            for (int h = s0; h < s1; ++h) cnt += keys[h] >= 0 ? 1 : 0;
+            int total = 0;
+            int idx = block_excl_scan<BS>(cnt, reinterpret_cast<int*>(rs.loff), &total);
+            // rs.loff was read by every thread before this point (set-up 3); it is restored below
+            const int need = stage_b + total * (int)(sizeof(float4) + sizeof(int));
+            const bool ok = !rs.hash_fail && total <= 65535 && need <= smem_bytes;
+            if (ok) {
+                nstage = total;
+                hrow = reinterpret_cast<int*>(stage + nstage);
+                for (int h = s0; h < s1; ++h) {
+                    if (keys[h] >= 0) {
+                        tidx[h] = (unsigned short)idx;
+                        hrow[idx] = keys[h];
+                        ++idx;
+                    }
+                }
+            }
+            __syncthreads();
+            if (ok) {
+                for (int e = threadIdx.x; e < rs.ho_total; e += BS) {
+                    const float w = B.hval[hbase + e];
+                    unsigned short k = 0;
+                    if (w != 0.f) {
+                        const int j = B.hcol[hbase + e];
+                        unsigned h = halo_hash(j) & mask;
+                        for (int probe = 0; probe < hsize && keys[h] != j; ++probe) h = (h + 1u) & mask;
+                        k = tidx[h];
+                    }
+                    shw[e] = w;
+                    shidx[e] = k;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // the chunk offsets of the local lists again (the scan used them as scratch)
+                int lo = 0;
+                for (int c = 0; c < kResChunks; ++c) {
+                    rs.loff[c] = lo;
+                    lo += 32 * rs.nloc[c];
+                }
+                rs.staged = ok ? 1 : 0;
+                rs.nstage = ok ? total : 0;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {   // off chip: 1, staged: 2 (summed by block 0 at the end of a fused launch)
+        if (fused)
+            B.partials[3 * kMaxPartials + bid] = (double)(rs.mode + 2 * rs.staged);
+        else if (rs.staged)
+            atomicAdd(&st->res_staged, 1);
+    }
+    const bool staged = onchip && rs.staged != 0;
+
     // ---- the initial residual (fused form): r = b - A x0 in double-float, or
     // r = b with x = 0, for the block's rows in slot order, with ||b||^2,
     // r.r and r.D^-1 r summed over the grid (as the initial-residual kernel)
@@ -1016,6 +1162,66 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         // ---- SpMV with the fused direction update; p.q
         dfloat pq{0.f, 0.f};
         const float betaf = sh.beta_f;
+        if (staged) {
+            // the halo rows' r (with D^-1 in .w), published before the last
+            // barrier, are copied into shared memory while the local half runs
+            for (int k = threadIdx.x; k < nstage; k += BS) cp_async16(stage + k, B.r4 + hrow[k]);
+            cp_async_commit();
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                const float di = __ldg(B.diag32 + row[u]);
+                const int c = u * (BS / 32) + warp;
+                const int lo = rs.loff[c] + lane, nl = rs.nloc[c];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                for (int k = 0; k < nl; ++k) {
+                    const float wl = sval[lo + 32 * k];
+                    const float4 zj = zbuf[scol[lo + 32 * k]];
+                    s0 = fmaf(wl, zj.x, s0);
+                    s1 = fmaf(wl, zj.y, s1);
+                    s2 = fmaf(wl, zj.z, s2);
+                }
+                const float z0 = dv[u] * r[u][0], z1 = dv[u] * r[u][1], z2 = dv[u] * r[u][2];
+                float q0 = fmaf(di, z0, -alpha_e * s0);
+                float q1 = fmaf(di, z1, -alpha_e * s1);
+                float q2 = fmaf(di, z2, -alpha_e * s2);
+                if (betaf != 0.f) {
+                    q0 = fmaf(betaf, q[u][0], q0);
+                    q1 = fmaf(betaf, q[u][1], q1);
+                    q2 = fmaf(betaf, q[u][2], q2);
+                    p[u][0] = fmaf(betaf, p[u][0], z0);
+                    p[u][1] = fmaf(betaf, p[u][1], z1);
+                    p[u][2] = fmaf(betaf, p[u][2], z2);
+                } else {
+                    p[u][0] = z0;
+                    p[u][1] = z1;
+                    p[u][2] = z2;
+                }
+                q[u][0] = q0;
+                q[u][1] = q1;
+                q[u][2] = q2;
+            }
+            cp_async_wait_all();
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                if (row[u] < 0) continue;
+                const int c = u * (BS / 32) + warp;
+                const int hb = rs.hoff[c] - hbase + lane, nh = rs.nhalo[c];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+                for (int k = 0; k < nh; ++k) {
+                    const float4 g = stage[shidx[hb + 32 * k]];
+                    const float ww = shw[hb + 32 * k] * g.w;
+                    s0 = fmaf(ww, g.x, s0);
+                    s1 = fmaf(ww, g.y, s1);
+                    s2 = fmaf(ww, g.z, s2);
+                }
+                q[u][0] = fmaf(-alpha_e, s0, q[u][0]);
+                q[u][1] = fmaf(-alpha_e, s1, q[u][1]);
+                q[u][2] = fmaf(-alpha_e, s2, q[u][2]);
+                pq.hi += p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2];   // FP32, as the block sums
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             if (row[u] < 0) continue;
@@ -1084,6 +1290,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             q[u][1] = q1;
             q[u][2] = q2;
             pq.hi += p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2];   // FP32, as the block sums
+        }
         }
         {
             const dfloat v[1] = {pq};
@@ -1340,9 +1547,14 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     }
     if (bid == 0 && threadIdx.x == 0) {
         if (fused) {   // every block wrote its mode before the first grid reduction
-            int off = 0;
-            for (int b = 0; b < nb; ++b) off += B.partials[3 * kMaxPartials + b] != 0.0 ? 1 : 0;
+            int off = 0, stg = 0;
+            for (int b = 0; b < nb; ++b) {
+                const int m = (int)B.partials[3 * kMaxPartials + b];
+                off += m & 1;
+                stg += m >> 1;
+            }
             st->res_offchip = off;
+            st->res_staged = stg;
         }
         st->iter = sh.iter;
         st->restarts = sh.restarts;
@@ -1384,10 +1596,13 @@ __global__ void __launch_bounds__(BS, MINB) k32_cg_persistent(KParams P, DevBuff
 
 // Batch: block b serves replica k with blk_off[k] <= b < blk_off[k + 1]; each
 // replica's blocks synchronise and reduce among themselves only, and leave
-// when their replica has converged.
-__global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KParams* __restrict__ Ps,
-                                                                     const DevBuffers* __restrict__ Bs,
-                                                                     const int* __restrict__ blk_off, int R)
+// when their replica has converged.  Tile configurations (gathers in flight
+// KB, resident blocks per SM MINB, threads per block BS) are chosen by
+// sp_batch_autotune.
+template <int KB, int MINB, int BS>
+__global__ void __launch_bounds__(BS, MINB) k32_cg_persistent_batch(const KParams* __restrict__ Ps,
+                                                                   const DevBuffers* __restrict__ Bs,
+                                                                   const int* __restrict__ blk_off, int R)
 {
     __shared__ PShared sh;
     __shared__ int rep;
@@ -1401,12 +1616,13 @@ __global__ void __launch_bounds__(kPBlock, 4) k32_cg_persistent_batch(const KPar
     }
     __syncthreads();
     const int k = rep;
-    persistent_solve<kBatchP, false>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
+    persistent_solve<KB, false>(Ps[k], Bs[k], (int)blockIdx.x - blk_off[k], blk_off[k + 1] - blk_off[k], sh);
     barrier_leave(Bs[k].st, blk_off[k + 1] - blk_off[k]);
 }
 
 namespace {
-// kResSmemBytes (190 KB) leaves a 196 KB carve-out's L1 for the halo gathers
+// kResSmemBytes (223 KB): the on-chip solve stages its halo rows in shared memory, so L1 serves
+// only the set-up's reads and the residual replacements
 
 struct PCfg {
     int kb, minb, pipe, bs;
@@ -1426,7 +1642,19 @@ PCfg g_pcfg[kPersistentConfigs] = {   // entry 0: the default without autotuning
     {kResHalo, 1, 0, 1024, (const void*)k32_cg_resident<1024, 2>, 0, 1},
     {kResHalo, 1, 0, 512, (const void*)k32_cg_resident<512, 4>, 0, 1},
 };
-int g_pocc_batch = 0;
+struct BCfg {
+    int kb, minb, bs;
+    const void* fn;
+    int occ;
+};
+BCfg g_bcfg[kBatchConfigs] = {   // entry 0: the default without autotuning
+    {6, 4, 256, (const void*)k32_cg_persistent_batch<6, 4, 256>, 0},
+    {4, 4, 256, (const void*)k32_cg_persistent_batch<4, 4, 256>, 0},
+    {8, 4, 256, (const void*)k32_cg_persistent_batch<8, 4, 256>, 0},
+    {6, 2, 512, (const void*)k32_cg_persistent_batch<6, 2, 512>, 0},
+    {6, 1, 1024, (const void*)k32_cg_persistent_batch<6, 1, 1024>, 0},
+    {8, 1, 1024, (const void*)k32_cg_persistent_batch<8, 1, 1024>, 0},
+};
 std::once_flag g_pocc_once;
 void pocc_init()
 {
@@ -1442,9 +1670,8 @@ void pocc_init()
             }
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, c.bs, smem) != cudaSuccess) c.occ = 0;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pocc_batch, k32_cg_persistent_batch, kPBlock, 0) !=
-            cudaSuccess)
-            g_pocc_batch = 0;
+        for (auto& c : g_bcfg)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, c.fn, c.bs, 0) != cudaSuccess) c.occ = 0;
         cudaGetLastError();
     });
 }
@@ -1476,27 +1703,40 @@ const PCfg& cfg_of(const KParams& P, const DevBuffers& B, Launch L)
 }
 }  // namespace
 
-int cg_persistent_batch_capacity(Launch L)
+int cg_persistent_batch_capacity(Launch L, int cfg)
 {
     pocc_init();
-    return L.num_sms * g_pocc_batch;
+    if (cfg < 0 || cfg >= kBatchConfigs) return 0;
+    return L.num_sms * g_bcfg[cfg].occ;
+}
+
+void cg_batch_config(int k, int* gathers, int* blocks_per_sm, int* block_threads)
+{
+    const BCfg& c = g_bcfg[(k >= 0 && k < kBatchConfigs) ? k : 0];
+    *gathers = c.kb;
+    *blocks_per_sm = c.minb;
+    *block_threads = c.bs;
 }
 
 cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,
-                                         int R, int total_blocks, Launch L)
+                                         int R, int total_blocks, int cfg, Launch L)
 {
-    if (total_blocks < 1 || total_blocks > cg_persistent_batch_capacity(L)) return cudaErrorCooperativeLaunchTooLarge;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)total_blocks);
-    cfg.blockDim = dim3(kPBlock);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = L.stream;
+    if (cfg < 0 || cfg >= kBatchConfigs) return cudaErrorInvalidValue;
+    if (total_blocks < 1 || total_blocks > cg_persistent_batch_capacity(L, cfg))
+        return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)total_blocks);
+    lc.blockDim = dim3((unsigned)g_bcfg[cfg].bs);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k32_cg_persistent_batch, Ps_dev, Bs_dev, blk_off_dev, R);
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    void* args[] = {const_cast<KParams**>(&Ps_dev), const_cast<DevBuffers**>(&Bs_dev), const_cast<int**>(&blk_off_dev),
+                    &R};
+    return cudaLaunchKernelExC(&lc, g_bcfg[cfg].fn, args);
 }
 
 void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads,

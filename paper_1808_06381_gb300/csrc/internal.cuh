@@ -52,12 +52,14 @@ struct KParams {
     float akl_hi, akl_lo;       // alpha kappa L_y
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
+    int res_stage;      // 1: the on-chip solve stages its halo rows in shared memory where they fit
     int fused_init;     // on-chip solve: 0 after the initial-residual kernel; 1 forms r = b itself (x0 = 0), 2 r = b - A x0
 };
 
 constexpr int kPersistentConfigs = 10;
-constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
-constexpr int kResLoStride = 32768;          // >= kResSmemBytes / 6: local entries of one block
+constexpr int kResSmemBytes = 223 * 1024;   // on-chip solve: dynamic shared memory per block (the
+                                             // most a block may have beside its 3.2 KB of static)
+constexpr int kResLoStride = 40960;          // >= kResSmemBytes / 6: local entries of one block
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {
@@ -89,6 +91,7 @@ struct DevState {
     alignas(128) unsigned int bar_exit;
     long long noise_step;     // step whose normals noise3 holds (-1: none)
     int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
+    int res_staged;           // on-chip solve: blocks that staged their halo rows in shared memory (last solve)
     double delta_next;        // the offset the position update advanced to (committed after the stress)
     unsigned long long bar_timeout_ns;   // limit of one grid-barrier wait of the persistent solvers
 };
@@ -774,9 +777,11 @@ void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipeline
 // most 2048 rows per block and its halo lists).
 bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L);
 // A batch of systems in one cooperative launch: blocks [blk_off[k], blk_off[k+1]) solve system k.
-int cg_persistent_batch_capacity(Launch L);
+constexpr int kBatchConfigs = 6;   // tile configurations of the batched solver (sp_batch_autotune)
+int cg_persistent_batch_capacity(Launch L, int cfg);
+void cg_batch_config(int k, int* gathers, int* blocks_per_sm, int* block_threads);
 cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers* Bs_dev, const int* blk_off_dev,
-                                         int R, int total_blocks, Launch L);
+                                         int R, int total_blocks, int cfg, Launch L);
 int cg_kernels_per_check(bool mixed);
 
 // mpnn.cu

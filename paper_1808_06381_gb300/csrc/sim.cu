@@ -163,6 +163,7 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.w_scale = 256.0 / k.two_lambda2;
     k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
     k.res_smem = kResSmemBytes;
+    k.res_stage = 1;
     k.alpha = p.alpha;
     k.mixed = p.precision == SP_PREC_MIXED ? 1 : 0;
     k.alpha_hi = (float)p.alpha;
@@ -690,6 +691,10 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     // fit on fewer SMs): only to exercise the fallback of blocks that do not fit
     if (const char* rsm = std::getenv("SHEARSIM_RESIDENT_SMEM"))
         s->kp.res_smem = std::min(std::max(std::atoi(rsm), 0), kResSmemBytes);
+    // the on-chip solve's halo rows gathered from global memory every iteration
+    // instead of staged in shared memory (the fallback of a block whose staging
+    // does not fit; to exercise and time it)
+    if (const char* hs = std::getenv("SHEARSIM_HALO_STAGE")) s->kp.res_stage = hs[0] == '0' ? 0 : 1;
     DevBuffers& B = s->B;
     const size_t v3 = 3 * (size_t)npad;
     int a = SP_OK;
@@ -857,6 +862,7 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
         info->residual = h.last_res;
         info->bnorm = std::sqrt(h.bnorm2);
         info->offchip_blocks = h.res_offchip;
+        info->staged_blocks = h.res_staged;
         info->host_driven = s->host_loop ? 1 : 0;
     }
     SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));

@@ -112,3 +112,35 @@ def test_batch_with_a_replica_at_the_largest_ensemble_size():
         d -= np.round(d / L) * L
         assert np.abs(d).max() < 1e-9 * steps, (k, np.abs(d).max())
     batch.close()
+
+
+def test_batch_autotune_keeps_the_state_and_the_results():
+    """sp_batch_autotune times every tile configuration of the batched solver, leaves the
+    replicas' state unchanged, and the tuned batch still matches the replicas stepped alone."""
+    reps = _replicas(1e-10)
+    pos = _positions()
+    batch = ss.Batch(reps, positions=pos)
+    batch.step(1)
+    before = [(batch.sim(k).get_positions(), batch.sim(k).state()) for k in range(len(reps))]
+    tune = batch.autotune(trials=2)
+    assert 0 <= tune["config"] < tune["num_configs"] and tune["ms"][tune["config"]] > 0
+    assert sum(1 for t in tune["ms"] if t > 0) >= 2
+    for k in range(len(reps)):
+        after = batch.sim(k).get_positions(), batch.sim(k).state()
+        assert np.array_equal(before[k][0], after[0]) and before[k][1] == after[1]
+    steps = 2
+    infos = batch.step(steps)
+    for k, kw in enumerate(reps):
+        assert infos[k]["status"] == 0 and infos[k]["steps_done"] == steps
+        with ss.Simulation(positions=pos[k], **kw) as sim:
+            sim.step(1 + steps)
+            ref = sim.get_positions()
+        L = kw["L"][0]
+        d = batch.sim(k).get_positions() - ref
+        d -= np.round(d / L) * L
+        assert np.abs(d).max() < 1e-8, (k, np.abs(d).max())
+    for cfg in range(tune["num_configs"]):   # every configuration steps correctly
+        batch.set_config(cfg)
+        infos = batch.step(1)
+        assert all(x["status"] == 0 and x["last_residual"] <= 1e-10 for x in infos), cfg
+    batch.close()

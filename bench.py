@@ -233,60 +233,77 @@ def run_steps(sim, steps, stream, flush):
     return total_ms, launches, iters, max_res
 
 
-def cpu_baseline(workload, precision: str, steps: int = 2):
-    """The CPU oracle as it stands (single thread), on a bounded sample of the workload."""
+def _oracle_steps(job):
+    """One host process: `steps` timed oracle steps (after `warm` untimed ones) of a replica of the
+    workload with its own seed; returns the per-step seconds."""
+    n, L, kappa_tau, tol, seed, steps, warm = job
     import oracle
-    p = oracle.Params.from_workload(workload)
-    pos = synth.uniform_positions(workload.n, workload.L, workload.seed)
-    delta = 0.0
-    t0 = time.perf_counter()
-    for s in range(steps):
-        r = oracle.step(p, pos, delta, s, tol=workload.tol, neighbor_method="cells")
+    import dataclasses
+    w = dataclasses.replace(synth.cubic("sample", n, kappa_tau, steps, tol, seed), L=tuple(L))
+    p = oracle.Params.from_workload(w)
+    pos = synth.uniform_positions(n, w.L, seed)
+    delta, times = 0.0, []
+    for s in range(warm + steps):
+        t0 = time.perf_counter()
+        r = oracle.step(p, pos, delta, s, tol=tol, neighbor_method="cells")
         pos, delta = r.pos, r.delta
-    dt = time.perf_counter() - t0
-    return {"value": workload.n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full steps of N={workload.n} (cell-list pair search, Jacobi-PCG to "
-                      f"{workload.tol:g}), single thread, {dt:.1f} s"}
+        if s >= warm:
+            times.append(time.perf_counter() - t0)
+    return times
 
 
-REFERENCE_SAMPLE_N = 32768   # particles per reference step: one oracle step then takes ~0.5 s
+def oracle_throughput(workload, n: int, steps: int, warm: int = 0):
+    """The CPU oracle as it stands (single-threaded code) on every host core at once: one process
+    per core, each stepping its own replica (own seed) of an n-particle box of the workload's
+    density, shear rate and tolerance.  Returns (particle-steps/s of all processes together,
+    processes, seconds of the slowest process's timed steps)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    procs = max(1, os.cpu_count() or 1)
+    L = (synth.box_length(n),) * 3 if n != workload.n else workload.L
+    jobs = [(n, L, workload.kappa_tau, workload.tol, workload.seed + 7919 * k, steps, warm) for k in range(procs)]
+    with mp.get_context("spawn").Pool(procs) as pool:   # spawned: this process has used the GPU
+        times = pool.map(_oracle_steps, jobs)
+    slowest = max(sum(t) for t in times)
+    return n * steps * procs / slowest, procs, slowest
+
+
+def cpu_baseline(workload, precision: str, steps: int = 2):
+    """The CPU oracle as it stands on all host cores (one process per core, each a replica of
+    the full workload), a bounded sample of 2 steps each."""
+    value, procs, slowest = oracle_throughput(workload, workload.n, steps)
+    return {"value": value, "unit": "particle-steps/s", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} concurrent single-thread oracle processes, each {steps} full steps of its own "
+                      f"N={workload.n} replica (cell-list pair search, Jacobi-PCG to {workload.tol:g}); "
+                      f"slowest {slowest:.1f} s"}
+
+
+REFERENCE_SAMPLE_N = 32768   # particles per process and reference step: one oracle step then takes ~0.5 s
 
 
 def run_reference(args, workload):
-    """The CPU oracle as it stands (single thread) on the same metric: each step is the
-    oracle's full step (cell-list pair search, assembly, Jacobi-PCG to the workload's
-    tolerance, sheared update) on a bounded sample of the workload — the same density,
-    shear rate, tolerance and seed in a box of REFERENCE_SAMPLE_N particles — so that any
-    --steps K --warmup W run ends within minutes."""
+    """The CPU oracle as it stands on the same metric, on every host core: each process steps its
+    own replica of a bounded sample of the workload (the same density, shear rate, tolerance and
+    seed family in a box of REFERENCE_SAMPLE_N particles: the oracle's full step of cell-list
+    search, assembly, Jacobi-PCG to the workload's tolerance and sheared update), so that any
+    --steps K --warmup W run ends within minutes; value = all processes' particle-steps / the
+    slowest process's timed seconds."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    import dataclasses
-    import oracle as orc
     ns = min(workload.n, REFERENCE_SAMPLE_N)
-    sample = dataclasses.replace(workload, n=ns, L=(synth.box_length(ns),) * 3)
-    p = orc.Params.from_workload(sample)
-    pos = synth.uniform_positions(sample.n, sample.L, sample.seed)
-    delta = 0.0
-    times = []
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = orc.step(p, pos, delta, s, tol=sample.tol, neighbor_method="cells")
-        pos, delta = r.pos, r.delta
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    value = ns * len(times) / tot
-    note = (f"{len(times)} oracle steps of a {ns}-particle sample of {workload.name} (same density, shear, "
-            f"tolerance, seed), single thread")
+    value, procs, slowest = oracle_throughput(workload, ns, args.steps, args.warmup)
+    note = (f"{procs} concurrent single-thread oracle processes (one per host core), each {args.steps} timed "
+            f"steps of its own {ns}-particle replica of {workload.name} (same density, shear, tolerance)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * slowest / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload.name, "n": workload.n, "box": workload.L[0],
-                       "kappa_tau": workload.kappa_tau, "cg_tol": workload.tol, "precision": "fp64",
-                       "sample_n": ns, "l2": "cpu"},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                       "kappa_tau": workload.kappa_tau, "cg_tol": workload.tol,
+                       "precision": "fp64", "sample_n": ns, "processes": procs, "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": procs, "kind": "oracle",
                              "sample": note},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -304,7 +321,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (diagnostics)")
     ap.add_argument("--workload", default="mixed",
-                    choices=["mixed", "lowshear", "plain", "learned", "batch", "large", "config5", "vcorr", "fdt"],
+                    choices=["mixed", "lowshear", "plain", "learned", "batch", "large", "config5", "flexible", "vcorr",
+                             "fdt"],
                     help="mixed: N=262,144 precision workload at kappa tau 0.5 (the default line); lowshear: "
                          "the same at kappa tau 0.05; plain: the FP64 workload (N=4,096, 1e-10); learned: "
                          "N=262,144 with the learned warm start; batch: 64 replicas; large: N=4,194,304; "
@@ -320,7 +338,7 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "ours" and args.workload not in ("mixed", "lowshear", "plain"):
         return {"learned": run_learned, "batch": run_batch, "large": run_large, "config5": run_large,
-                "vcorr": run_vcorr, "fdt": run_fdt}[args.workload](args)
+                "flexible": run_flexible, "vcorr": run_vcorr, "fdt": run_fdt}[args.workload](args)
 
     workload = {"mixed": synth.PRECISION, "lowshear": synth.PRECISION_LOW_SHEAR,
                 "plain": synth.PLAIN_FP64}[args.workload]
@@ -355,6 +373,14 @@ def main():
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    # clocks over the whole GPU phase of the run (the timed region alone is short)
+    clocks_run = ClockSampler(gpu_uuid)
+    clocks_run.start()
 
     # the FP64 solver on the same workload, for comparison (same steps, same timing)
     fp64 = None
@@ -378,11 +404,6 @@ def main():
         sim.step(1)
     torch.cuda.synchronize()
 
-    gpu_uuid = None
-    try:
-        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
-    except Exception:
-        pass
     clocks = ClockSampler(gpu_uuid)
     clocks.start()
     if dist is not None:
@@ -451,6 +472,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_value(n, world, args.e2e_steps, max_over_ranks(1e3 * e2e_s, dist, "cuda"))
+    clk_run = clocks_run.stop()
 
     line = None
     if rank == 0:
@@ -498,6 +520,7 @@ def main():
                     "d2h_bytes_per_step": n * 24 + int(ss.load().sp_state_record_bytes()),
                     "steps": args.e2e_steps},
             "clocks": clk,
+            "clocks_run": clk_run,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -642,9 +665,11 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def train_network(ss, steps: int):
+def train_network(ss, steps: int, prior: bool = True):
     """Online training on solves streamed from TRAIN_SEEDS trajectories of the precision workload
-    (N = 262,144); returns (weights, losses, seconds)."""
+    (N = 262,144); returns (weights, losses, seconds).  prior=False: the network's
+    previous-velocity feature is 0 (its readout starts at the Jacobi guess b / A_ii), as the
+    flexible solve's preconditioner applies it."""
     w = synth.LEARNED
     losses, weights = [], None
     per_seed = max(1, steps // TRAIN_SEEDS)
@@ -654,6 +679,12 @@ def train_network(ss, steps: int):
         tr = _sim(ss, w, "mixed", "prev", pos=synth.uniform_positions(w.n, w.L, seed), seed=seed)
         tr.step(3)
         tr.mpnn_enable(seed=1, weights=weights)
+        if not prior:
+            tr.mpnn_set_prior(False)
+            if weights is None:
+                wt = tr.mpnn_weights()
+                wt[len(wt) - 11 + 8], wt[len(wt) - 11 + 9] = 1.0, 0.0
+                tr.mpnn_set_weights(wt)
         for _ in range(per_seed):
             tr.step(1)
             losses.append(tr.mpnn_train_step(lr=2e-3))
@@ -755,6 +786,60 @@ def run_large(args):
                          "structure_factor_in_region": {"calls": n_sq, "ms": t_sq_in},
                          "steps_only_value": n * args.steps / (t / 1e3),
                          "training": training, "clocks": clk})
+    print(json.dumps(line), flush=True)
+
+
+def run_flexible(args):
+    """The learned preconditioner on the N = 262,144 system in FP64: flexible CG (FCG(1)) with the
+    network applied to the residual at every iteration, against FCG with Jacobi and against the
+    FP64 PCG of the time step (one graph launch), all from v0 = 0 to the workload's 1e-8.  The
+    network is trained beforehand (untimed) with its previous-velocity feature 0 on solves
+    streamed from TRAIN_SEEDS trajectories.  Value: particles per second of the flexible solve
+    with the network (solves of the N-particle system per second x N)."""
+    import torch
+    import paper_1808_06381_gb300 as ss
+    ss.load()
+    w = synth.PRECISION
+    weights, losses, t_train = train_network(ss, args.train_steps, prior=False)
+    sim = _sim(ss, w, "fp64", "none")
+    sim.step(args.warmup)
+    sim.build_neighbors()
+    sim.assemble()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        best, info = None, None
+        for _ in range(max(1, args.steps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, info
+
+    t_pcg, i_pcg = timed(lambda: sim.solve_velocities())
+    t_jac, i_jac = timed(lambda: sim.solve_flexible(0))
+    sim.mpnn_enable(weights=weights)
+    sim.mpnn_set_prior(False)
+    t_net, i_net = timed(lambda: sim.solve_flexible(1))
+    sim.close()
+    n = w.n
+    res = {"pcg_graph": (t_pcg, i_pcg), "fcg_jacobi": (t_jac, i_jac), "fcg_network_every_iteration": (t_net, i_net)}
+    line = {"metric": "particle-solves/s of the N=262,144 system to 1e-8 (flexible CG, learned preconditioner)",
+            "value": n / (t_net * 1e-3), "unit": "particle-solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_net, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (network bf16+f32)", "data": "synthetic",
+            "config": {"workload": "flexible-" + w.name, "n": n, "cg_tol": w.tol, "precision": "fp64",
+                       "start": "v0 = 0", "timing": "best of the timed solves, CUDA events"},
+            "comparison": {k: {"ms": v[0], "iterations": v[1]["iterations"], "residual": v[1]["residual"],
+                               "value": n / (v[0] * 1e-3)} for k, v in res.items()},
+            "training": {"solves": len(losses), "trajectories": TRAIN_SEEDS, "seconds": t_train,
+                         "prior": "previous-velocity feature 0"},
+            "gpu_launches": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
 

@@ -98,8 +98,6 @@ typedef struct sp_solve_info {
                                fit on their SM and were solved with global gathers (0 otherwise) */
     int32_t host_driven;    /* 1: the solve's CG loop was driven from the host (graph capture
                                unavailable, or SHEARSIM_HOST_LOOP=1); 0: it ran as one CUDA graph */
-    int32_t staged_blocks;  /* on-chip solver configuration: blocks that copied the rows of other
-                               blocks their entries reach into shared memory every iteration */
 } sp_solve_info;
 
 typedef struct sp_step_info {
@@ -151,6 +149,24 @@ int sp_assemble(sp_sim* sim);
  * start.  info may be NULL.  Returns SP_ERR_NOT_CONVERGED if the iteration
  * cap is hit; the velocities are kept either way. */
 int sp_solve_velocities(sp_sim* sim, const double* v0_dev, sp_solve_info* info);
+
+/* Step 3 by flexible conjugate gradients (FCG(1), Notay 2000) in FP64 with a
+ * preconditioner that may change between iterations: the learned network
+ * (sp_mpnn_enable) applied to the current residual at iterations k with
+ * net_every > 0 and k % net_every == 0 (the network maps a right-hand side to
+ * an approximation of A^-1 of it; its previous-velocity feature is 0 here),
+ * Jacobi D^-1 otherwise; net_every = 0 is Jacobi throughout (PCG in exact
+ * arithmetic).  Each new direction is A-orthogonalised against the previous
+ * one.  Not in the paper (its solver is unnamed); an alternative to the
+ * warm start for the learned part.  Starts from the configured warm start,
+ * stops at ||r|| <= cg_tol ||b|| on the recurrence residual, and reports the
+ * true residual b - A x (SP_ERR_NOT_CONVERGED if it is above cg_tol or
+ * cg_max_iter is reached).  The iteration is driven from the host (state
+ * polled every 8 iterations).  Requires an SP_PREC_FP64 simulation and
+ * sp_assemble; info->host_driven is 1.  Errors: SP_ERR_INVALID_ARG (mixed
+ * precision, no assembled system, net_every > 0 without a network),
+ * SP_ERR_NOT_CONVERGED, SP_ERR_NONFINITE, SP_ERR_OOM, SP_ERR_CUDA. */
+int sp_solve_flexible(sp_sim* sim, int32_t net_every, sp_solve_info* info);
 
 /* nsteps full time steps (steps 1-4), each run as one CUDA graph launch with
  * the CG loop inside the graph.  The noise of step k is keyed by the step
@@ -412,6 +428,12 @@ int sp_mpnn_num_params(void);
  * every step runs it before the solve and CG starts from its guess. */
 int sp_mpnn_enable(sp_sim* sim, uint64_t seed, const float* weights_host);
 int sp_mpnn_disable(sp_sim* sim);
+/* use_vprev = 0: the network's previous-velocity feature is 0 in every
+ * inference and training step from now on (a network trained that way maps a
+ * right-hand side alone to its solution, as the preconditioner of
+ * sp_solve_flexible applies it); 1 (the default after sp_mpnn_enable): the
+ * feature is the previous velocities.  Errors: SP_ERR_INVALID_ARG. */
+int sp_mpnn_set_prior(sp_sim* sim, int32_t use_vprev);
 int sp_mpnn_get_weights(sp_sim* sim, float* weights_host);
 int sp_mpnn_set_weights(sp_sim* sim, const float* weights_host);
 /* Run the network on the assembled system (after sp_assemble); its guess

@@ -52,8 +52,7 @@ class sp_params(ctypes.Structure):
 
 class sp_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("residual", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32), ("host_driven", ctypes.c_int32),
-                ("staged_blocks", ctypes.c_int32)]
+                ("bnorm", ctypes.c_double), ("offchip_blocks", ctypes.c_int32), ("host_driven", ctypes.c_int32)]
 
 
 class sp_step_info(ctypes.Structure):
@@ -110,7 +109,7 @@ def load(path: str = LIB_PATH):
     i32, i64, u64, d = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
     sims = [("sp_sim_create", [P(sp_params), vp, P(vp)]), ("sp_sim_destroy", [vp]),
             ("sp_build_neighbors", [vp]), ("sp_assemble", [vp]),
-            ("sp_solve_velocities", [vp, vp, P(sp_solve_info)]), ("sp_step", [vp, i32, P(sp_step_info)]),
+            ("sp_solve_velocities", [vp, vp, P(sp_solve_info)]), ("sp_solve_flexible", [vp, i32, P(sp_solve_info)]), ("sp_step", [vp, i32, P(sp_step_info)]),
             ("sp_step_host", [vp, vp, ctypes.c_double, i32, vp, P(sp_step_info)]),
             ("sp_structure_factor", [vp, i32, i32, i32, vp, vp, vp]), ("sp_stress_xy", [vp, P(d)]),
             ("sp_velocity_correlation", [vp, i32, d, vp, vp, P(d), P(sp_vcorr_info)]),
@@ -130,6 +129,7 @@ def load(path: str = LIB_PATH):
             ("sp_batch_blocks", [vp, vp]), ("sp_batch_autotune", [vp, i32, P(sp_tune_info)]),
             ("sp_batch_set_config", [vp, i32]),
             ("sp_mpnn_enable", [vp, u64, vp]), ("sp_mpnn_disable", [vp]), ("sp_mpnn_get_weights", [vp, vp]),
+            ("sp_mpnn_set_prior", [vp, i32]),
             ("sp_mpnn_set_weights", [vp, vp]), ("sp_mpnn_forward", [vp, vp]),
             ("sp_mpnn_train_step", [vp, ctypes.c_float, P(d), vp])]
     for name, args in sims:
@@ -328,8 +328,16 @@ class Simulation:
         if raise_on_error:
             self._c(rc)
         return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
-                "offchip_blocks": info.offchip_blocks, "host_driven": info.host_driven,
-                "staged_blocks": info.staged_blocks}
+                "offchip_blocks": info.offchip_blocks, "host_driven": info.host_driven}
+
+    def solve_flexible(self, net_every: int = 0, raise_on_error: bool = True) -> dict:
+        """FCG(1) in FP64, the network as preconditioner every net_every iterations (0: Jacobi)."""
+        info = sp_solve_info()
+        rc = load().sp_solve_flexible(self._h, int(net_every), ctypes.byref(info))
+        if raise_on_error:
+            self._c(rc)
+        return {"status": rc, "iterations": info.iterations, "residual": info.residual, "bnorm": info.bnorm,
+                "host_driven": info.host_driven}
 
     def step(self, nsteps: int = 1, raise_on_error: bool = True) -> dict:
         info = sp_step_info()
@@ -392,6 +400,10 @@ class Simulation:
         else:
             w = np.ascontiguousarray(weights, dtype=np.float32)
             self._c(load().sp_mpnn_enable(self._h, int(seed), _p(w)))
+
+    def mpnn_set_prior(self, use_vprev: bool):
+        """Whether the network's previous-velocity feature is the previous velocities (True) or 0."""
+        self._c(load().sp_mpnn_set_prior(self._h, 1 if use_vprev else 0))
 
     def mpnn_disable(self):
         self._c(load().sp_mpnn_disable(self._h))

@@ -158,7 +158,6 @@ __device__ __forceinline__ void init_scalars(const KParams& P, DevState* st, dou
     st->zero_b = 0;
     st->done = 0;
     st->res_offchip = 0;
-    st->res_staged = 0;
     if (!isfinite(bb) || !isfinite(rr)) {
         st->status = SP_ERR_NONFINITE;
         st->error = SP_ERR_NONFINITE;

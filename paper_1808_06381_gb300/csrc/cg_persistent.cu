@@ -636,54 +636,7 @@ struct RShared {
     int nhalo[kResChunks];   // halo entries per row of the chunk
     int hoff[kResChunks];    // global offset of the chunk's halo list
     int mode;                // 0: on chip; 1: the block's entries did not fit, all gathers global
-    int lo_total, ho_total;  // local and halo list lengths of the block (padding included)
-    int nstage;              // distinct rows of other blocks that the halo entries reach
-    int staged;              // 1: those rows' r are staged in shared memory every iteration
-    int hash_fail;
 };
-
-// cp.async of 16 bytes from global to shared memory (L2 only, bypassing L1)
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                     static_cast<unsigned>(__cvta_generic_to_shared(smem_dst))),
-                 "l"(gmem_src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__device__ __forceinline__ unsigned halo_hash(int j) { return (unsigned)j * 2654435761u; }
-
-// Exclusive prefix sum over the block of one value per thread (all threads
-// call it); returns this thread's offset and the block total in *total.
-template <int BS>
-__device__ __forceinline__ int block_excl_scan(int v, int* tmp, int* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) tmp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < BS / 32 ? tmp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < BS / 32) tmp[lane] = w;   // inclusive warp totals
-    }
-    __syncthreads();
-    const int before = (warp > 0 ? tmp[warp - 1] : 0) + x - v;
-    *total = tmp[BS / 32 - 1];
-    __syncthreads();   // tmp may be reused by the caller
-    return before;
-}
 
 __device__ __forceinline__ void res_halo_batch(const DevBuffers& B, int hb, int kb, int nh, float& s0, float& s1,
                                                float& s2)
@@ -739,7 +692,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows
     const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 6;
     float* sval = reinterpret_cast<float*>(dyn + nwmax * 256);
-    unsigned short* scol = nullptr;   // after the block's local entries are counted (set-up 2)
+    unsigned short* scol = reinterpret_cast<unsigned short*>(sval + cap);
     float* __restrict__ rlo = B.rlo + (size_t)bid * kResLoStride;   // low parts of the local weights
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
@@ -838,16 +791,13 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             ho += 32 * rs.nhalo[c];
         }
         rs.mode = (lo <= cap && ho <= hcap) ? 0 : 1;
-        rs.lo_total = lo;
-        rs.ho_total = ho;
-        rs.staged = 0;
-        rs.nstage = 0;
-        rs.hash_fail = 0;
-        if (!fused && rs.mode) atomicAdd(&st->res_offchip, 1);   // (fused: recorded after set-up 4)
+        if (fused)   // summed by block 0 at the end (the counter is not reset before this launch)
+            B.partials[3 * kMaxPartials + bid] = (double)rs.mode;
+        else if (rs.mode)
+            atomicAdd(&st->res_offchip, 1);
     }
     __syncthreads();
     const bool onchip = rs.mode == 0;
-    scol = reinterpret_cast<unsigned short*>(sval + rs.lo_total);   // 6 lo_total <= 6 cap bytes in mode 0
     if (!onchip) {   // the sliced layout's own assignment, every gather global
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
@@ -962,105 +912,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     }
     __syncthreads();   // sinv (in zbuf) is read until here
 
-    // ---- set-up 4 (on chip): the distinct rows of other blocks that the halo
-    // entries reach, numbered 0 .. nstage-1 by a hash table in zbuf (free
-    // until the iteration starts); each halo entry's column and weight are
-    // copied into shared memory with the row's number, and every SpMV phase
-    // stages those rows' r (and D^-1) into shared memory with asynchronous
-    // copies while the local half of the products runs.  Shared memory after
-    // the local entries: halo weights [ho], their numbers [ho], the staged
-    // rows [nstage] (float4) and their global rows [nstage].
-    const int hbase = B.chunk_off[wb * 8];
-    const int zbytes = nwmax * 256 * (int)sizeof(float4);
-    unsigned char* dynb = reinterpret_cast<unsigned char*>(dyn);
-    const int hoff_b = (zbytes + 6 * rs.lo_total + 15) & ~15;
-    float* shw = reinterpret_cast<float*>(dynb + hoff_b);
-    unsigned short* shidx = reinterpret_cast<unsigned short*>(shw + rs.ho_total);
-    const int stage_b = (hoff_b + 6 * rs.ho_total + 15) & ~15;
-    float4* stage = reinterpret_cast<float4*>(dynb + stage_b);
-    int nstage = 0;
-    int* hrow = nullptr;
-    if (onchip && P.res_stage && rs.ho_total > 0) {
-        int hsize = 4096;
-        while (hsize > 32 && 6 * hsize > zbytes) hsize >>= 1;
-        if (6 * hsize <= zbytes && hsize >= rs.ho_total / 2 + 32) {
-            int* keys = reinterpret_cast<int*>(zbuf);
-            unsigned short* tidx = reinterpret_cast<unsigned short*>(keys + hsize);
-            const unsigned mask = (unsigned)hsize - 1u;
-            for (int h = threadIdx.x; h < hsize; h += BS) keys[h] = -1;
-            __syncthreads();
-            bool fail = false;
-            for (int e = threadIdx.x; e < rs.ho_total; e += BS) {
-                if (B.hval[hbase + e] == 0.f) continue;   // padding of a chunk's list
-                const int j = B.hcol[hbase + e];
-                unsigned h = halo_hash(j) & mask;
-                int probe = 0;
-                for (; probe < hsize; ++probe) {
-                    const int old = atomicCAS(&keys[h], -1, j);
-                    if (old == -1 || old == j) break;
-                    h = (h + 1u) & mask;
-                }
-                if (probe == hsize) fail = true;
-            }
-            if (fail) rs.hash_fail = 1;
-            __syncthreads();
-            // number the occupied slots in slot order (each thread a run of slots)
-            const int per = (hsize + BS - 1) / BS, s0 = threadIdx.x * per, s1 = min(s0 + per, hsize);
-            int cnt = 0;
-            for (int h = s0; h < s1; ++h) cnt += keys[h] >= 0 ? 1 : 0;
-            int total = 0;
-            int idx = block_excl_scan<BS>(cnt, reinterpret_cast<int*>(rs.loff), &total);
-            // rs.loff was read by every thread before this point (set-up 3); it is restored below
-            const int need = stage_b + total * (int)(sizeof(float4) + sizeof(int));
-            const bool ok = !rs.hash_fail && total <= 65535 && need <= smem_bytes;
-            if (ok) {
-                nstage = total;
-                hrow = reinterpret_cast<int*>(stage + nstage);
-                for (int h = s0; h < s1; ++h) {
-                    if (keys[h] >= 0) {
-                        tidx[h] = (unsigned short)idx;
-                        hrow[idx] = keys[h];
-                        ++idx;
-                    }
-                }
-            }
-            __syncthreads();
-            if (ok) {
-                for (int e = threadIdx.x; e < rs.ho_total; e += BS) {
-                    const float w = B.hval[hbase + e];
-                    unsigned short k = 0;
-                    if (w != 0.f) {
-                        const int j = B.hcol[hbase + e];
-                        unsigned h = halo_hash(j) & mask;
-                        for (int probe = 0; probe < hsize && keys[h] != j; ++probe) h = (h + 1u) & mask;
-                        k = tidx[h];
-                    }
-                    shw[e] = w;
-                    shidx[e] = k;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // the chunk offsets of the local lists again (the scan used them as scratch)
-                int lo = 0;
-                for (int c = 0; c < kResChunks; ++c) {
-                    rs.loff[c] = lo;
-                    lo += 32 * rs.nloc[c];
-                }
-                rs.staged = ok ? 1 : 0;
-                rs.nstage = ok ? total : 0;
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x == 0) {   // off chip: 1, staged: 2 (summed by block 0 at the end of a fused launch)
-        if (fused)
-            B.partials[3 * kMaxPartials + bid] = (double)(rs.mode + 2 * rs.staged);
-        else if (rs.staged)
-            atomicAdd(&st->res_staged, 1);
-    }
-    const bool staged = onchip && rs.staged != 0;
-
     // ---- the initial residual (fused form): r = b - A x0 in double-float, or
     // r = b with x = 0, for the block's rows in slot order, with ||b||^2,
     // r.r and r.D^-1 r summed over the grid (as the initial-residual kernel)
@@ -1162,66 +1013,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         // ---- SpMV with the fused direction update; p.q
         dfloat pq{0.f, 0.f};
         const float betaf = sh.beta_f;
-        if (staged) {
-            // the halo rows' r (with D^-1 in .w), published before the last
-            // barrier, are copied into shared memory while the local half runs
-            for (int k = threadIdx.x; k < nstage; k += BS) cp_async16(stage + k, B.r4 + hrow[k]);
-            cp_async_commit();
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                if (row[u] < 0) continue;
-                const float di = __ldg(B.diag32 + row[u]);
-                const int c = u * (BS / 32) + warp;
-                const int lo = rs.loff[c] + lane, nl = rs.nloc[c];
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-                for (int k = 0; k < nl; ++k) {
-                    const float wl = sval[lo + 32 * k];
-                    const float4 zj = zbuf[scol[lo + 32 * k]];
-                    s0 = fmaf(wl, zj.x, s0);
-                    s1 = fmaf(wl, zj.y, s1);
-                    s2 = fmaf(wl, zj.z, s2);
-                }
-                const float z0 = dv[u] * r[u][0], z1 = dv[u] * r[u][1], z2 = dv[u] * r[u][2];
-                float q0 = fmaf(di, z0, -alpha_e * s0);
-                float q1 = fmaf(di, z1, -alpha_e * s1);
-                float q2 = fmaf(di, z2, -alpha_e * s2);
-                if (betaf != 0.f) {
-                    q0 = fmaf(betaf, q[u][0], q0);
-                    q1 = fmaf(betaf, q[u][1], q1);
-                    q2 = fmaf(betaf, q[u][2], q2);
-                    p[u][0] = fmaf(betaf, p[u][0], z0);
-                    p[u][1] = fmaf(betaf, p[u][1], z1);
-                    p[u][2] = fmaf(betaf, p[u][2], z2);
-                } else {
-                    p[u][0] = z0;
-                    p[u][1] = z1;
-                    p[u][2] = z2;
-                }
-                q[u][0] = q0;
-                q[u][1] = q1;
-                q[u][2] = q2;
-            }
-            cp_async_wait_all();
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                if (row[u] < 0) continue;
-                const int c = u * (BS / 32) + warp;
-                const int hb = rs.hoff[c] - hbase + lane, nh = rs.nhalo[c];
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-                for (int k = 0; k < nh; ++k) {
-                    const float4 g = stage[shidx[hb + 32 * k]];
-                    const float ww = shw[hb + 32 * k] * g.w;
-                    s0 = fmaf(ww, g.x, s0);
-                    s1 = fmaf(ww, g.y, s1);
-                    s2 = fmaf(ww, g.z, s2);
-                }
-                q[u][0] = fmaf(-alpha_e, s0, q[u][0]);
-                q[u][1] = fmaf(-alpha_e, s1, q[u][1]);
-                q[u][2] = fmaf(-alpha_e, s2, q[u][2]);
-                pq.hi += p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2];   // FP32, as the block sums
-            }
-        } else {
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             if (row[u] < 0) continue;
@@ -1290,7 +1081,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             q[u][1] = q1;
             q[u][2] = q2;
             pq.hi += p[u][0] * q[u][0] + p[u][1] * q[u][1] + p[u][2] * q[u][2];   // FP32, as the block sums
-        }
         }
         {
             const dfloat v[1] = {pq};
@@ -1547,14 +1337,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     }
     if (bid == 0 && threadIdx.x == 0) {
         if (fused) {   // every block wrote its mode before the first grid reduction
-            int off = 0, stg = 0;
-            for (int b = 0; b < nb; ++b) {
-                const int m = (int)B.partials[3 * kMaxPartials + b];
-                off += m & 1;
-                stg += m >> 1;
-            }
+            int off = 0;
+            for (int b = 0; b < nb; ++b) off += B.partials[3 * kMaxPartials + b] != 0.0 ? 1 : 0;
             st->res_offchip = off;
-            st->res_staged = stg;
         }
         st->iter = sh.iter;
         st->restarts = sh.restarts;
@@ -1621,8 +1406,7 @@ __global__ void __launch_bounds__(BS, MINB) k32_cg_persistent_batch(const KParam
 }
 
 namespace {
-// kResSmemBytes (223 KB): the on-chip solve stages its halo rows in shared memory, so L1 serves
-// only the set-up's reads and the residual replacements
+// kResSmemBytes (190 KB) leaves a 196 KB carve-out's L1 for the halo gathers
 
 struct PCfg {
     int kb, minb, pipe, bs;
@@ -1775,14 +1559,14 @@ cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g);
     cfg.blockDim = dim3((unsigned)c.bs);
-    cfg.dynamicSmemBytes = c.resident ? kResSmemBytes : 0;
+    int smem = std::min(std::max(P.res_smem, 0), kResSmemBytes);
+    cfg.dynamicSmemBytes = c.resident ? smem : 0;
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int smem = std::min(std::max(P.res_smem, 0), kResSmemBytes);
     void* args[] = {const_cast<KParams*>(&P), &B, &smem};
     return cudaLaunchKernelExC(&cfg, c.fn, args);
 }

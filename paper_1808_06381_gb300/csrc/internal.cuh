@@ -52,14 +52,12 @@ struct KParams {
     float akl_hi, akl_lo;       // alpha kappa L_y
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
-    int res_stage;      // 1: the on-chip solve stages its halo rows in shared memory where they fit
     int fused_init;     // on-chip solve: 0 after the initial-residual kernel; 1 forms r = b itself (x0 = 0), 2 r = b - A x0
 };
 
 constexpr int kPersistentConfigs = 10;
-constexpr int kResSmemBytes = 223 * 1024;   // on-chip solve: dynamic shared memory per block (the
-                                             // most a block may have beside its 3.2 KB of static)
-constexpr int kResLoStride = 40960;          // >= kResSmemBytes / 6: local entries of one block
+constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
+constexpr int kResLoStride = 32768;          // >= kResSmemBytes / 6: local entries of one block
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {
@@ -91,7 +89,6 @@ struct DevState {
     alignas(128) unsigned int bar_exit;
     long long noise_step;     // step whose normals noise3 holds (-1: none)
     int res_offchip;          // on-chip solve: blocks whose rows did not fit on their SM (last solve)
-    int res_staged;           // on-chip solve: blocks that staged their halo rows in shared memory (last solve)
     double delta_next;        // the offset the position update advanced to (committed after the stress)
     unsigned long long bar_timeout_ns;   // limit of one grid-barrier wait of the persistent solvers
 };
@@ -206,6 +203,12 @@ struct MpBuffers {
     double* scal;    // [0] = s (RMS of b), [1] = last loss
     double* part;    // [kMaxPartials] partial sums of the scale reduction
     unsigned int* ticket;
+    // inference on another vector (the flexible solve's preconditioner): input
+    // planes [3][npad] in place of b (NULL: b), output planes (NULL: x, the
+    // start vector of CG), and the vprev feature set to 0
+    const double* in;
+    double* out;
+    int zero_vprev;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -784,9 +787,24 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
                                          int R, int total_blocks, int cfg, Launch L);
 int cg_kernels_per_check(bool mixed);
 
+// fcg.cu: flexible CG (FCG(1)) in FP64 whose preconditioner is the network
+// (every net_every iterations, net != NULL) or Jacobi; x holds the start
+// vector; the state's status, iterations and true residual on return.
+struct FcgState {
+    double bb, rr, pq, alpha, beta, last_res;
+    int iter, done, status;
+    unsigned int ticket;
+};
+int fcg_solve(const KParams& P, DevBuffers& B, const MpBuffers* net, int net_every, FcgState* S, FcgState* S_host,
+              Launch L, long long* launches);
+
 // mpnn.cu
 void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L);
 int mp_infer_launches();
+// The network applied to the planes `in` ([3][npad], in place of b, with the
+// vprev feature 0), its output written to `out` (the flexible solve's
+// preconditioner; same 5 kernels as the warm start).
+void launch_mp_apply(const KParams& P, DevBuffers& B, const MpBuffers& M, const double* in, double* out, Launch L);
 void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, int t, Launch L);
 int mp_prepare();
 int mp_weights_bf16_count();

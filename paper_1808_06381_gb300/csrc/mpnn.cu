@@ -557,7 +557,7 @@ __global__ void k_mp_scale(KParams P, DevBuffers B, MpBuffers M)
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
         for (int c = 0; c < 3; ++c) {
-            const double b = b_at(B, np, c, i);
+            const double b = M.in ? M.in[c * np + i] : b_at(B, np, c, i);
             acc += b * b;
         }
     const double v[1] = {acc};
@@ -581,8 +581,9 @@ __global__ void k_mp_input(KParams P, DevBuffers B, MpBuffers M)
     const double di = B.bdf ? (double)B.dinv32[i] : B.dinv[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double b = b_at(B, np, c, i);
-        M.x0[3 * i + c] = make_float4((float)(b * di) * inv, (float)B.x[c * np + i] * inv, (float)b * inv, 0.f);
+        const double b = M.in ? M.in[c * np + i] : b_at(B, np, c, i);
+        const float vp = M.zero_vprev ? 0.f : (float)B.x[c * np + i] * inv;
+        M.x0[3 * i + c] = make_float4((float)(b * di) * inv, vp, (float)b * inv, 0.f);
     }
 }
 
@@ -663,7 +664,7 @@ __global__ void k_mp_aggregate_output(KParams P, DevBuffers B, MpBuffers M)
         const float4 y = M.y[r], x = M.x0[r];
         const float out = y.x * o[0] + y.y * o[1] + y.z * o[2] + y.w * o[3] + a.x * o[4] + a.y * o[5] + a.z * o[6] +
                           a.w * o[7] + x.x * o[8] + x.y * o[9] + x.z * o[10];
-        B.x[c * P.npad + i] = s * (double)out;
+        (M.out ? M.out : B.x)[c * P.npad + i] = s * (double)out;
     }
 }
 
@@ -762,6 +763,15 @@ void launch_mp_infer(const KParams& P, DevBuffers& B, MpBuffers& M, Launch L)
 }
 
 int mp_infer_launches() { return 5; }
+
+void launch_mp_apply(const KParams& P, DevBuffers& B, const MpBuffers& M, const double* in, double* out, Launch L)
+{
+    MpBuffers A = M;
+    A.in = in;
+    A.out = out;
+    A.zero_vprev = 1;
+    launch_mp_infer(P, B, A, L);
+}
 
 void launch_mp_train(const KParams& P, DevBuffers& B, MpBuffers& M, float lr, int t, Launch L)
 {

@@ -163,7 +163,6 @@ void derive(const sp_params& p, KParams& k, int npad)
     k.w_scale = 256.0 / k.two_lambda2;
     k.pcfg = 0;   // tile configuration of the persistent solver (sp_autotune)
     k.res_smem = kResSmemBytes;
-    k.res_stage = 1;
     k.alpha = p.alpha;
     k.mixed = p.precision == SP_PREC_MIXED ? 1 : 0;
     k.alpha_hi = (float)p.alpha;
@@ -624,6 +623,7 @@ int sp_sim_destroy(sp_sim* s)
             if (q) cudaFree(q);
     }
     if (s->st_host) cudaFreeHost(s->st_host);
+    if (s->fcg) cudaFree(s->fcg);
     for (auto& c : s->cap_stream)
         if (c) cudaStreamDestroy(c);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -691,10 +691,6 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     // fit on fewer SMs): only to exercise the fallback of blocks that do not fit
     if (const char* rsm = std::getenv("SHEARSIM_RESIDENT_SMEM"))
         s->kp.res_smem = std::min(std::max(std::atoi(rsm), 0), kResSmemBytes);
-    // the on-chip solve's halo rows gathered from global memory every iteration
-    // instead of staged in shared memory (the fallback of a block whose staging
-    // does not fit; to exercise and time it)
-    if (const char* hs = std::getenv("SHEARSIM_HALO_STAGE")) s->kp.res_stage = hs[0] == '0' ? 0 : 1;
     DevBuffers& B = s->B;
     const size_t v3 = 3 * (size_t)npad;
     int a = SP_OK;
@@ -862,7 +858,6 @@ int sp_solve_velocities(sp_sim* s, const double* v0_dev, sp_solve_info* info)
         info->residual = h.last_res;
         info->bnorm = std::sqrt(h.bnorm2);
         info->offchip_blocks = h.res_offchip;
-        info->staged_blocks = h.res_staged;
         info->host_driven = s->host_loop ? 1 : 0;
     }
     SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
@@ -1214,6 +1209,47 @@ int sp_set_step(sp_sim* s, int64_t step)
     long long v = step;
     SS_TRY(write_field(s, &s->B.st->step, v));
     return SP_OK;
+}
+
+int sp_solve_flexible(sp_sim* s, int32_t net_every, sp_solve_info* info)
+{
+    if (!s || net_every < 0) return SP_ERR_INVALID_ARG;
+    SS_TRY(set_device(s));
+    if (mixed(s)) {
+        s->err = "sp_solve_flexible needs an SP_PREC_FP64 simulation";
+        return SP_ERR_INVALID_ARG;
+    }
+    if (!s->assembled) {
+        s->err = "sp_solve_flexible needs sp_assemble first";
+        return SP_ERR_INVALID_ARG;
+    }
+    if (net_every > 0 && !s->mp_alloc) {
+        s->err = "sp_solve_flexible with net_every > 0 needs the network (sp_mpnn_enable)";
+        return SP_ERR_INVALID_ARG;
+    }
+    if (!s->fcg) SS_TRY(dev_alloc(s, &s->fcg, 1));
+    const size_t np = (size_t)s->kp.npad;
+    // start from zero unless the simulation starts from the previous velocities
+    // (which the build gathered into x); the network's warm-start guess is not used here
+    if (s->p.warm_start != SP_WARM_PREV) SS_CUDA(cudaMemsetAsync(s->B.x, 0, sizeof(double) * 3 * np, s->stream));
+    long long launches = 0;
+    SS_TRY(fcg_solve(s->kp, s->B, net_every > 0 ? &s->mp : nullptr, net_every, s->fcg, &s->fcg_host,
+                     launch_of(s, s->stream), &launches));
+    const FcgState& h = s->fcg_host;
+    int status = h.status;
+    if (status == SP_OK && !(h.last_res <= s->p.cg_tol)) status = SP_ERR_NOT_CONVERGED;
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = status;
+        info->iterations = h.iter;
+        info->residual = h.last_res;
+        info->bnorm = std::sqrt(h.bb);
+        info->host_driven = 1;
+    }
+    SS_CUDA(cudaMemcpyAsync(s->B.v_s, s->B.x, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice, s->stream));
+    SS_CUDA(cudaStreamSynchronize(s->stream));
+    if (status != SP_OK) s->err = status_text(status);
+    return status;
 }
 
 int sp_device_code_version(int32_t device, int32_t* binary_version, int32_t* ptx_version)
@@ -1719,6 +1755,14 @@ int sp_mpnn_enable(sp_sim* s, uint64_t seed, const float* weights_host)
     s->mp_t = 0;
     s->learned = true;
     free_graphs(s);
+    return SP_OK;
+}
+
+int sp_mpnn_set_prior(sp_sim* s, int32_t use_vprev)
+{
+    if (!s || !s->mp_alloc || (use_vprev != 0 && use_vprev != 1)) return SP_ERR_INVALID_ARG;
+    s->mp.zero_vprev = use_vprev ? 0 : 1;
+    free_graphs(s);   // the captured step graph holds the network's buffers by value
     return SP_OK;
 }
 

@@ -41,6 +41,8 @@ struct sp_sim {
     ss::VcBuffers vc{};           // velocity correlation (allocated by its first call)
     ss::FdtBuffers fdt{};         // A^(1/2)-correlated noise in the steps (sp_set_fdt_noise)
     int fdt_degree = 0;           // 0: independent noise per particle (the paper's)
+    ss::FcgState* fcg = nullptr;  // flexible solve's device state (allocated by its first call)
+    ss::FcgState fcg_host{};
     std::string err;
 };
 

@@ -143,9 +143,11 @@ class ClockSampler:
 # and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
 # block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {}
-# the same for the large workload (N = 4,194,304), by solver kernel
-LARGE_PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 96.0e6,
+                    ("mixed-n262144", 6, 1, False, 1024, False): 97.44e6}
+# the same for the large workload (N = 4,194,304), by solver kernel (one capture of the
+# DRAM counters alone, one pass, the launch of the first timed step)
+LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 56.37e9}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
@@ -428,7 +430,22 @@ def main():
     achieved = algo / (spmv_avg_ms * 1e-3) / 1e9
     upd_achieved = upd_algo / (prof["update_probe_ms"] * 1e-3) / 1e9
     persistent = None
-    if prof["persistent_ms"] > 0:
+    if prof["persistent_ms"] > 0 and args.precision == "fp64":
+        plan = plan_algorithmic_bytes(prof["n"], prof["cg_iterations"], "fp64")
+        pach = plan / (prof["persistent_ms"] * 1e-3) / 1e9
+        persistent = {"kernel": "k64_cg_persistent", "bound": "latency", "achieved": pach, "peak": peak,
+                      "unit": "GB/s", "frac": pach / peak, "traffic": None,
+                      "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
+                      "algorithmic_bytes_per_launch": plan,
+                      "algorithmic_bytes_rule": f"{FP64_BYTES_PER_PARTICLE_ITERATION:g} B per particle per CG "
+                                                "iteration x n x iterations",
+                      "avg_launch_ms": prof["persistent_ms"], "cg_iterations": prof["cg_iterations"],
+                      "true_residual_checks": prof["true_checks"], "grid": prof["persistent_blocks"],
+                      "note": "one cooperative launch per solve; the system stays in L2 and GB300 issues FP64 at "
+                              "~2 FMA per clock per SM: bound by the FP64 pipe, the gathers' latency and the grid "
+                              "reductions (two per iteration; one in the pipelined form that systems of fewer "
+                              "than 512 rows per SM take), so frac is an algorithmic-equivalent bandwidth"}
+    elif prof["persistent_ms"] > 0:
         pbytes = persistent_algorithmic_bytes(prof["n"], prof["nnz"], prof["cg_iterations"], prof["true_checks"],
                                               bool(prof.get("persistent_init")))
         pach_detail = pbytes / (prof["persistent_ms"] * 1e-3) / 1e9

@@ -44,6 +44,7 @@ struct PShared {
     int action;   // 0 continue, 1 replace the residual, 2 stop
     // thread 0's CG state, kept here rather than in every thread's registers
     double rho, rr_restart, bnorm2, last_res;
+    double alpha_d, beta_d;   // the pipelined FP64 solve's scalars (its reductions overwrite bcast)
     float rho_f, target_f;   // on-chip iteration: rho and its stopping target in FP32
     int iter, restarts, status;
 };
@@ -1366,6 +1367,621 @@ __global__ void __launch_bounds__(BS, 1) k32_cg_resident(KParams P, DevBuffers B
     barrier_leave(B.st, gridDim.x);
 }
 
+// ------------------------------------------------------ FP64 persistent solve
+// The FP64 solve in one cooperative launch, every scalar decided by thread 0
+// of every block from identical totals; the recurrence residual arms an FP64
+// true-residual check that accepts or restarts.
+// Large systems (TPR = 1): the FP64 solver's iteration as the two-kernel form
+// of cg.cu (Jacobi-PCG with the direction update fused into the SpMV: q = A z
+// + beta q, p = z + beta p; x += alpha p, r -= alpha q, z = D^-1 r), two grid
+// reductions per iteration (the barrier of the second one also publishes z
+// for the next SpMV); a block owns whole windows of 256 rows, one thread per
+// row, warps take the windows' chunks in zig-zag order (as the mixed
+// streaming solve).
+// Small systems (TPR = 4, fewer than two windows per SM): pipelined CG, one
+// grid reduction per iteration (below), where the barriers are a large share
+// of an iteration; a block owns a run of chunks of 32 rows and four
+// neighbouring lanes share a row, each summing every fourth of its entries,
+// so a row's gathers are in flight together; GB300 issues FP64 at ~2 FMA per
+// clock per SM, so a small system is also spread over as many SMs as it has
+// chunk pairs.  Gathered vectors go through plain (coherent) loads: other
+// blocks wrote them before the last barrier.
+constexpr int kBatch64 = 6;
+
+// s_a = sum over the row's entries k = sub, sub + TPR, ... of w_k v_a[col_k]
+template <int TPR>
+__device__ __forceinline__ void p_row_sum64(const int* __restrict__ col, const double* __restrict__ val,
+                                            const double* v, int np, int e0, int e1, int sub, bool active,
+                                            double& s0, double& s1, double& s2)
+{
+    s0 = s1 = s2 = 0.0;
+    if (active) {
+        for (int eb = e0 + 32 * sub; eb < e1; eb += 32 * TPR * kBatch64) {
+            int j[kBatch64];
+            double w[kBatch64];
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                const int e = eb + 32 * TPR * u;
+                j[u] = 0;
+                w[u] = 0.0;
+                if (e < e1) {
+                    j[u] = ld_stream(col + e);
+                    w[u] = __ldg(val + e);
+                }
+            }
+            double g0[kBatch64], g1[kBatch64], g2[kBatch64];
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                g0[u] = g1[u] = g2[u] = 0.0;
+                if (w[u] != 0.0) {
+                    g0[u] = v[j[u]];
+                    g1[u] = v[np + j[u]];
+                    g2[u] = v[2 * np + j[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                s0 += w[u] * g0[u];
+                s1 += w[u] * g1[u];
+                s2 += w[u] * g2[u];
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < TPR; o <<= 1) {   // the row's lanes are neighbours in the warp
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+}
+
+// The block's rows in slot order: calls f(slot, sub, active) the same number
+// of times in every thread of the block (the shuffles of p_row_sum64 need
+// whole warps).
+template <int TPR, class F>
+__device__ __forceinline__ void for_each_slot64(const KParams& P, int bid, int nb, F f)
+{
+    if (TPR == 1) {
+        const int nwin = P.nslots / 256;
+        const int wb = (int)((long long)bid * nwin / nb), we = (int)((long long)(bid + 1) * nwin / nb);
+        const int G = blockDim.x >> 8, t = threadIdx.x & 255;
+        for (int w = wb + (int)(threadIdx.x >> 8), k = 0; w < we; w += G, ++k) f(w * 256 + chunk_lane(k, t), 0, true);
+    } else {
+        const int s0 = 32 * (int)((long long)bid * P.nchunks / nb);
+        const int s1 = 32 * (int)((long long)(bid + 1) * P.nchunks / nb);
+        const int per = blockDim.x / TPR;
+        for (int base = s0; base < s1; base += per) {
+            const int slot = base + (int)threadIdx.x / TPR;
+            f(slot, (int)threadIdx.x % TPR, slot < s1);
+        }
+    }
+}
+
+template <int TPR>
+__device__ __forceinline__ void persistent_solve64(const KParams& P, const DevBuffers& B, int bid, int nb,
+                                                   PShared& sh, int from_x)
+{
+    DevState* st = B.st;
+    if (threadIdx.x == 0) sh.flag = 0;
+    __syncthreads();
+    if (st->error | st->overflow) return;   // uniform: set before the launch
+    unsigned int gen = 0u;   // barriers passed in this launch (the counter starts at 0)
+    const int np = P.npad;
+    double* x = B.x;
+    double* r = B.r;
+    double* z = B.z;
+    double* p = B.p;
+    double* q = B.q;
+    auto row_of = [&](int slot, bool active) { return active ? B.slot_row[slot] : -1; };
+    auto ends = [&](int slot, int& e0, int& e1) {
+        e0 = B.chunk_off[slot >> 5] + (slot & 31);
+        e1 = B.chunk_off[(slot >> 5) + 1];
+    };
+
+    // r = b - A x0 (or b, x = 0); z = D^-1 r; p = q = 0; ||b||^2, r.r, r.z
+    {
+        double bb = 0.0, rr = 0.0, rz = 0.0;
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int row = row_of(slot, active);
+            int e0 = 0, e1 = 0;
+            if (row >= 0) ends(slot, e0, e1);
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            if (from_x) p_row_sum64<TPR>(B.col, B.val, x, np, e0, e1, sub, row >= 0, s0, s1, s2);
+            if (row < 0 || sub != 0) return;
+            const double sv[3] = {s0, s1, s2};
+            const double d = B.diag[row], di = B.dinv[row];
+            double rs = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + row;
+                const double bk = B.b[k2];
+                double rk = bk;
+                if (from_x)
+                    rk = bk - (d * x[k2] - P.alpha * sv[c]);
+                else
+                    x[k2] = 0.0;
+                r[k2] = rk;
+                z[k2] = di * rk;
+                p[k2] = 0.0;
+                q[k2] = 0.0;
+                bb += bk * bk;
+                rs += rk * rk;
+            }
+            rr += rs;
+            rz += di * rs;
+        });
+        const double v[3] = {bb, rr, rz};
+        double tot[3];
+        if (!grid_allreduce<3>(st, gen, sh, v, B.partials, tot, bid, nb)) goto done;
+        if (threadIdx.x == 0) {
+            sh.bnorm2 = tot[0];
+            sh.rho = tot[2];
+            sh.rr_restart = tot[1];
+            sh.iter = 0;
+            sh.restarts = 0;
+            sh.status = SP_OK;
+            sh.last_res = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+            sh.action = 0;
+            sh.bcast[3] = 0.0;   // beta
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                sh.status = SP_ERR_NONFINITE;
+                sh.action = 2;
+            } else if (tot[0] == 0.0 || tot[1] <= P.tol2 * tot[0]) {
+                sh.action = 2;   // b = 0 (x = 0 then) or the start meets the tolerance
+            }
+            if (bid == 0) {
+                st->bnorm2 = tot[0];
+                st->zero_b = tot[0] == 0.0 ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (sh.action == 2) goto done;
+    }
+    for (;;) {
+        // ---- q = A z + beta q; p = z + beta p; p.q
+        const double beta = sh.bcast[3];
+        double pq = 0.0;
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int row = row_of(slot, active);
+            int e0 = 0, e1 = 0;
+            if (row >= 0) ends(slot, e0, e1);
+            double s0, s1, s2;
+            p_row_sum64<TPR>(B.col, B.val, z, np, e0, e1, sub, row >= 0, s0, s1, s2);
+            if (row < 0 || sub != 0) return;
+            const double sv[3] = {s0, s1, s2};
+            const double d = B.diag[row];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + row;
+                const double zk = z[k2];
+                const double az = d * zk - P.alpha * sv[c];
+                const double qk = beta == 0.0 ? az : az + beta * q[k2];
+                const double pk = beta == 0.0 ? zk : zk + beta * p[k2];
+                q[k2] = qk;
+                p[k2] = pk;
+                pq += pk * qk;
+            }
+        });
+        {
+            const double v[1] = {pq};
+            double tot[1];
+            if (!grid_allreduce<1>(st, gen, sh, v, B.partials + kMaxPartials, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                sh.action = 0;
+                if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.bcast[2] = sh.rho / tot[0];   // alpha
+                }
+            }
+            __syncthreads();
+            if (sh.action == 2) break;
+        }
+        // ---- x += alpha p; r -= alpha q; z = D^-1 r (own rows); r.r, r.z
+        const double a = sh.bcast[2];
+        double rr = 0.0, rz = 0.0;
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int i = row_of(slot, active);
+            if (i < 0 || sub != 0) return;
+            const double di = B.dinv[i];
+            double rs = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + i;
+                x[k2] += a * p[k2];
+                const double rk = r[k2] - a * q[k2];
+                r[k2] = rk;
+                z[k2] = di * rk;
+                rs += rk * rk;
+            }
+            rr += rs;
+            rz += di * rs;
+        });
+        {
+            const double v[2] = {rr, rz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials + 2 * kMaxPartials, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                ++sh.iter;
+                sh.action = 0;
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else {
+                    sh.bcast[3] = tot[1] / sh.rho;   // beta
+                    sh.rho = tot[1];
+                    if (tot[0] <= P.tol2 * sh.bnorm2 || sh.iter >= P.max_iter) sh.action = 1;
+                }
+            }
+            __syncthreads();
+            if (sh.action == 2) break;
+            if (sh.action == 0) continue;
+        }
+        // ---- the FP64 true residual r = b - A x (z = D^-1 r): accept, restart or give up
+        {
+            double trr = 0.0, trz = 0.0;
+            for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+                const int row = row_of(slot, active);
+                int e0 = 0, e1 = 0;
+                if (row >= 0) ends(slot, e0, e1);
+                double s0, s1, s2;
+                p_row_sum64<TPR>(B.col, B.val, x, np, e0, e1, sub, row >= 0, s0, s1, s2);
+                if (row < 0 || sub != 0) return;
+                const double sv[3] = {s0, s1, s2};
+                const double d = B.diag[row], di = B.dinv[row];
+                double rs = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k2 = c * np + row;
+                    const double rk = B.b[k2] - (d * x[k2] - P.alpha * sv[c]);
+                    r[k2] = rk;
+                    z[k2] = di * rk;
+                    rs += rk * rk;
+                }
+                trr += rs;
+                trz += di * rs;
+            });
+            const double v[2] = {trr, trz};
+            double tot[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, B.partials, tot, bid, nb)) break;
+            if (threadIdx.x == 0) {
+                sh.last_res = sqrt(tot[0] / sh.bnorm2);
+                if (bid == 0) st->true_checks += 1;
+                sh.action = 0;
+                if (!isfinite(tot[0])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else if (tot[0] <= P.tol2 * sh.bnorm2) {
+                    sh.action = 2;   // converged
+                } else if (sh.iter >= P.max_iter || sh.restarts >= kMaxCgRestarts + 8) {
+                    sh.status = SP_ERR_NOT_CONVERGED;
+                    sh.action = 2;
+                } else {
+                    ++sh.restarts;
+                    sh.rho = tot[1];
+                    sh.bcast[3] = 0.0;
+                }
+            }
+            __syncthreads();
+            if (sh.action == 2) break;
+        }
+    }
+done:
+    if (bid == 0 && threadIdx.x == 0) {
+        st->iter = sh.iter;
+        st->restarts = sh.restarts;
+        st->last_res = sh.last_res;
+        st->done = 1;
+        if (st->error == 0 && sh.status != SP_OK) {
+            st->status = sh.status;
+            st->error = sh.status;
+        } else if (st->error != 0) {
+            st->status = st->error;
+        } else {
+            st->status = SP_OK;
+        }
+    }
+}
+
+// s_a = sum over the row's entries k = sub, sub + TPR, ... of w_k D^-1_col v_a[col_k]
+template <int TPR>
+__device__ __forceinline__ void p_row_sum64_scaled(const int* __restrict__ col, const double* __restrict__ val,
+                                                   const double* __restrict__ dinv, const double* v, int np, int e0,
+                                                   int e1, int sub, bool active, double& s0, double& s1, double& s2)
+{
+    s0 = s1 = s2 = 0.0;
+    if (active) {
+        for (int eb = e0 + 32 * sub; eb < e1; eb += 32 * TPR * kBatch64) {
+            int j[kBatch64];
+            double w[kBatch64];
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                const int e = eb + 32 * TPR * u;
+                j[u] = 0;
+                w[u] = 0.0;
+                if (e < e1) {
+                    j[u] = ld_stream(col + e);
+                    w[u] = __ldg(val + e);
+                }
+            }
+            double g0[kBatch64], g1[kBatch64], g2[kBatch64], dj[kBatch64];
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                g0[u] = g1[u] = g2[u] = dj[u] = 0.0;
+                if (w[u] != 0.0) {
+                    dj[u] = __ldg(dinv + j[u]);
+                    g0[u] = v[j[u]];
+                    g1[u] = v[np + j[u]];
+                    g2[u] = v[2 * np + j[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch64; ++u) {
+                const double ww = w[u] * dj[u];
+                s0 += ww * g0[u];
+                s1 += ww * g1[u];
+                s2 += ww * g2[u];
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < TPR; o <<= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+}
+
+// Small systems: pipelined CG (Ghysels & Vanroose, Parallel Computing 40, 2014)
+// with the Jacobi preconditioner, FP64, one grid reduction per iteration.  With
+// u = D^-1 r and m = D^-1 w formed where they are used, per iteration:
+//   gamma = (r, u), delta = (w, u), ||r||^2           (the barrier's reduction)
+//   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+//   n = A m;  z = n + beta z;  s = w + beta s;  p = u + beta p;
+//   x += alpha p;  r -= alpha s;  w -= alpha z
+// so the reduction of the next iteration's scalars and the publication of w
+// for its SpMV share one barrier (w double-buffered: the SpMV reads the
+// iteration's w while the update writes the next one).  The recurrence
+// residual arms an FP64 true residual b - A x, which ends the solve or
+// restarts the recurrences from it.
+__device__ __forceinline__ void pipelined_solve64(const KParams& P, const DevBuffers& B, int bid, int nb, PShared& sh,
+                                                  int from_x)
+{
+    constexpr int TPR = 4;
+    DevState* st = B.st;
+    if (threadIdx.x == 0) sh.flag = 0;
+    __syncthreads();
+    if (st->error | st->overflow) return;   // uniform: set before the launch
+    unsigned int gen = 0u;
+    const int np = P.npad;
+    double* x = B.x;
+    double* r = B.r;
+    double* z = B.z;
+    double* p = B.p;
+    double* sv = B.s64;
+    double* wbuf[2] = {B.q, B.s64 + 3 * (size_t)np};
+    int cur = 0;        // the w buffer of the current iteration
+    int pset = 0;       // partial-sum set of the next reduction (consecutive ones differ)
+    auto row_of = [&](int slot, bool active) { return active ? B.slot_row[slot] : -1; };
+    auto ends = [&](int slot, int& e0, int& e1) {
+        e0 = B.chunk_off[slot >> 5] + (slot & 31);
+        e1 = B.chunk_off[(slot >> 5) + 1];
+    };
+    auto partials = [&]() {   // two sets of up to three sums each
+        double* q = B.partials + (size_t)pset * 4 * kMaxPartials;
+        pset ^= 1;
+        return q;
+    };
+    // w = A D^-1 r into wbuf[cur]; z = s = p = 0; gamma, delta, ||r||^2 (after a barrier that published r)
+    auto restart_w = [&](double (&tot)[3]) -> bool {
+        double g = 0.0, d = 0.0, rr = 0.0;
+        double* w = wbuf[cur];
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int row = row_of(slot, active);
+            int e0 = 0, e1 = 0;
+            if (row >= 0) ends(slot, e0, e1);
+            double s0, s1, s2;
+            p_row_sum64_scaled<TPR>(B.col, B.val, B.dinv, r, np, e0, e1, sub, row >= 0, s0, s1, s2);
+            if (row < 0 || sub != 0) return;
+            const double sm[3] = {s0, s1, s2};
+            const double dg = B.diag[row], di = B.dinv[row];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + row;
+                const double rk = r[k2], uk = di * rk;
+                const double wk = dg * uk - P.alpha * sm[c];
+                w[k2] = wk;
+                z[k2] = 0.0;
+                sv[k2] = 0.0;
+                p[k2] = 0.0;
+                g += rk * uk;
+                d += wk * uk;
+                rr += rk * rk;
+            }
+        });
+        const double v[3] = {g, d, rr};
+        return grid_allreduce<3>(st, gen, sh, v, partials(), tot, bid, nb);
+    };
+    // the true residual r = b - A x (after a barrier that published x); ||r||^2
+    auto true_residual = [&](double (&tot)[1], bool first) -> bool {
+        double rr = 0.0, bb = 0.0;
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int row = row_of(slot, active);
+            int e0 = 0, e1 = 0;
+            if (row >= 0) ends(slot, e0, e1);
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            if (!first || from_x) p_row_sum64<TPR>(B.col, B.val, x, np, e0, e1, sub, row >= 0, s0, s1, s2);
+            if (row < 0 || sub != 0) return;
+            const double sm[3] = {s0, s1, s2};
+            const double dg = B.diag[row];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + row;
+                const double bk = B.b[k2];
+                double rk = bk;
+                if (!first || from_x)
+                    rk = bk - (dg * x[k2] - P.alpha * sm[c]);
+                else
+                    x[k2] = 0.0;
+                r[k2] = rk;
+                rr += rk * rk;
+                bb += bk * bk;
+            }
+        });
+        if (first) {
+            const double v[2] = {rr, bb};
+            double t2[2];
+            if (!grid_allreduce<2>(st, gen, sh, v, partials(), t2, bid, nb)) return false;
+            if (threadIdx.x == 0) sh.bnorm2 = t2[1];
+            tot[0] = t2[0];
+            return true;
+        }
+        const double v[1] = {rr};
+        return grid_allreduce<1>(st, gen, sh, v, partials(), tot, bid, nb);
+    };
+
+    double t3[3], t1[1];
+    bool first = true;   // beta = 0: the first iteration of the solve or of a restart
+    if (!true_residual(t1, true)) goto done;
+    if (threadIdx.x == 0) {
+        sh.iter = 0;
+        sh.restarts = 0;
+        sh.status = SP_OK;
+        sh.last_res = sh.bnorm2 > 0.0 ? sqrt(t1[0] / sh.bnorm2) : 0.0;
+        sh.action = 0;
+        if (!isfinite(sh.bnorm2) || !isfinite(t1[0])) {
+            sh.status = SP_ERR_NONFINITE;
+            sh.action = 2;
+        } else if (sh.bnorm2 == 0.0 || t1[0] <= P.tol2 * sh.bnorm2) {
+            sh.action = 2;   // b = 0 (x = 0 then) or the start meets the tolerance
+        }
+        if (bid == 0) {
+            st->bnorm2 = sh.bnorm2;
+            st->zero_b = sh.bnorm2 == 0.0 ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (sh.action == 2) goto done;
+    if (!restart_w(t3)) goto done;
+    for (;;) {
+        // ---- the scalars of this iteration (thread 0, identical totals in every block)
+        if (threadIdx.x == 0) {
+            const double g = t3[0], d = t3[1], rr = t3[2];
+            sh.action = 0;
+            if (!isfinite(g) || !isfinite(d) || !isfinite(rr)) {
+                sh.status = SP_ERR_NONFINITE;
+                sh.action = 2;
+            } else if (rr <= P.tol2 * sh.bnorm2 || sh.iter >= P.max_iter) {
+                sh.action = 1;   // the true residual decides
+            } else {
+                const double beta = first ? 0.0 : g / sh.rho;
+                const double den = first ? d : d - beta * g / sh.alpha_d;   // (p, A p) of the new direction
+                if (!(den > 0.0)) {
+                    sh.action = 1;   // lost to rounding near convergence: the true residual decides
+                } else {
+                    sh.beta_d = beta;
+                    sh.alpha_d = g / den;
+                    sh.rho = g;
+                }
+            }
+        }
+        __syncthreads();
+        first = false;
+        if (sh.action == 2) break;
+        if (sh.action == 1) {
+            if (!true_residual(t1, false)) break;
+            if (threadIdx.x == 0) {
+                sh.last_res = sqrt(t1[0] / sh.bnorm2);
+                if (bid == 0) st->true_checks += 1;
+                sh.action = 0;
+                if (!isfinite(t1[0])) {
+                    sh.status = SP_ERR_NONFINITE;
+                    sh.action = 2;
+                } else if (t1[0] <= P.tol2 * sh.bnorm2) {
+                    sh.action = 2;   // converged
+                } else if (sh.iter >= P.max_iter || sh.restarts >= kMaxCgRestarts + 8) {
+                    sh.status = SP_ERR_NOT_CONVERGED;
+                    sh.action = 2;
+                } else {
+                    ++sh.restarts;
+                }
+            }
+            __syncthreads();
+            if (sh.action == 2) break;
+            if (!restart_w(t3)) break;
+            first = true;
+            continue;
+        }
+        // ---- n = A D^-1 w; the recurrences (w into the other buffer); the next reduction
+        const double a = sh.alpha_d, beta = sh.beta_d;
+        const double* w = wbuf[cur];
+        double* wn = wbuf[cur ^ 1];
+        double g = 0.0, d = 0.0, rr = 0.0;
+        for_each_slot64<TPR>(P, bid, nb, [&](int slot, int sub, bool active) {
+            const int row = row_of(slot, active);
+            int e0 = 0, e1 = 0;
+            if (row >= 0) ends(slot, e0, e1);
+            double s0, s1, s2;
+            p_row_sum64_scaled<TPR>(B.col, B.val, B.dinv, w, np, e0, e1, sub, row >= 0, s0, s1, s2);
+            if (row < 0 || sub != 0) return;
+            const double sm[3] = {s0, s1, s2};
+            const double dg = B.diag[row], di = B.dinv[row];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k2 = c * np + row;
+                const double wk = w[k2];
+                const double nk = dg * (di * wk) - P.alpha * sm[c];   // (A m)_k, m = D^-1 w
+                const double zk = nk + beta * z[k2];
+                const double sk = wk + beta * sv[k2];
+                const double pk = di * r[k2] + beta * p[k2];
+                z[k2] = zk;
+                sv[k2] = sk;
+                p[k2] = pk;
+                x[k2] += a * pk;
+                const double rk = r[k2] - a * sk;
+                r[k2] = rk;
+                const double wnk = wk - a * zk;
+                wn[k2] = wnk;
+                const double uk = di * rk;
+                g += rk * uk;
+                d += wnk * uk;
+                rr += rk * rk;
+            }
+        });
+        cur ^= 1;
+        const double v[3] = {g, d, rr};
+        if (!grid_allreduce<3>(st, gen, sh, v, partials(), t3, bid, nb)) break;
+        if (threadIdx.x == 0) ++sh.iter;
+    }
+done:
+    if (bid == 0 && threadIdx.x == 0) {
+        st->iter = sh.iter;
+        st->restarts = sh.restarts;
+        st->last_res = sh.last_res;
+        st->done = 1;
+        if (st->error == 0 && sh.status != SP_OK) {
+            st->status = sh.status;
+            st->error = sh.status;
+        } else if (st->error != 0) {
+            st->status = st->error;
+        } else {
+            st->status = SP_OK;
+        }
+    }
+}
+
+template <int TPR>
+__global__ void __launch_bounds__(512, 1) k64_cg_persistent(KParams P, DevBuffers B, int from_x)
+{
+    __shared__ PShared sh;
+    if (TPR == 1)
+        persistent_solve64<1>(P, B, blockIdx.x, gridDim.x, sh, from_x);
+    else
+        pipelined_solve64(P, B, blockIdx.x, gridDim.x, sh, from_x);
+    barrier_leave(B.st, gridDim.x);
+}
+
 // Tile configurations of the single-system kernel: gathers in flight per
 // thread (KB) against resident blocks per SM (MINB, which caps the registers
 // at 65536 / (256 MINB)), with or without requesting the next batch's
@@ -1549,6 +2165,53 @@ bool cg_persistent_on_chip(const KParams& P, const DevBuffers& B, Launch L)
 int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L)
 {
     return (int)grid_of(cfg_of(P, B, L), P, L);
+}
+
+// FP64 persistent solve.  Systems of at least two windows of 256 rows per SM:
+// blocks of 512 threads (two windows at a time), one per SM, one thread per
+// row.  Smaller ones: blocks of two chunks of 32 rows with four threads per
+// row (256 threads), as many blocks as chunk pairs up to one per SM.
+void cg64_shape(const KParams& P, Launch L, int* grid, int* threads, int* tpr)
+{
+    const int nwin = P.nslots / 256;
+    const int cap = std::min(L.num_sms, kMaxPartials);
+    if (nwin >= 2 * L.num_sms) {
+        *grid = std::min(cap, (nwin + 1) / 2);
+        *threads = 512;
+        *tpr = 1;
+    } else {
+        const int nch = std::max(P.nchunks, 1);
+        const int g = std::max(1, std::min(cap, (nch + 1) / 2));
+        *grid = g;
+        *threads = 4 * 32 * std::min(4, (nch + g - 1) / g);
+        *tpr = 4;
+    }
+}
+
+cudaError_t launch_cg64_persistent(const KParams& P, DevBuffers& B, int from_x, Launch L)
+{
+    int g = 1, bs = 32, tpr = 1;
+    cg64_shape(P, L, &g, &bs, &tpr);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3((unsigned)bs);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {const_cast<KParams*>(&P), &B, &from_x};
+    return cudaLaunchKernelExC(&cfg, tpr == 1 ? (const void*)k64_cg_persistent<1> : (const void*)k64_cg_persistent<4>,
+                               args);
+}
+
+int cg64_persistent_grid(const KParams& P, Launch L)
+{
+    int g = 1, bs = 32, tpr = 1;
+    cg64_shape(P, L, &g, &bs, &tpr);
+    return g;
 }
 
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)

@@ -143,6 +143,8 @@ struct DevBuffers {
     double* p;       // [3][npad]
     double* q;       // [3][npad]
     double* z;       // [3][npad] D^-1 r (FP64 solver)
+    double* s64;     // [6][npad] FP64 pipelined solve of small systems: s, and the second buffer of w
+                     // (w in q and s64 + 3 npad in turn, z in z)
     float4* r4;      // [npad] mixed solver vectors, (x, y, z, 0) per row
     float4* p4;
     float4* q4;
@@ -156,7 +158,7 @@ struct DevBuffers {
     double* exp_tab; // [kExpTab] exp(-k / 256), computed on the host
     float2* exp_tab_df; // [kExpTab] the same as double-floats
     float4* rng_tab;    // [kRngTab] double-float tables of the mixed path's normals (computed on the host)
-    double* partials;// [kMaxPartials * 4]
+    double* partials;// [kMaxPartials * 8]
     float2* partials_df; // [kMaxPartials * 4] double-float partial sums (mixed solver)
     int* scan_tmp;   // block sums of the scans
     double* stage;   // [n][3] staging for host transfers
@@ -765,6 +767,9 @@ int cg_kernels_per_iteration(bool mixed);
 void cg_prepare();   // resident-block counts of the solver kernels (once per process)
 // cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
+// The FP64 solver as one cooperative launch (r = b - A x0 with from_x, else x = 0).
+cudaError_t launch_cg64_persistent(const KParams& P, DevBuffers& B, int from_x, Launch L);
+int cg64_persistent_grid(const KParams& P, Launch L);
 // Whether the persistent solve of this system runs on chip (and so can form
 // its initial residual itself: launch it with fused_init set and without
 // launch_cg_init, after launch_cg_split_x where it starts from x).

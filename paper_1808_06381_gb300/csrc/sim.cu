@@ -2,12 +2,13 @@
 // graphs of a time step and of a solve, and the state-access calls.
 //
 // A time step is one CUDA graph: cell binning and sorting, pair search, the
-// fused pair/assembly kernel, CG (a conditional WHILE node whose body holds an
-// IF node for the true-residual check), the stress, and the position update.
-// The host launches nsteps graphs back to back and reads the device state
-// once at the end.  If conditional graph nodes are unavailable the same
-// kernels are launched from a host loop instead (SHEARSIM_HOST_LOOP=1 forces
-// that mode).
+// fused pair/assembly kernel, the solve (one cooperative persistent launch,
+// FP64 or mixed; with SHEARSIM_PERSISTENT=0 the two-kernel iteration as a
+// conditional WHILE node whose body holds an IF node for the true-residual
+// check), the stress, and the position update.  The host launches nsteps
+// graphs back to back and reads the device state once at the end.  If
+// conditional graph nodes are unavailable the same kernels are launched from
+// a host loop instead (SHEARSIM_HOST_LOOP=1 forces that mode).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -369,6 +370,17 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
         }
         return SP_OK;
     }
+    if (!mixed(s) && s->persistent) {   // the FP64 solve in one cooperative launch
+        SS_CUDA(launch_cg64_persistent(P, B, from_x ? 1 : 0, L));
+        *launches += 1;
+        launch_cg_finish(P, B, false, L);
+        *launches += 1;
+        if (with_stress) {
+            launch_stress(P, B, false, L);
+            *launches += 1;
+        }
+        return SP_OK;
+    }
     *launches += launch_cg_init(P, B, from_x, mixed(s), L);
     if (mixed(s) && s->persistent) {
         SS_CUDA(launch_cg32_persistent(P, B, L));
@@ -611,7 +623,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.cell_count, B.cell_start, B.row_cnt, B.slot_row, B.row_slot, B.chunk_len32,
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
                     B.diag32lo, B.bdf, B.xdf, B.rdf, B.rlo, B.hlo,
-                    B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.r4, B.p4, B.q4, B.d4,
+                    B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.s64, B.r4, B.p4, B.q4, B.d4,
                     B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -725,6 +737,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.p, v3));
     A(dev_alloc(s, &B.q, v3));
     A(dev_alloc(s, &B.z, v3));
+    if (!mixed(s)) A(dev_alloc(s, &B.s64, 2 * v3));
     A(dev_alloc(s, &B.r4, (size_t)npad));
     if (mixed(s)) {   // double-float forms of the mixed solver's true residuals
         A(dev_alloc(s, &B.diag32lo, (size_t)npad));
@@ -736,7 +749,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
     A(dev_alloc(s, &B.p4, (size_t)npad));
     A(dev_alloc(s, &B.q4, (size_t)npad));
     A(dev_alloc(s, &B.d4, (size_t)npad));
-    A(dev_alloc(s, &B.partials, 4 * (size_t)kMaxPartials));
+    A(dev_alloc(s, &B.partials, 8 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.partials_df, 4 * (size_t)kMaxPartials));
     A(dev_alloc(s, &B.exp_tab, (size_t)kExpTab));
     A(dev_alloc(s, &B.exp_tab_df, (size_t)kExpTab));
@@ -923,7 +936,7 @@ int run_steps(sp_sim* s, int32_t nsteps, double* pos_out, sp_step_info* info)
     const DevState& h = *s->st_host;
     if (!s->host_loop) {
         launches += h.steps_in_call * s->fixed_launches_step;
-        if (!(mixed(s) && s->persistent))
+        if (!s->persistent)
             launches += h.iter_sum * cg_kernels_per_iteration(mixed(s)) + h.true_checks * cg_kernels_per_check(mixed(s));
     }
     if (info) {
@@ -1023,18 +1036,25 @@ int sp_profile_step(sp_sim* s, sp_kernel_profile* out)
             rc = mark(MPNN);
         }
     }
-    const bool pers = mx && s->persistent;
+    const bool pers = s->persistent;
     // as a step runs it: the on-chip solve forms its initial residual itself
     // (init_ms then holds only the split of x0 into double-floats)
     const bool fused = pers && cg_persistent_on_chip(P, B, L);
-    if (rc == SP_OK) {
+    if (rc == SP_OK && pers && !mx) {   // the FP64 solve in one cooperative launch (it forms r itself)
+        rc = mark(INIT);
+        if (rc == SP_OK && launch_cg64_persistent(P, B, warm_from_prev(s) ? 1 : 0, L) != cudaSuccess) rc = SP_ERR_CUDA;
+        if (rc == SP_OK) rc = mark(PERSIST);
+        out->persistent_blocks = cg64_persistent_grid(P, L);
+        out->persistent_init = 1;
+    }
+    if (rc == SP_OK && (!pers || mx)) {
         if (!fused)
             launch_cg_init(P, B, warm_from_prev(s), mx, L);
         else if (warm_from_prev(s))
             launch_cg_split_x(P, B, L);
         rc = mark(INIT);
     }
-    if (rc == SP_OK && pers) {
+    if (rc == SP_OK && pers && mx) {
         KParams Pf = P;
         Pf.fused_init = fused ? (warm_from_prev(s) ? 2 : 1) : 0;
         if (launch_cg32_persistent(Pf, B, L) != cudaSuccess) rc = SP_ERR_CUDA;

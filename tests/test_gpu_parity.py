@@ -201,12 +201,13 @@ def test_plain_fp64_workload_follows_the_oracle_for_200_steps():
 
 
 def test_graph_and_host_loop_modes_agree(monkeypatch):
-    """The FP64 step as one CUDA graph (CG loop in a conditional WHILE node, thermal
-    normals on the graph's side branch) and the host-driven loop give identical steps;
-    the graph mode must really have captured (host_driven == 0)."""
+    """The FP64 step with the two-kernel iteration as one CUDA graph (CG loop in a conditional
+    WHILE node, thermal normals on the graph's side branch) and the host-driven loop give
+    identical steps; the graph mode must really have captured (host_driven == 0)."""
     n = 2000
     L = synth.box_length(n)
     outs = []
+    monkeypatch.setenv("SHEARSIM_PERSISTENT", "0")
     for mode in ("0", "1"):
         monkeypatch.setenv("SHEARSIM_HOST_LOOP", mode)
         sim, p, pos = make(n, L, seed=4, tol=1e-10, warm_start="prev")
@@ -220,8 +221,8 @@ def test_graph_and_host_loop_modes_agree(monkeypatch):
 
 
 @pytest.mark.parametrize("precision,persistent,warm", [
-    ("fp64", "1", "prev"), ("fp64", "1", "none"), ("mixed", "0", "prev"), ("mixed", "1", "prev"),
-    ("mixed", "1", "none")])
+    ("fp64", "1", "prev"), ("fp64", "1", "none"), ("fp64", "0", "prev"), ("fp64", "0", "none"),
+    ("mixed", "0", "prev"), ("mixed", "1", "prev"), ("mixed", "1", "none")])
 def test_steps_and_solves_never_fall_back_to_the_host_loop(monkeypatch, capfd, precision, persistent, warm):
     """Every form of the step and of the stand-alone solve captures its CUDA graph."""
     monkeypatch.delenv("SHEARSIM_HOST_LOOP", raising=False)
@@ -238,6 +239,26 @@ def test_steps_and_solves_never_fall_back_to_the_host_loop(monkeypatch, capfd, p
     sim.close()
     err = capfd.readouterr().err
     assert "capture failed" not in err, err
+
+
+@pytest.mark.parametrize("n", [777, 4096, 60000])
+def test_fp64_persistent_and_two_kernel_solvers_agree(monkeypatch, n):
+    """The FP64 solve as one cooperative launch and as the two-kernel graph iteration: same
+    system, both to 1e-12; velocities agree to the solve tolerance and with the oracle."""
+    L = synth.box_length(n)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SHEARSIM_PERSISTENT", flag)
+        sim, p, pos = make(n, L, seed=n + 3, delta=0.37 * L, tol=1e-12)
+        sim.build_neighbors()
+        sim.assemble()
+        info = sim.solve_velocities()
+        assert info["status"] == 0 and info["residual"] <= 1e-12 and info["host_driven"] == 0
+        res[flag] = (sim.get_velocities(), info["iterations"])
+        sim.close()
+    v1, v0 = res["1"][0], res["0"][0]
+    assert np.abs(v1 - v0).max() <= 1e-10 * np.abs(v0).max()
+    assert abs(res["1"][1] - res["0"][1]) <= 2
 
 
 def test_runs_are_deterministic():

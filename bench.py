@@ -147,7 +147,7 @@ PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 96.0e6,
                     ("mixed-n262144", 6, 1, False, 1024, False): 97.44e6}
 # the same for the large workload (N = 4,194,304), by solver kernel (one capture of the
 # DRAM counters alone, one pass, the launch of the first timed step)
-LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 56.37e9}
+LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 56.37e9, "k32_cg_persistent<4,3,0,256,1>": 52.28e9}
 
 
 def profiled_traffic(workload_name: str, tune) -> float | None:
@@ -163,8 +163,9 @@ def solver_kernel_name(tune) -> str:
         bt = tune["block_threads"]
         return f"k32_cg_resident<{bt},{2048 // bt}>"
     if tune:
+        mf = ",1" if tune.get("matrix_free") else ""
         return (f"k32_cg_persistent<{tune['gathers_in_flight']},{tune['blocks_per_sm']},{int(tune['pipelined'])},"
-                f"{tune['block_threads']}>")
+                f"{tune['block_threads']}{mf}>")
     return "k32_cg_persistent"
 
 

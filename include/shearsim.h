@@ -322,6 +322,11 @@ int sp_profile_step(sp_sim* sim, sp_kernel_profile* out);
  * matrix entries between two of them in shared memory, so that only entries
  * to other blocks' rows are gathered from global memory; it serves systems of
  * at most 2048 rows per SM and is not timed (ms 0) for larger ones.
+ * Two configurations (matrix_free = 1) stream only the columns in the
+ * iteration and recompute each pair weight w_ij = exp(-|R_ij|^2 / 2 lambda^2)
+ * (arXiv 1808.06381, §Method) in FP32 from the positions in 32-bit fixed
+ * point (~3e-7 of the assembled weight); their residual replacements use the
+ * assembled weights, so they meet the same tolerance on the same system.
  * sp_autotune builds the pair list
  * and the system for the current positions, times `trials` solves from a
  * zero start with every configuration on the simulation's stream, keeps the
@@ -343,6 +348,8 @@ typedef struct sp_tune_info {
     int32_t pipelined;           /* 1: the next batch of columns is requested during the current gathers */
     int32_t block_threads;       /* threads per block (256 per window processed at once) */
     int32_t resident;            /* 1: rows, their vectors and the entries between them kept on chip */
+    int32_t matrix_free;         /* 1: streaming solve whose SpMV recomputes the pair weights w_ij from
+                                    the positions every iteration (reads only the columns) */
 } sp_tune_info;
 int sp_autotune(sp_sim* sim, int32_t trials, sp_tune_info* info);
 /* Select tile configuration `config` (0 .. num_configs - 1) of the persistent

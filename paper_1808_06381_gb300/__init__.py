@@ -84,7 +84,8 @@ class sp_vcorr_info(ctypes.Structure):
 class sp_tune_info(ctypes.Structure):
     _fields_ = [("config", ctypes.c_int32), ("gathers_in_flight", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("num_configs", ctypes.c_int32), ("ms", ctypes.c_double * 12),
-                ("pipelined", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("resident", ctypes.c_int32)]
+                ("pipelined", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("resident", ctypes.c_int32),
+                ("matrix_free", ctypes.c_int32)]
 
 
 def declared_symbols() -> list:
@@ -381,6 +382,7 @@ class Simulation:
         return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
                 "blocks_per_sm": info.blocks_per_sm, "pipelined": bool(info.pipelined),
                 "block_threads": info.block_threads, "resident": bool(info.resident),
+                "matrix_free": bool(info.matrix_free),
                 "num_configs": info.num_configs}
 
     def autotune(self, trials: int = 3) -> dict:
@@ -390,6 +392,7 @@ class Simulation:
         return {"config": info.config, "gathers_in_flight": info.gathers_in_flight,
                 "blocks_per_sm": info.blocks_per_sm, "pipelined": bool(info.pipelined),
                 "block_threads": info.block_threads, "resident": bool(info.resident),
+                "matrix_free": bool(info.matrix_free),
                 "from_cache": bool(info.from_cache),
                 "ms": [info.ms[k] for k in range(info.num_configs)]}
 

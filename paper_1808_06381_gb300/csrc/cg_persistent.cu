@@ -343,6 +343,103 @@ __device__ __forceinline__ void p_row_sum32(const int* __restrict__ col, const f
     }
 }
 
+// ---- matrix-free SpMV (the streaming solve's inner iteration without the
+// stored weights).  The weight of Eq. algebra's pair term, w_ij =
+// exp(-|R_ij|^2 / 2 lambda^2) (§Method; the pair list, and with it the 5 %
+// truncation, is the assembly's), recomputed in FP32 from the positions in
+// 32-bit fixed point of each box edge (one unit L / 2^32, ~3e-8 of a
+// particle spacing at the benchmark's densities).  Differences of fixed-point
+// coordinates wrap modulo 2^32, which is the periodic minimum image in x and
+// z; in y the wrap also yields the Lees-Edwards image crossing m (-1, 0, 1),
+// whose x shift m delta is a fixed-point constant of the step, so the
+// separation is exact integer arithmetic up to the positions' rounding.  A
+// pair of the list lies within r_c < L / 2 of every edge, so the wrapped
+// image is the pair's image.  The weights agree with the assembled ones to
+// ~3e-7 (relative); the residual replacements use the assembled double-float
+// weights, so the solve still meets its tolerance on the assembled system.
+__device__ __forceinline__ unsigned int fixed_coord(double x, double inv)
+{
+    return (unsigned int)(unsigned long long)__double2ll_rn(x * inv);   // x in [0, L): modulo 2^32
+}
+
+// delta / L_x in fixed point (modulo 2^32)
+__device__ __forceinline__ unsigned int fixed_shift(double delta, const KParams& P)
+{
+    const double f = delta / P.L[0];
+    return (unsigned int)(unsigned long long)__double2ll_rn((f - floor(f)) * 4294967296.0);
+}
+
+__device__ __forceinline__ float pair_weight_fixed(uint4 a, uint4 b, unsigned int dfix, const KParams& P)
+{
+    const int dy = (int)(a.y - b.y);
+    const int m = (int)(((long long)a.y - (long long)b.y - (long long)dy) >> 32);   // y images crossed
+    const int dx = (int)(a.x - b.x - (unsigned int)m * dfix);
+    const int dz = (int)(a.z - b.z);
+    const float fx = (float)dx * P.fix_scale[0], fy = (float)dy * P.fix_scale[1], fz = (float)dz * P.fix_scale[2];
+    return exp2f(P.w_exp2 * fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
+}
+
+// s = sum_j w_ij D^-1_j r_j (FP32) with w_ij recomputed from the fixed-point
+// positions pf; the row's padding entries (column = the row itself) are
+// skipped.  r gathers through plain loads (other blocks wrote it before the
+// last barrier), the positions through the read-only path.
+template <int KB, bool PIPE>
+__device__ __forceinline__ void p_row_sum32_mf(const KParams& P, const int* __restrict__ col, const float4* r,
+                                               const uint4* __restrict__ pf, uint4 pi, int row, unsigned int dfix,
+                                               int e0, int e1, float& s0, float& s1, float& s2)
+{
+    s0 = s1 = s2 = 0.f;
+    int j[KB];
+    auto load_batch = [&](int eb, int (&jj)[KB]) {
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = eb + 32 * u;
+            jj[u] = e < e1 ? ld_stream(col + e) : row;
+        }
+    };
+    if (PIPE) load_batch(e0, j);
+    for (int eb = e0; eb < e1; eb += 32 * KB) {
+        if (!PIPE) load_batch(eb, j);
+        float4 g[KB];
+        uint4 q[KB];
+        bool on[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            on[u] = j[u] != row;
+            g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            q[u] = pi;
+            if (on[u]) {
+                g[u] = r[j[u]];
+                q[u] = __ldg(pf + j[u]);
+            }
+        }
+        if (PIPE) load_batch(eb + 32 * KB, j);
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            if (!on[u]) continue;
+            const float ww = pair_weight_fixed(pi, q[u], dfix, P) * g[u].w;
+            s0 = fmaf(ww, g[u].x, s0);
+            s1 = fmaf(ww, g[u].y, s1);
+            s2 = fmaf(ww, g[u].z, s2);
+        }
+    }
+}
+
+// The fixed-point positions of the rows (from the double-float positions of
+// the step's assembly).
+__global__ void k32_pos_fixed(KParams P, DevBuffers B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int np = P.npad;
+    uint4 q;
+    q.x = fixed_coord((double)B.pos32[i] + (double)B.pos32lo[i], P.fix_inv[0]);
+    q.y = fixed_coord((double)B.pos32[np + i] + (double)B.pos32lo[np + i], P.fix_inv[1]);
+    q.z = fixed_coord((double)B.pos32[2 * np + i] + (double)B.pos32lo[2 * np + i], P.fix_inv[2]);
+    q.w = 0u;
+    B.posfix[i] = q;
+}
+
 }  // namespace
 
 // x += d of one row in double-float (the correction d accumulated in FP32
@@ -394,7 +491,7 @@ __device__ __forceinline__ int chunk_lane(int k, int t)
 // with r = b - A x, p4 = q4 = d4 = 0 and the scalars, from the set-up kernel.
 // A block of 256 G threads is G window groups of 256; group g takes the
 // block's windows wb + g, wb + g + G, ... (one row per thread and window).
-template <int KB, bool PIPE>
+template <int KB, bool PIPE, bool MF = false>
 __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuffers& B, int bid, int nb,
                                                  PShared& sh)
 {
@@ -411,6 +508,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
     const int t = threadIdx.x & 255, wg = wb + (threadIdx.x >> 8);   // lane in window, first window
     const int np = P.npad;
     const float alpha_e = (float)P.alpha;
+    const unsigned int dfix = MF ? fixed_shift(st->delta, P) : 0u;
 
     // CG scalars: thread 0 keeps them in FP64 and makes every decision; the
     // other threads see the FP32 step lengths and the action code.
@@ -457,7 +555,11 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                     po = B.p4[row];
                 }
                 float s0, s1, s2;
-                p_row_sum32<KB, PIPE>(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
+                if constexpr (MF)
+                    p_row_sum32_mf<KB, PIPE>(P, B.col, B.r4, B.posfix, B.posfix[row], row, dfix, e0, e1, s0, s1,
+                                             s2);
+                else
+                    p_row_sum32<KB, PIPE>(B.col, B.val32, B.r4, e0, e1, s0, s1, s2);
                 const float z0 = ri.w * ri.x, z1 = ri.w * ri.y, z2 = ri.w * ri.z;
                 float q0 = fmaf(d, z0, -alpha_e * s0);
                 float q1 = fmaf(d, z1, -alpha_e * s1);
@@ -1987,11 +2089,11 @@ __global__ void __launch_bounds__(512, 1) k64_cg_persistent(KParams P, DevBuffer
 // at 65536 / (256 MINB)), with or without requesting the next batch's
 // columns during the current gathers (PIPE).  Chosen per system by the
 // autotuner.
-template <int KB, int MINB, bool PIPE, int BS>
+template <int KB, int MINB, bool PIPE, int BS, bool MF = false>
 __global__ void __launch_bounds__(BS, MINB) k32_cg_persistent(KParams P, DevBuffers B)
 {
     __shared__ PShared sh;
-    persistent_solve<KB, PIPE>(P, B, blockIdx.x, gridDim.x, sh);
+    persistent_solve<KB, PIPE, MF>(P, B, blockIdx.x, gridDim.x, sh);
     barrier_leave(B.st, gridDim.x);
 }
 
@@ -2029,6 +2131,7 @@ struct PCfg {
     const void* fn;
     int occ;
     int resident;   // 1: the on-chip solve (k32_cg_resident), dynamic shared memory kResSmemBytes
+    int mf;         // 1: the streaming solve with the matrix-free SpMV (weights recomputed)
 };
 PCfg g_pcfg[kPersistentConfigs] = {   // entry 0: the default without autotuning
     {6, 1, 0, 1024, (const void*)k32_cg_persistent<6, 1, false, 1024>, 0, 0},
@@ -2041,6 +2144,8 @@ PCfg g_pcfg[kPersistentConfigs] = {   // entry 0: the default without autotuning
     {6, 3, 1, 256, (const void*)k32_cg_persistent<6, 3, true, 256>, 0, 0},
     {kResHalo, 1, 0, 1024, (const void*)k32_cg_resident<1024, 2>, 0, 1},
     {kResHalo, 1, 0, 512, (const void*)k32_cg_resident<512, 4>, 0, 1},
+    {4, 1, 0, 512, (const void*)k32_cg_persistent<4, 1, false, 512, true>, 0, 0, 1},
+    {4, 3, 0, 256, (const void*)k32_cg_persistent<4, 3, false, 256, true>, 0, 0, 1},
 };
 struct BCfg {
     int kb, minb, bs;
@@ -2140,7 +2245,7 @@ cudaError_t launch_cg32_persistent_batch(const KParams* Ps_dev, const DevBuffers
 }
 
 void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads,
-                          int* resident)
+                          int* resident, int* matrix_free)
 {
     const PCfg& c = g_pcfg[(k >= 0 && k < kPersistentConfigs) ? k : 0];
     *gathers = c.kb;
@@ -2148,6 +2253,12 @@ void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipeline
     *pipelined = c.pipe;
     *block_threads = c.bs;
     *resident = c.resident;
+    *matrix_free = c.mf;
+}
+
+int cg_persistent_prelaunches(const KParams& P, const DevBuffers& B, Launch L)
+{
+    return cfg_of(P, B, L).mf ? 1 : 0;
 }
 
 bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L)
@@ -2219,6 +2330,10 @@ cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L)
     const PCfg& c = cfg_of(P, B, L);
     const int g = (int)grid_of(c, P, L);
     if (g < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (c.mf) {
+        if (!B.posfix || !B.pos32lo) return cudaErrorInvalidValue;
+        k32_pos_fixed<<<(P.n + 255) / 256, 256, 0, L.stream>>>(P, B);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g);
     cfg.blockDim = dim3((unsigned)c.bs);

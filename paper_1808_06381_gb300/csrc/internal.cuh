@@ -53,9 +53,14 @@ struct KParams {
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
     int fused_init;     // on-chip solve: 0 after the initial-residual kernel; 1 forms r = b itself (x0 = 0), 2 r = b - A x0
+    // matrix-free SpMV of the streaming mixed solve: positions in 32-bit fixed
+    // point of each box edge (one unit L / 2^32), w = 2^(w_exp2 |R|^2)
+    double fix_inv[3];  // 2^32 / L
+    float fix_scale[3]; // L / 2^32
+    float w_exp2;       // -log2(e) / (2 lambda^2)
 };
 
-constexpr int kPersistentConfigs = 10;
+constexpr int kPersistentConfigs = 12;
 constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
 constexpr int kResLoStride = 32768;          // >= kResSmemBytes / 6: local entries of one block
 
@@ -145,6 +150,8 @@ struct DevBuffers {
     double* z;       // [3][npad] D^-1 r (FP64 solver)
     double* s64;     // [6][npad] FP64 pipelined solve of small systems: s, and the second buffer of w
                      // (w in q and s64 + 3 npad in turn, z in z)
+    uint4* posfix;   // [npad] mixed: positions in 32-bit fixed point of the box edges (x, y, z, 0), built
+                     // before each matrix-free solve
     float4* r4;      // [npad] mixed solver vectors, (x, y, z, 0) per row
     float4* p4;
     float4* q4;
@@ -766,7 +773,10 @@ void launch_cg_finish(const KParams& P, DevBuffers& B, bool mixed, Launch L);
 int cg_kernels_per_iteration(bool mixed);
 void cg_prepare();   // resident-block counts of the solver kernels (once per process)
 // cg_persistent.cu: the whole mixed solve (after launch_cg_init) in one cooperative launch
+// (preceded, for a matrix-free configuration, by the fixed-point positions'
+// kernel: cg_persistent_prelaunches kernels before the solve)
 cudaError_t launch_cg32_persistent(const KParams& P, DevBuffers& B, Launch L);
+int cg_persistent_prelaunches(const KParams& P, const DevBuffers& B, Launch L);
 // The FP64 solver as one cooperative launch (r = b - A x0 with from_x, else x = 0).
 cudaError_t launch_cg64_persistent(const KParams& P, DevBuffers& B, int from_x, Launch L);
 int cg64_persistent_grid(const KParams& P, Launch L);
@@ -778,9 +788,10 @@ void launch_cg_split_x(const KParams& P, DevBuffers& B, Launch L);
 int cg_persistent_grid(const KParams& P, const DevBuffers& B, Launch L);
 // Tile configuration k of the persistent solver: gathers in flight, blocks per
 // SM, next batch requested during the current gathers (1) or not (0), threads
-// per block (256 G: G windows at a time), on-chip solve (1) or not (0).
+// per block (256 G: G windows at a time), on-chip solve (1) or not (0),
+// weights recomputed from positions in the iteration (1) or read (0).
 void cg_persistent_config(int k, int* gathers, int* blocks_per_sm, int* pipelined, int* block_threads,
-                          int* resident);
+                          int* resident, int* matrix_free);
 // Whether configuration k can solve this system (the on-chip solve needs at
 // most 2048 rows per block and its halo lists).
 bool cg_persistent_usable(int k, const KParams& P, const DevBuffers& B, Launch L);

@@ -238,6 +238,11 @@ void derive(const sp_params& p, KParams& k, int npad)
     // the FP64 residual is recomputed (well above FP32 attainable accuracy)
     k.inner2 = 1e-8;
     k.max_iter = p.cg_max_iter;
+    for (int a = 0; a < 3; ++a) {
+        k.fix_inv[a] = 4294967296.0 / p.L[a];
+        k.fix_scale[a] = (float)(p.L[a] / 4294967296.0);
+    }
+    k.w_exp2 = (float)(-1.4426950408889634 / k.two_lambda2);
 }
 
 // --------------------------------------------------------------- enqueueing
@@ -384,7 +389,7 @@ int enqueue_solve(sp_sim* s, cudaStream_t cs, bool from_x, bool in_graph, long l
     *launches += launch_cg_init(P, B, from_x, mixed(s), L);
     if (mixed(s) && s->persistent) {
         SS_CUDA(launch_cg32_persistent(P, B, L));
-        *launches += 1;
+        *launches += 1 + cg_persistent_prelaunches(P, B, L);
     } else if (in_graph) {
         SS_TRY(capture_cg_loop(s, cs));
     } else {
@@ -624,7 +629,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
                     B.diag32lo, B.bdf, B.xdf, B.rdf, B.rlo, B.hlo,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.s64, B.r4, B.p4, B.q4, B.d4,
-                    B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.posfix, B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -745,6 +750,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         A(dev_alloc(s, &B.xdf, 2 * (size_t)npad));
         A(dev_alloc(s, &B.rdf, 2 * (size_t)npad));
         A(dev_alloc(s, &B.rlo, (size_t)s->num_sms * kResLoStride));
+        A(dev_alloc(s, &B.posfix, (size_t)npad));
     }
     A(dev_alloc(s, &B.p4, (size_t)npad));
     A(dev_alloc(s, &B.q4, (size_t)npad));

@@ -67,7 +67,7 @@ extern "C" int sp_set_solver_config(sp_sim* s, int32_t config, sp_tune_info* inf
         out.config = config;
         out.num_configs = std::min(kPersistentConfigs, SP_TUNE_MAX_CONFIGS);
         cg_persistent_config(config, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads,
-                             &out.resident);
+                             &out.resident, &out.matrix_free);
         *info = out;
     }
     return SP_OK;
@@ -84,7 +84,7 @@ extern "C" int sp_autotune(sp_sim* s, int32_t trials, sp_tune_info* info)
         free_graphs(s);   // captured graphs hold the previous configuration's kernel
         out.config = cfg;
         cg_persistent_config(cfg, &out.gathers_in_flight, &out.blocks_per_sm, &out.pipelined, &out.block_threads,
-                             &out.resident);
+                             &out.resident, &out.matrix_free);
         if (info) *info = out;
         return SP_OK;
     };

@@ -8,8 +8,8 @@ are checked against the system the FP64 CPU oracle assembles for the same
 positions, offset and step (its own cell-list pair search and its own
 normals): the oracle's residual ||b - A v|| / ||b|| must be <= 1e-8 and agree
 with the residual the GPU reports.  Both shear rates of that workload
-(kappa tau = 0.5 and 0.05), the on-chip solver (the benchmark's choice) and
-the streaming one.
+(kappa tau = 0.5 and 0.05), the on-chip solver (the benchmark's choice), the
+streaming one, and the streaming one with the matrix-free SpMV.
 """
 import numpy as np
 import pytest
@@ -22,6 +22,7 @@ ss = pytest.importorskip("paper_1808_06381_gb300")
 pytestmark = pytest.mark.gpu
 
 RESIDENT_CONFIG = 9   # k32_cg_resident<512, 4>, the autotuner's choice at this size
+MATRIX_FREE_CONFIG = 11   # the streaming solve with the matrix-free SpMV
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,7 +31,8 @@ def _lib():
 
 
 @pytest.mark.parametrize("workload,config", [(synth.PRECISION, RESIDENT_CONFIG), (synth.PRECISION, 0),
-                                             (synth.PRECISION_LOW_SHEAR, RESIDENT_CONFIG)])
+                                             (synth.PRECISION_LOW_SHEAR, RESIDENT_CONFIG),
+                                             (synth.PRECISION, MATRIX_FREE_CONFIG)])
 def test_benchmark_steps_meet_the_tolerance_on_the_oracle_system(workload, config):
     w = workload
     pos = synth.uniform_positions(w.n, w.L, w.seed)
@@ -40,6 +42,7 @@ def test_benchmark_steps_meet_the_tolerance_on_the_oracle_system(workload, confi
                         positions=pos)
     tune = sim.set_solver_config(config)
     assert tune["resident"] == (config == RESIDENT_CONFIG)
+    assert tune["matrix_free"] == (config == MATRIX_FREE_CONFIG)
     p = oracle.Params.from_workload(w)
     sim.step(2)   # the warm start then comes from real previous velocities
     for _ in range(3):

@@ -143,7 +143,7 @@ class ClockSampler:
 # and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
 # block, on-chip); any other
 # kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 96.0e6,
+PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 100.5e6,
                     ("mixed-n262144", 6, 1, False, 1024, False): 97.44e6}
 # the same for the large workload (N = 4,194,304), by solver kernel (one capture of the
 # DRAM counters alone, one pass, the launch of the first timed step)

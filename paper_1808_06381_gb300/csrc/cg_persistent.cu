@@ -729,7 +729,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 constexpr int kResWindows = 8;                       // 2048 rows per block
 constexpr int kResChunks = kResWindows * 8;
 constexpr int kResHalo = 4;                          // halo gathers in flight per thread
-constexpr int kResSetupBatch = 8;                    // entries requested at a time in the set-up
+constexpr int kResSetupBatch = 6;                    // entries requested at a time in the set-up
 constexpr int kResCheckBatch = 4;                    // gathers in flight in the off-chip blocks' true residual
 constexpr int kResCheckLocal = 8;                    // low parts requested at a time in the on-chip check
 
@@ -822,6 +822,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         if (row < 0) continue;
         const int c = slot >> 5, e1 = B.chunk_off[c + 1];
         int nl = 0, nh = 0;
+        unsigned long long hist = 0ull;   // local entries per bank group (column mod 8), 8 bits each
         // the columns alone: a padding entry of the sliced layout points at its
         // own row (and has weight 0), a real partner never does
         for (int eb = B.chunk_off[c] + (slot & 31); eb < e1; eb += 32 * 2 * KS) {
@@ -834,12 +835,18 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
             for (int u = 0; u < 2 * KS; ++u) {
                 if (j[u] != row) {
-                    if (j[u] >= rb && j[u] < re) ++nl; else ++nh;
+                    if (j[u] >= rb && j[u] < re) {
+                        ++nl;
+                        hist += 1ull << (8 * ((j[u] - rb) & 7));
+                    } else {
+                        ++nh;
+                    }
                 }
             }
         }
         const int i = row - rb;
         scnt[i] = (unsigned)nl | ((unsigned)nh << 16);
+        B.res_hist[slot] = hist;   // read back by this thread when it places the row's entries
         skey[i] = ((unsigned)(31 - min(nh, 31)) << 17) | ((unsigned)(63 - min(nl, 63)) << 11) | (unsigned)i;
     }
     __syncthreads();
@@ -954,6 +961,43 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const int lo = rs.loff[c] + (owner & 31), nl = rs.nloc[c], nh = rs.nhalo[c];
             const int hb = rs.hoff[c] + (owner & 31);
             const int e1 = B.chunk_off[(slot >> 5) + 1];
+            // The order of the row's local entries.  Its owner reads entry k
+            // in step k of the local sums together with the other 7 lanes of
+            // its quarter warp (one 16-byte gather of z each; lanes that hit
+            // the same 16-byte bank group, column mod 8, at different columns
+            // are served one after another).  Entry positions k whose group is
+            // (k + l) mod 8, l the owner's lane in its quarter, keep the
+            // quarter's gathers of a step on 8 different groups: each group's
+            // entries take its positions k = (g - l) mod 8 + 8 m first, the
+            // rest fill the positions left over, lowest first, in column
+            // order.  Position k < nlr belongs to group (k + l) mod 8 as its
+            // (k / 8)-th; it is left over when that group has at most k / 8
+            // entries (E, counted in set-up 1, 8 bits per group).  M counts
+            // the entries placed per group (4 bits, saturating: a group never
+            // has more than 8 positions).
+            const int nlr = (int)(scnt[row - rb] & 0xffffu), ql = owner & 7;
+            unsigned long long free_pos = 0ull;
+            {   // group h's positions from its E_h-th on: every 8th bit from (h - l) mod 8 + 8 E_h
+                const unsigned long long E = B.res_hist[slot];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const int k0 = ((h - ql) & 7) + 8 * (int)((E >> (8 * h)) & 0xffull);
+                    if (k0 < 64) free_pos |= 0x0101010101010101ull << k0;
+                }
+                free_pos &= nlr >= 64 ? ~0ull : (1ull << nlr) - 1ull;
+            }
+            unsigned int M = 0u;
+            auto local_pos = [&](int gg) {   // position of the next local entry of group gg
+                const int m = (int)((M >> (4 * gg)) & 15u);
+                if (m < 15) M += 1u << (4 * gg);
+                const int d = (gg - ql) & 7;
+                if (d + 8 * m < nlr) return d + 8 * m;
+                // as many positions are left over as entries go beyond their
+                // group's, so a bit is set (0 keeps even a miscount in bounds)
+                const int k = max(__ffsll((long long)free_pos) - 1, 0);
+                free_pos &= free_pos - 1ull;
+                return k;
+            };
             int kl = 0, kh = 0;
             dfloat sd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int eb = B.chunk_off[slot >> 5] + (slot & 31); eb < e1; eb += 32 * KS) {
@@ -987,10 +1031,11 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
                 for (int u = 0; u < KS; ++u) {
                     if (v[u] == 0.f) continue;
-                    if (j[u] >= rb && j[u] < re) {
-                        scol[lo + 32 * kl] = (unsigned short)(j[u] - rb);
-                        sval[lo + 32 * kl] = v[u];
-                        rlo[lo + 32 * kl] = vl[u];
+                    if (j[u] != row && j[u] >= rb && j[u] < re) {   // as counted in set-up 1
+                        const int k = local_pos((j[u] - rb) & 7);
+                        scol[lo + 32 * k] = (unsigned short)(j[u] - rb);
+                        sval[lo + 32 * k] = v[u];
+                        rlo[lo + 32 * k] = vl[u];
                         ++kl;
                     } else {
                         B.hcol[hb + 32 * kh] = j[u];
@@ -2192,7 +2237,7 @@ long long grid_of(const PCfg& c, const KParams& P, Launch L)
 // The on-chip solve needs its halo lists and at most kResWindows windows per block.
 bool resident_fits(const PCfg& c, const KParams& P, const DevBuffers& B, Launch L)
 {
-    if (!B.hcol || !B.hval || !B.hlo || !B.rlo || !B.rdf) return false;
+    if (!B.hcol || !B.hval || !B.hlo || !B.rlo || !B.rdf || !B.res_hist) return false;
     const long long g = grid_of(c, P, L);   // at most one block per SM: rlo holds num_sms blocks
     return g >= 1 && g <= L.num_sms && (P.nslots / 256 + g - 1) / g <= kResWindows;
 }

@@ -13,6 +13,22 @@ namespace ss {
 // new state is written in the current cell order together with the ids and
 // the velocities (the next step's warm start).  The last block advances the
 // device's offset and step counter.
+// wrap_box for a coordinate at most one box edge outside [0, L) (a step moves
+// a particle by v dt, the sheared re-entry by at most L_x more) without its
+// FP64 division (GB300 issues FP64 at 1/64 of the FP32 rate): the same value
+// (x - L and x + L are what x - L floor(x / L) rounds to there); further out,
+// wrap_box itself.
+__device__ __forceinline__ double wrap_near(double x, double L)
+{
+    if (x >= 0.0 && x < L) return x;
+    if (x >= L && x < 2.0 * L) return __dsub_rn(x, L);
+    if (x < 0.0 && x >= -L) {
+        const double y = __dadd_rn(x, L);
+        return y < L ? y : 0.0;   // x + L rounds to L for tiny negative x: wrap_box gives 0 there
+    }
+    return wrap_box(x, L);
+}
+
 __global__ void __launch_bounds__(kVecBlock) k_integrate(KParams P, DevBuffers B)
 {
     DevState* st = B.st;
@@ -32,9 +48,9 @@ __global__ void __launch_bounds__(kVecBlock) k_integrate(KParams P, DevBuffers B
             y = y - P.L[1];
             x = x - dnew;
         }
-        B.pos_s[i] = wrap_box(x, P.L[0]);
+        B.pos_s[i] = wrap_near(x, P.L[0]);
         B.pos_s[np + i] = y;
-        B.pos_s[2 * np + i] = wrap_box(z, P.L[2]);
+        B.pos_s[2 * np + i] = wrap_near(z, P.L[2]);
         B.id_s[i] = B.id_w[i];
         B.v_s[i] = vx;
         B.v_s[np + i] = vy;

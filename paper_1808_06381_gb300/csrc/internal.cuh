@@ -138,6 +138,8 @@ struct DevBuffers {
     float* hlo;      // [nnz_cap] the low parts of those weights (double-float)
     float* rlo;      // [SMs][kResLoStride] on-chip solve: the local entries' weight low parts, per block
                      // in its shared-memory layout
+    unsigned long long* res_hist; // [nslots] on-chip solve set-up: each row's local entries per bank
+                                  // group of z (column mod 8), 8 bits each
     double* diag;    // [n] A_ii
     double* dinv;    // [n] 1 / A_ii
     float* diag32;   // [n]

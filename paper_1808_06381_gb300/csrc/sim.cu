@@ -629,7 +629,7 @@ int sp_sim_destroy(sp_sim* s)
                     B.chunk_off, B.col, B.img, B.val, B.val32, B.val32lo, B.hcol, B.hval, B.diag, B.partials_df,
                     B.diag32lo, B.bdf, B.xdf, B.rdf, B.rlo, B.hlo,
                     B.dinv, B.diag32, B.dinv32, B.b, B.x, B.r, B.p, B.q, B.z, B.s64, B.r4, B.p4, B.q4, B.d4,
-                    B.posfix, B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
+                    B.posfix, B.res_hist, B.xi_inj, B.exp_tab, B.exp_tab_df, B.rng_tab, B.pos32lo, B.cand_j, B.cand_img, B.noise3, B.partials, B.scan_tmp, B.stage, B.st};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (s->mp_alloc) {
@@ -751,6 +751,7 @@ int sp_sim_create(const sp_params* p, const double* pos_host, sp_sim** out)
         A(dev_alloc(s, &B.rdf, 2 * (size_t)npad));
         A(dev_alloc(s, &B.rlo, (size_t)s->num_sms * kResLoStride));
         A(dev_alloc(s, &B.posfix, (size_t)npad));
+        A(dev_alloc(s, &B.res_hist, (size_t)s->kp.nslots));
     }
     A(dev_alloc(s, &B.p4, (size_t)npad));
     A(dev_alloc(s, &B.q4, (size_t)npad));

@@ -1045,8 +1045,8 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     }
                 }
             }
-            for (; kl < nl; ++kl) {
-                scol[lo + 32 * kl] = 0;
+            for (; kl < nl; ++kl) {   // padding: weight 0 at a record of the position's own bank group
+                scol[lo + 32 * kl] = (unsigned short)(R >= 8 ? (kl + ql) & 7 : 0);
                 sval[lo + 32 * kl] = 0.f;
                 rlo[lo + 32 * kl] = 0.f;
             }
@@ -1116,6 +1116,17 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         __syncthreads();
         if (start_done || sh.action == 2) start_done = true;
     }
+
+    // Rows whose r (and d) other blocks gather: on chip, those with an entry
+    // to another block's row (pairs are symmetric, so exactly the rows of the
+    // other blocks' halo lists; a warp's rows of one index u share their
+    // chunk's halo count, sorted first); every row of a block whose entries
+    // are off chip (its own gathers read them too).  Fewer stores before each
+    // barrier's release.
+    unsigned int pub = 0u;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+        if (!onchip || rs.nhalo[u * (BS / 32) + warp] != 0) pub |= 1u << u;
 
     // ---- load r and D^-1 of the own rows
     float r[RPT][3], dv[RPT], p[RPT][3], q[RPT][3], d[RPT][3];
@@ -1261,7 +1272,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
             rr.hi += rsq;   // FP32, as the block sums
             rz.hi += dv[u] * rsq;
-            B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
+            if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
             zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
         }
         {
@@ -1312,7 +1323,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                              c = df_add(dfloat{xh[u].z, xl[u].z}, df.z);
                 B.xdf[2 * row[u]] = make_float4(a.hi, b.hi, c.hi, 0.f);
                 B.xdf[2 * row[u] + 1] = make_float4(a.lo, b.lo, c.lo, 0.f);
-                B.d4[row[u]] = df;
+                if (pub & (1u << u)) B.d4[row[u]] = df;
                 zbuf[row[u] - rb] = df;
                 // r, p and q are set anew after the check (beta = 0), so none of
                 // them holds a register through it
@@ -1409,7 +1420,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
             for (int u = 0; u < RPT; ++u) {
                 if (row[u] < 0) continue;
-                B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
+                if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
                 zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
             }
         } else {

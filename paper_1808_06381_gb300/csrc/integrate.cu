@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(kVecBlock) k_stress(KParams P, DevBuffers B)
 // separations from the FP32 positions and the pair's image (for box edges L
 // each component is within about 5 L 2^-24 of the exact one, below 1e-5
 // relative for the boxes used here), weights from the FP32 matrix, FP32
-// velocities, and a double-float accumulation.
+// velocities, and a double-float accumulation.  Each pair once (the entry of
+// its lower row; y_ij f_ij,x is symmetric in i and j), so half the gathers.
 constexpr int kStressBatch = 4;   // entries requested at a time
 
 __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
             }
 #pragma unroll
             for (int u = 0; u < kStressBatch; ++u) {
+                if (j[u] <= i) continue;   // the pair's other entry (padding points at the row itself)
                 const int a = (code[u] & 7) - 2, m = ((code[u] >> 3) & 3) - 1;
                 const float ax = a == 0 ? 0.f : (a == 1 ? P.Lf[0] : (a == -1 ? -P.Lf[0] : (a == 2 ? 2.f * P.Lf[0] : -2.f * P.Lf[0])));
                 const float dx = (xi - B.pos32[j[u]]) - (sel(m, deltaf) + ax);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
     dfloat v[1] = {acc};
     double out[1];
     if (publish_reduce_df<1>(v, B.partials_df, &st->ticket[0], out) && threadIdx.x == 0)
-        st->stress_xy = -0.5 * out[0] / (P.L[0] * P.L[1] * P.L[2]);
+        st->stress_xy = -out[0] / (P.L[0] * P.L[1] * P.L[2]);
 }
 
 void launch_stress(const KParams& P, DevBuffers& B, bool mixed, Launch L)

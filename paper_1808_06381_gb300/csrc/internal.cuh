@@ -112,7 +112,7 @@ struct DevBuffers {
     float* pos32lo;  // [3][npad] pos_w - pos32: positions as double-floats (pos32, pos32lo)
     int* id_w;       // [n]
     int* cell_of;    // [n] cell of each row: in the state order while binning, then (written by the
-                     // gather) in the cell order of the current rows, where the pair search reads it
+                     // per-cell sort) in the cell order of the current rows, where the pair search reads it
     int* slot;       // [n]
     int* perm;       // [n] new row -> state row
     int* cell_count; // [ncell]
@@ -731,11 +731,12 @@ struct Launch {
 // neighbors.cu
 void launch_bin(const KParams& P, DevBuffers& B, Launch L);
 // mode 0: plain scan; mode 2: the total is the matrix size with padding
-// (st->nnz_slots), and exceeding cap_check raises the overflow flag.
-void launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st,
-                 int mode, Launch L);
+// (st->nnz_slots), and exceeding cap_check raises the overflow flag.  Both
+// return the kernels they launched.
+int launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st, int mode,
+                Launch L);
 void launch_sell_plan(const KParams& P, DevBuffers& B, Launch L);
-void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
+int launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L);
 // The step's pair search; with draw_noise it also draws the thermal normals
 // of every row (FP64 Box-Muller, overlapping the search's memory latency).

@@ -149,13 +149,56 @@ __global__ void k_scan_down(const int* __restrict__ in, int* __restrict__ out, i
     }
 }
 
-void launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st,
-                 int mode, Launch L)
+// An input of one chunk in one block: the chunk's exclusive scan and the total.
+__global__ void k_scan_single(const int* __restrict__ in, int* __restrict__ out, int n, long long cap_check,
+                              DevState* st, int mode)
+{
+    if (st->error | st->overflow) return;
+    __shared__ int s[kScanChunk];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int idx = k * kScanThreads + threadIdx.x;
+        s[idx] = idx < n ? in[idx] : 0;
+    }
+    __syncthreads();
+    int loc[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = sum;
+        sum += s[threadIdx.x * kScanItems + k];
+    }
+    int tot;
+    const int off = block_exclusive_scan_int(sum, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s[threadIdx.x * kScanItems + k] = loc[k] + off;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int idx = k * kScanThreads + threadIdx.x;
+        if (idx < n) out[idx] = s[idx];
+    }
+    if (threadIdx.x == 0) {
+        out[n] = tot;
+        if (mode == 2) {
+            st->nnz_slots = tot;
+            if (tot > cap_check) st->overflow = 1;
+        }
+    }
+}
+
+int launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_check, DevState* st, int mode,
+                Launch L)
 {
     const int nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb <= 1) {
+        k_scan_single<<<1, kScanThreads, 0, L.stream>>>(in, out, n, cap_check, st, mode);
+        return 1;
+    }
     k_scan_reduce<<<nb, kScanThreads, 0, L.stream>>>(in, n, block_tmp, st);
     k_scan_top<<<1, 1024, 0, L.stream>>>(block_tmp, nb, out, n, cap_check, st, mode);
     k_scan_down<<<nb, kScanThreads, 0, L.stream>>>(in, out, n, block_tmp, st);
+    return 3;
 }
 
 // ------------------------------------------------- scatter, sort by id, gather
@@ -171,13 +214,9 @@ __global__ void k_scatter(int n, const int* __restrict__ cell_of, const int* __r
 }
 
 // One thread per cell: order the cell's particles by id (the atomic slots of
-// k_bin are not deterministic), then gather positions, ids and the warm-start
-// velocities into the new order.
-__global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int* __restrict__ perm,
-                              const int* __restrict__ id_s, const double* __restrict__ pos_s,
-                              const double* __restrict__ v_s, double* __restrict__ pos_w,
-                              float* __restrict__ pos32, float* __restrict__ pos32lo, int* __restrict__ id_w,
-                              double* __restrict__ x, int* __restrict__ cell_w, int warm, const DevState* st)
+// k_bin are not deterministic) and record the cell of its rows.
+__global__ void k_sort_cells(KParams P, const int* __restrict__ cell_start, int* __restrict__ perm,
+                             const int* __restrict__ id_s, int* __restrict__ cell_w, const DevState* st)
 {
     if (st->error | st->overflow) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,32 +232,43 @@ __global__ void k_sort_gather(KParams P, const int* __restrict__ cell_start, int
         }
         perm[j + 1] = key;
     }
-    const int np = P.npad;
-    for (int k = beg; k < end; ++k) {
-        const int s = perm[k];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double v = pos_s[a * np + s];
-            pos_w[a * np + k] = v;
-            const float vh = (float)v;
-            pos32[a * np + k] = vh;
-            pos32lo[a * np + k] = (float)(v - (double)vh);
-        }
-        id_w[k] = id_s[s];
-        cell_w[k] = c;   // the cell of row k (the pair search reads it instead of recomputing it)
-        x[k] = warm ? v_s[s] : 0.0;
-        x[np + k] = warm ? v_s[np + s] : 0.0;
-        x[2 * np + k] = warm ? v_s[2 * np + s] : 0.0;
-    }
+    for (int k = beg; k < end; ++k) cell_w[k] = c;   // the cell of row k (the pair search reads it)
 }
 
-void launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L)
+// One thread per row: positions (FP64 and as double-floats), id and the
+// warm-start velocities of row k from its particle's row s of the state.
+__global__ void k_gather_rows(KParams P, const int* __restrict__ perm, const int* __restrict__ id_s,
+                              const double* __restrict__ pos_s, const double* __restrict__ v_s,
+                              double* __restrict__ pos_w, float* __restrict__ pos32, float* __restrict__ pos32lo,
+                              int* __restrict__ id_w, double* __restrict__ x, int warm, const DevState* st)
+{
+    if (st->error | st->overflow) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    const int np = P.npad;
+    const int s = perm[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double v = pos_s[a * np + s];
+        pos_w[a * np + k] = v;
+        const float vh = (float)v;
+        pos32[a * np + k] = vh;
+        pos32lo[a * np + k] = (float)(v - (double)vh);
+    }
+    id_w[k] = id_s[s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a * np + k] = warm ? v_s[a * np + s] : 0.0;
+}
+
+int launch_scatter_sort_gather(const KParams& P, DevBuffers& B, bool warm, Launch L)
 {
     k_scatter<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(P.n, B.cell_of, B.slot,
                                                                                 B.cell_start, B.perm, B.st);
-    k_sort_gather<<<grid_for(P.ncell, 128, 1 << 30), 128, 0, L.stream>>>(
-        P, B.cell_start, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, B.cell_of,
-        warm ? 1 : 0, B.st);
+    k_sort_cells<<<grid_for(P.ncell, 128, 1 << 30), 128, 0, L.stream>>>(P, B.cell_start, B.perm, B.id_s, B.cell_of,
+                                                                         B.st);
+    k_gather_rows<<<grid_for(P.n, kVecBlock, 1 << 30), kVecBlock, 0, L.stream>>>(
+        P, B.perm, B.id_s, B.pos_s, B.v_s, B.pos_w, B.pos32, B.pos32lo, B.id_w, B.x, warm ? 1 : 0, B.st);
+    return 3;
 }
 
 // Single-cell boxes (every edge below 3 r_c): keep the state order.

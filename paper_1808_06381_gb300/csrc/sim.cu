@@ -259,9 +259,8 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent
         launches += 1;
     } else {
         launch_bin(P, B, L);
-        launch_scan(B.cell_count, B.cell_start, P.ncell, B.scan_tmp, 0, B.st, 0, L);
-        launch_scatter_sort_gather(P, B, warm, L);
-        launches += 6;
+        launches += 1 + launch_scan(B.cell_count, B.cell_start, P.ncell, B.scan_tmp, 0, B.st, 0, L);
+        launches += launch_scatter_sort_gather(P, B, warm, L);
     }
     if (side && ev && split_x) {   // x0 (just gathered) split into double-floats beside the search and assembly
         cudaEventRecord(ev[0], cs);
@@ -272,8 +271,8 @@ long long enqueue_build(sp_sim* s, cudaStream_t cs, cudaStream_t side, cudaEvent
     }
     launches += launch_nbr_count(P, B, !s->use_inj && P.noise_amp != 0.0, L, side, (side && ev) ? ev + 2 : nullptr);
     launch_sell_plan(P, B, L);
-    launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
-    return launches + 4;
+    launches += 1 + launch_scan(B.chunk_len32, B.chunk_off, P.nchunks, B.scan_tmp, s->nnz_cap, B.st, 2, L);
+    return launches;
 }
 
 // Conditional WHILE node holding one CG iteration, with an IF node for the

@@ -139,8 +139,12 @@ __global__ void __launch_bounds__(kVecBlock) k_stress32(KParams P, DevBuffers B)
     DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int np = P.npad;
-    const float deltaf = (float)st->delta;
-    const float c_ev = (float)P.c_ev, za = (float)(P.zeta * P.alpha), kl = (float)(P.kappa * P.L[1]);
+    // the step's offset in FP32 once per block (a conversion runs on GB300's slow FP64 pipe)
+    __shared__ float s_deltaf;
+    if (threadIdx.x == 0) s_deltaf = (float)st->delta;
+    __syncthreads();
+    const float deltaf = s_deltaf;
+    const float c_ev = P.c_ev_f, za = P.za_f, kl = P.kly_f;
     // shifts of the image codes by selection (GB300 converts integers to
     // floats at the FP64 rate); velocities from the solver's double-float x
     auto sel = [](int k, float v) { return k == 0 ? 0.f : (k > 0 ? v : -v); };

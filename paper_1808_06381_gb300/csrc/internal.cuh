@@ -58,6 +58,7 @@ struct KParams {
     double fix_inv[3];  // 2^32 / L
     float fix_scale[3]; // L / 2^32
     float w_exp2;       // -log2(e) / (2 lambda^2)
+    float c_ev_f, za_f, kly_f;  // c_ev, zeta alpha and kappa L_y in FP32 (the mixed path's stress)
 };
 
 constexpr int kPersistentConfigs = 12;

@@ -303,6 +303,18 @@ void launch_identity_gather(const KParams& P, DevBuffers& B, bool warm, Launch L
 
 // ------------------------------------------------------------- pair search
 
+// The exact predicate |R|^2 < r_c^2 of a candidate in the FP32 margin band,
+// in FP64 at the image (code) the cell walk found.  Not inlined: the band
+// holds ~0.03 candidates per row, and inlined FP64 work would be predicated
+// into every candidate's path on GB300's 1/64-rate FP64 pipe.
+__device__ __noinline__ bool band_pair(const KParams& P, double delta, double xi, double yi, double zi,
+                                       const double* __restrict__ pos, int np, int j, unsigned char code)
+{
+    double dx, dy, dz;
+    image_separation(P, delta, xi, yi, zi, pos[j], pos[np + j], pos[2 * np + j], code, dx, dy, dz);
+    return sq_norm_exact(dx, dy, dz) < P.rc2;
+}
+
 // Canonical minimum image (min_image) that also reports the two rounded
 // quotients, i.e. the image of the partner as a code.
 __device__ __forceinline__ unsigned char min_image_code(const KParams& P, double delta, double xi,
@@ -480,10 +492,11 @@ __device__ __forceinline__ void for_each_neighbor_fast(const KParams& P, double 
                     if (r2f < P.rc2_lo) {
                         visit(j, code);
                     } else {
-                        double r2;
-                        const unsigned char ce = min_image_code(P, delta, xi, yi, zi, pos[j], pos[np + j],
-                                                                pos[2 * np + j], r2);
-                        if (r2 < P.rc2) visit(j, ce);
+                        // the margin band: the exact FP64 predicate at the image the walk
+                        // found, which is the canonical one of min_image_code for any |R|
+                        // below L / 2 (bit-identical, without its three FP64 divisions:
+                        // GB300 issues FP64 at 1/64 of the FP32 rate, and the warp waits)
+                        if (band_pair(P, delta, xi, yi, zi, pos, np, j, code)) visit(j, code);
                     }
                 }
             }

@@ -243,6 +243,9 @@ void derive(const sp_params& p, KParams& k, int npad)
         k.fix_scale[a] = (float)(p.L[a] / 4294967296.0);
     }
     k.w_exp2 = (float)(-1.4426950408889634 / k.two_lambda2);
+    k.c_ev_f = (float)k.c_ev;
+    k.za_f = (float)(k.zeta * k.alpha);
+    k.kly_f = (float)(k.kappa * k.L[1]);
 }
 
 // --------------------------------------------------------------- enqueueing

@@ -94,8 +94,9 @@ typedef struct sp_solve_info {
     int32_t iterations;   /* CG iterations of this solve */
     double residual;      /* final true relative residual ||b - A v|| / ||b|| (FP64) */
     double bnorm;         /* ||b||_2 */
-    int32_t offchip_blocks; /* on-chip solver configuration: blocks whose rows and entries did not
-                               fit on their SM and were solved with global gathers (0 otherwise) */
+    int32_t offchip_blocks; /* on-chip solver configuration: blocks some of whose entries (the
+                               chunks that found no room) or all of them did not fit on their SM
+                               and were gathered from global memory (0 otherwise) */
     int32_t host_driven;    /* 1: the solve's CG loop was driven from the host (graph capture
                                unavailable, or SHEARSIM_HOST_LOOP=1); 0: it ran as one CUDA graph */
 } sp_solve_info;

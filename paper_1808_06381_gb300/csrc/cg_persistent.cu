@@ -182,25 +182,36 @@ __device__ __forceinline__ bool grid_allreduce_df(DevState* st, unsigned int& ge
         }
         __syncwarp();   // orders thread 0's acquire before the other lanes' loads
         // all of a lane's loads are issued before the first sum (one latency)
-        float2 pv[K][kPartialsPerLane];
+        if constexpr (f32) {   // the blocks' FP32 sums, summed in FP32 in a fixed order
+            float pv[K][kPartialsPerLane];   // the high parts only (the low ones are 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k)
+            for (int k = 0; k < K; ++k)
 #pragma unroll
-            for (int u = 0; u < kPartialsPerLane; ++u) {
-                const int b = lane + 32 * u;
-                pv[k][u] = b < nb ? __ldcg(partials + k * kMaxPartials + b) : make_float2(0.f, 0.f);
-            }
+                for (int u = 0; u < kPartialsPerLane; ++u) {
+                    const int b = lane + 32 * u;
+                    pv[k][u] = b < nb ? __ldcg(&partials[k * kMaxPartials + b].x) : 0.f;
+                }
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if constexpr (f32) {   // the blocks' FP32 sums, summed in FP32 in a fixed order
+            for (int k = 0; k < K; ++k) {
                 float a = 0.f;
 #pragma unroll
-                for (int u = 0; u < kPartialsPerLane; ++u) a += pv[k][u].x;
-                for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) a += __ldcg(partials + k * kMaxPartials + b).x;
+                for (int u = 0; u < kPartialsPerLane; ++u) a += pv[k][u];
+                for (int b = lane + 32 * kPartialsPerLane; b < nb; b += 32) a += __ldcg(&partials[k * kMaxPartials + b].x);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
                 if (lane == 0) sh.bcastf[k] = a;   // no FP64 operation on the iteration's path
-            } else {
+            }
+        } else {
+            float2 pv[K][kPartialsPerLane];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int u = 0; u < kPartialsPerLane; ++u) {
+                    const int b = lane + 32 * u;
+                    pv[k][u] = b < nb ? __ldcg(partials + k * kMaxPartials + b) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
                 dfloat a{0.f, 0.f};
 #pragma unroll
                 for (int u = 0; u < kPartialsPerLane; ++u) a = df_add(a, dfloat{pv[k][u].x, pv[k][u].y});
@@ -733,12 +744,40 @@ constexpr int kResSetupBatch = 6;                    // entries requested at a t
 constexpr int kResCheckBatch = 4;                    // gathers in flight in the off-chip blocks' true residual
 constexpr int kResCheckLocal = 8;                    // low parts requested at a time in the on-chip check
 
+// A local entry of the on-chip solve in one 32-bit word, so that one
+// shared-memory load serves the column and the weight: the column (11 bits:
+// a block holds fewer than 2048 rows) and the FP32 weight rounded to 18
+// mantissa bits, its exponent in 3 bits (a weight of the 5 % truncation lies
+// in (0.05, 1], five binades from 2^-5).  Word 0 is column 0 with weight 0
+// (padding); a real weight never encodes as 0.  The iteration's products use
+// the rounded weight (2^-19 relative: the inner FP32 solve converges as
+// fast); the residual replacements add the stored low part, which the
+// placement takes as (w_hi - rounded) + w_lo.
+__device__ __forceinline__ unsigned int pack_entry(int col, float w, float& rounded)
+{
+    unsigned int b = (__float_as_uint(w) + 0x10u) & ~0x1Fu;   // to 18 mantissa bits, to nearest
+    const int e = min(max((int)(b >> 23) - 122, 0), 7);
+    const unsigned int code = ((unsigned int)e << 18) | ((b >> 5) & 0x3FFFFu);
+    rounded = __uint_as_float((((code >> 18) + 122u) << 23) | ((code & 0x3FFFFu) << 5));
+    return (unsigned int)col | (code << 11);
+}
+
+__device__ __forceinline__ int entry_col(unsigned int word) { return (int)(word & 0x7FFu); }
+
+__device__ __forceinline__ float entry_weight(unsigned int word)
+{
+    const unsigned int code = word >> 11;
+    return code ? __uint_as_float((((code >> 18) + 122u) << 23) | ((code & 0x3FFFFu) << 5)) : 0.f;
+}
+
 struct RShared {
     int loff[kResChunks];    // shared-memory offset of the chunk's local entries
     int nloc[kResChunks];    // local entries per row of the chunk (its longest row's count)
     int nhalo[kResChunks];   // halo entries per row of the chunk
     int hoff[kResChunks];    // global offset of the chunk's halo list
-    int mode;                // 0: on chip; 1: the block's entries did not fit, all gathers global
+    unsigned long long spill;   // chunks whose local entries found no room: all their entries in the halo list
+    int nlocal;              // entries of the local lists (every chunk's, padding included)
+    int mode;                // 0: on chip; 1: the block's lists did not fit at all, all gathers global
 };
 
 __device__ __forceinline__ void res_halo_batch(const DevBuffers& B, int hb, int kb, int nh, float& s0, float& s1,
@@ -793,9 +832,8 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     const int rb = wb * 256, re = min(we * 256, P.n);   // the block's rows
     const int R = re - rb;
     float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows
-    const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 6;
-    float* sval = reinterpret_cast<float*>(dyn + nwmax * 256);
-    unsigned short* scol = reinterpret_cast<unsigned short*>(sval + cap);
+    const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 4;
+    unsigned int* sent = reinterpret_cast<unsigned int*>(dyn + nwmax * 256);   // packed local entries
     float* __restrict__ rlo = B.rlo + (size_t)bid * kResLoStride;   // low parts of the local weights
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
@@ -892,22 +930,40 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // a chunk whose local entries find no room in shared memory keeps them
+        // in its halo list (gathered from global memory, like the entries to
+        // other blocks); the other chunks stay on chip
         const int hbase = B.chunk_off[wb * 8], hcap = B.chunk_off[we * 8] - hbase;
         int lo = 0, ho = 0;
+        unsigned long long spill = 0ull;
         for (int c = 0; c < kResChunks; ++c) {
             rs.loff[c] = lo;
-            rs.hoff[c] = hbase + ho;
+            if (lo + 32 * rs.nloc[c] > cap) {
+                spill |= 1ull << c;
+                rs.nhalo[c] += rs.nloc[c];
+                rs.nloc[c] = 0;
+            }
             lo += 32 * rs.nloc[c];
+            rs.hoff[c] = hbase + ho;
             ho += 32 * rs.nhalo[c];
         }
-        rs.mode = (lo <= cap && ho <= hcap) ? 0 : 1;
+        rs.spill = spill;
+        rs.nlocal = lo;
+        rs.mode = ho <= hcap ? 0 : 1;
+        const int off = (rs.mode != 0 || spill != 0ull) ? 1 : 0;   // some or all entries gathered globally
         if (fused)   // summed by block 0 at the end (the counter is not reset before this launch)
-            B.partials[3 * kMaxPartials + bid] = (double)rs.mode;
-        else if (rs.mode)
+            B.partials[3 * kMaxPartials + bid] = (double)off;
+        else if (off)
             atomicAdd(&st->res_offchip, 1);
     }
     __syncthreads();
     const bool onchip = rs.mode == 0;
+    if (onchip) {   // lanes of the last chunk without a row keep these (column 0, weight 0)
+        for (int e = threadIdx.x; e < rs.nlocal; e += BS) {
+            sent[e] = 0u;
+        }
+        __syncthreads();   // before any entry is placed
+    }
     if (!onchip) {   // the sliced layout's own assignment, every gather global
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
@@ -961,6 +1017,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             const int lo = rs.loff[c] + (owner & 31), nl = rs.nloc[c], nh = rs.nhalo[c];
             const int hb = rs.hoff[c] + (owner & 31);
             const int e1 = B.chunk_off[(slot >> 5) + 1];
+            const bool spilled = (rs.spill >> c) & 1ull;   // every entry of the row to its halo list
             // The order of the row's local entries.  Its owner reads entry k
             // in step k of the local sums together with the other 7 lanes of
             // its quarter warp (one 16-byte gather of z each; lanes that hit
@@ -973,9 +1030,11 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             // order.  Position k < nlr belongs to group (k + l) mod 8 as its
             // (k / 8)-th; it is left over when that group has at most k / 8
             // entries (E, counted in set-up 1, 8 bits per group).  M counts
-            // the entries placed per group (4 bits, saturating: a group never
-            // has more than 8 positions).
+            // the entries placed per group (4 bits, saturating: a group has at
+            // most 8 positions below 64).  The left-over positions are a 64-bit
+            // mask: a row of more than 64 local entries keeps column order.
             const int nlr = (int)(scnt[row - rb] & 0xffffu), ql = owner & 7;
+            const bool bank_order = nlr <= 64;
             unsigned long long free_pos = 0ull;
             {   // group h's positions from its E_h-th on: every 8th bit from (h - l) mod 8 + 8 E_h
                 const unsigned long long E = B.res_hist[slot];
@@ -987,7 +1046,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 free_pos &= nlr >= 64 ? ~0ull : (1ull << nlr) - 1ull;
             }
             unsigned int M = 0u;
+            int kl = 0, kh = 0;
             auto local_pos = [&](int gg) {   // position of the next local entry of group gg
+                if (!bank_order) return kl;
                 const int m = (int)((M >> (4 * gg)) & 15u);
                 if (m < 15) M += 1u << (4 * gg);
                 const int d = (gg - ql) & 7;
@@ -998,7 +1059,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 free_pos &= free_pos - 1ull;
                 return k;
             };
-            int kl = 0, kh = 0;
             dfloat sd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (int eb = B.chunk_off[slot >> 5] + (slot & 31); eb < e1; eb += 32 * KS) {
                 int j[KS];
@@ -1031,11 +1091,11 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
                 for (int u = 0; u < KS; ++u) {
                     if (v[u] == 0.f) continue;
-                    if (j[u] != row && j[u] >= rb && j[u] < re) {   // as counted in set-up 1
+                    if (!spilled && j[u] != row && j[u] >= rb && j[u] < re) {   // as counted in set-up 1
                         const int k = local_pos((j[u] - rb) & 7);
-                        scol[lo + 32 * k] = (unsigned short)(j[u] - rb);
-                        sval[lo + 32 * k] = v[u];
-                        rlo[lo + 32 * k] = vl[u];
+                        float vr;
+                        sent[lo + 32 * k] = pack_entry(j[u] - rb, v[u], vr);
+                        rlo[lo + 32 * k] = __fadd_rn(__fsub_rn(v[u], vr), vl[u]);   // v - vr exact
                         ++kl;
                     } else {
                         B.hcol[hb + 32 * kh] = j[u];
@@ -1046,8 +1106,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 }
             }
             for (; kl < nl; ++kl) {   // padding: weight 0 at a record of the position's own bank group
-                scol[lo + 32 * kl] = (unsigned short)(R >= 8 ? (kl + ql) & 7 : 0);
-                sval[lo + 32 * kl] = 0.f;
+                sent[lo + 32 * kl] = (unsigned int)(R >= 8 ? (kl + ql) & 7 : 0);   // weight 0
                 rlo[lo + 32 * kl] = 0.f;
             }
             for (; kh < nh; ++kh) {
@@ -1059,6 +1118,19 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
     }
     __syncthreads();   // sinv (in zbuf) is read until here
+    if (onchip) {
+        // every local column indexes one of the block's rows; an entry that
+        // does not (a broken invariant of the placement) is neutralised and
+        // raises an error rather than read outside zbuf
+        int bad = 0;
+        for (int e = threadIdx.x; e < rs.nlocal; e += BS) {
+            if (entry_col(sent[e]) >= R) {
+                sent[e] = 0u;
+                bad = 1;
+            }
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
+    }
 
     // ---- the initial residual (fused form): r = b - A x0 in double-float, or
     // r = b with x = 0, for the block's rows in slot order, with ||b||^2,
@@ -1120,13 +1192,13 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     // Rows whose r (and d) other blocks gather: on chip, those with an entry
     // to another block's row (pairs are symmetric, so exactly the rows of the
     // other blocks' halo lists; a warp's rows of one index u share their
-    // chunk's halo count, sorted first); every row of a block whose entries
-    // are off chip (its own gathers read them too).  Fewer stores before each
-    // barrier's release.
+    // chunk's halo count, sorted first); every row of a block with entries
+    // off chip (a spilled chunk, or all of them: its own gathers read them
+    // too).  Fewer stores before each barrier's release.
     unsigned int pub = 0u;
 #pragma unroll
     for (int u = 0; u < RPT; ++u)
-        if (!onchip || rs.nhalo[u * (BS / 32) + warp] != 0) pub |= 1u << u;
+        if (!onchip || rs.spill != 0ull || rs.nhalo[u * (BS / 32) + warp] != 0) pub |= 1u << u;
 
     // ---- load r and D^-1 of the own rows
     float r[RPT][3], dv[RPT], p[RPT][3], q[RPT][3], d[RPT][3];
@@ -1201,8 +1273,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     if (w[k] != 0.f) gh[k] = B.r4[j[k]];
                 }
                 for (int k = 0; k < nl; ++k) {
-                    const float wl = sval[lo + 32 * k];
-                    const float4 zj = zbuf[scol[lo + 32 * k]];
+                    const unsigned int ew = sent[lo + 32 * k];
+                    const float wl = entry_weight(ew);
+                    const float4 zj = zbuf[entry_col(ew)];
                     s0 = fmaf(wl, zj.x, s0);
                     s1 = fmaf(wl, zj.y, s1);
                     s2 = fmaf(wl, zj.z, s2);
@@ -1370,7 +1443,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     for (int k = 0; k < kResCheckLocal; ++k) {
                         if (kb + k < nl) {
                             const int e = lo + 32 * (kb + k);
-                            add(sval[e], wl[k], zbuf[scol[e]]);
+                            add(entry_weight(sent[e]), wl[k], zbuf[entry_col(sent[e])]);
                         }
                     }
                 }
@@ -2180,7 +2253,9 @@ __global__ void __launch_bounds__(BS, MINB) k32_cg_persistent_batch(const KParam
 }
 
 namespace {
-// kResSmemBytes (190 KB) leaves a 196 KB carve-out's L1 for the halo gathers
+// kResSmemBytes (220 KB): the largest carve-out; more blocks keep every local entry
+// on chip (at 190 KB the densest blocks of some steps fell back to global gathers),
+// and the halo gathers keep ~28 KB of L1
 
 struct PCfg {
     int kb, minb, pipe, bs;

@@ -63,7 +63,7 @@ struct KParams {
 
 constexpr int kPersistentConfigs = 12;
 constexpr int kResSmemBytes = 190 * 1024;   // on-chip solve: dynamic shared memory per block
-constexpr int kResLoStride = 32768;          // >= kResSmemBytes / 6: local entries of one block
+constexpr int kResLoStride = 49152;          // >= kResSmemBytes / 4: local entries of one block
 
 // Scalars that live on the device so that a whole step runs without the host.
 struct DevState {

@@ -150,8 +150,10 @@ PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 100.5e6,
 LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 56.37e9, "k32_cg_persistent<4,3,0,256,1>": 52.28e9}
 
 
-def profiled_traffic(workload_name: str, tune) -> float | None:
-    if not tune:
+def profiled_traffic(workload_name: str, tune, burn_in: int = 0) -> float | None:
+    """The capture's DRAM bytes, where it matches this launch: the captures ran a few steps
+    from the uniform start, so a line timed after a burn-in has none."""
+    if not tune or burn_in:
         return None
     return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"],
                                  tune["pipelined"], tune["block_threads"], tune.get("resident", False)))
@@ -278,8 +280,9 @@ def cpu_baseline(workload, precision: str, steps: int = 2):
     value, procs, slowest = oracle_throughput(workload, workload.n, steps)
     return {"value": value, "unit": "particle-steps/s", "cores": procs, "kind": "oracle",
             "sample": f"{procs} concurrent single-thread oracle processes, each {steps} full steps of its own "
-                      f"N={workload.n} replica (cell-list pair search, Jacobi-PCG to {workload.tol:g}); "
-                      f"slowest {slowest:.1f} s"}
+                      f"N={workload.n} replica (cell-list pair search, Jacobi-PCG to {workload.tol:g}) from "
+                      f"the uniform start (fewer pairs and CG iterations per step than the steady state the "
+                      f"GPU line is timed in); slowest {slowest:.1f} s"}
 
 
 REFERENCE_SAMPLE_N = 32768   # particles per process and reference step: one oracle step then takes ~0.5 s
@@ -333,6 +336,11 @@ def main():
                          "A^(1/2) g (FDT-consistent noise) on the N=262,144 system")
     ap.add_argument("--train-steps", type=int, default=520,
                     help="learned workload: solves streamed into the online training (13 trajectories)")
+    ap.add_argument("--burn-in", type=int, default=None,
+                    help="untimed steps before the warm-up, so that the timed steps come from the trajectory's "
+                         "steady state (the uniform start clusters: ~13 -> ~18 pairs per row and 42 -> 56 CG "
+                         "iterations by step ~400 of the 2,000-step N = 262,144 runs); default 1000 for the "
+                         "N = 262,144 workloads, 0 for plain (its 200 timed steps are the whole run)")
     ap.add_argument("--solver-config", type=int, default=None,
                     help="tile configuration of the persistent mixed solver (sp_set_solver_config) instead of "
                          "autotuning; 9 is the on-chip k32_cg_resident<512,4>, 0 the streaming "
@@ -347,6 +355,8 @@ def main():
                 "plain": synth.PLAIN_FP64}[args.workload]
     if args.workload == "plain":
         args.precision = "fp64"
+    if args.burn_in is None:
+        args.burn_in = 0 if args.workload == "plain" or args.n else 1000
     if args.n:
         workload = synth.cubic(f"n{args.n}", args.n, workload.kappa_tau, workload.steps, workload.tol,
                                workload.seed)
@@ -389,6 +399,8 @@ def main():
     fp64 = None
     if args.precision == "mixed" and not args.no_fp64_comparison:
         sim64 = make_sim("fp64")
+        if args.burn_in:
+            sim64.step(args.burn_in)
         for _ in range(args.warmup):
             sim64.step(1)
         t64, _, it64, res64 = run_steps(sim64, args.steps, stream, flush)
@@ -397,6 +409,8 @@ def main():
         sim64.close()
 
     sim = make_sim(args.precision)
+    if args.burn_in:   # untimed: the trajectory's steady state
+        sim.step(args.burn_in)
     # the persistent solver's tile configuration for this system (cached on disk
     # when SHEARSIM_TUNE_CACHE names a file); untimed, like the warm-up
     tune = None
@@ -454,7 +468,7 @@ def main():
         pach = plan / (prof["persistent_ms"] * 1e-3) / 1e9
         kname = solver_kernel_name(tune)
         resident = bool(tune and tune.get("resident"))
-        traffic = profiled_traffic(workload.name, tune)
+        traffic = profiled_traffic(workload.name, tune, args.burn_in)
         persistent = {"kernel": kname, "bound": "latency" if resident else "hbm", "achieved": pach, "peak": peak,
                       "unit": "GB/s", "frac": pach / peak, "traffic": traffic,
                       "peak_source": f"hbm_gbs {peak_kind} (burst copy)",
@@ -505,7 +519,10 @@ def main():
             "config": {"workload": workload.name, "n": n, "box": L[0], "density": 3.0,
                        "kappa_tau": workload.kappa_tau, "alpha": workload.alpha, "dt": workload.dt,
                        "cg_tol": workload.tol, "precision": args.precision, "warm_start": "prev",
-                       "replicas": world, "l2": "flushed between timed steps (512 MB write)"},
+                       "replicas": world, "l2": "flushed between timed steps (512 MB write)",
+                       "burn_in_steps": args.burn_in,
+                       "regime": ("steady state: timed after the untimed burn-in" if args.burn_in
+                                  else "from the uniform start")},
             "cg_iterations_per_step": iters / args.steps, "max_true_residual": max_res,
             "gpu_launches": launches,
             "roofline": persistent if persistent else {

@@ -738,6 +738,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 // lists; a chunk whose local entries find no room in shared memory keeps all
 // its entries in the halo list (slower, same result).
 constexpr int kResWindows = 8;                       // 2048 rows per block
+constexpr int kResMaxBlocks = 192;                   // blocks the entry-balanced split serves
 constexpr int kResChunks = kResWindows * 8;
 constexpr int kResHalo = 4;                          // halo gathers in flight per thread
 constexpr int kResSetupBatch = 6;                    // entries requested at a time in the set-up
@@ -776,6 +777,8 @@ struct RShared {
     int nhalo[kResChunks];   // halo entries per row of the chunk
     int hoff[kResChunks];    // global offset of the chunk's halo list
     unsigned long long spill;   // chunks whose local entries found no room: all their entries in the halo list
+    int bnd[kResMaxBlocks + 1]; // first window of every block (entry-balanced split)
+    int split_ok;
     int nlocal;              // entries of the local lists (every chunk's, padding included)
     int mode;                // 0: on chip; 1: the block's lists did not fit at all, all gathers global
 };
@@ -826,9 +829,44 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     unsigned int gen = 0u;   // barriers passed in this launch (the counter starts at 0)
 
     const int nwin = P.nslots / 256;
-    const int wb = (int)((long long)bid * nwin / nb);
-    const int we = (int)((long long)(bid + 1) * nwin / nb);
-    const int nwmax = (nwin + nb - 1) / nb;
+    // The block's windows.  The blocks split the windows so that each holds
+    // about the same number of matrix entries (the sliced layout's offsets at
+    // the window starts; a sheared run clusters, and its dense regions carry
+    // up to ~1.3x the mean entries per row), every block computing the same
+    // boundaries; where a block would get no window or more than kResWindows,
+    // every block takes the same number of windows instead.
+    int wb = (int)((long long)bid * nwin / nb), we = (int)((long long)(bid + 1) * nwin / nb);
+    {
+        const long long E = B.chunk_off[nwin * 8];
+        const bool split = nb <= kResMaxBlocks && E > 0;
+        if (threadIdx.x == 0) {
+            rs.bnd[0] = 0;
+            rs.bnd[min(nb, kResMaxBlocks)] = nwin;
+        }
+        if (split) {
+            for (int w = threadIdx.x; w < nwin; w += BS) {
+                const long long lo = B.chunk_off[w * 8], hi = B.chunk_off[(w + 1) * 8];
+                // block b starts at the first window whose start reaches b E / nb
+                const int b0 = max(1, (int)(lo * nb / E)), b1 = min(nb - 1, (int)(hi * nb / E) + 1);
+                for (int b = b0; b <= b1; ++b) {
+                    const long long T = (long long)b * E / nb;
+                    if (T > lo && T <= hi) rs.bnd[b] = w + 1;
+                }
+            }
+        }
+        __syncthreads();
+        int bad = !split;
+        if (split)
+            for (int b = threadIdx.x; b < nb; b += BS) {
+                const int nw = rs.bnd[b + 1] - rs.bnd[b];
+                bad |= nw < 1 || nw > kResWindows;
+            }
+        if (!__syncthreads_or(bad)) {
+            wb = rs.bnd[bid];
+            we = rs.bnd[bid + 1];
+        }
+    }
+    const int nwmax = we - wb;   // this block's windows
     const int rb = wb * 256, re = min(we * 256, P.n);   // the block's rows
     const int R = re - rb;
     float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows

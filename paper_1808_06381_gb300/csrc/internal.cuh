@@ -187,7 +187,8 @@ constexpr int kRngConstLn = kLnTab;                 // (ln 2, 1 / 3)
 constexpr int kRngTrig = kLnTab + 1;                // cos, sin of 2 pi j / 64
 constexpr int kRngConstTrig = kRngTrig + kTrigTab;  // (2 pi, -1 / 6)
 constexpr int kRngTab = kRngConstTrig + 1;
-constexpr int kCandCap = 32;    // partners kept per row by the search (rows with more are searched again)
+constexpr int kCandCap = 64;    // partners kept per row by the search (rows with more are searched again; the
+                                 // clustered steady state of a sheared run has many rows above 32)
 constexpr int kMaxSmIds = 1024;   // weight table: exp(-t) for t < 4 (pairs have t < ln 20)
 
 // Learned warm start (mpnn.cu): flat FP32 weights W1 [6][64], W2 [64][64],

@@ -800,7 +800,7 @@ cudaError_t upload_exp_table(double* exp_tab, float2* exp_tab_df, cudaStream_t s
 }
 
 // The partners of row i written straight into its slots (rows with more than
-// kCandCap partners; rare), in the order of the counting search.
+// kCandCap partners), in the order of the counting search.
 __device__ __noinline__ void search_row_into_slots(const KParams& P, const DevBuffers& B, int i, double delta,
                                                    int base, int cnt)
 {

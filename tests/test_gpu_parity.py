@@ -354,6 +354,29 @@ def test_dense_cluster_grows_pair_storage():
     sim.close()
 
 
+def test_on_chip_rows_with_many_local_entries():
+    """~77 partners per row, all in the on-chip solve's one block: rows with more
+    than 64 local entries keep column order in shared memory (the bank-aware order
+    tracks its left-over positions in 64 bits) and the solve still meets the
+    tolerance on the oracle's system."""
+    n = 256
+    L = 2.4   # density ~18.5: ~77 partners per particle, one block of 256 rows
+    pos = synth.uniform_positions(n, (L,) * 3, 11)
+    sim, p, _ = make(n, L, pos=pos, tol=1e-8, precision="mixed", delta=0.8)
+    info = sim.set_solver_config(9)
+    assert info["resident"]
+    sim.build_neighbors()
+    sim.assemble()
+    res = sim.solve_velocities()
+    assert res["status"] == 0 and res["offchip_blocks"] == 0, res
+    pairs = pairs_equal(sim, p, pos, 0.8)
+    assert pairs.shape[0] * 2 / n > 64
+    sysr = oracle.assemble(p, pos, pairs, oracle.noise(p.seed, 0, np.arange(n)), 0.8)
+    v = sim.get_velocities()
+    assert np.linalg.norm(sysr.b - sysr.matvec(v)) / np.linalg.norm(sysr.b) <= 1e-8
+    sim.close()
+
+
 # ------------------------------------------------ full size (262,144 particles)
 
 

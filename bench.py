@@ -345,6 +345,9 @@ def main():
                     help="tile configuration of the persistent mixed solver (sp_set_solver_config) instead of "
                          "autotuning; 9 is the on-chip k32_cg_resident<512,4>, 0 the streaming "
                          "k32_cg_persistent<6,1,0,1024>")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed steps of the main line with cudaProfilerStart/Stop, so that "
+                         "`ncu --profile-from-start off` captures the steady state and not the burn-in")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "ours" and args.workload not in ("mixed", "lowshear", "plain"):
@@ -426,8 +429,12 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.profiler.start()
     total_ms, launches, iters, max_res = run_steps(sim, args.steps, stream, flush)
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.profiler.stop()
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()

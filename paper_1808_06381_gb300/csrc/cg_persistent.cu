@@ -988,6 +988,25 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         rs.spill = spill;
         rs.nlocal = lo;
         rs.mode = ho <= hcap ? 0 : 1;
+        if (rs.mode != 0) {
+            // the halo lists cannot hold the block's entries: every entry is
+            // gathered, from lists that are the sliced layout's own (copied
+            // below), each thread's rows those of its own slots (chunk_lane)
+            for (int c = 0; c < kResChunks; ++c) {
+                const int u = c / (BS / 32), wp = c % (BS / 32);
+                const int w = wb + (wp >> 3) + (BS / 256) * u;
+                rs.loff[c] = 0;
+                rs.nloc[c] = 0;
+                rs.hoff[c] = hbase;
+                rs.nhalo[c] = 0;
+                if (w < we) {
+                    const int sc = w * 8 + ((u & 1) ? (wp & 7) ^ 7 : (wp & 7));
+                    rs.hoff[c] = B.chunk_off[sc];
+                    rs.nhalo[c] = (B.chunk_off[sc + 1] - B.chunk_off[sc]) / 32;
+                }
+            }
+            rs.nlocal = 0;
+        }
         const int off = (rs.mode != 0 || spill != 0ull) ? 1 : 0;   // some or all entries gathered globally
         if (fused)   // summed by block 0 at the end (the counter is not reset before this launch)
             B.partials[3 * kMaxPartials + bid] = (double)off;
@@ -1002,11 +1021,16 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         __syncthreads();   // before any entry is placed
     }
-    if (!onchip) {   // the sliced layout's own assignment, every gather global
+    if (!onchip) {   // the sliced layout's own assignment and lists, every gather global
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int w = wb + g + (BS / 256) * u;
             row[u] = w < we ? B.slot_row[w * 256 + chunk_lane(u, t)] : -1;
+        }
+        for (int e = B.chunk_off[wb * 8] + (int)threadIdx.x; e < B.chunk_off[we * 8]; e += BS) {
+            B.hcol[e] = B.col[e];
+            B.hval[e] = B.val32[e];
+            B.hlo[e] = B.val32lo[e];
         }
     }
 
@@ -1238,11 +1262,13 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     for (int u = 0; u < RPT; ++u)
         if (!onchip || rs.spill != 0ull || rs.nhalo[u * (BS / 32) + warp] != 0) pub |= 1u << u;
 
-    // ---- load r and D^-1 of the own rows
-    float r[RPT][3], dv[RPT], p[RPT][3], q[RPT][3], d[RPT][3];
+    // ---- load r and D^-1 of the own rows.  An own row's z = D^-1 r is kept in
+    // zbuf with D^-1 in its w (rather than in registers: the kernel is at its
+    // 128-register limit), so the direction update reads z there
+    float r[RPT][3], p[RPT][3], q[RPT][3], d[RPT][3];
+    auto dv_of = [&](int u) { return zbuf[row[u] - rb].w; };
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
-        dv[u] = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[u][c] = p[u][c] = q[u][c] = d[u][c] = 0.f;
     }
@@ -1253,8 +1279,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         r[u][0] = r4.x;
         r[u][1] = r4.y;
         r[u][2] = r4.z;
-        dv[u] = r4.w;
-        zbuf[row[u] - rb] = make_float4(r4.w * r4.x, r4.w * r4.y, r4.w * r4.z, 0.f);
+        zbuf[row[u] - rb] = make_float4(r4.w * r4.x, r4.w * r4.y, r4.w * r4.z, r4.w);
     }
     if (threadIdx.x == 0) {
         if (fused) {
@@ -1287,7 +1312,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             if (row[u] < 0) continue;
             const float di = __ldg(B.diag32 + row[u]);
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            if (onchip) {
+            {
                 const int c = u * (BS / 32) + warp;
                 const int lo = rs.loff[c] + lane, nl = rs.nloc[c], nh = rs.nhalo[c];
                 const int hb = rs.hoff[c] + lane;
@@ -1326,12 +1351,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     s2 = fmaf(ww, gh[k].z, s2);
                 }
                 for (int kb = kResHalo; kb < nh; kb += kResHalo) res_halo_batch(B, hb, kb, nh, s0, s1, s2);
-            } else {
-                const int slot = B.row_slot[row[u]];
-                p_row_sum32<2, false>(B.col, B.val32, B.r4, B.chunk_off[slot >> 5] + (slot & 31),
-                                      B.chunk_off[(slot >> 5) + 1], s0, s1, s2);
             }
-            const float z0 = dv[u] * r[u][0], z1 = dv[u] * r[u][1], z2 = dv[u] * r[u][2];
+            const float4 zo = zbuf[row[u] - rb];   // D^-1 r of the row, as the update wrote it
+            const float z0 = zo.x, z1 = zo.y, z2 = zo.z;
             float q0 = fmaf(di, z0, -alpha_e * s0);
             float q1 = fmaf(di, z1, -alpha_e * s1);
             float q2 = fmaf(di, z2, -alpha_e * s2);
@@ -1381,10 +1403,11 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 r[u][c] = fmaf(-af, q[u][c], r[u][c]);
             }
             const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
+            const float dvu = dv_of(u);
             rr.hi += rsq;   // FP32, as the block sums
-            rz.hi += dv[u] * rsq;
-            if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
-            zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
+            rz.hi += dvu * rsq;
+            if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dvu);
+            zbuf[row[u] - rb] = make_float4(dvu * r[u][0], dvu * r[u][1], dvu * r[u][2], dvu);
         }
         {
             const dfloat v[2] = {rr, rz};
@@ -1414,7 +1437,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         // as FP32): the local half from shared memory (d of the block's rows in
         // zbuf), the halo half from d published in global memory; the residual
         // itself kept as a double-float record per row (rdf).  A block whose
-        // entries are off chip recomputes b - A x from x in slot order.
+        // entries are all off chip forms A d the same way from its lists.
         {
             // every row's x record is requested before the first is updated
             float4 xh[RPT], xl[RPT];
@@ -1429,13 +1452,13 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
             for (int u = 0; u < RPT; ++u) {
                 if (row[u] < 0) continue;
-                const float4 df = make_float4(d[u][0], d[u][1], d[u][2], 0.f);
+                const float4 df = make_float4(d[u][0], d[u][1], d[u][2], dv_of(u));
                 const dfloat a = df_add(dfloat{xh[u].x, xl[u].x}, df.x), b = df_add(dfloat{xh[u].y, xl[u].y}, df.y),
                              c = df_add(dfloat{xh[u].z, xl[u].z}, df.z);
                 B.xdf[2 * row[u]] = make_float4(a.hi, b.hi, c.hi, 0.f);
                 B.xdf[2 * row[u] + 1] = make_float4(a.lo, b.lo, c.lo, 0.f);
-                if (pub & (1u << u)) B.d4[row[u]] = df;
-                zbuf[row[u] - rb] = df;
+                if (pub & (1u << u)) B.d4[row[u]] = make_float4(df.x, df.y, df.z, 0.f);
+                zbuf[row[u] - rb] = df;   // d, D^-1 in w
                 // r, p and q are set anew after the check (beta = 0), so none of
                 // them holds a register through it
 #pragma unroll
@@ -1444,7 +1467,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         if (!grid_sync(st, gen, sh, nb)) break;
         double trr = 0.0, trz = 0.0;
-        if (onchip) {
+        {
 #pragma unroll
             for (int u = 0; u < RPT; ++u) {
                 if (row[u] < 0) continue;
@@ -1525,33 +1548,15 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 B.rdf[2 * row[u] + 1] = make_float4(rn[0].lo, rn[1].lo, rn[2].lo, 0.f);
                 const float rsq = r[u][0] * r[u][0] + r[u][1] * r[u][1] + r[u][2] * r[u][2];
                 trr += (double)rsq;
-                trz += (double)(dv[u] * rsq);
+                trz += (double)(dv_of(u) * rsq);
             }
             __syncthreads();   // zbuf (d) read by every row before it changes
 #pragma unroll
             for (int u = 0; u < RPT; ++u) {
                 if (row[u] < 0) continue;
-                if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dv[u]);
-                zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < RPT; ++u)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) d[u][c] = 0.f;
-            __syncthreads();   // zbuf (d) is not read off chip, but it is rewritten below
-            // in slot order (coalesced); r goes to the owners through zbuf and is
-            // published for the other blocks' halo gathers before the barrier
-            for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
-                const int slot = w * 256 + chunk_lane(k, t);
-                const int rw = B.slot_row[slot];
-                if (rw < 0) continue;
-                float rs;
-                const float4 rf = true_residual_row<KC>(P, B, slot, rw, rs);
-                trr += (double)rs;
-                trz += (double)(rf.w * rs);
-                B.r4[rw] = rf;
-                zbuf[rw - rb] = rf;
+                const float dvu = dv_of(u);
+                if (pub & (1u << u)) B.r4[row[u]] = make_float4(r[u][0], r[u][1], r[u][2], dvu);
+                zbuf[row[u] - rb] = make_float4(dvu * r[u][0], dvu * r[u][1], dvu * r[u][2], dvu);
             }
         }
         {
@@ -1582,23 +1587,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         }
         __syncthreads();
         if (sh.action == 2) break;
-        if (!onchip) {
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                if (row[u] < 0) continue;
-                const float4 rf = zbuf[row[u] - rb];
-                r[u][0] = rf.x;
-                r[u][1] = rf.y;
-                r[u][2] = rf.z;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < RPT; ++u) {
-                if (row[u] < 0) continue;
-                zbuf[row[u] - rb] = make_float4(dv[u] * r[u][0], dv[u] * r[u][1], dv[u] * r[u][2], 0.f);
-            }
-            __syncthreads();
-        }
     }
     if (!(fused && sh.iter == 0)) {   // a solve that met the tolerance at x0 keeps x0 as it was
 #pragma unroll

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kBlock) k32_update(KParams P, DevBuffers B, Cg
     if (publish_reduce_df<2>(v, B.partials_df, &st->ticket[0], out) && threadIdx.x == 0 && !probe) {
         // stop the FP32 inner solve once the residual dropped by the inner
         // factor since the last restart, or meets half the tolerance
-        const double target = fmax(P.inner2 * st->rr_restart, 0.25 * P.tol2 * st->bnorm2);
+        const double target = fmax(P.inner2 * st->rr_restart, kInnerFinal2 * P.tol2 * st->bnorm2);
         update_scalars(P, st, out[0], out[1], target, C);
     }
 }

@@ -643,7 +643,7 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
                 } else {
                     sh.beta_f = (float)(tot[1] / sh.rho);
                     sh.rho = tot[1];
-                    const double target = fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
+                    const double target = fmax(P.inner2 * sh.rr_restart, kInnerFinal2 * P.tol2 * sh.bnorm2);
                     if (tot[0] <= target || sh.iter >= P.max_iter) sh.action = 1;
                 }
             }
@@ -1299,7 +1299,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         // the iteration's scalars in FP32 (its vectors are FP32; the FP64
         // divisions cost ~0.5 us per iteration on GB300's FP64 pipe)
         sh.rho_f = (float)sh.rho;
-        sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
+        sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, kInnerFinal2 * P.tol2 * sh.bnorm2);
     }
     __syncthreads();
 
@@ -1581,7 +1581,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                     sh.beta_f = 0.f;
                     sh.rr_restart = tot[0];
                     sh.rho_f = (float)tot[1];
-                    sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, 0.25 * P.tol2 * sh.bnorm2);
+                    sh.target_f = (float)fmax(P.inner2 * sh.rr_restart, kInnerFinal2 * P.tol2 * sh.bnorm2);
                 }
             }
         }

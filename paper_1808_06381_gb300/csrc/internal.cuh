@@ -12,6 +12,12 @@
 namespace ss {
 
 constexpr int kMaxCgRestarts = 4;    // true-residual restarts per solve before giving up
+// Mixed solver: the inner FP32 iteration that may end the solve stops once its
+// recursive ||r||^2 <= kInnerFinal2 tol^2 ||b||^2.  The recursion started from
+// a true residual at most ~1e-4 ||b|| (or from the initial residual), so FP32
+// rounding and the rounded weights move it from the true residual by ~1e-10
+// ||b||, far inside the 10 % margin; the true residual in double-float decides.
+constexpr double kInnerFinal2 = 0.81;
 constexpr int kVecBlock = 256;       // threads per block of the streaming kernels
 
 // Constants of one simulation, passed by value to every kernel.

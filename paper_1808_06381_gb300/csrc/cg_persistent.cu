@@ -777,7 +777,8 @@ struct RShared {
     int nhalo[kResChunks];   // halo entries per row of the chunk
     int hoff[kResChunks];    // global offset of the chunk's halo list
     unsigned long long spill;   // chunks whose local entries found no room: all their entries in the halo list
-    int bnd[kResMaxBlocks + 1]; // first window of every block (entry-balanced split)
+    short bnd[kResMaxBlocks + 1];  // first window of every block (entry-balanced split by windows; < 2^15)
+    int rbnd[kResMaxBlocks + 1];   // first row of every block (entry-balanced split by rows)
     int split_ok;
     int nlocal;              // entries of the local lists (every chunk's, padding included)
     int mode;                // 0: on chip; 1: the block's lists did not fit at all, all gathers global
@@ -829,49 +830,94 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     unsigned int gen = 0u;   // barriers passed in this launch (the counter starts at 0)
 
     const int nwin = P.nslots / 256;
-    // The block's windows.  The blocks split the windows so that each holds
-    // about the same number of matrix entries (the sliced layout's offsets at
-    // the window starts; a sheared run clusters, and its dense regions carry
-    // up to ~1.3x the mean entries per row), every block computing the same
-    // boundaries; where a block would get no window or more than kResWindows,
-    // every block takes the same number of windows instead.
+    // The block's rows.  Every block computes the same split of the rows into
+    // nb shares with about equal numbers of matrix entries (a sheared run
+    // clusters, and its dense regions carry up to ~1.3x the mean entries per
+    // row): block b starts where the sliced layout's entry count reaches
+    // T_b = b E / nb, at the row interpolated inside that window of 256 rows
+    // (a window's rows are spatially compact, so their lengths are similar).
+    // A window at a share's edge is read by both blocks, each keeping its own
+    // rows.  Where a share would be empty, hold more than 2048 rows or touch
+    // more than kResWindows windows, or no separate region exists for the
+    // lists of blocks whose entries cannot stay on chip, the shares are whole
+    // windows with about equal entries instead (block b from the first window
+    // that starts at or after T_b), and failing that equal numbers of windows.
     int wb = (int)((long long)bid * nwin / nb), we = (int)((long long)(bid + 1) * nwin / nb);
+    int rb = wb * 256, re = min(we * 256, P.n);
+    int hbase = -1, hcap = 0;   // the block's range of the halo lists (set below for the window split)
     {
         const long long E = B.chunk_off[nwin * 8];
         const bool split = nb <= kResMaxBlocks && E > 0;
+        for (int b = threadIdx.x; b <= min(nb, kResMaxBlocks); b += BS) {
+            rs.bnd[b] = -1;   // every interior boundary is set by the window that holds T_b
+            rs.rbnd[b] = -1;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             rs.bnd[0] = 0;
-            rs.bnd[min(nb, kResMaxBlocks)] = nwin;
+            rs.bnd[min(nb, kResMaxBlocks)] = (short)nwin;
+            rs.rbnd[0] = 0;
+            rs.rbnd[min(nb, kResMaxBlocks)] = P.n;
         }
         if (split) {
             for (int w = threadIdx.x; w < nwin; w += BS) {
                 const long long lo = B.chunk_off[w * 8], hi = B.chunk_off[(w + 1) * 8];
-                // block b starts at the first window whose start reaches b E / nb
                 const int b0 = max(1, (int)(lo * nb / E)), b1 = min(nb - 1, (int)(hi * nb / E) + 1);
                 for (int b = b0; b <= b1; ++b) {
                     const long long T = (long long)b * E / nb;
-                    if (T > lo && T <= hi) rs.bnd[b] = w + 1;
+                    if (T > lo && T <= hi) rs.bnd[b] = (short)(w + 1);
+                    if (T >= lo && T < hi) rs.rbnd[b] = min(w * 256 + (int)((T - lo) * 256 / (hi - lo)), P.n);
                 }
             }
         }
         __syncthreads();
-        int bad = !split;
+        if (split && threadIdx.x == 0) {
+            // a share ends within the kResWindows-th window from the one it
+            // starts in (so it holds at most 2048 rows and the rows of a block
+            // whose lists cannot stay on chip map to its threads' slots), and
+            // leaves at least a row to every later share; boundaries that
+            // miss T_b stay monotone, and a share the clamp leaves invalid is
+            // caught below
+            for (int b = 1; b < nb; ++b) {
+                int r = rs.rbnd[b];
+                if (r < 0) break;
+                r = min(r, (rs.rbnd[b - 1] / 256 + kResWindows) * 256);
+                r = min(r, P.n - (nb - b));
+                rs.rbnd[b] = max(r, rs.rbnd[b - 1] + 1);
+            }
+        }
+        __syncthreads();
+        int bad_w = !split, bad_r = !split || P.hcopy <= 0;
         if (split)
             for (int b = threadIdx.x; b < nb; b += BS) {
                 const int nw = rs.bnd[b + 1] - rs.bnd[b];
-                bad |= nw < 1 || nw > kResWindows;
+                bad_w |= rs.bnd[b] < 0 || nw < 1 || nw > kResWindows;
+                const int r0 = rs.rbnd[b], r1 = rs.rbnd[b + 1];
+                bad_r |= r0 < 0 || r1 - r0 < 1 || r1 - r0 > kResWindows * 256 ||
+                         (r1 + 255) / 256 - r0 / 256 > kResWindows;
             }
-        if (!__syncthreads_or(bad)) {
+        if (!__syncthreads_or(bad_r)) {
+            rb = rs.rbnd[bid];
+            re = rs.rbnd[bid + 1];
+            wb = rb / 256;
+            we = (re + 255) / 256;
+            hbase = (int)((long long)bid * E / nb);
+            hcap = (int)((long long)(bid + 1) * E / nb) - hbase;
+        } else if (!__syncthreads_or(bad_w)) {
             wb = rs.bnd[bid];
             we = rs.bnd[bid + 1];
+            rb = wb * 256;
+            re = min(we * 256, P.n);
+        }
+        if (hbase < 0) {
+            hbase = B.chunk_off[wb * 8];
+            hcap = B.chunk_off[we * 8] - hbase;
         }
     }
-    const int nwmax = we - wb;   // this block's windows
-    const int rb = wb * 256, re = min(we * 256, P.n);   // the block's rows
-    const int R = re - rb;
-    float4* zbuf = dyn;                                  // [nwmax * 256] z of the block's rows
-    const int cap = max(smem_bytes - nwmax * 256 * (int)sizeof(float4), 0) / 4;
-    unsigned int* sent = reinterpret_cast<unsigned int*>(dyn + nwmax * 256);   // packed local entries
+    const int R = re - rb;                               // the block's rows: rb .. re - 1
+    float4* zbuf = dyn;                                  // [R] z of the block's rows (D^-1 in w)
+    const int cap = max(smem_bytes - R * (int)sizeof(float4), 0) / 4;
+    unsigned int* sent = reinterpret_cast<unsigned int*>(dyn + R);   // packed local entries
     float* __restrict__ rlo = B.rlo + (size_t)bid * kResLoStride;   // low parts of the local weights
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int np = P.npad;
@@ -895,7 +941,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     for (int w = wb + g; w < we; w += BS / 256) {
         const int slot = w * 256 + t;
         const int row = B.slot_row[slot];
-        if (row < 0) continue;
+        if (row < rb || row >= re) continue;   // no row, or another block's (a window at a share's edge)
         const int c = slot >> 5, e1 = B.chunk_off[c + 1];
         int nl = 0, nh = 0;
         unsigned long long hist = 0ull;   // local entries per bank group (column mod 8), 8 bits each
@@ -971,7 +1017,6 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         // a chunk whose local entries find no room in shared memory keeps them
         // in its halo list (gathered from global memory, like the entries to
         // other blocks); the other chunks stay on chip
-        const int hbase = B.chunk_off[wb * 8], hcap = B.chunk_off[we * 8] - hbase;
         int lo = 0, ho = 0;
         unsigned long long spill = 0ull;
         for (int c = 0; c < kResChunks; ++c) {
@@ -990,8 +1035,9 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         rs.mode = ho <= hcap ? 0 : 1;
         if (rs.mode != 0) {
             // the halo lists cannot hold the block's entries: every entry is
-            // gathered, from lists that are the sliced layout's own (copied
-            // below), each thread's rows those of its own slots (chunk_lane)
+            // gathered, from lists that are the sliced layout's own (each row's
+            // entries copied below to the same positions, offset by hcopy),
+            // each thread's rows those of its own slots (chunk_lane)
             for (int c = 0; c < kResChunks; ++c) {
                 const int u = c / (BS / 32), wp = c % (BS / 32);
                 const int w = wb + (wp >> 3) + (BS / 256) * u;
@@ -1001,7 +1047,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
                 rs.nhalo[c] = 0;
                 if (w < we) {
                     const int sc = w * 8 + ((u & 1) ? (wp & 7) ^ 7 : (wp & 7));
-                    rs.hoff[c] = B.chunk_off[sc];
+                    rs.hoff[c] = (int)P.hcopy + B.chunk_off[sc];
                     rs.nhalo[c] = (B.chunk_off[sc + 1] - B.chunk_off[sc]) / 32;
                 }
             }
@@ -1025,12 +1071,16 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int w = wb + g + (BS / 256) * u;
-            row[u] = w < we ? B.slot_row[w * 256 + chunk_lane(u, t)] : -1;
-        }
-        for (int e = B.chunk_off[wb * 8] + (int)threadIdx.x; e < B.chunk_off[we * 8]; e += BS) {
-            B.hcol[e] = B.col[e];
-            B.hval[e] = B.val32[e];
-            B.hlo[e] = B.val32lo[e];
+            const int slot = w * 256 + chunk_lane(u, t);
+            row[u] = w < we ? B.slot_row[slot] : -1;
+            if (row[u] < rb || row[u] >= re) row[u] = -1;   // a window at the edge of a row share
+            if (row[u] < 0) continue;
+            const int e1 = B.chunk_off[(slot >> 5) + 1];
+            for (int e = B.chunk_off[slot >> 5] + (slot & 31); e < e1; e += 32) {
+                B.hcol[P.hcopy + e] = B.col[e];
+                B.hval[P.hcopy + e] = B.val32[e];
+                B.hlo[P.hcopy + e] = B.val32lo[e];
+            }
         }
     }
 
@@ -1071,7 +1121,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
         for (int w = wb + g; w < we; w += BS / 256) {
             const int slot = w * 256 + t;
             const int row = B.slot_row[slot];
-            if (row < 0) continue;
+            if (row < rb || row >= re) continue;
             const int pos = sinv[row - rb];
             const int u = pos / BS, rem = pos - u * BS;
             const int owner = (u & 1) ? BS - 1 - rem : rem;
@@ -1208,7 +1258,7 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             for (int w = wb + g, k = 0; w < we; w += BS / 256, ++k) {
                 const int slot = w * 256 + chunk_lane(k, t);
                 const int rw = B.slot_row[slot];
-                if (rw < 0) continue;
+                if (rw < rb || rw >= re) continue;
                 dfloat sd[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
                 if (from_x)
                     row_sum_df<KC>(B.col, B.val32, B.val32lo, B.xdf, B.chunk_off[slot >> 5] + (slot & 31),

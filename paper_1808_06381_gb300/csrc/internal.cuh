@@ -59,6 +59,9 @@ struct KParams {
     int pcfg;           // tile configuration of the persistent solver (index, autotuned)
     int res_smem;       // shared memory the on-chip solve uses (<= kResSmemBytes; less only to test its fallback)
     int fused_init;     // on-chip solve: 0 after the initial-residual kernel; 1 forms r = b itself (x0 = 0), 2 r = b - A x0
+    long long hcopy;    // on-chip solve: where hcol / hval / hlo hold a second copy region (the lists of blocks
+                        // whose entries all stay off chip, at their sliced positions + hcopy); 0: none, and the
+                        // blocks then take whole windows
     // matrix-free SpMV of the streaming mixed solve: positions in 32-bit fixed
     // point of each box edge (one unit L / 2^32), w = 2^(w_exp2 |R|^2)
     double fix_inv[3];  // 2^32 / L

@@ -120,11 +120,19 @@ int alloc_pairs(sp_sim* s, long long cap)
     SS_TRY(dev_alloc(s, &B.val, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.val32, (size_t)cap));
     SS_TRY(dev_alloc(s, &B.img, (size_t)cap));
+    s->kp.hcopy = 0;
     if (mixed(s)) {   // low parts of the weights; halo lists of the on-chip solve
+        // systems small enough for the on-chip solve get a second region for
+        // the lists of blocks whose entries cannot stay on chip, so that the
+        // blocks can split the rows at any row (their halo lists then take
+        // entry shares that do not follow the sliced layout's windows)
+        const bool second = (long long)s->kp.n <= 2048ll * s->num_sms && 2 * cap < 0x7fffffffll;
+        const size_t hcap = (size_t)cap * (second ? 2 : 1);
         SS_TRY(dev_alloc(s, &B.val32lo, (size_t)cap));
-        SS_TRY(dev_alloc(s, &B.hcol, (size_t)cap));
-        SS_TRY(dev_alloc(s, &B.hval, (size_t)cap));
-        SS_TRY(dev_alloc(s, &B.hlo, (size_t)cap));
+        SS_TRY(dev_alloc(s, &B.hcol, hcap));
+        SS_TRY(dev_alloc(s, &B.hval, hcap));
+        SS_TRY(dev_alloc(s, &B.hlo, hcap));
+        if (second) s->kp.hcopy = cap;
     }
     s->nnz_cap = cap;
     s->st_host->nnz_cap = cap;

@@ -878,12 +878,14 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
             // leaves at least a row to every later share; boundaries that
             // miss T_b stay monotone, and a share the clamp leaves invalid is
             // caught below
+            int prev = 0;   // carried in a register: one dependent chain of integer operations per share
             for (int b = 1; b < nb; ++b) {
                 int r = rs.rbnd[b];
                 if (r < 0) break;
-                r = min(r, (rs.rbnd[b - 1] / 256 + kResWindows) * 256);
+                r = min(r, (prev / 256 + kResWindows) * 256);
                 r = min(r, P.n - (nb - b));
-                rs.rbnd[b] = max(r, rs.rbnd[b - 1] + 1);
+                prev = max(r, prev + 1);
+                rs.rbnd[b] = prev;
             }
         }
         __syncthreads();
@@ -938,16 +940,34 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     unsigned int* scnt = skey + npow;
     unsigned short* sinv = reinterpret_cast<unsigned short*>(scnt + R);
     for (int i = R + (int)threadIdx.x; i < npow; i += BS) skey[i] = 0xffffffffu;
-    for (int w = wb + g; w < we; w += BS / 256) {
-        const int slot = w * 256 + t;
-        const int row = B.slot_row[slot];
+    // a thread's slots are slot t of the windows wb + g, wb + g + BS / 256, ...
+    // (at most kWin of them: every split keeps a block within kResWindows
+    // windows); their rows and chunk bounds are requested together
+    constexpr int kWin = kResWindows / (BS / 256);
+    if (we - wb > kResWindows) {   // never: the split guarantees it
+        if (threadIdx.x == 0) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
+        we = wb;
+    }
+    int srow[kWin], sc0[kWin], sc1[kWin];
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+        const int slot = (wb + g + (BS / 256) * k) * 256 + t;
+        const bool in = wb + g + (BS / 256) * k < we;
+        srow[k] = in ? B.slot_row[slot] : -1;
+        sc0[k] = in ? B.chunk_off[slot >> 5] : 0;
+        sc1[k] = in ? B.chunk_off[(slot >> 5) + 1] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+        const int slot = (wb + g + (BS / 256) * k) * 256 + t;
+        const int row = srow[k];
         if (row < rb || row >= re) continue;   // no row, or another block's (a window at a share's edge)
-        const int c = slot >> 5, e1 = B.chunk_off[c + 1];
+        const int e1 = sc1[k];
         int nl = 0, nh = 0;
         unsigned long long hist = 0ull;   // local entries per bank group (column mod 8), 8 bits each
         // the columns alone: a padding entry of the sliced layout points at its
         // own row (and has weight 0), a real partner never does
-        for (int eb = B.chunk_off[c] + (slot & 31); eb < e1; eb += 32 * 2 * KS) {
+        for (int eb = sc0[k] + (slot & 31); eb < e1; eb += 32 * 2 * KS) {
             int j[2 * KS];
 #pragma unroll
             for (int u = 0; u < 2 * KS; ++u) {

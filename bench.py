@@ -139,24 +139,22 @@ class ClockSampler:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# persistent solve from one ncu capture of this command's kernel, keyed by workload
-# and tile configuration (gathers in flight, blocks per SM, pipelined, threads per
-# block, on-chip); any other
-# kernel or workload reports null.
-PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True): 100.5e6,
-                    ("mixed-n262144", 6, 1, False, 1024, False): 97.44e6}
+# persistent solve from one ncu capture of the current kernel on this command's
+# workload, keyed by workload, tile configuration (gathers in flight, blocks per
+# SM, pipelined, threads per block, on-chip) and burn-in steps (the regime the
+# captured launch came from); any other kernel, workload or regime reports null.
+PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True, 1000): 172.4e6}
 # the same for the large workload (N = 4,194,304), by solver kernel (one capture of the
 # DRAM counters alone, one pass, the launch of the first timed step)
-LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 56.37e9, "k32_cg_persistent<4,3,0,256,1>": 52.28e9}
+LARGE_PROFILED_TRAFFIC = {}
 
 
 def profiled_traffic(workload_name: str, tune, burn_in: int = 0) -> float | None:
-    """The capture's DRAM bytes, where it matches this launch: the captures ran a few steps
-    from the uniform start, so a line timed after a burn-in has none."""
-    if not tune or burn_in:
+    """The capture's DRAM bytes, where it matches this launch's kernel, workload and regime."""
+    if not tune:
         return None
     return PROFILED_TRAFFIC.get((workload_name, tune["gathers_in_flight"], tune["blocks_per_sm"],
-                                 tune["pipelined"], tune["block_threads"], tune.get("resident", False)))
+                                 tune["pipelined"], tune["block_threads"], tune.get("resident", False), burn_in))
 
 
 def solver_kernel_name(tune) -> str:

@@ -149,15 +149,18 @@ __global__ void k_scan_down(const int* __restrict__ in, int* __restrict__ out, i
     }
 }
 
-// An input of one chunk in one block: the chunk's exclusive scan and the total.
-__global__ void k_scan_single(const int* __restrict__ in, int* __restrict__ out, int n, long long cap_check,
-                              DevState* st, int mode)
+// An input of at most TH x kScanItems in one block: its exclusive scan and
+// the total (one launch instead of three; TH = 1024 covers the 8,192 chunk
+// lengths of a 262,144-row sliced layout).
+template <int TH>
+__global__ void __launch_bounds__(TH) k_scan_single(const int* __restrict__ in, int* __restrict__ out, int n,
+                                                    long long cap_check, DevState* st, int mode)
 {
     if (st->error | st->overflow) return;
-    __shared__ int s[kScanChunk];
+    __shared__ int s[TH * kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int idx = k * kScanThreads + threadIdx.x;
+        const int idx = k * TH + threadIdx.x;
         s[idx] = idx < n ? in[idx] : 0;
     }
     __syncthreads();
@@ -175,7 +178,7 @@ __global__ void k_scan_single(const int* __restrict__ in, int* __restrict__ out,
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int idx = k * kScanThreads + threadIdx.x;
+        const int idx = k * TH + threadIdx.x;
         if (idx < n) out[idx] = s[idx];
     }
     if (threadIdx.x == 0) {
@@ -192,7 +195,11 @@ int launch_scan(const int* in, int* out, int n, int* block_tmp, long long cap_ch
 {
     const int nb = (n + kScanChunk - 1) / kScanChunk;
     if (nb <= 1) {
-        k_scan_single<<<1, kScanThreads, 0, L.stream>>>(in, out, n, cap_check, st, mode);
+        k_scan_single<kScanThreads><<<1, kScanThreads, 0, L.stream>>>(in, out, n, cap_check, st, mode);
+        return 1;
+    }
+    if (n <= 1024 * kScanItems) {
+        k_scan_single<1024><<<1, 1024, 0, L.stream>>>(in, out, n, cap_check, st, mode);
         return 1;
     }
     k_scan_reduce<<<nb, kScanThreads, 0, L.stream>>>(in, n, block_tmp, st);

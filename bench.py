@@ -146,7 +146,7 @@ class ClockSampler:
 PROFILED_TRAFFIC = {("mixed-n262144", 4, 1, False, 512, True, 1000): 172.4e6}
 # the same for the large workload (N = 4,194,304), by solver kernel (one capture of the
 # DRAM counters alone, one pass, the launch of the first timed step)
-LARGE_PROFILED_TRAFFIC = {}
+LARGE_PROFILED_TRAFFIC = {"k32_cg_persistent<6,1,0,1024>": 53.90e9, "k32_cg_persistent<4,3,0,256,1>": 49.99e9}
 
 
 def profiled_traffic(workload_name: str, tune, burn_in: int = 0) -> float | None:

@@ -34,7 +34,12 @@ __global__ void __launch_bounds__(kVecBlock) k_integrate(KParams P, DevBuffers B
     DevState* st = B.st;
     if (st->error | st->overflow) return;
     const int np = P.npad;
-    const double dnew = wrap_box(st->delta + P.kappa * P.L[1] * P.dt, P.L[0]);
+    // the advanced offset once per block: its FP64 division runs on GB300's
+    // 1/64-rate FP64 pipe, and per thread it cost more than the rows' update
+    __shared__ double s_dnew;
+    if (threadIdx.x == 0) s_dnew = wrap_box(st->delta + P.kappa * P.L[1] * P.dt, P.L[0]);
+    __syncthreads();
+    const double dnew = s_dnew;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const double vx = B.x[i], vy = B.x[np + i], vz = B.x[2 * np + i];
         double x = __dadd_rn(B.pos_w[i], __dmul_rn(vx, P.dt));

@@ -129,6 +129,40 @@ def test_resident_full_size_against_fp64(full64, smem, monkeypatch):
     sim.close()
 
 
+@pytest.mark.parametrize("extra", [0, 1])
+def test_resident_at_its_largest_system(extra, monkeypatch):
+    """2048 rows per SM, the largest system the on-chip form takes: every block
+    holds exactly eight windows (the split by entry shares at any row cannot
+    keep within eight windows per block there and falls back to whole windows).
+    One row more leaves the on-chip form for the streaming one.  A 40 KB
+    shared-memory budget shows which form ran: only the on-chip form reports
+    blocks whose entries did not fit."""
+    import torch
+    n = 2048 * torch.cuda.get_device_properties(0).multi_processor_count + extra
+    onchip = extra == 0
+    res_oracle = None
+    for smem in (None, 40 * 1024):
+        if smem is None:
+            monkeypatch.delenv("SHEARSIM_RESIDENT_SMEM", raising=False)
+        else:
+            monkeypatch.setenv("SHEARSIM_RESIDENT_SMEM", str(smem))
+        sim, p, pos, delta = _make(n, 19, 1e-8)
+        for k in _resident_configs(sim):
+            sim.set_solver_config(k)
+            sim.build_neighbors()
+            sim.assemble()
+            info = sim.solve_velocities()
+            assert info["status"] == 0 and info["residual"] <= 1e-8, (n, smem, k, info)
+            assert (info["offchip_blocks"] > 0) == (onchip and smem is not None), (n, smem, k, info)
+            if res_oracle is None:   # the oracle's FP64 system of the same positions, once per size
+                sysr = oracle.assemble(p, pos, oracle.neighbors(p, pos, delta, "cells"),
+                                       oracle.noise(p.seed, 0, np.arange(n)), delta)
+                v = sim.get_velocities()
+                res_oracle = np.linalg.norm(sysr.b - sysr.matvec(v)) / np.linalg.norm(sysr.b)
+                assert res_oracle <= 1e-8 + 2e-11, (n, res_oracle)
+        sim.close()
+
+
 def test_resident_steps_are_deterministic_and_follow_config_zero():
     n = 200000
     runs = []

@@ -724,19 +724,21 @@ __device__ __forceinline__ void persistent_solve(const KParams& P, const DevBuff
 }
 
 // ------------------------------------------------------------ on-chip solve
-// The same iteration for systems whose rows fit on the chip: with at most
-// kResWindows windows per block, a thread of a block of BS owns at most RPT
-// rows (BS RPT = 2048) and keeps their solver vectors (r, D^-1, p, q, d) in
-// registers for the whole solve;
-// the block keeps z = D^-1 r of its rows and the matrix entries that couple
-// two of its rows (16-bit local column, FP32 weight) in shared memory.  Only
-// the entries that couple its rows to other blocks' rows ("halo" entries,
-// about a sixth with the tiled Morton row order) and those rows' r are read
-// from global memory in the iteration.  A block's windows hold one contiguous
-// range of rows, so an entry is local when its column lies in that range.
-// The set-up at the start of the solve sorts each row's entries into the two
-// lists; a chunk whose local entries find no room in shared memory keeps all
-// its entries in the halo list (slower, same result).
+// The same iteration for systems whose rows fit on the chip: a block holds
+// one contiguous range of at most 2048 rows within at most kResWindows
+// windows, a thread of a block of BS owns at most RPT rows (BS RPT = 2048)
+// and keeps their solver vectors (r, p, q, d) in registers for the whole
+// solve; the block keeps z = D^-1 r of its rows (D^-1 in the fourth lane) and
+// the matrix entries that couple two of its rows (packed words, below) in
+// shared memory.  Only the entries that couple its rows to other blocks' rows
+// ("halo" entries, about a sixth with the tiled Morton row order) and those
+// rows' r are read from global memory in the iteration; an entry is local
+// when its column lies in the block's row range.  The set-up at the start of
+// the solve sorts each row's entries into the two lists; a chunk whose local
+// entries find no room in shared memory keeps all its entries in the halo
+// list, and a block whose halo lists do not fit its share of the list buffers
+// gathers every entry from copies of its rows' sliced lists (slower, same
+// result).
 constexpr int kResWindows = 8;                       // 2048 rows per block
 constexpr int kResMaxBlocks = 192;                   // blocks the entry-balanced split serves
 constexpr int kResChunks = kResWindows * 8;

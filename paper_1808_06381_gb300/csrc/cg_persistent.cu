@@ -946,9 +946,11 @@ __device__ __forceinline__ void resident_solve(const KParams& P, const DevBuffer
     // (at most kWin of them: every split keeps a block within kResWindows
     // windows); their rows and chunk bounds are requested together
     constexpr int kWin = kResWindows / (BS / 256);
-    if (we - wb > kResWindows) {   // never: the split guarantees it
+    if (we - wb > kResWindows) {   // never: every split keeps a block within kResWindows windows
+        // leave before any row is placed; the other blocks' barrier waits end
+        // at their limit, and the solve reports the error
         if (threadIdx.x == 0) atomicCAS(&st->error, 0, (int)SP_ERR_INVALID_ARG);
-        we = wb;
+        return;
     }
     int srow[kWin], sc0[kWin], sc1[kWin];
 #pragma unroll

@@ -2114,14 +2114,13 @@ __device__ __forceinline__ void pipelined_solve64(const KParams& P, const DevBuf
             if (row >= 0) ends(slot, e0, e1);
             double s0, s1, s2;
             p_row_sum64_scaled<TPR>(B.col, B.val, B.dinv, r, np, e0, e1, sub, row >= 0, s0, s1, s2);
-            if (row < 0 || sub != 0) return;
-            const double sm[3] = {s0, s1, s2};
+            if (row < 0 || sub >= 3) return;   // lane c: component c
+            const double sm = sub == 0 ? s0 : (sub == 1 ? s1 : s2);
             const double dg = B.diag[row], di = B.dinv[row];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int k2 = c * np + row;
+            {
+                const int k2 = sub * np + row;
                 const double rk = r[k2], uk = di * rk;
-                const double wk = dg * uk - P.alpha * sm[c];
+                const double wk = dg * uk - P.alpha * sm;
                 w[k2] = wk;
                 z[k2] = 0.0;
                 sv[k2] = 0.0;
@@ -2143,16 +2142,15 @@ __device__ __forceinline__ void pipelined_solve64(const KParams& P, const DevBuf
             if (row >= 0) ends(slot, e0, e1);
             double s0 = 0.0, s1 = 0.0, s2 = 0.0;
             if (!first || from_x) p_row_sum64<TPR>(B.col, B.val, x, np, e0, e1, sub, row >= 0, s0, s1, s2);
-            if (row < 0 || sub != 0) return;
-            const double sm[3] = {s0, s1, s2};
+            if (row < 0 || sub >= 3) return;   // lane c: component c
+            const double sm = sub == 0 ? s0 : (sub == 1 ? s1 : s2);
             const double dg = B.diag[row];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int k2 = c * np + row;
+            {
+                const int k2 = sub * np + row;
                 const double bk = B.b[k2];
                 double rk = bk;
                 if (!first || from_x)
-                    rk = bk - (dg * x[k2] - P.alpha * sm[c]);
+                    rk = bk - (dg * x[k2] - P.alpha * sm);
                 else
                     x[k2] = 0.0;
                 r[k2] = rk;
@@ -2255,14 +2253,15 @@ __device__ __forceinline__ void pipelined_solve64(const KParams& P, const DevBuf
             if (row >= 0) ends(slot, e0, e1);
             double s0, s1, s2;
             p_row_sum64_scaled<TPR>(B.col, B.val, B.dinv, w, np, e0, e1, sub, row >= 0, s0, s1, s2);
-            if (row < 0 || sub != 0) return;
-            const double sm[3] = {s0, s1, s2};
+            // every lane of the row holds the sums: lane c updates component c
+            // (a third of the FP64 instructions per warp of a lane doing all three)
+            if (row < 0 || sub >= 3) return;
+            const double sm = sub == 0 ? s0 : (sub == 1 ? s1 : s2);
             const double dg = B.diag[row], di = B.dinv[row];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int k2 = c * np + row;
+            {
+                const int k2 = sub * np + row;
                 const double wk = w[k2];
-                const double nk = dg * (di * wk) - P.alpha * sm[c];   // (A m)_k, m = D^-1 w
+                const double nk = dg * (di * wk) - P.alpha * sm;   // (A m)_k, m = D^-1 w
                 const double zk = nk + beta * z[k2];
                 const double sk = wk + beta * sv[k2];
                 const double pk = di * r[k2] + beta * p[k2];
